@@ -1,0 +1,568 @@
+/*
+ * mpwos_oracle.c — plain, slow, FP64 CPU oracle of the MPWoS walk.
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code with the
+ * CUDA path; it is compiled with -ffp-contract=off so that every + and * is
+ * one IEEE operation.
+ *
+ * Arithmetic order is that of Algorithm 1 with the path score of eq.
+ * path_score_definition: per step the radius (eq. radius_rule_unified), the
+ * screened factor c_{sigma,r} and omega = (1 - c)/sigma (Thm 2.2, eq.
+ * omega_explicit_formula), the sphere sample Theta = Y + r zeta (eq.
+ * projected_chain_update), N_V interior samples Z ~ rho(Y, .) (eq.
+ * Z_sampling_density) averaged into F_k (eq. local_average_source), the score
+ * update S += W_k omega F_k, W_{k+1} = W_k c, Y_{k+1} = cp(Theta).
+ *
+ * Readings of points the paper leaves open (each also listed in the design
+ * notes): the stopping test is applied at k = 0 as well (K = inf{k >= 0 ...});
+ * f at an off-manifold Z is the extension f(cp(Z)) (eq. cp_extension); the
+ * interior sample's radius is drawn by inverting the radial CDF of the
+ * Green density (derived from the Remark's G), its direction independently
+ * uniform; m_* = 0 (the baseline variant of Sec. 2.3.3); a walk that reaches
+ * max_steps is flagged, never silently cut; a boundary-case walk whose weight
+ * has underflowed to exactly 0 stops (all later terms vanish).
+ */
+#include "mpwos_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_TWO_PI 6.283185307179586
+#define ORC_EULER_GAMMA 0.57721566490153286
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10: round function and Weyl key schedule as published by        */
+/* Salmon et al. (SC'11): multipliers 0xD2511F53, 0xCD9E8D57; key increments  */
+/* 0x9E3779B9, 0xBB67AE85; ten rounds.                                         */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+  uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+    uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t y0 = hi1 ^ x1 ^ k0;
+    uint32_t y1 = lo1;
+    uint32_t y2 = hi0 ^ x3 ^ k1;
+    uint32_t y3 = lo0;
+    x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* 53-bit uniform in (0, 1]: the top 53 bits of (hi:lo), plus one, times 2^-53. */
+double orc_u53(uint32_t hi, uint32_t lo) {
+  uint64_t m = (((uint64_t)hi << 32) | (uint64_t)lo) >> 11;
+  return (double)(m + 1u) * 0x1p-53;
+}
+
+static void block(uint64_t seed, uint32_t j, uint32_t k, uint32_t i, uint32_t p, uint32_t out[4]) {
+  uint32_t ctr[4] = {j, k, i, p};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  orc_philox4x32_10(ctr, key, out);
+}
+
+/* n standard Gaussians from blocks j0, j0+1, ... (two per block, Box-Muller:
+ * sqrt(-2 ln u_a) (cos 2 pi u_b, sin 2 pi u_b)); an odd n drops the last one. */
+void orc_gaussians(uint64_t seed, uint32_t j0, uint32_t k, uint32_t i, uint32_t p, int n, double* g) {
+  int nb = (n + 1) / 2;
+  for (int b = 0; b < nb; ++b) {
+    uint32_t x[4];
+    block(seed, j0 + (uint32_t)b, k, i, p, x);
+    double ua = orc_u53(x[0], x[1]);
+    double ub = orc_u53(x[2], x[3]);
+    double rad = sqrt(-2.0 * log(ua));
+    double ang = ORC_TWO_PI * ub;
+    g[2 * b] = rad * cos(ang);
+    if (2 * b + 1 < n) g[2 * b + 1] = rad * sin(ang);
+  }
+}
+
+static double uniform_at(uint64_t seed, uint32_t j, uint32_t k, uint32_t i, uint32_t p) {
+  uint32_t x[4];
+  block(seed, j, k, i, p, x);
+  return orc_u53(x[0], x[1]);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Screened factor (Lemma 2.1, series of Lemma 3.1):                           */
+/*   c_{sigma,r} = 1 / I~_nu(a),  I~_nu(a) = sum_j (a^2/4)^j / (j! (nu+1)_j),  */
+/*   a = sqrt(sigma) r, nu = (n-2)/2.  em1 = I~_nu(a) - 1 (no leading 1).      */
+/* ------------------------------------------------------------------------- */
+double orc_em1(int n, double a) {
+  double nu = 0.5 * (double)(n - 2);
+  double z = 0.25 * (a * a);
+  double term = 1.0, sum = 0.0;
+  for (int j = 1; j < 100000; ++j) {
+    term *= z / ((double)j * (nu + (double)j));
+    sum += term;
+    if (term <= 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+double orc_c_sigma_r(int n, double a) { return 1.0 / (1.0 + orc_em1(n, a)); }
+
+/* 0F1(;b;z) = sum_k z^k / (k! (b)_k), b > 0. */
+static double hyp0f1(double b, double z) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 100000; ++k) {
+    term *= z / ((double)k * (b + (double)k - 1.0));
+    sum += term;
+    if (term <= 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+/* K~_mu(x) - 1, where K~_mu(x) = 2 (x/2)^mu K_mu(x) / Gamma(mu) (-> 1 as x -> 0).
+ * Non-integer mu: K_mu = (pi/2)(I_{-mu} - I_mu)/sin(mu pi) gives
+ *   K~_mu = 0F1(;1-mu;z) - [Gamma(1-mu)/Gamma(1+mu)] (x/2)^{2mu} 0F1(;1+mu;z).
+ * Integer mu = m: Abramowitz & Stegun 9.6.11 gives
+ *   K~_m = sum_{k<m} z^k/(k!(1-m)_k)
+ *        + (-1)^{m+1} 2 (x/2)^{2m}/((m-1)! m!) sum_k z^k m!/(k!(m+k)!)
+ *                     [ln(x/2) + gamma - (H_k + H_{m+k})/2].
+ * z = x^2/4. */
+double orc_kt_minus_one(double mu, double x) {
+  double z = 0.25 * (x * x);
+  double hx = log(0.5 * x);
+  double m_round = floor(mu + 0.5);
+  if (fabs(mu - m_round) < 1e-12) {
+    int m = (int)m_round;
+    double s = 0.0, term = 1.0;
+    for (int k = 1; k <= m - 1; ++k) {
+      term *= z / ((double)k * ((double)k - (double)m));
+      s += term;
+      if (term == 0.0) break;
+    }
+    double lg = log(2.0) + 2.0 * (double)m * hx - lgamma((double)m) - lgamma((double)m + 1.0);
+    double lp = 0.0;
+    if (lg > -740.0) {
+      double Hm = 0.0;
+      for (int q = 1; q <= m; ++q) Hm += 1.0 / (double)q;
+      double inner = 0.0, tk = 1.0, Hk = 0.0, Hmk = Hm;
+      for (int k = 0; k < 100000; ++k) {
+        double add = tk * (hx + ORC_EULER_GAMMA - 0.5 * (Hk + Hmk));
+        inner += add;
+        if (k > 2 && fabs(add) <= 1e-18 * fabs(inner)) break;
+        tk *= z / ((double)(k + 1) * (double)(m + k + 1));
+        Hk += 1.0 / (double)(k + 1);
+        Hmk += 1.0 / (double)(m + k + 1);
+      }
+      double sign = ((m + 1) % 2 == 0) ? 1.0 : -1.0;
+      lp = sign * exp(lg) * inner;
+    }
+    return s + lp;
+  } else {
+    double s = 0.0, term = 1.0;
+    for (int k = 1; k < 100000; ++k) {
+      term *= z / ((double)k * ((double)k - mu));
+      s += term;
+      if (term == 0.0) break;
+      if ((double)k > mu + 1.0 && fabs(term) <= 1e-18 * fabs(s)) break;
+    }
+    double sp = sin(M_PI * mu);
+    double lg = log(M_PI) - log(fabs(sp)) - lgamma(mu) - lgamma(mu + 1.0) + 2.0 * mu * hx;
+    double second = 0.0;
+    if (lg > -740.0) second = -((sp > 0) ? 1.0 : -1.0) * exp(lg) * hyp0f1(1.0 + mu, z);
+    return s + second;
+  }
+}
+
+/* n = 3 closed forms (the Remark's G for n = 3):
+ *   P(x) = 1 - e^{-x}(1+x),  Q(x) = x cosh x - sinh x. */
+static double p3(double x) {
+  if (x < 1.0) {
+    double term = x, sum = 0.0;       /* term = x^k / k! */
+    for (int k = 2; k < 200; ++k) {
+      term *= x / (double)k;
+      double add = ((k % 2 == 0) ? 1.0 : -1.0) * (double)(k - 1) * term;
+      sum += add;
+      if (fabs(add) <= 1e-18 * fabs(sum)) break;
+    }
+    return sum;
+  }
+  return 1.0 - exp(-x) * (1.0 + x);
+}
+
+static double q3(double x) {
+  if (x < 1.0) {
+    double term = x, sum = 0.0;       /* term = x^(2k+1)/(2k+1)! */
+    for (int k = 1; k < 200; ++k) {
+      term *= x * x / ((double)(2 * k) * (double)(2 * k + 1));
+      double add = 2.0 * (double)k * term;
+      sum += add;
+      if (add <= 1e-18 * sum) break;
+    }
+    return sum;
+  }
+  return x * cosh(x) - sinh(x);
+}
+
+/* Radial CDF of |Z - y| / r under rho(y, .) (eq. Z_sampling_density).
+ * With H(x) = x^{nu+1}[K_{nu+1}(x) + (K_nu(a)/I_nu(a)) I_{nu+1}(x)]/(2^nu Gamma(nu+1)),
+ * Green's identity on the sub-ball of radius t r and the Wronskian
+ * I_nu K_{nu+1} + I_{nu+1} K_nu = 1/x give F(t) = (1 - H(a t)) / (1 - c).
+ * In normalised functions:
+ *   1 - H(x) = [1 - K~_{nu+1}(x)] - c K~_nu(a) I~_{nu+1}(x) (x/2)^2 t^{2nu} / (nu(nu+1)).
+ * n = 3 uses the elementary forms:
+ *   1 - H(x) = P(x) - Q(x) e^{-a}/sinh(a),  e^{-a}/sinh(a) = 2/expm1(2a). */
+double orc_green_cdf(int n, double a, double t) {
+  if (t <= 0.0) return 0.0;
+  if (t >= 1.0) return 1.0;
+  double em1 = orc_em1(n, a);
+  double c = 1.0 / (1.0 + em1);
+  double omc = (em1 <= 1.0) ? em1 * c : 1.0 - c;
+  double x = a * t;
+  if (n == 3) {
+    double second;
+    if (x < 1.0) {
+      second = q3(x) * (2.0 / expm1(2.0 * a));
+    } else {
+      /* Q(x) 2/(e^{2a}-1) = [(x-1) e^{x-2a} + (x+1) e^{-x-2a}] / (1 - e^{-2a}), no overflow */
+      second = ((x - 1.0) * exp(x - 2.0 * a) + (x + 1.0) * exp(-x - 2.0 * a)) / (-expm1(-2.0 * a));
+    }
+    return (p3(x) - second) / omc;
+  }
+  double nu = 0.5 * (double)(n - 2);
+  double sk = -orc_kt_minus_one(nu + 1.0, x);
+  double kta = 1.0 + orc_kt_minus_one(nu, a);
+  double it1 = hyp0f1(nu + 2.0, 0.25 * (x * x));
+  double second = c * kta * it1 * (0.25 * (x * x)) * pow(t, 2.0 * nu) / (nu * (nu + 1.0));
+  return (sk - second) / omc;
+}
+
+/* Inverse of the radial CDF by plain bisection on [0, 1] down to adjacent doubles. */
+double orc_green_cdf_inv(int n, double a, double U) {
+  if (U >= 1.0) return 1.0;
+  double lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 2000; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (orc_green_cdf(n, a, mid) < U) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Geometry: closest point (eq. cp_map), curvature indicator (eq.               */
+/* rho_geo_curvature), effective boundary distance (eq. delta_Gamma_general).   */
+/* ------------------------------------------------------------------------- */
+static double dot(const double* a, const double* b, int n) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+void orc_cp(const orc_manifold* m, const double* x, double* out) {
+  int n = m->n;
+  if (m->kind == ORC_EUCLID) {
+    memcpy(out, x, sizeof(double) * (size_t)n);
+  } else if (m->kind == ORC_SPHERE) {
+    double nx = sqrt(dot(x, x, n));
+    for (int i = 0; i < n; ++i) out[i] = x[i] / nx;
+  } else if (m->kind == ORC_TORUS) {
+    /* nearest point of the centre circle, then the tube of radius a around it */
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+    double c[3] = {m->R * x[0] / rho, m->R * x[1] / rho, 0.0};
+    double w[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
+    double nw = sqrt(dot(w, w, 3));
+    double s = m->a / nw;
+    for (int i = 0; i < 3; ++i) out[i] = c[i] + s * w[i];
+  } else { /* embedded unit sphere: cp(x) = Q normalize(Q^T (x - b)) + b */
+    int D = m->d + 1;
+    double* s = (double*)malloc(sizeof(double) * (size_t)D);
+    for (int j = 0; j < D; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < n; ++i) acc += m->Q[(size_t)i * D + j] * (x[i] - m->b[i]);
+      s[j] = acc;
+    }
+    double ns = sqrt(dot(s, s, D));
+    for (int j = 0; j < D; ++j) s[j] /= ns;
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < D; ++j) acc += m->Q[(size_t)i * D + j] * s[j];
+      out[i] = acc + m->b[i];
+    }
+    free(s);
+  }
+}
+
+static double kappa_of(const orc_manifold* m) {
+  /* largest absolute principal curvature (constant on these manifolds) */
+  if (m->kind == ORC_EUCLID) return 0.0;
+  if (m->kind == ORC_TORUS) return 1.0 / m->a;
+  return 1.0; /* unit sphere, embedded unit sphere */
+}
+
+/* delta_Gamma(y) = ( |P_T r_Gamma|^2 + (|P_N r_Gamma| - ell)_+^2 )^{1/2},
+ * r_Gamma = y_Gamma - y, ell = rho_geo(y_Gamma).  Boundary: half-space
+ * {e.x > h} intersected with M (unit sphere or Euclidean space).  A state with
+ * e.y <= h is outside Omega and counts as inside the boundary layer (0). */
+double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                       const double* y, double* yg) {
+  int n = m->n;
+  const double* e = pb->bnd_normal;
+  double h = pb->bnd_offset;
+  double ey = dot(e, y, n);
+  double ell = pr->c_kappa / (1.0 + kappa_of(m));
+  if (m->kind == ORC_EUCLID) {
+    for (int i = 0; i < n; ++i) yg[i] = y[i] - (ey - h) * e[i];
+    double d = fabs(ey - h);
+    return (ey <= h) ? 0.0 : d;
+  }
+  /* unit sphere: y_Gamma = h e + sqrt(1-h^2) w/|w|, w = y - (e.y) e */
+  double* w = (double*)malloc(sizeof(double) * (size_t)n);
+  for (int i = 0; i < n; ++i) w[i] = y[i] - ey * e[i];
+  double nw = sqrt(dot(w, w, n));
+  if (nw == 0.0) {
+    /* non-unique nearest point: lowest-index axis not parallel to e */
+    for (int j = 0; j < n; ++j) {
+      for (int i = 0; i < n; ++i) w[i] = ((i == j) ? 1.0 : 0.0) - e[j] * e[i];
+      nw = sqrt(dot(w, w, n));
+      if (nw > 1e-8) break;
+    }
+  }
+  double sh = sqrt(1.0 - h * h);
+  for (int i = 0; i < n; ++i) yg[i] = h * e[i] + sh * (w[i] / nw);
+  /* r_Gamma, its normal part along y_Gamma (the sphere's unit normal there) */
+  double rn = 0.0;
+  for (int i = 0; i < n; ++i) rn += (yg[i] - y[i]) * yg[i];
+  double rt2 = 0.0;
+  for (int i = 0; i < n; ++i) {
+    double rti = (yg[i] - y[i]) - rn * yg[i];
+    rt2 += rti * rti;
+  }
+  free(w);
+  if (ey <= h) return 0.0;
+  double ex = fabs(rn) - ell;
+  if (ex < 0.0) ex = 0.0;
+  return sqrt(rt2 + ex * ex);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Problem data f, g evaluated at a point x of M.                              */
+/* ------------------------------------------------------------------------- */
+static double trig(int kind, double v) { return kind == 0 ? cos(v) : sin(v); }
+
+double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, const double* x) {
+  if (f->kind == ORC_POLY) {
+    double total = 0.0;
+    for (int t = 0; t < f->n_terms; ++t) {
+      double prod = f->coef[t];
+      for (int q = f->term_off[t]; q < f->term_off[t + 1]; ++q)
+        for (int e = 0; e < f->pw[q]; ++e) prod *= x[f->var[q]];
+      total += prod;
+    }
+    return total;
+  }
+  if (f->kind == ORC_TORUS_FOURIER) {
+    double R = m->R, a = m->a;
+    double rho = sqrt(x[0] * x[0] + x[1] * x[1]);
+    double th = atan2(x[2], rho - R);
+    double ph = atan2(x[1], x[0]);
+    double ct = cos(th), st = sin(th);
+    double total = 0.0;
+    for (int t = 0; t < f->n_terms; ++t) {
+      int mm = f->modes[4 * t], q = f->modes[4 * t + 1];
+      int tk = f->modes[4 * t + 2], pk = f->modes[4 * t + 3];
+      double T = trig(tk, mm * th);
+      double P = trig(pk, q * ph);
+      double val;
+      if (!f->apply_op) {
+        val = T * P;
+      } else {
+        /* -Delta_T of T(theta)P(phi) on the torus (R + a cos th) e_r + a sin th e_z:
+         * P [ m^2 T / a^2 + sin th T' / (a (R + a cos th)) + q^2 T / (R + a cos th)^2 ] */
+        double Tp = (tk == 0) ? -(double)mm * sin(mm * th) : (double)mm * cos(mm * th);
+        double rr = R + a * ct;
+        double lap = (double)(mm * mm) * T / (a * a) + st * Tp / (a * rr) + (double)(q * q) * T / (rr * rr);
+        val = P * (lap + sigma * T);
+      }
+      total += f->coef[t] * val;
+    }
+    return total;
+  }
+  /* sphere quad: intrinsic unit vector s of the round sphere S^d */
+  int D = m->d + 1;
+  double* s = (double*)malloc(sizeof(double) * (size_t)D);
+  if (m->kind == ORC_EMBEDDED_SPHERE) {
+    for (int j = 0; j < D; ++j) {
+      double acc = 0.0;
+      for (int i = 0; i < m->n; ++i) acc += m->Q[(size_t)i * D + j] * (x[i] - m->b[i]);
+      s[j] = acc;
+    }
+  } else {
+    for (int j = 0; j < D; ++j) s[j] = x[j];
+  }
+  double ns = sqrt(dot(s, s, D));
+  for (int j = 0; j < D; ++j) s[j] /= ns;
+  double lin = dot(f->v, s, D);
+  double quad = 0.0, tr = 0.0;
+  for (int i = 0; i < D; ++i) {
+    tr += f->A[(size_t)i * D + i];
+    for (int j = 0; j < D; ++j) quad += f->A[(size_t)i * D + j] * s[i] * s[j];
+  }
+  free(s);
+  if (!f->apply_op) return f->c0 + lin + quad;
+  /* on S^d: degree-k harmonics have -Delta eigenvalue k(k+d-1); s^T A s splits
+   * into its trace-free part (k = 2) and the constant tr(A)/(d+1). */
+  double d = (double)m->d;
+  double mean = tr / (double)D;
+  return sigma * (f->c0 + mean) + (d + sigma) * lin + (2.0 * (d + 1.0) + sigma) * (quad - mean);
+}
+
+/* ------------------------------------------------------------------------- */
+/* One walk (Algorithm 1 + eq. path_score_definition).                          */
+/*   blocks of step k: Theta direction [0, nb); Z_l direction                   */
+/*   [nb(1+l), nb(2+l)); U_l at nb(1+N_V) + l;  nb = ceil(n/2).                 */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+  double *Y, *Th, *Z, *cZ, *g, *yg;
+} work_t;
+
+static void work_alloc(work_t* w, int n) {
+  w->Y = (double*)malloc(sizeof(double) * (size_t)n * 6);
+  w->Th = w->Y + n; w->Z = w->Th + n; w->cZ = w->Z + n; w->g = w->cZ + n; w->yg = w->g + n;
+}
+static void work_free(work_t* w) { free(w->Y); }
+
+static int run_walk(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                    const double* y0, uint32_t p, uint32_t i, work_t* w,
+                    double* S_out, int64_t* K_out, orc_trace_rec* rec, int64_t cap, int64_t* nrec) {
+  int n = m->n;
+  uint32_t nb = (uint32_t)((n + 1) / 2);
+  double sqs = sqrt(pb->sigma);
+  memcpy(w->Y, y0, sizeof(double) * (size_t)n);
+  double W = 1.0, S = 0.0;
+  int64_t k = 0;
+  int flag = 0;
+  for (;;) {
+    double dG = INFINITY;
+    if (!pb->closed) {
+      dG = orc_delta_gamma(m, pb, pr, w->Y, w->yg);
+      if (dG < pr->eps) {
+        S += W * orc_func_eval(m, &pb->g, pb->sigma, w->yg);
+        break;
+      }
+      /* W = 0 (underflow): every later term of the score is multiplied by W,
+       * so stopping is exact. */
+      if (W == 0.0) break;
+    } else if (W < pr->tau_w) {
+      break;
+    }
+    if (k >= pr->max_steps) { flag = 1; break; }
+    double rgeo = pr->c_kappa / (1.0 + kappa_of(m));
+    double r = pr->theta * (dG < rgeo ? dG : rgeo);
+    double a = sqs * r;
+    double em1 = orc_em1(n, a);
+    double c = 1.0 / (1.0 + em1);
+    /* 1 - c = em1/(1+em1) without cancellation; 1 - c directly once c <= 1/2 */
+    double omega = ((em1 <= 1.0) ? em1 * c : 1.0 - c) / pb->sigma;
+    /* Theta = Y + r g/|g| */
+    orc_gaussians(pr->seed, 0u, (uint32_t)k, i, p, n, w->g);
+    double gn = sqrt(dot(w->g, w->g, n));
+    double sc = r / gn;
+    for (int q = 0; q < n; ++q) w->Th[q] = w->Y[q] + sc * w->g[q];
+    /* F_k: N_V interior samples */
+    double F = 0.0, U0 = 0.0, t0 = 0.0;
+    for (int l = 0; l < pr->n_v; ++l) {
+      double U = uniform_at(pr->seed, nb * (uint32_t)(1 + pr->n_v) + (uint32_t)l, (uint32_t)k, i, p);
+      double t = orc_green_cdf_inv(n, a, U);
+      if (l == 0) { U0 = U; t0 = t; }
+      orc_gaussians(pr->seed, nb * (uint32_t)(1 + l), (uint32_t)k, i, p, n, w->g);
+      double zn = sqrt(dot(w->g, w->g, n));
+      double zs = (r * t) / zn;
+      for (int q = 0; q < n; ++q) w->Z[q] = w->Y[q] + zs * w->g[q];
+      orc_cp(m, w->Z, w->cZ);
+      F += orc_func_eval(m, &pb->f, pb->sigma, w->cZ);
+    }
+    if (pr->n_v > 1) F /= (double)pr->n_v;
+    S += (W * omega) * F;
+    W *= c;
+    orc_cp(m, w->Th, w->Y);
+    if (rec && *nrec < cap) {
+      orc_trace_rec* R = &rec[*nrec];
+      R->k = k; R->r = r; R->c = c; R->omega = omega; R->delta_gamma = dG; R->W = W; R->S = S;
+      R->F = F; R->U0 = U0; R->t0 = t0; R->theta_norm = gn;
+      for (int q = 0; q < 3; ++q) R->y[q] = q < n ? w->Y[q] : 0.0;
+      (*nrec)++;
+    }
+    k++;
+  }
+  *S_out = S;
+  *K_out = k;
+  return flag;
+}
+
+int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                    const double* pts, int64_t P, int64_t N, double* S, int64_t* K,
+                    int32_t* flags, int n_threads) {
+#ifdef _OPENMP
+  if (n_threads > 0) omp_set_num_threads(n_threads);
+#endif
+  int64_t total = P * N;
+#pragma omp parallel
+  {
+    work_t w;
+    work_alloc(&w, m->n);
+#pragma omp for schedule(dynamic, 4)
+    for (int64_t q = 0; q < total; ++q) {
+      int64_t p = q / N, i = q % N;
+      int64_t nrec = 0;
+      flags[q] = run_walk(m, pb, pr, pts + (size_t)p * (size_t)m->n, (uint32_t)p, (uint32_t)i, &w,
+                          &S[q], &K[q], NULL, 0, &nrec);
+    }
+    work_free(&w);
+  }
+  return 0;
+}
+
+/* Per-point estimator (eq. mc_estimator): Kahan sums of S and S^2 in walk order. */
+int orc_solve(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+              const double* pts, int64_t P, int64_t N, double* mean, double* stderr_,
+              double* mean_steps, int64_t* n_flagged, int n_threads) {
+  double* S = (double*)malloc(sizeof(double) * (size_t)(P * N));
+  int64_t* K = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P * N));
+  int32_t* fl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P * N));
+  orc_walk_scores(m, pb, pr, pts, P, N, S, K, fl, n_threads);
+  int64_t nf = 0;
+  for (int64_t p = 0; p < P; ++p) {
+    double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, ks = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      double v = S[p * N + i];
+      double y = v - c1, t = s1 + y; c1 = (t - s1) - y; s1 = t;
+      double y2 = v * v - c2, t2 = s2 + y2; c2 = (t2 - s2) - y2; s2 = t2;
+      ks += (double)K[p * N + i];
+      nf += fl[p * N + i];
+    }
+    double mu = s1 / (double)N;
+    double var = (N > 1) ? (s2 - (double)N * mu * mu) / (double)(N - 1) : 0.0;
+    if (var < 0.0) var = 0.0;
+    mean[p] = mu;
+    stderr_[p] = sqrt(var / (double)N);
+    mean_steps[p] = ks / (double)N;
+  }
+  if (n_flagged) *n_flagged = nf;
+  free(S); free(K); free(fl);
+  return 0;
+}
+
+int64_t orc_trace(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                  const double* y0, int64_t p, int64_t i, orc_trace_rec* rec, int64_t cap,
+                  double* S_out, int64_t* K_out) {
+  work_t w;
+  work_alloc(&w, m->n);
+  int64_t nrec = 0;
+  run_walk(m, pb, pr, y0, (uint32_t)p, (uint32_t)i, &w, S_out, K_out, rec, cap, &nrec);
+  work_free(&w);
+  return nrec;
+}

@@ -1,0 +1,102 @@
+/*
+ * mpwos_oracle.h — FP64 CPU oracle for the modified projected Walk on Spheres
+ * (MPWoS) recursion.  TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check
+ * and the benchmark's CPU-baseline leg call it; the product library never does.
+ * It shares no code, header or table with the CUDA path.
+ *
+ * Every routine follows the paper's definitions in their plain form:
+ *   - problem                 Sec. 2.1, eqs. surface_pde / surface_bc
+ *   - c_{sigma,r}             Lemma 2.1 (eq. def_c_sigma_r) via the Bessel-free
+ *                             series of Lemma 3.1
+ *   - Green density / omega   Remark after Lemma 2.1, eq. omega_of_y, Thm 2.2
+ *   - radius rule             eqs. radius_rule_unified, delta_Gamma_general,
+ *                             rho_geo_curvature
+ *   - projected chain         eq. projected_chain_update
+ *   - path score / stopping   eqs. local_average_source, path_score_definition
+ *   - estimator               eq. mc_estimator, Algorithm 1
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) at the
+ * counter (block j, step k, walk i, point p), key = 64-bit seed.
+ */
+#ifndef MPWOS_ORACLE_H
+#define MPWOS_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { ORC_EUCLID = 0, ORC_SPHERE = 1, ORC_TORUS = 2, ORC_EMBEDDED_SPHERE = 3 };
+enum { ORC_POLY = 0, ORC_TORUS_FOURIER = 1, ORC_SPHERE_QUAD = 2 };
+
+typedef struct {
+  int kind, n, d;
+  double R, a;            /* torus: centre-circle radius, tube radius          */
+  const double* Q;        /* embedded sphere: n x (d+1) row-major, orthonormal */
+  const double* b;        /* embedded sphere: shift, length n                  */
+} orc_manifold;
+
+typedef struct {
+  int kind, apply_op, n_terms;
+  const double* coef;     /* n_terms                                           */
+  const int* term_off;    /* poly: n_terms+1 offsets into var/pw               */
+  const int* var;
+  const int* pw;
+  const int* modes;       /* torus: 4 ints per term (m, q, theta trig, phi trig) */
+  double c0;              /* sphere quad: u = c0 + v.s + s^T A s               */
+  const double* v;        /* d+1                                               */
+  const double* A;        /* (d+1)^2 row-major                                 */
+} orc_func;
+
+typedef struct {
+  double sigma;
+  int closed;
+  const double* bnd_normal;   /* unit normal e of the half-space {e.x > h}  */
+  double bnd_offset;          /* h                                          */
+  orc_func f, g;
+} orc_problem;
+
+typedef struct {
+  double eps, tau_w, theta, c_kappa;
+  int n_v;
+  int64_t max_steps;
+  uint64_t seed;
+} orc_params;
+
+/* One trace record per step of one walk (tiny-case pins). */
+typedef struct {
+  int64_t k;
+  double r, c, omega, delta_gamma, W, S, F, U0, t0, theta_norm;
+  double y[3];
+} orc_trace_rec;
+
+/* primitives */
+void   orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double orc_u53(uint32_t hi, uint32_t lo);
+void   orc_gaussians(uint64_t seed, uint32_t j0, uint32_t k, uint32_t i, uint32_t p, int n, double* g);
+double orc_em1(int n, double a);          /* I~_nu(a) - 1 (Lemma 3.1 series)      */
+double orc_c_sigma_r(int n, double a);    /* 1 / I~_nu(a)                          */
+double orc_green_cdf(int n, double a, double t);
+double orc_green_cdf_inv(int n, double a, double U);
+double orc_kt_minus_one(double mu, double x);
+void   orc_cp(const orc_manifold* m, const double* x, double* out);
+double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                       const double* y, double* y_gamma);
+double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, const double* x);
+
+/* the walk: per-walk score S, stopping index K, flag (1 = hit max_steps) */
+int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                    const double* pts, int64_t P, int64_t N, double* S, int64_t* K,
+                    int32_t* flags, int n_threads);
+/* per-point mean / standard error / mean steps (Kahan sums in walk order) */
+int orc_solve(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+              const double* pts, int64_t P, int64_t N, double* mean, double* stderr_,
+              double* mean_steps, int64_t* n_flagged, int n_threads);
+/* one walk with a per-step trace; returns number of records written */
+int64_t orc_trace(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                  const double* y0, int64_t p, int64_t i, orc_trace_rec* rec, int64_t cap,
+                  double* S_out, int64_t* K_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,291 @@
+"""Seeded synthetic inputs for the MPWoS workloads.
+
+This module only draws query points, embeddings and coefficient sets from
+seeded NumPy generators and writes the problem data (manifold, source f,
+boundary data g, screening sigma) as plain descriptors.  It holds none of the
+walk's arithmetic: both the CUDA library binding and the CPU oracle consume
+what it produces, and neither is imported here.
+
+Problem data conventions (the screened Poisson problem of Sec. 2.1, eqs.
+surface_pde / surface_bc):
+
+* a *function* (f or g) is one of
+    - ``poly``: sparse polynomial in the ambient coordinates of a point on M,
+      ``sum_t coef_t * prod_j x[var_tj] ** pow_tj``;
+    - ``torus_fourier``: ``sum_t coef_t * T_t(m_t theta) * P_t(q_t phi)`` in
+      the torus angles, T/P in {cos, sin}; with ``apply_op`` the function is
+      replaced by ``(-Delta_M + sigma)`` applied to that series (closed form);
+    - ``sphere_quad``: ``c0 + v.s + s^T A s`` in the intrinsic unit vector s
+      of a (possibly embedded) round sphere; with ``apply_op`` likewise.
+* manufactured solutions follow the workloads' definitions: the source is
+  ``(-Delta_M + sigma) u`` written out with the sphere/torus spectra.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+
+# ----------------------------------------------------------------------------
+# function descriptors
+# ----------------------------------------------------------------------------
+
+FUNC_POLY = 0
+FUNC_TORUS_FOURIER = 1
+FUNC_SPHERE_QUAD = 2
+
+MANIFOLD_EUCLID = 0
+MANIFOLD_SPHERE = 1
+MANIFOLD_TORUS = 2
+MANIFOLD_EMBEDDED_SPHERE = 3
+
+TRIG_COS = 0
+TRIG_SIN = 1
+
+
+@dataclass
+class Func:
+    kind: int
+    apply_op: int = 0
+    coef: List[float] = field(default_factory=list)
+    # poly: per term list of (var, pow)
+    terms: List[List[Tuple[int, int]]] = field(default_factory=list)
+    # torus: per term (m, q, theta_trig, phi_trig)
+    modes: List[Tuple[int, int, int, int]] = field(default_factory=list)
+    # sphere quad
+    c0: float = 0.0
+    v: Optional[np.ndarray] = None
+    A: Optional[np.ndarray] = None
+
+    @staticmethod
+    def poly(terms: Sequence[Tuple[float, Sequence[Tuple[int, int]]]]) -> "Func":
+        return Func(kind=FUNC_POLY, coef=[float(c) for c, _ in terms],
+                    terms=[[(int(v), int(p)) for v, p in vp] for _, vp in terms])
+
+    @staticmethod
+    def const(value: float) -> "Func":
+        return Func.poly([(value, [])])
+
+    @staticmethod
+    def torus(terms: Sequence[Tuple[float, int, int, int, int]], apply_op: bool) -> "Func":
+        return Func(kind=FUNC_TORUS_FOURIER, apply_op=int(apply_op),
+                    coef=[float(t[0]) for t in terms],
+                    modes=[(int(t[1]), int(t[2]), int(t[3]), int(t[4])) for t in terms])
+
+    @staticmethod
+    def sphere_quad(c0: float, v: np.ndarray, A: np.ndarray, apply_op: bool) -> "Func":
+        return Func(kind=FUNC_SPHERE_QUAD, apply_op=int(apply_op), c0=float(c0),
+                    v=np.ascontiguousarray(v, dtype=np.float64),
+                    A=np.ascontiguousarray(A, dtype=np.float64))
+
+    # flattened arrays shared by both bindings -------------------------------
+    def flat_poly(self):
+        off = [0]
+        var: List[int] = []
+        pw: List[int] = []
+        for t in self.terms:
+            for v, p in t:
+                var.append(v)
+                pw.append(p)
+            off.append(len(var))
+        return (np.asarray(self.coef, dtype=np.float64), np.asarray(off, dtype=np.int32),
+                np.asarray(var if var else [0], dtype=np.int32),
+                np.asarray(pw if pw else [0], dtype=np.int32))
+
+    def flat_modes(self):
+        m = np.asarray(self.modes, dtype=np.int32).reshape(-1)
+        return np.asarray(self.coef, dtype=np.float64), (m if m.size else np.zeros(4, np.int32))
+
+
+@dataclass
+class Manifold:
+    kind: int
+    n: int
+    d: int
+    R: float = 0.0
+    a: float = 0.0
+    Q: Optional[np.ndarray] = None   # n x (d+1), row-major float64
+    b: Optional[np.ndarray] = None   # n
+
+
+@dataclass
+class Problem:
+    manifold: Manifold
+    sigma: float
+    closed: bool
+    f: Func
+    g: Func
+    bnd_normal: Optional[np.ndarray] = None
+    bnd_offset: float = 0.0
+
+
+@dataclass
+class Params:
+    eps: float = 1e-3
+    tau_w: float = 1e-8
+    theta: float = 0.95
+    c_kappa: float = 1.2
+    n_v: int = 1
+    max_steps: int = 10_000_000
+    seed: int = 0
+
+
+# ----------------------------------------------------------------------------
+# seeded geometry
+# ----------------------------------------------------------------------------
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def sphere_cap_points(P: int, seed: int = 0) -> np.ndarray:
+    """Uniform (area) points on the cap z>0 of the unit sphere S^2."""
+    x = _rng(seed).standard_normal((P, 3))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    x[:, 2] = np.abs(x[:, 2])
+    return x
+
+
+def hemisphere_points(P: int, n: int, seed: int = 0) -> np.ndarray:
+    """Uniform points on the half {x_1 > 0} of the unit sphere S^{n-1}."""
+    x = _rng(seed).standard_normal((P, n))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    x[:, 0] = np.abs(x[:, 0])
+    return x
+
+
+def torus_angles(P: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """(theta, phi) uniform in [0, 2pi)^2 (parameter-uniform)."""
+    g = _rng(seed)
+    return g.uniform(0.0, 2 * math.pi, P), g.uniform(0.0, 2 * math.pi, P)
+
+
+def torus_points(theta: np.ndarray, phi: np.ndarray, R: float, a: float) -> np.ndarray:
+    """X(theta, phi) = ((R + a cos t) cos p, (R + a cos t) sin p, a sin t) (Example 1's parametrisation)."""
+    rr = R + a * np.cos(theta)
+    return np.stack([rr * np.cos(phi), rr * np.sin(phi), a * np.sin(theta)], axis=1)
+
+
+def embedding(n: int, d: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """Seeded orthonormal Q (n x (d+1), from a Gaussian QR, sign-fixed) and shift b ~ N(0, I)."""
+    g = _rng(seed)
+    G = g.standard_normal((n, d + 1))
+    Q, Rm = np.linalg.qr(G)
+    Q = Q * np.sign(np.diag(Rm))[None, :]
+    b = g.standard_normal(n)
+    return np.ascontiguousarray(Q), np.ascontiguousarray(b)
+
+
+def embedded_sphere_points(P: int, Q: np.ndarray, b: np.ndarray, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """Uniform intrinsic s on S^d and the ambient points Q s + b."""
+    s = _rng(seed).standard_normal((P, Q.shape[1]))
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    return s @ Q.T + b[None, :], s
+
+
+def quadratic_coeffs(dim: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """v ~ N(0, I)/sqrt(dim); A symmetric, trace-free, ||A||_F = 1."""
+    g = _rng(seed)
+    v = g.standard_normal(dim) / math.sqrt(dim)
+    M = g.standard_normal((dim, dim))
+    A = 0.5 * (M + M.T)
+    A -= np.trace(A) / dim * np.eye(dim)
+    A /= np.linalg.norm(A)
+    return v, A
+
+
+# ----------------------------------------------------------------------------
+# the workloads
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Workload:
+    name: str
+    problem: Problem
+    points: np.ndarray          # P x n float64
+    walks: int
+    params: Params
+    exact: np.ndarray           # manufactured solution at the points
+    precision: str              # "f64" or "f32"
+
+
+def sphere_cap(P: int = 64, walks: int = 1000, seed: int = 0) -> Workload:
+    """Unit S^2, domain z>0, sigma=1, u = xy + z  =>  f = 7xy + 3z, g = xy on z=0.
+
+    xy and z are spherical harmonics of degree 2 and 1 (-Delta eigenvalues 6, 2)."""
+    man = Manifold(MANIFOLD_SPHERE, n=3, d=2)
+    f = Func.poly([(7.0, [(0, 1), (1, 1)]), (3.0, [(2, 1)])])
+    g = Func.poly([(1.0, [(0, 1), (1, 1)])])
+    prob = Problem(man, sigma=1.0, closed=False, f=f, g=g,
+                   bnd_normal=np.array([0.0, 0.0, 1.0]), bnd_offset=0.0)
+    pts = sphere_cap_points(P, seed)
+    exact = pts[:, 0] * pts[:, 1] + pts[:, 2]
+    return Workload("s2_cap", prob, pts, walks, Params(eps=1e-3), exact, "f64")
+
+
+def torus_closed(P: int = 4096, walks: int = 10_000, seed: int = 0, R: float = 1.0, a: float = 0.4,
+                 sigma: float = 2.0) -> Workload:
+    """Closed torus R=1, tube radius 0.4, sigma=2, u = sin(theta) cos(2 phi)."""
+    man = Manifold(MANIFOLD_TORUS, n=3, d=2, R=R, a=a)
+    term = [(1.0, 1, 2, TRIG_SIN, TRIG_COS)]
+    f = Func.torus(term, apply_op=True)
+    g = Func.const(0.0)
+    prob = Problem(man, sigma=sigma, closed=True, f=f, g=g)
+    th, ph = torus_angles(P, seed)
+    pts = torus_points(th, ph, R, a)
+    exact = np.sin(th) * np.cos(2 * ph)
+    return Workload("torus_closed", prob, pts, walks, Params(), exact, "f32")
+
+
+def hypersphere_half(P: int = 16384, walks: int = 4096, n: int = 1000, seed: int = 0) -> Workload:
+    """S^{n-1} in R^n, domain x_1>0, sigma=1, u = x_1 + x_2 x_3.
+
+    On S^{n-1}: x_1 has eigenvalue n-1, x_2 x_3 has 2n; f = n x_1 + (2n+1) x_2 x_3, g = x_2 x_3."""
+    man = Manifold(MANIFOLD_SPHERE, n=n, d=n - 1)
+    f = Func.poly([(float(n), [(0, 1)]), (float(2 * n + 1), [(1, 1), (2, 1)])])
+    g = Func.poly([(1.0, [(1, 1), (2, 1)])])
+    e = np.zeros(n)
+    e[0] = 1.0
+    prob = Problem(man, sigma=1.0, closed=False, f=f, g=g, bnd_normal=e, bnd_offset=0.0)
+    pts = hemisphere_points(P, n, seed)
+    exact = pts[:, 0] + pts[:, 1] * pts[:, 2]
+    return Workload("s999_half", prob, pts, walks, Params(eps=1e-3), exact, "f32")
+
+
+def embedded_s20(P: int = 32768, walks: int = 2048, n: int = 1000, d: int = 20, sigma: float = 0.5,
+                 seed: int = 0) -> Workload:
+    """S^d embedded in R^n by a seeded orthonormal Q plus shift b; u = v.s + s^T A s (A trace-free)."""
+    Q, b = embedding(n, d, seed)
+    v, A = quadratic_coeffs(d + 1, seed + 1)
+    man = Manifold(MANIFOLD_EMBEDDED_SPHERE, n=n, d=d, Q=Q, b=b)
+    f = Func.sphere_quad(0.0, v, A, apply_op=True)
+    g = Func.const(0.0)
+    prob = Problem(man, sigma=sigma, closed=True, f=f, g=g)
+    pts, s = embedded_sphere_points(P, Q, b, seed + 2)
+    exact = s @ v + np.einsum("pi,ij,pj->p", s, A, s)
+    return Workload("s20_in_r1000", prob, pts, walks, Params(), exact, "f32")
+
+
+def constant_solution(base: Workload) -> Workload:
+    """Same geometry with f = sigma, g = 1: u = 1 exactly (each walk telescopes)."""
+    p = base.problem
+    prob = Problem(p.manifold, p.sigma, p.closed, Func.const(p.sigma), Func.const(1.0),
+                   p.bnd_normal, p.bnd_offset)
+    return Workload(base.name + "_const", prob, base.points, base.walks, base.params,
+                    np.ones(len(base.points)), base.precision)
+
+
+def euclid_halfspace(P: int = 16, walks: int = 2000, n: int = 3, sigma: float = 1.0, seed: int = 0) -> Workload:
+    """M = R^n (cp = identity), domain x_1 > 0, f = 0, g = 1: u = exp(-sqrt(sigma) x_1)."""
+    man = Manifold(MANIFOLD_EUCLID, n=n, d=n)
+    e = np.zeros(n)
+    e[0] = 1.0
+    prob = Problem(man, sigma=sigma, closed=False, f=Func.const(0.0), g=Func.const(1.0),
+                   bnd_normal=e, bnd_offset=0.0)
+    g = _rng(seed)
+    pts = g.standard_normal((P, n))
+    pts[:, 0] = g.uniform(0.05, 1.5, P)
+    exact = np.exp(-math.sqrt(sigma) * pts[:, 0])
+    return Workload("euclid_half", prob, pts, walks, Params(eps=1e-3), exact, "f64")
