@@ -1,0 +1,172 @@
+/*
+ * mpwos.h — C ABI of the B300 MPWoS library (libmpwos.so).
+ *
+ * The library estimates the solution of the screened Poisson equation
+ *     -Delta_M u + sigma u = f  on Omega in M,   u = g  on Gamma = boundary of Omega
+ * (Sec. 2.1, eqs. surface_pde / surface_bc) at query points y_0 on an embedded
+ * manifold M in R^n by the modified projected Walk on Spheres recursion
+ * (Algorithm 1; path score eq. path_score_definition; estimator eq.
+ * mc_estimator).  Every walk step runs in CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - the return value is a status code below; the message of the last
+ *     failure is kept per context (mpwos_last_error);
+ *   - problem data (f, g coefficients, Q, b, the boundary normal) are HOST
+ *     pointers, read during the call and copied; the caller keeps ownership;
+ *   - query points and result arrays may be host or device pointers; the
+ *     library inspects them with cudaPointerGetAttributes.  Host arrays are
+ *     copied in/out inside the call; device arrays are read/written in place;
+ *   - a call returns after its results are written (synchronous) unless it
+ *     is one of the asynchronous request calls (mpwos_submit ...);
+ *   - query points must lie on M (the walk starts at y_0 as given).
+ */
+#ifndef MPWOS_H
+#define MPWOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define MPWOS_OK 0
+#define MPWOS_EINVAL 1      /* invalid argument (message says which)               */
+#define MPWOS_ENOMEM 2      /* device allocation failed                            */
+#define MPWOS_ECUDA 3       /* a CUDA call failed (message has the CUDA error)     */
+#define MPWOS_ETIMEDOUT 4   /* a bounded wait ran out                              */
+#define MPWOS_ECANCELED 5   /* request cancelled                                   */
+#define MPWOS_EMAXSTEPS 6   /* results written, but some walks reached max_steps   */
+#define MPWOS_ENOTFOUND 7   /* unknown request id                                  */
+#define MPWOS_EBUSY 8       /* admission refused: no slot or memory free now       */
+
+/* ---- manifold kinds (Sec. 2.1: parametrized manifolds with closed-form cp) */
+#define MPWOS_EUCLID 0            /* M = R^n, cp = identity                      */
+#define MPWOS_SPHERE 1            /* unit sphere S^{n-1} in R^n, cp(x) = x/|x|    */
+#define MPWOS_TORUS 2             /* torus in R^3, centre radius R, tube radius a */
+#define MPWOS_EMBEDDED_SPHERE 3   /* Q S^d + b, Q (n x (d+1)) orthonormal columns */
+
+/* ---- function kinds for f and g (a C ABI cannot pass device code) ------- */
+#define MPWOS_FUNC_POLY 0          /* sum_t coef_t prod_j x[var]^pw (ambient coords)  */
+#define MPWOS_FUNC_TORUS_FOURIER 1 /* sum_t coef_t T(m theta) P(q phi); T,P in {cos,sin} */
+#define MPWOS_FUNC_SPHERE_QUAD 2   /* c0 + v.s + s^T A s, s = intrinsic unit vector   */
+
+/* ---- precision of the walk --------------------------------------------- */
+#define MPWOS_FP64 0   /* FP64 walk; per-walk identical draws to the CPU oracle         */
+#define MPWOS_FP32 1   /* FP32 positions/projection/sampling, FP64 weights and sums     */
+
+typedef struct mpwos_ctx mpwos_ctx;
+
+/* Manifold M (Sec. 2.1).  Q, b are host arrays (embedded sphere only),
+ * Q row-major n x (d+1) with orthonormal columns; copied at the call. */
+typedef struct {
+  int kind;
+  int n;            /* ambient dimension                                  */
+  int d;            /* manifold dimension                                 */
+  double R, a;      /* torus: centre-circle radius, tube radius           */
+  const double* Q;  /* embedded sphere                                    */
+  const double* b;  /* embedded sphere shift, length n                    */
+} mpwos_manifold_desc;
+
+/* A function on M given as a small closed family of device-evaluable forms.
+ * apply_op != 0 (torus Fourier, sphere quad): evaluate (-Delta_M + sigma) of
+ * the series in closed form instead of the series itself — the source of a
+ * manufactured solution. */
+typedef struct {
+  int kind;
+  int apply_op;
+  int n_terms;
+  const double* coef;     /* n_terms                                        */
+  const int* term_off;    /* POLY: n_terms + 1 offsets into var / pw        */
+  const int* var;         /* POLY: coordinate index (0-based)               */
+  const int* pw;          /* POLY: power                                    */
+  const int* modes;       /* TORUS_FOURIER: 4 ints per term (m, q, Ttrig, Ptrig), trig 0 = cos, 1 = sin */
+  double c0;              /* SPHERE_QUAD                                    */
+  const double* v;        /* SPHERE_QUAD: d + 1                             */
+  const double* A;        /* SPHERE_QUAD: (d + 1)^2 row-major               */
+} mpwos_func;
+
+/* The screened Poisson problem (eqs. surface_pde, surface_bc).  Boundary:
+ * Omega = M intersected with the half-space {x : e.x > h} (EUCLID, SPHERE),
+ * or closed = 1 (Omega = M). */
+typedef struct {
+  double sigma;               /* screening, > 0                         */
+  int closed;
+  const double* bnd_normal;   /* unit e, length n (host)                */
+  double bnd_offset;          /* h                                      */
+  mpwos_func f, g;
+} mpwos_problem;
+
+/* Walk parameters (Algorithm 1; radius rule eq. radius_rule_unified). */
+typedef struct {
+  double eps;        /* boundary layer width epsilon (eq. boundary_layer)      */
+  double tau_w;      /* closed-manifold weight cut-off tau_W                   */
+  double theta;      /* radius safety factor, 0 < theta < 1                    */
+  double c_kappa;    /* rho_geo = c_kappa / (1 + kappa) (eq. rho_geo_curvature) */
+  int n_v;           /* interior samples per step N_V (eq. local_average_source) */
+  int64_t max_steps; /* per-walk cap; walks reaching it are flagged (EMAXSTEPS) */
+  uint64_t seed;     /* Philox key                                              */
+  int precision;     /* MPWOS_FP64 or MPWOS_FP32                                */
+} mpwos_params;
+
+/* Fill a params struct with the defaults: eps 1e-3, tau_w 1e-8, theta 0.95,
+ * c_kappa 1.2, n_v 1, max_steps 1e7, seed 0, FP64. */
+void mpwos_params_default(mpwos_params* p);
+
+/* Create a context on CUDA device `device` (owns device state, tables, a
+ * stream).  Returns MPWOS_EINVAL for a bad device, MPWOS_ECUDA otherwise. */
+int mpwos_create(int device, mpwos_ctx** out);
+
+/* Destroy a context and free its device memory.  NULL is a no-op. */
+void mpwos_destroy(mpwos_ctx* ctx);
+
+/* Message of the last failed call on this context ("" if none). */
+const char* mpwos_last_error(const mpwos_ctx* ctx);
+
+/* Use `stream` (a cudaStream_t, borrowed, may be NULL for the context's own
+ * stream) for subsequent synchronous calls. */
+int mpwos_set_stream(mpwos_ctx* ctx, void* stream);
+
+/* Estimate u at P query points (pts: P x n row-major FP64, host or device)
+ * with N walks each (Algorithm 1, estimator eq. mc_estimator).  Outputs (P
+ * each, host or device, caller-owned): the mean of the path scores, its
+ * standard error, the mean stopping index K.  Returns MPWOS_EMAXSTEPS (with
+ * results written) if any walk reached max_steps. */
+int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+                const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
+                double* mean, double* stderr_, double* mean_steps);
+
+/* Per-walk path scores S^i (eq. path_score_definition), stopping indices K^i
+ * and max-steps flags, P x N row-major (walk i of point p at p*N + i); host
+ * or device.  Walk (p, i) draws its random numbers from Philox4x32-10 at
+ * counter (block, step, i, p), so each value depends on (seed, p, i) only. */
+int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+                      const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
+                      double* S, int32_t* K, int32_t* flags);
+
+/* ---- primitives exposed for verification ------------------------------ */
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4q..4q+3] =
+ * Philox(ctr[4q..4q+3], key); count blocks; host arrays. */
+int mpwos_philox(mpwos_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t key1,
+                 uint32_t* out, int64_t count);
+
+/* Radius fraction t = R/r of the interior sample Z ~ rho(y, .) (eq.
+ * Z_sampling_density) for uniform U, computed by the device sampler at
+ * precision `precision` for ambient dimension n and a = sqrt(sigma) r, through
+ * the same tables the walk uses (built for a in [0, a_max]); host arrays. */
+int mpwos_green_radius(mpwos_ctx* ctx, int n, double a_max, const double* a, const double* U,
+                       double* t, int64_t count, int precision);
+
+/* c_{sigma,r} (Lemma 2.1 via the Lemma 3.1 series) for ambient dimension n at
+ * a = sqrt(sigma) r, evaluated by the device code; host arrays. */
+int mpwos_c_sigma_r(mpwos_ctx* ctx, int n, const double* a, double* c, int64_t count);
+
+/* Number of the library's own kernel launches so far on this context. */
+int64_t mpwos_launch_count(const mpwos_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,229 @@
+"""B300 MPWoS: the modified projected Walk on Spheres hot path in CUDA (sm_103a).
+
+This module is the thin Python binding of the C ABI in ``include/mpwos.h``
+(``libmpwos.so``, built in-tree by ``build.py``).  It only marshals arguments:
+every step of the walk runs in the library's kernels.  Importing the package
+does not load the library; the first call does, and raises if the library or
+a CUDA device is missing — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+__all__ = ["lib", "Context", "MPWOS_OK", "MPWOS_EMAXSTEPS", "FP64", "FP32", "MpwosError"]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpwos.so")
+
+MPWOS_OK, MPWOS_EINVAL, MPWOS_ENOMEM, MPWOS_ECUDA = 0, 1, 2, 3
+MPWOS_ETIMEDOUT, MPWOS_ECANCELED, MPWOS_EMAXSTEPS, MPWOS_ENOTFOUND, MPWOS_EBUSY = 4, 5, 6, 7, 8
+FP64, FP32 = 0, 1
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class MpwosError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"mpwos error {code}: {msg}")
+        self.code = code
+
+
+class ManifoldDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int), ("d", C.c_int), ("R", C.c_double), ("a", C.c_double),
+                ("Q", _dp), ("b", _dp)]
+
+
+class Func(C.Structure):
+    _fields_ = [("kind", C.c_int), ("apply_op", C.c_int), ("n_terms", C.c_int), ("coef", _dp),
+                ("term_off", _ip), ("var", _ip), ("pw", _ip), ("modes", _ip), ("c0", C.c_double),
+                ("v", _dp), ("A", _dp)]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("closed", C.c_int), ("bnd_normal", _dp), ("bnd_offset", C.c_double),
+                ("f", Func), ("g", Func)]
+
+
+class Params(C.Structure):
+    _fields_ = [("eps", C.c_double), ("tau_w", C.c_double), ("theta", C.c_double), ("c_kappa", C.c_double),
+                ("n_v", C.c_int), ("max_steps", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int)]
+
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib() -> C.CDLL:
+    """Load libmpwos.so (built in-tree); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run paper_2606_21883_b300/build.py (no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        L.mpwos_last_error.restype = C.c_char_p
+        L.mpwos_launch_count.restype = C.c_int64
+        L.mpwos_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+        for name in ("mpwos_destroy", "mpwos_last_error", "mpwos_launch_count"):
+            getattr(L, name).argtypes = [C.c_void_p]
+        L.mpwos_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.mpwos_solve.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc), C.POINTER(Params),
+                                  C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.mpwos_walk_scores.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc),
+                                        C.POINTER(Params), C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
+        L.mpwos_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64]
+        L.mpwos_green_radius.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_int64, C.c_int]
+        L.mpwos_c_sigma_r.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64]
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """Address of a host numpy array or a device torch tensor."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+class _Marshal:
+    """Keeps the arrays behind a ProblemDesc alive for the duration of a call."""
+
+    def __init__(self):
+        self.keep = []
+
+    def arr(self, a, dtype=np.float64):
+        a = np.ascontiguousarray(a, dtype=dtype)
+        self.keep.append(a)
+        return a
+
+    def func(self, f) -> Func:
+        from . import workloads as W
+        cf = Func(kind=f.kind, apply_op=f.apply_op, n_terms=len(f.coef), c0=f.c0)
+        if f.kind == W.FUNC_POLY:
+            coef, off, var, pw = f.flat_poly()
+            cf.coef = self.arr(coef).ctypes.data_as(_dp)
+            cf.term_off = self.arr(off, np.int32).ctypes.data_as(_ip)
+            cf.var = self.arr(var, np.int32).ctypes.data_as(_ip)
+            cf.pw = self.arr(pw, np.int32).ctypes.data_as(_ip)
+        elif f.kind == W.FUNC_TORUS_FOURIER:
+            coef, modes = f.flat_modes()
+            cf.coef = self.arr(coef).ctypes.data_as(_dp)
+            cf.modes = self.arr(modes, np.int32).ctypes.data_as(_ip)
+        else:
+            cf.v = self.arr(f.v).ctypes.data_as(_dp)
+            cf.A = self.arr(f.A).ctypes.data_as(_dp)
+        return cf
+
+    def problem(self, problem):
+        m = problem.manifold
+        md = ManifoldDesc(kind=m.kind, n=m.n, d=m.d, R=m.R, a=m.a)
+        if m.Q is not None:
+            md.Q = self.arr(m.Q).ctypes.data_as(_dp)
+            md.b = self.arr(m.b).ctypes.data_as(_dp)
+        pd = ProblemDesc(sigma=problem.sigma, closed=int(problem.closed), bnd_offset=problem.bnd_offset)
+        if problem.bnd_normal is not None:
+            pd.bnd_normal = self.arr(problem.bnd_normal).ctypes.data_as(_dp)
+        pd.f = self.func(problem.f)
+        pd.g = self.func(problem.g)
+        return md, pd
+
+
+def make_params(params, precision) -> Params:
+    return Params(eps=params.eps, tau_w=params.tau_w, theta=params.theta, c_kappa=params.c_kappa,
+                  n_v=params.n_v, max_steps=params.max_steps, seed=params.seed, precision=precision)
+
+
+class Context:
+    """One library context (mpwos_create) on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.L = lib()
+        h = C.c_void_p()
+        rc = self.L.mpwos_create(device, C.byref(h))
+        if rc != MPWOS_OK:
+            raise MpwosError(rc, f"mpwos_create(device={device}) failed")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.mpwos_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self.L.mpwos_last_error(self.h).decode()
+
+    def launch_count(self) -> int:
+        return int(self.L.mpwos_launch_count(self.h))
+
+    def _check(self, rc, allow=(MPWOS_OK,)):
+        if rc not in allow:
+            raise MpwosError(rc, self.last_error())
+        return rc
+
+    def set_stream(self, stream_handle: int):
+        return self._check(self.L.mpwos_set_stream(self.h, C.c_void_p(stream_handle)))
+
+    # -- the walk ---------------------------------------------------------------
+    def solve(self, problem, params, pts, N, precision=FP64, out=None):
+        """mpwos_solve: returns (mean, stderr, mean_steps, status); pts host or device."""
+        mar = _Marshal()
+        md, pd = mar.problem(problem)
+        prm = make_params(params, precision)
+        P = int(pts.shape[0])
+        if out is None:
+            out = (np.zeros(P), np.zeros(P), np.zeros(P))
+        if not hasattr(pts, "data_ptr"):
+            pts = mar.arr(pts)
+        rc = self.L.mpwos_solve(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
+                                _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
+        self._check(rc, (MPWOS_OK, MPWOS_EMAXSTEPS))
+        return out[0], out[1], out[2], rc
+
+    def walk_scores(self, problem, params, pts, N, precision=FP64):
+        """mpwos_walk_scores: per-walk S (P x N), K, flags."""
+        mar = _Marshal()
+        md, pd = mar.problem(problem)
+        prm = make_params(params, precision)
+        P = int(pts.shape[0])
+        if not hasattr(pts, "data_ptr"):
+            pts = mar.arr(pts)
+        S = np.zeros((P, int(N)))
+        K = np.zeros((P, int(N)), dtype=np.int32)
+        fl = np.zeros((P, int(N)), dtype=np.int32)
+        rc = self.L.mpwos_walk_scores(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
+                                      _ptr(S), _ptr(K), _ptr(fl))
+        self._check(rc)
+        return S, K, fl
+
+    # -- primitives -------------------------------------------------------------
+    def philox(self, ctr, key0, key1):
+        ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+        out = np.zeros_like(ctr)
+        self._check(self.L.mpwos_philox(self.h, _ptr(ctr), key0, key1, _ptr(out), ctr.shape[0]))
+        return out
+
+    def green_radius(self, n, a_max, a, U, precision=FP64):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        t = np.zeros_like(a)
+        self._check(self.L.mpwos_green_radius(self.h, n, a_max, _ptr(a), _ptr(U), _ptr(t), a.size, precision))
+        return t
+
+    def c_sigma_r(self, n, a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        c = np.zeros_like(a)
+        self._check(self.L.mpwos_c_sigma_r(self.h, n, _ptr(a), _ptr(c), a.size))
+        return c

@@ -1,0 +1,143 @@
+// geom3.cuh — closest point (eq. cp_map), effective boundary distance (eq.
+// delta_Gamma_general) and the problem data f, g for manifolds in R^3, in
+// scalar type T (double for the FP64 walk, float for the FP32 walk).
+#pragma once
+#include "dev_common.cuh"
+
+namespace mpwos {
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+
+template <typename T>
+__device__ __forceinline__ T dot3(const T* a, const T* b) {
+  T s = T(0);
+  s += a[0] * b[0];
+  s += a[1] * b[1];
+  s += a[2] * b[2];
+  return s;
+}
+
+// cp(x) for the R^3 manifolds.
+template <int MK, typename T>
+__device__ __forceinline__ void cp3(const DevProblem& pb, const T* x, T* out) {
+  if (MK == kEuclid) {
+    out[0] = x[0]; out[1] = x[1]; out[2] = x[2];
+  } else if (MK == kSphere) {
+    const T nx = dsqrt<T>(dot3(x, x));
+    out[0] = x[0] / nx; out[1] = x[1] / nx; out[2] = x[2] / nx;
+  } else {  // torus: nearest point of the centre circle, then the tube around it
+    const T R = T(pb.R), a = T(pb.a_tube);
+    const T rho = dsqrt<T>(x[0] * x[0] + x[1] * x[1]);
+    const T c0 = R * x[0] / rho, c1 = R * x[1] / rho;
+    T w[3] = {x[0] - c0, x[1] - c1, x[2] - T(0)};
+    const T nw = dsqrt<T>(dot3(w, w));
+    const T s = a / nw;
+    out[0] = c0 + s * w[0];
+    out[1] = c1 + s * w[1];
+    out[2] = T(0) + s * w[2];
+  }
+}
+
+// delta_Gamma(y) = (|P_T r_G|^2 + (|P_N r_G| - ell)_+^2)^{1/2}, r_G = y_G - y, for
+// Omega = M intersected with {e.x > h}; y_G = cp_Gamma(y) is written to yg.  A state
+// with e.y <= h is outside Omega: distance 0.
+template <int MK, typename T>
+__device__ __forceinline__ T delta_gamma3(const DevProblem& pb, const T* y, T* yg) {
+  const T e[3] = {T(pb.e[0]), T(pb.e[1]), T(pb.e[2])};
+  const T h = T(pb.h);
+  const T ey = dot3(e, y);
+  if constexpr (MK == kEuclid) {
+    for (int i = 0; i < 3; ++i) yg[i] = y[i] - (ey - h) * e[i];
+    const T d = fabs(ey - h);
+    return (ey <= h) ? T(0) : d;
+  } else {
+  // unit sphere: y_G = h e + sqrt(1 - h^2) w/|w|, w = y - (e.y) e
+  T w[3];
+  for (int i = 0; i < 3; ++i) w[i] = y[i] - ey * e[i];
+  T nw = dsqrt<T>(dot3(w, w));
+  if (nw == T(0)) {  // pole: lowest-index axis not parallel to e
+    for (int j = 0; j < 3; ++j) {
+      for (int i = 0; i < 3; ++i) w[i] = ((i == j) ? T(1) : T(0)) - e[j] * e[i];
+      nw = dsqrt<T>(dot3(w, w));
+      if (nw > T(1e-8)) break;
+    }
+  }
+  const T sh = dsqrt<T>(T(1) - h * h);
+  for (int i = 0; i < 3; ++i) yg[i] = h * e[i] + sh * (w[i] / nw);
+  T rn = T(0);
+  for (int i = 0; i < 3; ++i) rn += (yg[i] - y[i]) * yg[i];
+  T rt2 = T(0);
+  for (int i = 0; i < 3; ++i) {
+    const T rti = (yg[i] - y[i]) - rn * yg[i];
+    rt2 += rti * rti;
+  }
+  if (ey <= h) return T(0);
+  T ex = fabs(rn) - T(pb.rho_geo);
+  if (ex < T(0)) ex = T(0);
+  return dsqrt<T>(rt2 + ex * ex);
+  }
+}
+
+// Problem data at a point x of M (f(cp(Z)) and g(cp_Gamma(Y)) of Algorithm 1).
+template <int MK, typename T>
+__device__ __forceinline__ T func3(const DevProblem& pb, const DevFunc& fn, const T* x) {
+  if (fn.kind == kPoly) {
+    T total = T(0);
+    for (int t = 0; t < fn.n_terms; ++t) {
+      T prod = T(fn.coef[t]);
+      for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
+        const T xv = x[fn.var[q]];
+        for (int e = 0; e < fn.pw[q]; ++e) prod *= xv;
+      }
+      total += prod;
+    }
+    return total;
+  }
+  if (fn.kind == kTorusFourier) {
+    const T R = T(pb.R), a = T(pb.a_tube);
+    const T rho = dsqrt<T>(x[0] * x[0] + x[1] * x[1]);
+    const T dr = rho - R;
+    const T nr = dsqrt<T>(dr * dr + x[2] * x[2]);
+    const T ct = dr / nr, st = x[2] / nr;       // theta of the point
+    const T cp = x[0] / rho, sp = x[1] / rho;    // phi of the point
+    T total = T(0);
+    for (int t = 0; t < fn.n_terms; ++t) {
+      const int m = fn.modes[t][0], q = fn.modes[t][1];
+      // cos/sin of m theta and q phi by angle addition
+      T cm = T(1), sm = T(0), cq = T(1), sq = T(0);
+      for (int j = 0; j < m; ++j) { const T c2 = cm * ct - sm * st; sm = sm * ct + cm * st; cm = c2; }
+      for (int j = 0; j < q; ++j) { const T c2 = cq * cp - sq * sp; sq = sq * cp + cq * sp; cq = c2; }
+      const T Tv = fn.modes[t][2] == 0 ? cm : sm;
+      const T Pv = fn.modes[t][3] == 0 ? cq : sq;
+      T val;
+      if (!fn.apply_op) {
+        val = Tv * Pv;
+      } else {
+        // -Delta_M(T P) = P [m^2 T/a^2 + sin(th) T'/(a (R + a cos th)) + q^2 T/(R + a cos th)^2]
+        const T Tp = fn.modes[t][2] == 0 ? -T(m) * sm : T(m) * cm;
+        const T rr = R + a * ct;
+        const T lap = T(m * m) * Tv / (a * a) + st * Tp / (a * rr) + T(q * q) * Tv / (rr * rr);
+        val = Pv * (lap + T(pb.sigma) * Tv);
+      }
+      total += T(fn.coef[t]) * val;
+    }
+    return total;
+  }
+  // sphere quad on the unit sphere of R^3 (s = x/|x|, d = 2)
+  const T nx = dsqrt<T>(dot3(x, x));
+  const T s[3] = {x[0] / nx, x[1] / nx, x[2] / nx};
+  T lin = T(0), quad = T(0), tr = T(0);
+  for (int i = 0; i < 3; ++i) {
+    lin += T(fn.v[i]) * s[i];
+    tr += T(fn.A[i * 3 + i]);
+    for (int j = 0; j < 3; ++j) quad += T(fn.A[i * 3 + j]) * s[i] * s[j];
+  }
+  if (!fn.apply_op) return T(fn.c0) + lin + quad;
+  const T mean = tr / T(3);
+  const T sg = T(pb.sigma);
+  return sg * (T(fn.c0) + mean) + (T(2) + sg) * lin + (T(6) + sg) * (quad - mean);
+}
+
+}  // namespace mpwos

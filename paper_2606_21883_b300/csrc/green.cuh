@@ -1,0 +1,219 @@
+// green.cuh — screened factor c_{sigma,r}, the radial law of the interior
+// sample Z ~ rho(y, .) = G(y, .)/omega(y), and its inverse.
+//
+//   c_{sigma,r} = 1 / I~_nu(a),  I~_nu(a) = sum_j (a^2/4)^j / (j! (nu+1)_j)
+//       (Lemma 2.1, eq. def_c_sigma_r, through the Bessel-free series of
+//        Lemma 3.1); a = sqrt(sigma) r, nu = (n-2)/2.
+//   omega = (1 - c)/sigma  (Thm 2.2, eq. omega_explicit_formula).
+//   Radial CDF of t = |Z - y|/r (eq. Z_sampling_density with the Remark's G):
+//       F(t) = [ (1 - K~_{nu+1}(x)) - c K~_nu(a) I~_{nu+1}(x) (x/2)^2 t^{2nu}/(nu(nu+1)) ] / (1 - c),
+//       F'(t) = (a x / (2 nu)) [ K~_nu(x) - c K~_nu(a) I~_nu(x) t^{2nu} ] / (1 - c),   x = a t,
+//   where K~_mu(x) = 2 (x/2)^mu K_mu(x)/Gamma(mu).  For n = 3 these reduce to
+//       F(t) = [P(x) - Q(x) e^{-a}/sinh a]/(1-c),  F'(t) = a x sinh(a - x)/(sinh a (1-c)),
+//       P(x) = 1 - e^{-x}(1+x), Q(x) = x cosh x - sinh x.
+// FP64 throughout (these are the FP64 parts of the walk in every precision).
+#pragma once
+#include <cuda_runtime.h>
+#include "dev_common.cuh"
+
+namespace mpwos {
+
+constexpr double kEulerGamma = 0.57721566490153286;
+constexpr double kPi = 3.141592653589793;
+
+// I~_nu(a) - 1 with z = a^2/4.
+__device__ __forceinline__ double em1_series(double nu, double z) {
+  double term = 1.0, sum = 0.0;
+  for (int j = 1; j < 10000; ++j) {
+    term *= z / (static_cast<double>(j) * (nu + static_cast<double>(j)));
+    sum += term;
+    if (term <= 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+// 1 - c from em1 without cancellation.
+__device__ __forceinline__ double one_minus_c(double em1, double c) {
+  return (em1 <= 1.0) ? em1 * c : 1.0 - c;
+}
+
+// 0F1(;b;z), b > 0.
+__device__ inline double hyp0f1_dev(double b, double z) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 10000; ++k) {
+    term *= z / (static_cast<double>(k) * (b + static_cast<double>(k) - 1.0));
+    sum += term;
+    if (term <= 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+// K~_mu(x) - 1.  Non-integer mu: reflection formula K = (pi/2)(I_{-mu} - I_mu)/sin(pi mu);
+// integer mu: the logarithmic expansion (Abramowitz & Stegun 9.6.11).
+__device__ inline double kt_m1(double mu, double x) {
+  const double z = 0.25 * (x * x);
+  const double hx = log(0.5 * x);
+  const double mr = floor(mu + 0.5);
+  double s = 0.0, term = 1.0;
+  if (fabs(mu - mr) < 1e-12) {
+    const int m = static_cast<int>(mr);
+    for (int k = 1; k <= m - 1; ++k) {
+      term *= z / (static_cast<double>(k) * (static_cast<double>(k) - mr));
+      s += term;
+      if (fabs(term) <= 1e-18 * fabs(s)) break;
+    }
+    const double lg = 0.6931471805599453 + 2.0 * mr * hx - lgamma(mr) - lgamma(mr + 1.0);
+    if (lg > -740.0) {
+      double Hm = 0.0;
+      for (int q = 1; q <= m; ++q) Hm += 1.0 / static_cast<double>(q);
+      double inner = 0.0, tk = 1.0, Hk = 0.0, Hmk = Hm;
+      for (int k = 0; k < 10000; ++k) {
+        const double add = tk * (hx + kEulerGamma - 0.5 * (Hk + Hmk));
+        inner += add;
+        if (k > 2 && fabs(add) <= 1e-18 * fabs(inner)) break;
+        tk *= z / (static_cast<double>(k + 1) * static_cast<double>(m + k + 1));
+        Hk += 1.0 / static_cast<double>(k + 1);
+        Hmk += 1.0 / static_cast<double>(m + k + 1);
+      }
+      s += (((m + 1) & 1) ? -1.0 : 1.0) * exp(lg) * inner;
+    }
+    return s;
+  }
+  for (int k = 1; k < 10000; ++k) {
+    term *= z / (static_cast<double>(k) * (static_cast<double>(k) - mu));
+    s += term;
+    if (term == 0.0) break;
+    if (static_cast<double>(k) > mu + 1.0 && fabs(term) <= 1e-18 * fabs(s)) break;
+  }
+  const double sp = sin(kPi * mu);
+  const double lg = log(kPi) - log(fabs(sp)) - lgamma(mu) - lgamma(mu + 1.0) + 2.0 * mu * hx;
+  if (lg > -740.0) s -= ((sp > 0.0) ? 1.0 : -1.0) * exp(lg) * hyp0f1_dev(1.0 + mu, z);
+  return s;
+}
+
+// P(x) = 1 - e^{-x}(1+x) and Q(x) = x cosh x - sinh x for x < 1 (series).
+__device__ __forceinline__ double p3_series(double x) {
+  double term = x, sum = 0.0;
+  for (int k = 2; k < 60; ++k) {
+    term *= x / static_cast<double>(k);
+    const double add = ((k & 1) ? -1.0 : 1.0) * static_cast<double>(k - 1) * term;
+    sum += add;
+    if (fabs(add) <= 1e-18 * fabs(sum)) break;
+  }
+  return sum;
+}
+
+__device__ __forceinline__ double q3_series(double x) {
+  double term = x, sum = 0.0;
+  for (int k = 1; k < 60; ++k) {
+    term *= x * x / (static_cast<double>(2 * k) * static_cast<double>(2 * k + 1));
+    const double add = 2.0 * static_cast<double>(k) * term;
+    sum += add;
+    if (add <= 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+// Constants of one radial law (depend on n and a only).
+struct GreenLaw {
+  int n;
+  double nu, a, c, omc, kta;   // kta = K~_nu(a) (general n)
+};
+
+__device__ inline GreenLaw green_law(int n, double a) {
+  GreenLaw L;
+  L.n = n;
+  L.nu = 0.5 * static_cast<double>(n - 2);
+  L.a = a;
+  const double em1 = em1_series(L.nu, 0.25 * (a * a));
+  L.c = 1.0 / (1.0 + em1);
+  L.omc = one_minus_c(em1, L.c);
+  L.kta = (n == 3 || a == 0.0) ? 1.0 : 1.0 + kt_m1(L.nu, a);
+  return L;
+}
+
+// F(t) and F'(t).  a == 0 is the Laplace limit (n t^2 - 2 t^n)/(n - 2).
+__device__ inline void green_cdf_pdf(const GreenLaw& L, double t, double& F, double& dF) {
+  const double a = L.a, x = a * t;
+  if (a == 0.0) {
+    const double tn2 = pow(t, static_cast<double>(L.n - 2));
+    F = (static_cast<double>(L.n) * t * t - 2.0 * t * t * tn2) / static_cast<double>(L.n - 2);
+    dF = 2.0 * static_cast<double>(L.n) * t * (1.0 - tn2) / static_cast<double>(L.n - 2);
+    return;
+  }
+  if (L.n == 3) {
+    double second, ratio_d;
+    if (x < 1.0) {
+      const double k = 2.0 / expm1(2.0 * a);
+      second = q3_series(x) * k;
+      F = (p3_series(x) - second) / L.omc;
+    } else {
+      const double den = -expm1(-2.0 * a);
+      second = ((x - 1.0) * exp(x - 2.0 * a) + (x + 1.0) * exp(-x - 2.0 * a)) / den;
+      F = ((1.0 - exp(-x) * (1.0 + x)) - second) / L.omc;
+    }
+    // sinh(a - x)/sinh(a) = e^{-x} (1 - e^{-2(a-x)}) / (1 - e^{-2a})
+    ratio_d = exp(-x) * (-expm1(-2.0 * (a - x))) / (-expm1(-2.0 * a));
+    dF = a * x * ratio_d / L.omc;
+    return;
+  }
+  const double nu = L.nu, zx = 0.25 * (x * x);
+  const double t2nu = pow(t, 2.0 * nu);
+  const double sk = -kt_m1(nu + 1.0, x);
+  const double it1 = hyp0f1_dev(nu + 2.0, zx);
+  F = (sk - L.c * L.kta * it1 * zx * t2nu / (nu * (nu + 1.0))) / L.omc;
+  const double ktx = 1.0 + kt_m1(nu, x);
+  const double itx = hyp0f1_dev(nu + 1.0, zx);
+  dF = (a * x / (2.0 * nu)) * (ktx - L.c * L.kta * itx * t2nu) / L.omc;
+}
+
+// Safeguarded Newton for F(t) = U on [0, 1] from guess t0.
+__device__ inline double green_invert64(const GreenLaw& L, double U, double t0) {
+  if (U >= 1.0) return 1.0;
+  double lo = 0.0, hi = 1.0;
+  double t = (t0 > 0.0 && t0 < 1.0) ? t0 : 0.5;
+  for (int it = 0; it < 100; ++it) {
+    double F, dF;
+    green_cdf_pdf(L, t, F, dF);
+    const double res = F - U;
+    if (res < 0.0) lo = t; else hi = t;
+    double tn = (dF > 0.0) ? t - res / dF : 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    const bool conv = fabs(tn - t) <= 4e-16 * t || hi - lo <= 4e-16 * hi;
+    t = tn;
+    if (conv || res == 0.0) break;
+  }
+  return t;
+}
+
+// s = (2/pi) asin(sqrt(U)): the table's abscissa.
+__device__ __forceinline__ double s_of_u64(double U) { return 0.6366197723675814 * asin(sqrt(U)); }
+__device__ __forceinline__ float s_of_u32(float U) { return 0.636619772f * asinf(sqrtf(U)); }
+
+template <typename T>
+__device__ __forceinline__ T catmull_rom(const T* row, int j, T f) {
+  const T p0 = row[j], p1 = row[j + 1], p2 = row[j + 2], p3 = row[j + 3];
+  return p1 + T(0.5) * f * (p2 - p0 + f * (T(2) * p0 - T(5) * p1 + T(4) * p2 - p3 +
+                                           f * (T(3) * (p1 - p2) + p3 - p0)));
+}
+
+// Table lookup t(s; z): rows over z = a^2/4 in [0, z_max] (NA rows; NA = 1 is a
+// single law), NS nodes over s in [0, 1] plus a ghost node at each end.
+template <typename T>
+__device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS, double z_max, T a, T s) {
+  const int rs = NS + 2;
+  T xs = s * T(NS - 1);
+  int j = static_cast<int>(xs);
+  j = j < 0 ? 0 : (j > NS - 2 ? NS - 2 : j);
+  const T f = xs - T(j);
+  if (NA == 1) return catmull_rom(tab, j, f);
+  const T fa = (a * a * T(0.25)) / T(z_max) * T(NA - 1);
+  int ia = static_cast<int>(fa);
+  ia = ia < 0 ? 0 : (ia > NA - 2 ? NA - 2 : ia);
+  const T wa = fa - T(ia);
+  const T v0 = catmull_rom(tab + static_cast<size_t>(ia) * rs, j, f);
+  const T v1 = catmull_rom(tab + static_cast<size_t>(ia + 1) * rs, j, f);
+  return v0 + wa * (v1 - v0);
+}
+
+}  // namespace mpwos

@@ -1,0 +1,61 @@
+// kernels_f32.cu — FP32 walks (FP64 weights and score) and the FP32 radius
+// sampler.  Compiled with fast single-precision math (MUFU transcendentals,
+// FMA contraction); the FP64 parts keep IEEE double arithmetic.
+#include "launch.h"
+#include "walk3.cuh"
+#include "walkn.cuh"
+
+namespace mpwos {
+
+cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  switch (pb.mkind) {
+    case kEuclid: walk3_f32_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
+    case kSphere: walk3_f32_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
+    case kTorus: walk3_f32_kernel<kTorus><<<grid, block, 0, st>>>(pb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  switch (pb.mkind) {
+    case kEuclid: walkn_f32_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
+    case kSphere: walkn_f32_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
+    case kEmbeddedSphere: walkn_f32_kernel<kEmbeddedSphere><<<grid, block, 0, st>>>(pb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
+  int nb = 0;
+  const void* fn = nullptr;
+  if (n3) {
+    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid>)
+       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walk3_f32_kernel<kSphere>)
+                             : reinterpret_cast<const void*>(walk3_f32_kernel<kTorus>);
+  } else {
+    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walkn_f32_kernel<kEuclid>)
+       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walkn_f32_kernel<kSphere>)
+                             : reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere>);
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
+  return nb < 1 ? 1 : nb;
+}
+
+__global__ void green_radius32_kernel(const double* a, const double* U, double* t, int64_t count,
+                                      const float* tab32, int NA, int NS, double z_max) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  float v = table_lookup<float>(tab32, NA, NS, z_max, static_cast<float>(a[q]), s_of_u32(static_cast<float>(U[q])));
+  t[q] = static_cast<double>(fminf(fmaxf(v, 0.0f), 1.0f));
+}
+
+cudaError_t launch_green_radius32(const double* a, const double* U, double* t, int64_t count, const float* tab32,
+                                  int NA, int NS, double z_max, cudaStream_t st) {
+  green_radius32_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(a, U, t, count, tab32, NA, NS,
+                                                                                   z_max);
+  return cudaGetLastError();
+}
+
+}  // namespace mpwos

@@ -1,0 +1,242 @@
+// kernels_f64.cu — FP64 kernels: the FP64 walks, the radius tables, the
+// per-point reduction and the verification primitives.  Compiled with
+// --fmad=false so that every FP64 + and * is one IEEE operation.
+#include "launch.h"
+#include "walk3.cuh"
+#include "walkn.cuh"
+
+namespace mpwos {
+
+// ---------------------------------------------------------------------------
+// Radius tables: t(s; z) with U = sin^2(pi s / 2); s uniform on [0, 1].
+// Bisection to a bracket, then the safeguarded Newton polish.
+// ---------------------------------------------------------------------------
+__global__ void build_table_kernel(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
+                                   float* tab32) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NA * NS) return;
+  const int ia = idx / NS, j = idx % NS;
+  const double a = (NA == 1) ? a_fixed : 2.0 * sqrt(z_max * static_cast<double>(ia) / static_cast<double>(NA - 1));
+  const double s = static_cast<double>(j) / static_cast<double>(NS - 1);
+  const double sn = sin(0.5 * kPi * s);
+  const double U = sn * sn;
+  const GreenLaw L = green_law(n, a);
+  double t;
+  if (j == 0) {
+    t = 0.0;
+  } else if (j == NS - 1) {
+    t = 1.0;
+  } else {
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 40; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      double F, dF;
+      green_cdf_pdf(L, mid, F, dF);
+      if (F < U) lo = mid; else hi = mid;
+    }
+    t = green_invert64(L, U, 0.5 * (lo + hi));
+  }
+  const int rs = NS + 2;
+  tab64[static_cast<size_t>(ia) * rs + j + 1] = t;
+  tab32[static_cast<size_t>(ia) * rs + j + 1] = static_cast<float>(t);
+}
+
+// Ghost nodes: t is odd about s = 0 and 1 - t is odd about s = 1.
+__global__ void table_ghosts_kernel(int NA, int NS, double* tab64, float* tab32) {
+  const int ia = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ia >= NA) return;
+  double* row = tab64 + static_cast<size_t>(ia) * (NS + 2);
+  row[0] = -row[2];
+  row[NS + 1] = 2.0 - row[NS - 1];
+  float* rowf = tab32 + static_cast<size_t>(ia) * (NS + 2);
+  rowf[0] = static_cast<float>(row[0]);
+  rowf[NS + 1] = static_cast<float>(row[NS + 1]);
+}
+
+cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
+                               float* tab32, cudaStream_t st) {
+  const int total = NA * NS;
+  build_table_kernel<<<(total + 127) / 128, 128, 0, st>>>(n, NA, NS, z_max, a_fixed, tab64, tab32);
+  table_ghosts_kernel<<<(NA + 63) / 64, 64, 0, st>>>(NA, NS, tab64, tab32);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Per-point estimator (eq. mc_estimator): one warp per point, lane-strided
+// Kahan sums of S and S^2 in walk order, combined across lanes in a fixed
+// tree order with error-free additions.  Deterministic for given inputs.
+// ---------------------------------------------------------------------------
+struct KSum { double s, c; };
+
+__device__ __forceinline__ void kahan_add(KSum& k, double v) {
+  const double y = v - k.c;
+  const double t = k.s + y;
+  k.c = (t - k.s) - y;
+  k.s = t;
+}
+
+__device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
+  // TwoSum of the leading parts, compensations carried along
+  const double s = a.s + b.s;
+  const double bb = s - a.s;
+  const double err = (a.s - (s - bb)) + (b.s - bb);
+  return KSum{s, a.c + b.c - err};
+}
+
+__global__ void reduce_kernel(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                              double* mean, double* se, double* msteps, unsigned long long* n_flagged) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (p >= P) return;
+  KSum s1{0.0, 0.0}, s2{0.0, 0.0};
+  long long ks = 0, nf = 0;
+  const double* Sp = S + p * N;
+  for (int64_t i = lane; i < N; i += 32) {
+    const double v = Sp[i];
+    kahan_add(s1, v);
+    kahan_add(s2, v * v);
+    ks += K[p * N + i];
+    nf += flags[p * N + i];
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    KSum o1{__shfl_down_sync(0xffffffffu, s1.s, off), __shfl_down_sync(0xffffffffu, s1.c, off)};
+    KSum o2{__shfl_down_sync(0xffffffffu, s2.s, off), __shfl_down_sync(0xffffffffu, s2.c, off)};
+    s1 = ksum_merge(s1, o1);
+    s2 = ksum_merge(s2, o2);
+    ks += __shfl_down_sync(0xffffffffu, ks, off);
+    nf += __shfl_down_sync(0xffffffffu, nf, off);
+  }
+  if (lane == 0) {
+    const double sum = s1.s - s1.c, sum2 = s2.s - s2.c;
+    const double dn = static_cast<double>(N);
+    const double mu = sum / dn;
+    double var = (N > 1) ? (sum2 - dn * mu * mu) / (dn - 1.0) : 0.0;
+    if (var < 0.0) var = 0.0;
+    mean[p] = mu;
+    se[p] = sqrt(var / dn);
+    msteps[p] = static_cast<double>(ks) / dn;
+    if (nf) atomicAdd(n_flagged, static_cast<unsigned long long>(nf));
+  }
+}
+
+cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                          double* mean, double* se, double* msteps, unsigned long long* n_flagged,
+                          cudaStream_t st) {
+  const int block = 256;
+  const int64_t grid = (P * 32 + block - 1) / block;
+  reduce_kernel<<<static_cast<unsigned>(grid), block, 0, st>>>(S, K, flags, P, N, mean, se, msteps, n_flagged);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 walks
+// ---------------------------------------------------------------------------
+cudaError_t launch_walk3_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  switch (pb.mkind) {
+    case kEuclid: walk3_f64_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
+    case kSphere: walk3_f64_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
+    case kTorus: walk3_f64_kernel<kTorus><<<grid, block, 0, st>>>(pb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  switch (pb.mkind) {
+    case kEuclid: walkn_f64_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
+    case kSphere: walkn_f64_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
+    case kEmbeddedSphere: walkn_f64_kernel<kEmbeddedSphere><<<grid, block, 0, st>>>(pb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int occupancy_walk_f64(const DevProblem& pb, bool n3, int block) {
+  int nb = 0;
+  const void* fn = nullptr;
+  if (n3) {
+    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walk3_f64_kernel<kEuclid>)
+       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walk3_f64_kernel<kSphere>)
+                             : reinterpret_cast<const void*>(walk3_f64_kernel<kTorus>);
+  } else {
+    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walkn_f64_kernel<kEuclid>)
+       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walkn_f64_kernel<kSphere>)
+                             : reinterpret_cast<const void*>(walkn_f64_kernel<kEmbeddedSphere>);
+  }
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
+  return nb < 1 ? 1 : nb;
+}
+
+// ---------------------------------------------------------------------------
+// Verification primitives
+// ---------------------------------------------------------------------------
+__global__ void philox_kernel(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t count) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const U4 r = philox4x32_10(ctr[4 * q], ctr[4 * q + 1], ctr[4 * q + 2], ctr[4 * q + 3], k0, k1);
+  out[4 * q] = r.x; out[4 * q + 1] = r.y; out[4 * q + 2] = r.z; out[4 * q + 3] = r.w;
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t count,
+                          cudaStream_t st) {
+  philox_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(ctr, k0, k1, out, count);
+  return cudaGetLastError();
+}
+
+__global__ void green_radius64_kernel(int n, const double* a, const double* U, double* t, int64_t count,
+                                      const double* tab64, int NA, int NS, double z_max) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const GreenLaw L = green_law(n, a[q]);
+  const double guess = table_lookup<double>(tab64, NA, NS, z_max, a[q], s_of_u64(U[q]));
+  t[q] = green_invert64(L, U[q], guess);
+}
+
+cudaError_t launch_green_radius64(int n, const double* a, const double* U, double* t, int64_t count,
+                                  const double* tab64, int NA, int NS, double z_max, cudaStream_t st) {
+  green_radius64_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(n, a, U, t, count, tab64,
+                                                                                   NA, NS, z_max);
+  return cudaGetLastError();
+}
+
+__global__ void c_sigma_r_kernel(int n, const double* a, double* c, int64_t count) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const double em1 = em1_series(0.5 * static_cast<double>(n - 2), 0.25 * (a[q] * a[q]));
+  c[q] = 1.0 / (1.0 + em1);
+}
+
+cudaError_t launch_c_sigma_r(int n, const double* a, double* c, int64_t count, cudaStream_t st) {
+  c_sigma_r_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(n, a, c, count);
+  return cudaGetLastError();
+}
+
+}  // namespace mpwos
+
+namespace mpwos {
+
+// s0 = normalize(Q^T (y0 - b)) for each query point (embedded sphere start state).
+__global__ void intrinsic_start_kernel(const double* pts, const double* QT, const double* b, int n, int D,
+                                       int64_t P, double* s0) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  if (p >= P) return;
+  double sj = 0.0;
+  if (lane < D) {
+    const double* y = pts + p * n;
+    const double* row = QT + static_cast<size_t>(lane) * n;
+    for (int i = 0; i < n; ++i) sj += row[i] * (y[i] - b[i]);
+  }
+  const double nn = sqrt(warp_sum1(sj * sj));
+  if (lane < D) s0[p * D + lane] = sj / nn;
+}
+
+cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const double* b, int n, int D, int64_t P,
+                                   double* s0, cudaStream_t st) {
+  const int block = 128;
+  intrinsic_start_kernel<<<static_cast<unsigned>((P * 32 + block - 1) / block), block, 0, st>>>(pts, QT, b, n, D, P,
+                                                                                               s0);
+  return cudaGetLastError();
+}
+
+}  // namespace mpwos

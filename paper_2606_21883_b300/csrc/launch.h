@@ -1,0 +1,42 @@
+// launch.h — host-side launchers of the library's kernels (internal C++ API).
+#pragma once
+#include <cuda_runtime.h>
+#include "dev_common.cuh"
+
+namespace mpwos {
+
+// Walks for R^3 manifolds, one thread per walker (kernels_f64.cu / kernels_f32.cu).
+cudaError_t launch_walk3_f64(const DevProblem& pb, int grid, int block, cudaStream_t st);
+cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStream_t st);
+// Walks for R^n manifolds (n > 3), one warp per walker.
+cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStream_t st);
+cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st);
+// Resident blocks per SM of the walk kernel chosen for pb.
+int occupancy_walk_f64(const DevProblem& pb, bool n3, int block);
+int occupancy_walk_f32(const DevProblem& pb, bool n3, int block);
+
+// Intrinsic start points s0 = normalize(Q^T (y0 - b)) of an embedded sphere
+// (QT: D x n device array), one warp per point.
+cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const double* b, int n, int D, int64_t P,
+                                   double* s0, cudaStream_t st);
+
+// Per-point mean, standard error and mean steps from per-walk scores.
+cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                          double* mean, double* se, double* msteps, unsigned long long* n_flagged,
+                          cudaStream_t st);
+
+// Inverse-CDF tables of the radial Green law: NA rows over z = a^2/4 in
+// [0, z_max] (NA == 1: the single law at a = a_fixed), NS nodes + 2 ghosts.
+cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
+                               float* tab32, cudaStream_t st);
+
+// Verification primitives.
+cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t count,
+                          cudaStream_t st);
+cudaError_t launch_green_radius64(int n, const double* a, const double* U, double* t, int64_t count,
+                                  const double* tab64, int NA, int NS, double z_max, cudaStream_t st);
+cudaError_t launch_green_radius32(const double* a, const double* U, double* t, int64_t count, const float* tab32,
+                                  int NA, int NS, double z_max, cudaStream_t st);
+cudaError_t launch_c_sigma_r(int n, const double* a, double* c, int64_t count, cudaStream_t st);
+
+}  // namespace mpwos

@@ -1,0 +1,515 @@
+// mpwos_abi.cu — host side of the C ABI declared in include/mpwos.h: argument
+// validation, device copies of the problem data, radius-table cache, launch
+// configuration and the per-walk / per-point output paths.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/mpwos.h"
+#include "launch.h"
+
+using namespace mpwos;
+
+namespace {
+
+constexpr int kTableNS = 1025;   // s-nodes per radius-table row
+constexpr int kTableNA = 65;     // rows over z = a^2/4 for variable-radius problems
+
+struct Table {
+  double* tab64 = nullptr;
+  float* tab32 = nullptr;
+  int NA = 0, NS = 0;
+  double z_max = 0.0;
+};
+
+}  // namespace
+
+struct mpwos_ctx {
+  int device = 0;
+  int sm_count = 0;
+  cudaStream_t own = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  long long launches = 0;
+  std::map<std::tuple<int, int, double>, Table> tables;  // (n, NA, z_max or a) -> table
+};
+
+namespace {
+
+int fail(mpwos_ctx* ctx, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx) ctx->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+double kappa_of(const mpwos_manifold_desc* m) {
+  if (m->kind == MPWOS_EUCLID) return 0.0;
+  if (m->kind == MPWOS_TORUS) return 1.0 / m->a;
+  return 1.0;
+}
+
+// Stream-ordered device buffers released at the end of a call.
+struct Scratch {
+  mpwos_ctx* ctx;
+  std::vector<void*> bufs;
+  explicit Scratch(mpwos_ctx* c) : ctx(c) {}
+  ~Scratch() {
+    for (void* b : bufs) cudaFreeAsync(b, ctx->stream);
+  }
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    if (cudaMallocAsync(&p, count * sizeof(T), ctx->stream) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    bufs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  template <typename T>
+  T* upload(const T* host, size_t count) {
+    T* d = alloc<T>(count);
+    if (d && count) cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+    return d;
+  }
+};
+
+int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* pr, const mpwos_params* pa,
+             int64_t P, int64_t N) {
+  if (!m || !pr || !pa) return fail(ctx, MPWOS_EINVAL, "null manifold, problem or params");
+  if (P < 0 || N < 1) return fail(ctx, MPWOS_EINVAL, "need P >= 0 and N >= 1 (got P=%lld N=%lld)", (long long)P, (long long)N);
+  if (N > 0x7fffffffLL || P > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "P and N must fit in 32 bits (Philox counter words)");
+  if (!(pr->sigma > 0.0)) return fail(ctx, MPWOS_EINVAL, "sigma must be > 0 (got %g)", pr->sigma);
+  if (!(pa->theta > 0.0 && pa->theta < 1.0)) return fail(ctx, MPWOS_EINVAL, "theta must lie in (0, 1)");
+  if (!(pa->c_kappa > 0.0)) return fail(ctx, MPWOS_EINVAL, "c_kappa must be > 0");
+  if (pa->n_v < 1 || pa->n_v > 64) return fail(ctx, MPWOS_EINVAL, "n_v must lie in [1, 64]");
+  if (pa->max_steps < 0 || pa->max_steps > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "max_steps must lie in [0, 2^31)");
+  if (pa->precision != MPWOS_FP64 && pa->precision != MPWOS_FP32) return fail(ctx, MPWOS_EINVAL, "unknown precision %d", pa->precision);
+  if (m->n < 3 || m->n > 1024) return fail(ctx, MPWOS_EINVAL, "ambient dimension must lie in [3, 1024] (got %d)", m->n);
+  switch (m->kind) {
+    case MPWOS_EUCLID:
+      if (m->d != m->n) return fail(ctx, MPWOS_EINVAL, "EUCLID needs d == n");
+      break;
+    case MPWOS_SPHERE:
+      if (m->d != m->n - 1) return fail(ctx, MPWOS_EINVAL, "SPHERE needs d == n - 1");
+      break;
+    case MPWOS_TORUS:
+      if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "TORUS lives in R^3 (n = 3, d = 2)");
+      if (!(m->R > m->a && m->a > 0.0)) return fail(ctx, MPWOS_EINVAL, "TORUS needs R > a > 0");
+      if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "TORUS supports the closed problem only");
+      break;
+    case MPWOS_EMBEDDED_SPHERE:
+      if (m->n <= 3) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs n > 3");
+      if (m->d < 1 || m->d + 1 > kMaxQuadDim || m->d + 1 > m->n) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs 1 <= d < min(n, 32)");
+      if (!m->Q || !m->b) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs Q and b");
+      if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE supports the closed problem only");
+      break;
+    default:
+      return fail(ctx, MPWOS_EINVAL, "unknown manifold kind %d", m->kind);
+  }
+  if (!pr->closed) {
+    if (m->kind != MPWOS_EUCLID && m->kind != MPWOS_SPHERE) return fail(ctx, MPWOS_EINVAL, "boundary needs EUCLID or SPHERE");
+    if (!pr->bnd_normal) return fail(ctx, MPWOS_EINVAL, "boundary problem needs bnd_normal");
+    double nn = 0.0;
+    for (int i = 0; i < m->n; ++i) nn += pr->bnd_normal[i] * pr->bnd_normal[i];
+    if (std::fabs(nn - 1.0) > 1e-12) return fail(ctx, MPWOS_EINVAL, "bnd_normal must be a unit vector");
+    if (m->kind == MPWOS_SPHERE && !(std::fabs(pr->bnd_offset) < 1.0)) return fail(ctx, MPWOS_EINVAL, "|bnd_offset| < 1 on the unit sphere");
+    if (!(pa->eps > 0.0)) return fail(ctx, MPWOS_EINVAL, "eps must be > 0");
+  } else if (!(pa->tau_w > 0.0 && pa->tau_w < 1.0)) {
+    return fail(ctx, MPWOS_EINVAL, "tau_w must lie in (0, 1)");
+  }
+  // function kinds each kernel evaluates
+  const mpwos_func* fs[2] = {&pr->f, &pr->g};
+  for (int q = 0; q < 2; ++q) {
+    const mpwos_func* f = fs[q];
+    if (q == 1 && pr->closed) continue;
+    if (f->n_terms < 0 || f->n_terms > kMaxTerms) return fail(ctx, MPWOS_EINVAL, "at most %d terms per function", kMaxTerms);
+    if (f->kind == MPWOS_FUNC_POLY) {
+      if (f->n_terms && (!f->coef || !f->term_off)) return fail(ctx, MPWOS_EINVAL, "POLY needs coef and term_off");
+      int nf = f->n_terms ? f->term_off[f->n_terms] : 0;
+      if (nf > kMaxPolyFactors) return fail(ctx, MPWOS_EINVAL, "at most %d polynomial factors", kMaxPolyFactors);
+      for (int t = 0; t < nf; ++t)
+        if (f->var[t] < 0 || f->var[t] >= m->n || f->pw[t] < 0 || f->pw[t] > 100)
+          return fail(ctx, MPWOS_EINVAL, "POLY factor %d out of range", t);
+      if (m->kind == MPWOS_EMBEDDED_SPHERE) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE data must be SPHERE_QUAD");
+    } else if (f->kind == MPWOS_FUNC_TORUS_FOURIER) {
+      if (m->kind != MPWOS_TORUS) return fail(ctx, MPWOS_EINVAL, "TORUS_FOURIER needs the TORUS manifold");
+      if (f->n_terms && (!f->coef || !f->modes)) return fail(ctx, MPWOS_EINVAL, "TORUS_FOURIER needs coef and modes");
+      for (int t = 0; t < f->n_terms; ++t)
+        if (f->modes[4 * t] < 0 || f->modes[4 * t] > 64 || f->modes[4 * t + 1] < 0 || f->modes[4 * t + 1] > 64)
+          return fail(ctx, MPWOS_EINVAL, "torus mode numbers must lie in [0, 64]");
+    } else if (f->kind == MPWOS_FUNC_SPHERE_QUAD) {
+      if (!(m->kind == MPWOS_EMBEDDED_SPHERE || (m->kind == MPWOS_SPHERE && m->n == 3)))
+        return fail(ctx, MPWOS_EINVAL, "SPHERE_QUAD needs EMBEDDED_SPHERE or the sphere in R^3");
+      if (!f->v || !f->A) return fail(ctx, MPWOS_EINVAL, "SPHERE_QUAD needs v and A");
+    } else {
+      return fail(ctx, MPWOS_EINVAL, "unknown function kind %d", f->kind);
+    }
+  }
+  if (m->kind == MPWOS_EMBEDDED_SPHERE && pr->f.kind != MPWOS_FUNC_SPHERE_QUAD)
+    return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE source must be SPHERE_QUAD");
+  return MPWOS_OK;
+}
+
+void copy_func(const mpwos_func& f, DevFunc& d) {
+  std::memset(&d, 0, sizeof d);
+  d.kind = f.kind;
+  d.apply_op = f.apply_op;
+  d.n_terms = f.n_terms;
+  d.c0 = f.c0;
+  for (int t = 0; t < f.n_terms; ++t) d.coef[t] = f.coef[t];
+  if (f.kind == MPWOS_FUNC_POLY) {
+    for (int t = 0; t <= f.n_terms; ++t) d.term_off[t] = static_cast<int16_t>(f.n_terms ? f.term_off[t] : 0);
+    const int nf = f.n_terms ? f.term_off[f.n_terms] : 0;
+    for (int q = 0; q < nf; ++q) {
+      d.var[q] = static_cast<int16_t>(f.var[q]);
+      d.pw[q] = static_cast<int8_t>(f.pw[q]);
+    }
+  } else if (f.kind == MPWOS_FUNC_TORUS_FOURIER) {
+    for (int t = 0; t < f.n_terms; ++t)
+      for (int q = 0; q < 4; ++q) d.modes[t][q] = static_cast<int8_t>(f.modes[4 * t + q]);
+  }
+}
+
+// The radius table for (n, law range): cached per context.
+int get_table(mpwos_ctx* ctx, int n, bool fixed, double a_or_zmax, Table** out) {
+  const int NA = fixed ? 1 : kTableNA;
+  auto key = std::make_tuple(n, NA, a_or_zmax);
+  auto it = ctx->tables.find(key);
+  if (it != ctx->tables.end()) {
+    *out = &it->second;
+    return MPWOS_OK;
+  }
+  Table t;
+  t.NA = NA;
+  t.NS = kTableNS;
+  t.z_max = fixed ? 0.25 * a_or_zmax * a_or_zmax : a_or_zmax;
+  const size_t cnt = static_cast<size_t>(NA) * (kTableNS + 2);
+  CK(cudaMalloc(&t.tab64, cnt * sizeof(double)));
+  CK(cudaMalloc(&t.tab32, cnt * sizeof(float)));
+  CK(launch_build_table(n, NA, kTableNS, t.z_max, fixed ? a_or_zmax : 0.0, t.tab64, t.tab32, ctx->stream));
+  ctx->launches += 2;
+  auto res = ctx->tables.emplace(key, t);
+  *out = &res.first->second;
+  return MPWOS_OK;
+}
+
+// Everything a walk launch needs, built in `sc`.
+int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpwos_problem* pr,
+            const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb) {
+  std::memset(&pb, 0, sizeof pb);
+  pb.mkind = m->kind;
+  pb.n = m->n;
+  pb.d = m->d;
+  pb.R = m->R;
+  pb.a_tube = m->a;
+  pb.sigma = pr->sigma;
+  pb.sqrt_sigma = std::sqrt(pr->sigma);
+  pb.closed = pr->closed;
+  pb.h = pr->bnd_offset;
+  pb.eps = pa->eps;
+  pb.tau_w = pa->tau_w;
+  pb.theta = pa->theta;
+  pb.c_kappa = pa->c_kappa;
+  pb.kappa = kappa_of(m);
+  pb.rho_geo = pa->c_kappa / (1.0 + pb.kappa);
+  pb.n_v = pa->n_v;
+  pb.max_steps = pa->max_steps;
+  pb.seed = pa->seed;
+  pb.P = P;
+  pb.N = N;
+  copy_func(pr->f, pb.f);
+  if (!pr->closed) copy_func(pr->g, pb.g);
+  const int n = m->n;
+  if (!pr->closed) {
+    pb.e = sc.upload(pr->bnd_normal, n);
+    if (!pb.e) return fail(ctx, MPWOS_ENOMEM, "boundary normal");
+  }
+  // SPHERE_QUAD coefficient arrays
+  const int D = m->d + 1;
+  for (DevFunc* df : {&pb.f, &pb.g}) {
+    const mpwos_func& hf = (df == &pb.f) ? pr->f : pr->g;
+    if (df == &pb.g && pr->closed) continue;
+    if (hf.kind == MPWOS_FUNC_SPHERE_QUAD) {
+      const int Dq = (m->kind == MPWOS_SPHERE) ? 3 : D;
+      df->v = sc.upload(hf.v, Dq);
+      df->A = sc.upload(hf.A, static_cast<size_t>(Dq) * Dq);
+      if (!df->v || !df->A) return fail(ctx, MPWOS_ENOMEM, "SPHERE_QUAD data");
+    }
+  }
+  // query points
+  if (is_device_ptr(pts)) {
+    pb.pts = pts;
+  } else {
+    pb.pts = sc.upload(pts, static_cast<size_t>(P) * n);
+    if (!pb.pts && P) return fail(ctx, MPWOS_ENOMEM, "query points");
+  }
+  if (m->kind == MPWOS_EMBEDDED_SPHERE) {
+    std::vector<double> qt(static_cast<size_t>(D) * n);
+    std::vector<float> qtf(qt.size());
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < D; ++j) {
+        qt[static_cast<size_t>(j) * n + i] = m->Q[static_cast<size_t>(i) * D + j];
+        qtf[static_cast<size_t>(j) * n + i] = static_cast<float>(m->Q[static_cast<size_t>(i) * D + j]);
+      }
+    double* qtd = sc.upload(qt.data(), qt.size());
+    float* qtfd = sc.upload(qtf.data(), qtf.size());
+    double* bd = sc.upload(m->b, n);
+    double* s0 = sc.alloc<double>(static_cast<size_t>(P) * D);
+    if (!qtd || !qtfd || !bd || !s0) return fail(ctx, MPWOS_ENOMEM, "embedding");
+    pb.Q = qtd;   // Q^T, D x n
+    pb.Qf = qtfd;
+    pb.b = bd;
+    pb.s0 = s0;
+    if (P) {
+      CK(launch_intrinsic_start(pb.pts, qtd, bd, n, D, P, s0, ctx->stream));
+      ctx->launches++;
+    }
+  }
+  // radius tables
+  const double a_max = pb.sqrt_sigma * pb.theta * pb.rho_geo;
+  const double nu = 0.5 * (n - 2);
+  if (n > 3 && 0.25 * a_max * a_max > 0.5 * nu)
+    return fail(ctx, MPWOS_EINVAL,
+                "sigma (theta rho_geo)^2 / 4 = %g exceeds (n-2)/4 = %g: outside the series evaluation range", 0.25 * a_max * a_max, 0.5 * nu);
+  Table* tab = nullptr;
+  int rc = pr->closed ? get_table(ctx, n, true, a_max, &tab) : get_table(ctx, n, false, 0.25 * a_max * a_max, &tab);
+  if (rc) return rc;
+  pb.tab64 = tab->tab64;
+  pb.tab32 = tab->tab32;
+  pb.NA = tab->NA;
+  pb.NS = tab->NS;
+  pb.z_max = tab->z_max;
+  return MPWOS_OK;
+}
+
+int run_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64) {
+  if (pb.P == 0) return MPWOS_OK;
+  const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
+  const int block = n3 ? (fp64 ? 128 : 256) : 128;
+  const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
+  const int64_t per_block = n3 ? block : block / 32;
+  int64_t grid = static_cast<int64_t>(ctx->sm_count) * occ;
+  const int64_t need = (pb.P * pb.N + per_block - 1) / per_block;
+  if (grid > need) grid = need;
+  cudaError_t e;
+  if (n3) e = fp64 ? launch_walk3_f64(pb, (int)grid, block, ctx->stream) : launch_walk3_f32(pb, (int)grid, block, ctx->stream);
+  else e = fp64 ? launch_walkn_f64(pb, (int)grid, block, ctx->stream) : launch_walkn_f32(pb, (int)grid, block, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "walk launch: %s", cudaGetErrorString(e));
+  ctx->launches++;
+  return MPWOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mpwos_params_default(mpwos_params* p) {
+  if (!p) return;
+  p->eps = 1e-3;
+  p->tau_w = 1e-8;
+  p->theta = 0.95;
+  p->c_kappa = 1.2;
+  p->n_v = 1;
+  p->max_steps = 10000000;
+  p->seed = 0;
+  p->precision = MPWOS_FP64;
+}
+
+int mpwos_create(int device, mpwos_ctx** out) {
+  if (!out) return MPWOS_EINVAL;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    return MPWOS_EINVAL;
+  }
+  mpwos_ctx* ctx = new mpwos_ctx();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->own, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return MPWOS_ECUDA;
+  }
+  ctx->stream = ctx->own;
+  *out = ctx;
+  return MPWOS_OK;
+}
+
+void mpwos_destroy(mpwos_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->tables) {
+    cudaFree(kv.second.tab64);
+    cudaFree(kv.second.tab32);
+  }
+  if (ctx->own) cudaStreamDestroy(ctx->own);
+  delete ctx;
+}
+
+const char* mpwos_last_error(const mpwos_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int mpwos_set_stream(mpwos_ctx* ctx, void* stream) {
+  if (!ctx) return MPWOS_EINVAL;
+  ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own;
+  return MPWOS_OK;
+}
+
+int64_t mpwos_launch_count(const mpwos_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+                      const mpwos_params* prm, const double* pts, int64_t P, int64_t N, double* S, int32_t* K,
+                      int32_t* flags) {
+  if (!ctx) return MPWOS_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  int rc = validate(ctx, m, prob, prm, P, N);
+  if (rc) return rc;
+  if (!S || !K || !flags) return fail(ctx, MPWOS_EINVAL, "null output");
+  Scratch sc(ctx);
+  DevProblem pb;
+  rc = prepare(ctx, sc, m, prob, prm, pts, P, N, pb);
+  if (rc) return rc;
+  const size_t W = static_cast<size_t>(P) * N;
+  const bool dS = is_device_ptr(S), dK = is_device_ptr(K), dF = is_device_ptr(flags);
+  pb.S_out = dS ? S : sc.alloc<double>(W);
+  pb.K_out = dK ? K : sc.alloc<int32_t>(W);
+  pb.flag_out = dF ? flags : sc.alloc<int32_t>(W);
+  if (!pb.S_out || !pb.K_out || !pb.flag_out) return fail(ctx, MPWOS_ENOMEM, "per-walk outputs (%zu walks)", W);
+  rc = run_walks(ctx, pb, prm->precision == MPWOS_FP64);
+  if (rc) return rc;
+  if (!dS) CK(cudaMemcpyAsync(S, pb.S_out, W * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dK) CK(cudaMemcpyAsync(K, pb.K_out, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dF) CK(cudaMemcpyAsync(flags, pb.flag_out, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MPWOS_OK;
+}
+
+int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob, const mpwos_params* prm,
+                const double* pts, int64_t P, int64_t N, double* mean, double* stderr_, double* mean_steps) {
+  if (!ctx) return MPWOS_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  int rc = validate(ctx, m, prob, prm, P, N);
+  if (rc) return rc;
+  if (!mean || !stderr_ || !mean_steps) return fail(ctx, MPWOS_EINVAL, "null output");
+  Scratch sc(ctx);
+  DevProblem pb;
+  rc = prepare(ctx, sc, m, prob, prm, pts, P, N, pb);
+  if (rc) return rc;
+  const size_t W = static_cast<size_t>(P) * N;
+  pb.S_out = sc.alloc<double>(W);
+  pb.K_out = sc.alloc<int32_t>(W);
+  pb.flag_out = sc.alloc<int32_t>(W);
+  unsigned long long* nflag = sc.alloc<unsigned long long>(1);
+  const bool dm = is_device_ptr(mean), ds = is_device_ptr(stderr_), dt = is_device_ptr(mean_steps);
+  double* om = dm ? mean : sc.alloc<double>(P);
+  double* os = ds ? stderr_ : sc.alloc<double>(P);
+  double* ot = dt ? mean_steps : sc.alloc<double>(P);
+  if (!pb.S_out || !pb.K_out || !pb.flag_out || !nflag || !om || !os || !ot)
+    return fail(ctx, MPWOS_ENOMEM, "scratch for %zu walks", W);
+  CK(cudaMemsetAsync(nflag, 0, sizeof(unsigned long long), ctx->stream));
+  rc = run_walks(ctx, pb, prm->precision == MPWOS_FP64);
+  if (rc) return rc;
+  if (P) {
+    CK(launch_reduce(pb.S_out, pb.K_out, pb.flag_out, P, N, om, os, ot, nflag, ctx->stream));
+    ctx->launches++;
+  }
+  unsigned long long hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, nflag, sizeof hflag, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dm) CK(cudaMemcpyAsync(mean, om, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (!ds) CK(cudaMemcpyAsync(stderr_, os, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dt) CK(cudaMemcpyAsync(mean_steps, ot, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hflag) return fail(ctx, MPWOS_EMAXSTEPS, "%llu walks reached max_steps", hflag);
+  return MPWOS_OK;
+}
+
+int mpwos_philox(mpwos_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out, int64_t count) {
+  if (!ctx || !ctr || !out || count < 0) return MPWOS_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  Scratch sc(ctx);
+  uint32_t* dc = sc.upload(ctr, static_cast<size_t>(count) * 4);
+  uint32_t* dout = sc.alloc<uint32_t>(static_cast<size_t>(count) * 4);
+  if (!dc || !dout) return fail(ctx, MPWOS_ENOMEM, "philox buffers");
+  if (count) {
+    CK(launch_philox(dc, key0, key1, dout, count, ctx->stream));
+    ctx->launches++;
+  }
+  CK(cudaMemcpyAsync(out, dout, static_cast<size_t>(count) * 16, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MPWOS_OK;
+}
+
+int mpwos_green_radius(mpwos_ctx* ctx, int n, double a_max, const double* a, const double* U, double* t,
+                       int64_t count, int precision) {
+  if (!ctx || !a || !U || !t || count < 0 || n < 3 || n > 1024 || !(a_max > 0.0)) return MPWOS_EINVAL;
+  if (n > 3 && 0.25 * a_max * a_max > 0.25 * (n - 2)) return fail(ctx, MPWOS_EINVAL, "a_max outside the series range");
+  CK(cudaSetDevice(ctx->device));
+  Table* tab = nullptr;
+  int rc = get_table(ctx, n, false, 0.25 * a_max * a_max, &tab);
+  if (rc) return rc;
+  Scratch sc(ctx);
+  double* da = sc.upload(a, count);
+  double* dU = sc.upload(U, count);
+  double* dt = sc.alloc<double>(count);
+  if (!da || !dU || !dt) return fail(ctx, MPWOS_ENOMEM, "radius buffers");
+  if (count) {
+    if (precision == MPWOS_FP64)
+      CK(launch_green_radius64(n, da, dU, dt, count, tab->tab64, tab->NA, tab->NS, tab->z_max, ctx->stream));
+    else
+      CK(launch_green_radius32(da, dU, dt, count, tab->tab32, tab->NA, tab->NS, tab->z_max, ctx->stream));
+    ctx->launches++;
+  }
+  CK(cudaMemcpyAsync(t, dt, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MPWOS_OK;
+}
+
+int mpwos_c_sigma_r(mpwos_ctx* ctx, int n, const double* a, double* c, int64_t count) {
+  if (!ctx || !a || !c || count < 0 || n < 3) return MPWOS_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  Scratch sc(ctx);
+  double* da = sc.upload(a, count);
+  double* dc = sc.alloc<double>(count);
+  if (!da || !dc) return fail(ctx, MPWOS_ENOMEM, "c buffers");
+  if (count) {
+    CK(launch_c_sigma_r(n, da, dc, count, ctx->stream));
+    ctx->launches++;
+  }
+  CK(cudaMemcpyAsync(c, dc, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MPWOS_OK;
+}
+
+}  // extern "C"
