@@ -22,7 +22,7 @@ constexpr double kEulerGamma = 0.57721566490153286;
 constexpr double kPi = 3.141592653589793;
 
 // I~_nu(a) - 1 with z = a^2/4.
-__device__ __forceinline__ double em1_series(double nu, double z) {
+__host__ __device__ __forceinline__ double em1_series(double nu, double z) {
   double term = 1.0, sum = 0.0;
   for (int j = 1; j < 10000; ++j) {
     term *= z / (static_cast<double>(j) * (nu + static_cast<double>(j)));
@@ -33,12 +33,12 @@ __device__ __forceinline__ double em1_series(double nu, double z) {
 }
 
 // 1 - c from em1 without cancellation.
-__device__ __forceinline__ double one_minus_c(double em1, double c) {
+__host__ __device__ __forceinline__ double one_minus_c(double em1, double c) {
   return (em1 <= 1.0) ? em1 * c : 1.0 - c;
 }
 
 // 0F1(;b;z), b > 0.
-__device__ inline double hyp0f1_dev(double b, double z) {
+__host__ __device__ inline double hyp0f1_dev(double b, double z) {
   double term = 1.0, sum = 1.0;
   for (int k = 1; k < 10000; ++k) {
     term *= z / (static_cast<double>(k) * (b + static_cast<double>(k) - 1.0));
@@ -50,7 +50,7 @@ __device__ inline double hyp0f1_dev(double b, double z) {
 
 // K~_mu(x) - 1.  Non-integer mu: reflection formula K = (pi/2)(I_{-mu} - I_mu)/sin(pi mu);
 // integer mu: the logarithmic expansion (Abramowitz & Stegun 9.6.11).
-__device__ inline double kt_m1(double mu, double x) {
+__host__ __device__ inline double kt_m1(double mu, double x) {
   const double z = 0.25 * (x * x);
   const double hx = log(0.5 * x);
   const double mr = floor(mu + 0.5);
@@ -92,7 +92,7 @@ __device__ inline double kt_m1(double mu, double x) {
 }
 
 // P(x) = 1 - e^{-x}(1+x) and Q(x) = x cosh x - sinh x for x < 1 (series).
-__device__ __forceinline__ double p3_series(double x) {
+__host__ __device__ __forceinline__ double p3_series(double x) {
   double term = x, sum = 0.0;
   for (int k = 2; k < 60; ++k) {
     term *= x / static_cast<double>(k);
@@ -103,7 +103,7 @@ __device__ __forceinline__ double p3_series(double x) {
   return sum;
 }
 
-__device__ __forceinline__ double q3_series(double x) {
+__host__ __device__ __forceinline__ double q3_series(double x) {
   double term = x, sum = 0.0;
   for (int k = 1; k < 60; ++k) {
     term *= x * x / (static_cast<double>(2 * k) * static_cast<double>(2 * k + 1));
@@ -120,7 +120,7 @@ struct GreenLaw {
   double nu, a, c, omc, kta;   // kta = K~_nu(a) (general n)
 };
 
-__device__ inline GreenLaw green_law(int n, double a) {
+__host__ __device__ inline GreenLaw green_law(int n, double a) {
   GreenLaw L;
   L.n = n;
   L.nu = 0.5 * static_cast<double>(n - 2);
@@ -133,7 +133,7 @@ __device__ inline GreenLaw green_law(int n, double a) {
 }
 
 // F(t) and F'(t).  a == 0 is the Laplace limit (n t^2 - 2 t^n)/(n - 2).
-__device__ inline void green_cdf_pdf(const GreenLaw& L, double t, double& F, double& dF) {
+__host__ __device__ inline void green_cdf_pdf(const GreenLaw& L, double t, double& F, double& dF) {
   const double a = L.a, x = a * t;
   if (a == 0.0) {
     const double tn2 = pow(t, static_cast<double>(L.n - 2));
@@ -168,7 +168,7 @@ __device__ inline void green_cdf_pdf(const GreenLaw& L, double t, double& F, dou
 }
 
 // Safeguarded Newton for F(t) = U on [0, 1] from guess t0.
-__device__ inline double green_invert64(const GreenLaw& L, double U, double t0) {
+__host__ __device__ inline double green_invert64(const GreenLaw& L, double U, double t0) {
   if (U >= 1.0) return 1.0;
   double lo = 0.0, hi = 1.0;
   double t = (t0 > 0.0 && t0 < 1.0) ? t0 : 0.5;
@@ -176,22 +176,23 @@ __device__ inline double green_invert64(const GreenLaw& L, double U, double t0) 
     double F, dF;
     green_cdf_pdf(L, t, F, dF);
     const double res = F - U;
+    if (res == 0.0) break;
     if (res < 0.0) lo = t; else hi = t;
     double tn = (dF > 0.0) ? t - res / dF : 0.5 * (lo + hi);
-    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (!(tn >= lo && tn <= hi)) tn = 0.5 * (lo + hi);
     const bool conv = fabs(tn - t) <= 4e-16 * t || hi - lo <= 4e-16 * hi;
     t = tn;
-    if (conv || res == 0.0) break;
+    if (conv) break;
   }
   return t;
 }
 
 // s = (2/pi) asin(sqrt(U)): the table's abscissa.
-__device__ __forceinline__ double s_of_u64(double U) { return 0.6366197723675814 * asin(sqrt(U)); }
+__host__ __device__ __forceinline__ double s_of_u64(double U) { return 0.6366197723675814 * asin(sqrt(U)); }
 __device__ __forceinline__ float s_of_u32(float U) { return 0.636619772f * asinf(sqrtf(U)); }
 
 template <typename T>
-__device__ __forceinline__ T catmull_rom(const T* row, int j, T f) {
+__host__ __device__ __forceinline__ T catmull_rom(const T* row, int j, T f) {
   const T p0 = row[j], p1 = row[j + 1], p2 = row[j + 2], p3 = row[j + 3];
   return p1 + T(0.5) * f * (p2 - p0 + f * (T(2) * p0 - T(5) * p1 + T(4) * p2 - p3 +
                                            f * (T(3) * (p1 - p2) + p3 - p0)));
@@ -200,7 +201,7 @@ __device__ __forceinline__ T catmull_rom(const T* row, int j, T f) {
 // Table lookup t(s; z): rows over z = a^2/4 in [0, z_max] (NA rows; NA = 1 is a
 // single law), NS nodes over s in [0, 1] plus a ghost node at each end.
 template <typename T>
-__device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS, double z_max, T a, T s) {
+__host__ __device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS, double z_max, T a, T s) {
   const int rs = NS + 2;
   T xs = s * T(NS - 1);
   int j = static_cast<int>(xs);
