@@ -1,0 +1,274 @@
+"""Benchmark of the MPWoS hot path on B300.
+
+Workload (the metric's configuration): the closed torus R = 1, tube radius
+0.4, sigma = 2, manufactured u = sin(theta) cos(2 phi), 4096 query points
+uniform in (theta, phi), 10^4 walks each (every walk takes exactly 525
+steps: 2.15e10 walk-steps per step of the benchmark), FP32 walks with FP64
+weights and estimator sums.  A benchmark "step" is one mpwos_solve of that
+whole batch (walk kernel + per-point reduction).
+
+Output: one JSON line (rank 0).  ``value`` is whole-job walk-steps/s with the
+query points already on the device; ``e2e`` is the same metric through the C
+ABI with pinned host buffers (host<->device copies inside the timed region);
+``roofline`` is the walk kernel's algorithmic ALU work per launch over its
+CUDA-event duration against the SM issue peak; ``cpu_baseline`` times the CPU
+oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2606_21883_b300 import workloads as W  # noqa: E402
+
+METRIC = "walk-steps/s at fixed RMSE (torus, FP32 walk + FP64 accumulation)"
+UNIT = "walk-steps/s"
+# Algorithmic lane-operations per walk-step of the FP32 torus walk (N_V = 1);
+# breakdown in the design notes: Philox 2 x 80, Box-Muller 3 x 16, sphere and
+# interior samples 20, radius table 32, torus cp 2 x 25, torus source 50,
+# FP64 weights/score 4, loop and stop test 6.
+OPS_PER_STEP = 370
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for ln in fh:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = sorted(sm)[len(sm) // 4:] if sm else []
+        return {"sm_mhz": float(np.median(loaded)) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(target_s: float = 15.0):
+    """The CPU oracle, as it stands, on a bounded sample of the torus workload."""
+    import oracle as O
+    w = W.torus_closed(P=64, walks=1)
+    cores = os.cpu_count() or 1
+    # calibrate on a short run, then size the sample for ~target_s of CPU work
+    t0 = time.perf_counter()
+    O.solve(w.problem, w.params, w.points[:8], 8, n_threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_walk = dt / 64.0
+    walks = int(max(8, min(4000, target_s / per_walk / 64)))
+    t0 = time.perf_counter()
+    m, se, ms, nf = O.solve(w.problem, w.params, w.points, walks, n_threads=cores)
+    dt = time.perf_counter() - t0
+    steps = float(ms.sum() * walks)
+    return {"value": steps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"torus 64 points x {walks} walks x 525 steps ({steps:.3g} walk-steps, FP64, "
+                      f"OpenMP over walks), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    base = cpu_baseline(target_s=min(20.0, 100.0 / max(args.steps + args.warmup, 1)))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "torus_closed R=1 a=0.4 sigma=2, 4096 pts x 1e4 walks (sampled)",
+                       "model": "MPWoS CPU oracle"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--points", type=int, default=4096)
+    ap.add_argument("--walks", type=int, default=10_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2606_21883_b300 as M
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    # weak scaling: every rank solves its own 4096-point batch (seed = rank)
+    w = W.torus_closed(P=args.points, walks=args.walks, seed=rank)
+    ctx = M.Context(local)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    P, N = args.points, args.walks
+    pts_dev = torch.tensor(w.points, dtype=torch.float64, device="cuda")
+    outs = tuple(torch.zeros(P, dtype=torch.float64, device="cuda") for _ in range(3))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+
+    def step():
+        return ctx.solve(w.problem, w.params, pts_dev, N, precision=M.FP32, out=outs)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launch_count()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        flush.zero_()                       # L2 flushed between timed steps (outside the events)
+        starts[s].record(stream)
+        step()
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    launches = ctx.launch_count() - launches0
+    t_dev = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3
+    mean = outs[0].cpu().numpy()
+    msteps = outs[2].cpu().numpy()
+
+    # the walk kernel alone (device-resident per-walk outputs): its launch duration
+    S_dev = torch.empty(P * N, dtype=torch.float64, device="cuda")
+    K_dev = torch.empty(P * N, dtype=torch.int32, device="cuda")
+    F_dev = torch.empty(P * N, dtype=torch.int32, device="cuda")
+    kt = []
+    for s in range(3):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx.walk_scores_device(w.problem, w.params, pts_dev, N, M.FP32, S_dev, K_dev, F_dev)
+        b.record(stream)
+        torch.cuda.synchronize()
+        kt.append(a.elapsed_time(b) / 1e3)
+    t_kernel = float(np.median(kt))
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    pts_host = torch.tensor(w.points, dtype=torch.float64).pin_memory()
+    host_out = tuple(torch.zeros(P, dtype=torch.float64).pin_memory() for _ in range(3))
+    e2e_t = []
+    for s in range(max(2, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve(w.problem, w.params, pts_host, N, precision=M.FP32, out=host_out)
+        e2e_t.append(time.perf_counter() - t0)
+    clocks = sampler.stop()
+
+    steps_per_solve = float(msteps.sum() * N)
+    tmax = t_dev
+    e2e_mean = float(np.mean(e2e_t))
+    if dist:
+        tt = torch.tensor([t_dev, e2e_mean], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tmax, e2e_mean = float(tt[0]), float(tt[1])
+    total_steps = steps_per_solve * args.steps * world
+    value = total_steps / tmax
+    rmse = float(np.sqrt(np.mean((mean - w.exact) ** 2)))
+
+    if rank == 0:
+        peaks, src = _peaks()
+        sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+        peak_ops = 148 * 4 * 32 * sm_mhz * 1e6          # lane-ops/s: one warp instruction per SMSP per clock
+        achieved = OPS_PER_STEP * steps_per_solve / t_kernel
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "torus_closed R=1 a=0.4 sigma=2 u=sin(th)cos(2ph)", "points": P,
+                       "walks_per_point": N, "steps_per_walk": 525, "walk_steps_per_step": steps_per_solve,
+                       "precision": "FP32 walk, FP64 weights + Kahan sums", "parallelism": f"dp{world} (points)",
+                       "l2": "flushed between timed steps (256 MB write)", "rmse": rmse,
+                       "query_pts_per_s": P * args.steps * world / tmax},
+            "rmse": rmse,
+            "query_pts_per_s": P * args.steps * world / tmax,
+            "e2e": {"value": steps_per_solve * world / e2e_mean, "unit": UNIT,
+                    "h2d_bytes_per_step": int(P * 3 * 8), "d2h_bytes_per_step": int(3 * P * 8)},
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": achieved / peak_ops, "traffic": None,
+                         "kernel": "walk3_f32_kernel<torus>", "kernel_ms": 1e3 * t_kernel,
+                         "ops_per_walk_step": OPS_PER_STEP,
+                         "peak_source": f"148 SM x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz ({src} max clock)"},
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

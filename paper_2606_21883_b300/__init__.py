@@ -208,6 +208,15 @@ class Context:
         self._check(rc)
         return S, K, fl
 
+    def walk_scores_device(self, problem, params, pts, N, precision, S, K, flags):
+        """mpwos_walk_scores into caller-owned device tensors (no host copies)."""
+        mar = _Marshal()
+        md, pd = mar.problem(problem)
+        prm = make_params(params, precision)
+        rc = self.L.mpwos_walk_scores(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
+                                      int(pts.shape[0]), int(N), _ptr(S), _ptr(K), _ptr(flags))
+        return self._check(rc)
+
     # -- primitives -------------------------------------------------------------
     def philox(self, ctr, key0, key1):
         ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
