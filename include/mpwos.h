@@ -145,6 +145,32 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
                       const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
                       double* S, int32_t* K, int32_t* flags);
 
+/* Allocation-free variant of mpwos_solve (the paper has no counterpart: this
+ * is a deployment convenience).  For callers that cannot call cudaMalloc — an
+ * application whose device memory is owned by another allocator, or a
+ * latency-critical loop where an allocation (which can synchronize the
+ * device) is not allowed.  It runs the same walk and reduction kernels as
+ * mpwos_solve, on the same draws, with all scratch (per-walk scores, stopping
+ * indices, flags, radius tables, boundary normal, counter) in one fixed 32 MiB
+ * device array inside the library, which each GPU holds from its first use
+ * until the process exits.
+ *   - pts (P x n) and the three outputs must be DEVICE pointers (EINVAL
+ *     otherwise); problem data are host pointers as for mpwos_solve;
+ *   - P * N must not exceed mpwos_noalloc_max_walks() (EINVAL with the limit
+ *     in the message); EMBEDDED_SPHERE is not supported (EINVAL);
+ *   - the first call on a device looks up the array's device address; make
+ *     that first call before any stream capture;
+ *   - every call shares the array: calls that overlap on the GPU (other
+ *     streams, other contexts on the same device) race and must be serialized
+ *     by the caller.  Each call clears and rebuilds what it needs.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+                        const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
+                        double* mean, double* stderr_, double* mean_steps);
+
+/* Largest P * N accepted by mpwos_solve_noalloc. */
+int64_t mpwos_noalloc_max_walks(void);
+
 /* ---- primitives exposed for verification ------------------------------ */
 
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4q..4q+3] =

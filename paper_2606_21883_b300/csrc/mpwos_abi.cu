@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -513,3 +514,158 @@ int mpwos_c_sigma_r(mpwos_ctx* ctx, int n, const double* a, double* c, int64_t c
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of mpwos_solve.
+//
+// Some callers cannot call cudaMalloc: an application whose device memory is
+// entirely owned by another allocator (a framework's caching pool that has
+// reserved the free memory), or a latency-critical request loop where an
+// allocation — which may synchronize the device — is not allowed.  For them
+// mpwos_solve_noalloc runs the same walk and reduction kernels with all of
+// their scratch (per-walk scores, stopping indices and flags, the radius
+// tables, the boundary normal, the max-steps counter) carved out of one
+// file-scope device array of fixed size.  Every GPU that loads the library
+// holds this array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocBytes = size_t(32) << 20;   // 32 MiB per device
+constexpr size_t kNaHeader = 256;                      // max-steps counter
+constexpr size_t kNaNormal = 8192;                     // boundary normal, n <= 1024 doubles
+constexpr size_t kNaQuad = 256;                        // SPHERE_QUAD v, A on S^2 (12 doubles)
+constexpr size_t kNaTab64 = 534272;                    // 65 x 1027 doubles, rounded up to 256
+constexpr size_t kNaTab32 = 267264;                    // 65 x 1027 floats, rounded up to 256
+constexpr size_t kNaFixed = kNaHeader + kNaNormal + kNaQuad + kNaTab64 + kNaTab32;
+constexpr size_t kNaPerWalk = sizeof(double) + 2 * sizeof(int32_t);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device (looked up once
+// per device; host code may not use the symbol itself as a device address).
+int noalloc_scratch(mpwos_ctx* ctx, unsigned char** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (ctx->device < 0 || ctx->device >= 256) return fail(ctx, MPWOS_EINVAL, "device index out of range");
+  if (!g_noalloc_ptr[ctx->device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return fail(ctx, MPWOS_ECUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[ctx->device] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_ptr[ctx->device]);
+  return MPWOS_OK;
+}
+
+}  // namespace
+
+extern "C" int64_t mpwos_noalloc_max_walks(void) {
+  return static_cast<int64_t>((kNoAllocBytes - kNaFixed) / kNaPerWalk);
+}
+
+extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+                                   const mpwos_params* prm, const double* pts, int64_t P, int64_t N, double* mean,
+                                   double* stderr_, double* mean_steps) {
+  if (!ctx) return MPWOS_EINVAL;
+  CK(cudaSetDevice(ctx->device));
+  int rc = validate(ctx, m, prob, prm, P, N);
+  if (rc) return rc;
+  if (m->kind == MPWOS_EMBEDDED_SPHERE)
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE is not supported (use mpwos_solve)");
+  if (P > 0 && (!is_device_ptr(pts) || !is_device_ptr(mean) || !is_device_ptr(stderr_) || !is_device_ptr(mean_steps)))
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: pts and the three outputs must be device pointers");
+  const int64_t walks = P * N;
+  if (walks > mpwos_noalloc_max_walks())
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: P*N = %lld walks exceeds the fixed scratch limit of %lld",
+                (long long)walks, (long long)mpwos_noalloc_max_walks());
+  unsigned char* base = nullptr;
+  rc = noalloc_scratch(ctx, &base);
+  if (rc) return rc;
+  unsigned long long* nflag = reinterpret_cast<unsigned long long*>(base);
+  unsigned char* cur = base + kNaHeader;
+  double* e_dev = reinterpret_cast<double*>(cur);
+  cur += kNaNormal;
+  double* quad_dev = reinterpret_cast<double*>(cur);
+  cur += kNaQuad;
+  double* tab64 = reinterpret_cast<double*>(cur);
+  cur += kNaTab64;
+  float* tab32 = reinterpret_cast<float*>(cur);
+  cur += kNaTab32;
+  double* S = reinterpret_cast<double*>(cur);
+  int32_t* K = reinterpret_cast<int32_t*>(cur + walks * sizeof(double));
+  int32_t* F = K + walks;
+
+  DevProblem pb;
+  std::memset(&pb, 0, sizeof pb);
+  pb.mkind = m->kind;
+  pb.n = m->n;
+  pb.d = m->d;
+  pb.R = m->R;
+  pb.a_tube = m->a;
+  pb.sigma = prob->sigma;
+  pb.sqrt_sigma = std::sqrt(prob->sigma);
+  pb.closed = prob->closed;
+  pb.h = prob->bnd_offset;
+  pb.eps = prm->eps;
+  pb.tau_w = prm->tau_w;
+  pb.theta = prm->theta;
+  pb.c_kappa = prm->c_kappa;
+  pb.kappa = kappa_of(m);
+  pb.rho_geo = prm->c_kappa / (1.0 + pb.kappa);
+  pb.n_v = prm->n_v;
+  pb.max_steps = prm->max_steps;
+  pb.seed = prm->seed;
+  pb.P = P;
+  pb.N = N;
+  pb.pts = pts;
+  copy_func(prob->f, pb.f);
+  if (!prob->closed) {
+    copy_func(prob->g, pb.g);
+    CK(cudaMemcpyAsync(e_dev, prob->bnd_normal, sizeof(double) * m->n, cudaMemcpyHostToDevice, ctx->stream));
+    pb.e = e_dev;
+  }
+  // SPHERE_QUAD data on S^2: v (3) then A (9)
+  for (DevFunc* df : {&pb.f, &pb.g}) {
+    const mpwos_func& hf = (df == &pb.f) ? prob->f : prob->g;
+    if ((df == &pb.g && prob->closed) || hf.kind != MPWOS_FUNC_SPHERE_QUAD) continue;
+    if (df == &pb.g && prob->f.kind == MPWOS_FUNC_SPHERE_QUAD)
+      return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: at most one SPHERE_QUAD function");
+    CK(cudaMemcpyAsync(quad_dev, hf.v, 3 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(quad_dev + 3, hf.A, 9 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    df->v = quad_dev;
+    df->A = quad_dev + 3;
+  }
+  // the radius table, rebuilt in the shared array on every call
+  const double a_max = pb.sqrt_sigma * pb.theta * pb.rho_geo;
+  const int n = m->n;
+  if (n > 3 && 0.25 * a_max * a_max > 0.25 * (n - 2))
+    return fail(ctx, MPWOS_EINVAL, "sigma (theta rho_geo)^2 / 4 = %g exceeds (n-2)/4: outside the series range",
+                0.25 * a_max * a_max);
+  pb.NS = kTableNS;
+  pb.NA = prob->closed ? 1 : kTableNA;
+  pb.z_max = 0.25 * a_max * a_max;
+  CK(launch_build_table(n, pb.NA, pb.NS, pb.z_max, prob->closed ? a_max : 0.0, tab64, tab32, ctx->stream));
+  ctx->launches += 2;
+  pb.tab64 = tab64;
+  pb.tab32 = tab32;
+  pb.S_out = S;
+  pb.K_out = K;
+  pb.flag_out = F;
+  CK(cudaMemsetAsync(nflag, 0, sizeof(unsigned long long), ctx->stream));
+  rc = run_walks(ctx, pb, prm->precision == MPWOS_FP64);
+  if (rc) return rc;
+  if (P) {
+    CK(launch_reduce(S, K, F, P, N, mean, stderr_, mean_steps, nflag, ctx->stream));
+    ctx->launches++;
+  }
+  unsigned long long hflag = 0;
+  CK(cudaMemcpyAsync(&hflag, nflag, sizeof hflag, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hflag) return fail(ctx, MPWOS_EMAXSTEPS, "%llu walks reached max_steps", hflag);
+  return MPWOS_OK;
+}
