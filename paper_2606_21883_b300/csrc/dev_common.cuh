@@ -49,7 +49,14 @@ struct DevProblem {
   int n_v;
   int64_t max_steps;
   uint64_t seed;
-  // radius tables (inverse CDF of the Green density in s = (2/pi) asin(sqrt U))
+  // FP32 survival weight: em1(z) = I~_nu(a) - 1 = sum_{j=1..T} k_j z^j (Lemma 3.1
+  // series, coefficients k_j = 1/(j! (nu+1)_j) from FP64 on the host, T chosen
+  // so the truncation is below 1e-9 relative at z_max); em1_fp64 = 1 when T
+  // terms do not suffice (the FP32 walk then uses the FP64 series).
+  float em1_k[32];
+  int em1_terms;
+  int em1_fp64;
+  // radius tables (inverse CDF of the Green law; layout in green.cuh)
   const double* tab64;
   const float* tab32;
   int NA, NS;         // a-rows (uniform in z = a^2/4), s-nodes (+2 ghosts per row)
@@ -67,6 +74,32 @@ struct DevProblem {
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 // ---------------------------------------------------------------------------
 struct U4 { uint32_t x, y, z, w; };
+
+// Round keys of one seed: k_r = (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85), r = 0..9.
+struct PhiloxKeys { uint32_t a[10], b[10]; };
+
+__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+  PhiloxKeys K;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    K.a[r] = k0 + static_cast<uint32_t>(r) * 0x9E3779B9u;
+    K.b[r] = k1 + static_cast<uint32_t>(r) * 0xBB67AE85u;
+  }
+  return K;
+}
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                             const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c0;
+    const uint64_t p1 = static_cast<uint64_t>(0xCD9E8D57u) * c2;
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ c1 ^ K.a[r];
+    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ c3 ^ K.b[r];
+    c0 = n0; c1 = static_cast<uint32_t>(p1); c2 = n2; c3 = static_cast<uint32_t>(p0);
+  }
+  return U4{c0, c1, c2, c3};
+}
 
 __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                              uint32_t k0, uint32_t k1) {
@@ -94,6 +127,12 @@ __device__ __forceinline__ float u24(uint32_t x) {
   return static_cast<float>((x >> 8) + 1u) * 0x1p-24f;
 }
 
+// 23-bit uniform in (0, 1] from one word without an int->float conversion:
+// 2 - [1, 2) built from the top 23 bits as a float mantissa.
+__device__ __forceinline__ float u23(uint32_t x) {
+  return 2.0f - __uint_as_float(0x3f800000u | (x >> 9));
+}
+
 constexpr double kTwoPi = 6.283185307179586;
 constexpr float kTwoPiF = 6.28318530717958648f;
 
@@ -114,6 +153,62 @@ __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, floa
   __sincosf(kTwoPiF * ub, &s, &c);
   g0 = rad * c;
   g1 = rad * s;
+}
+
+// ---------------------------------------------------------------------------
+// Pairs of floats (hi + lo, |lo| <= ulp(hi)/2) with error-free transformations
+// (Knuth TwoSum, FMA TwoProd): ~2^-48 relative precision on the FP32 pipes.
+// Used for each walk's running weight W and score S in the FP32 walk, where
+// B300's FP64 pipe (about 1/64 of the FP32 rate) would otherwise co-limit the
+// step; per-point sums over walks stay in FP64.
+// ---------------------------------------------------------------------------
+struct F2 { float hi, lo; };
+
+// c = 1 / (1 + em1) as a float pair and omega = (1 - c)/sigma, from an FP32
+// em1.  For em1 <= 1, c = 1 - delta with delta = em1/(1 + em1) held exactly
+// as (hi, lo); otherwise c = 1/(1 + em1) directly.
+__device__ __forceinline__ void weights_from_em1(float em1, float inv_sigma, F2& c, F2& om) {
+  if (em1 <= 1.0f) {
+    const float delta = __fdividef(em1, 1.0f + em1);
+    const float hi = __fadd_rn(1.0f, -delta);
+    c = F2{hi, __fadd_rn(__fadd_rn(1.0f, -hi), -delta)};
+    om = F2{delta * inv_sigma, 0.0f};
+  } else {
+    const float cc = __fdividef(1.0f, 1.0f + em1);
+    c = F2{cc, 0.0f};
+    om = F2{(1.0f - cc) * inv_sigma, 0.0f};
+  }
+}
+
+__device__ __forceinline__ F2 f2_from_double(double x) {
+  const float hi = static_cast<float>(x);
+  return F2{hi, static_cast<float>(x - static_cast<double>(hi))};
+}
+__device__ __forceinline__ double f2_to_double(F2 x) {
+  return static_cast<double>(x.hi) + static_cast<double>(x.lo);
+}
+__device__ __forceinline__ F2 f2_fast_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fadd_rn(b, -__fadd_rn(s, -a))};
+}
+__device__ __forceinline__ F2 f2_mul(F2 x, F2 y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return f2_fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2 f2_mul_f(F2 x, float f) {
+  const float p = __fmul_rn(x.hi, f);
+  float e = __fmaf_rn(x.hi, f, -p);
+  e = __fmaf_rn(x.lo, f, e);
+  return f2_fast_two_sum(p, e);
+}
+__device__ __forceinline__ F2 f2_add(F2 x, F2 y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fadd_rn(s, -x.hi);
+  const float err = __fadd_rn(__fadd_rn(x.hi, -__fadd_rn(s, -bb)), __fadd_rn(y.hi, -bb));
+  return f2_fast_two_sum(s, __fadd_rn(err, __fadd_rn(x.lo, y.lo)));
 }
 
 }  // namespace mpwos

@@ -32,6 +32,13 @@ __host__ __device__ __forceinline__ double em1_series(double nu, double z) {
   return sum;
 }
 
+// em1(z) from the FP32 polynomial of a problem (Horner).
+__device__ __forceinline__ float em1_poly32(const DevProblem& pb, float z) {
+  float acc = pb.em1_k[pb.em1_terms - 1];
+  for (int j = pb.em1_terms - 2; j >= 0; --j) acc = fmaf(acc, z, pb.em1_k[j]);
+  return acc * z;
+}
+
 // 1 - c from em1 without cancellation.
 __host__ __device__ __forceinline__ double one_minus_c(double em1, double c) {
   return (em1 <= 1.0) ? em1 * c : 1.0 - c;
@@ -187,9 +194,13 @@ __host__ __device__ inline double green_invert64(const GreenLaw& L, double U, do
   return t;
 }
 
-// s = (2/pi) asin(sqrt(U)): the table's abscissa.
-__host__ __device__ __forceinline__ double s_of_u64(double U) { return 0.6366197723675814 * asin(sqrt(U)); }
-__device__ __forceinline__ float s_of_u32(float U) { return 0.636619772f * asinf(sqrtf(U)); }
+// Radius tables.  Each law (row) holds two sides of NS + 2 nodes: side A
+// tabulates t over v = sqrt(U) for U <= 1/2, side B over v = sqrt(1 - U) for
+// U > 1/2.  Both ends of t(U) behave like square roots (t ~ sqrt(U) at 0,
+// 1 - t ~ sqrt(1 - U) at 1), so t is smooth in v on each side; nodes v_j = j h,
+// h = sqrt(1/2)/(NS - 1), j = -1 .. NS (node j at offset j + 1; j = -1 from the
+// odd symmetries t(-v) = -t(v), 1 - t(-v) = -(1 - t(v))).
+constexpr double kTableVmax = 0.70710678118654752;
 
 template <typename T>
 __host__ __device__ __forceinline__ T catmull_rom(const T* row, int j, T f) {
@@ -198,22 +209,26 @@ __host__ __device__ __forceinline__ T catmull_rom(const T* row, int j, T f) {
                                            f * (T(3) * (p1 - p2) + p3 - p0)));
 }
 
-// Table lookup t(s; z): rows over z = a^2/4 in [0, z_max] (NA rows; NA = 1 is a
-// single law), NS nodes over s in [0, 1] plus a ghost node at each end.
+// Table lookup t(U; z), rows over z = a^2/4 in [0, z_max] (NA = 1: one law),
+// Catmull-Rom along v, linear across rows.
 template <typename T>
-__host__ __device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS, double z_max, T a, T s) {
-  const int rs = NS + 2;
-  T xs = s * T(NS - 1);
+__host__ __device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS, double z_max, T a, T U) {
+  const int side_len = NS + 2;
+  const bool upper = U > T(0.5);
+  const T v = sqrt(upper ? T(1) - U : U);
+  const T xs = v * T(static_cast<double>(NS - 1) / kTableVmax);
   int j = static_cast<int>(xs);
   j = j < 0 ? 0 : (j > NS - 2 ? NS - 2 : j);
   const T f = xs - T(j);
-  if (NA == 1) return catmull_rom(tab, j, f);
+  const int side = upper ? side_len : 0;
+  if (NA == 1) return catmull_rom(tab + side, j, f);
   const T fa = (a * a * T(0.25)) / T(z_max) * T(NA - 1);
   int ia = static_cast<int>(fa);
   ia = ia < 0 ? 0 : (ia > NA - 2 ? NA - 2 : ia);
   const T wa = fa - T(ia);
-  const T v0 = catmull_rom(tab + static_cast<size_t>(ia) * rs, j, f);
-  const T v1 = catmull_rom(tab + static_cast<size_t>(ia + 1) * rs, j, f);
+  const T* r0 = tab + static_cast<size_t>(ia) * (2 * side_len) + side;
+  const T v0 = catmull_rom(r0, j, f);
+  const T v1 = catmull_rom(r0 + 2 * side_len, j, f);
   return v0 + wa * (v1 - v0);
 }
 

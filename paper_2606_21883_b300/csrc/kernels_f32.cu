@@ -17,14 +17,22 @@ cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
-  switch (pb.mkind) {
-    case kEuclid: walkn_f32_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
-    case kSphere: walkn_f32_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
-    case kEmbeddedSphere: walkn_f32_kernel<kEmbeddedSphere><<<grid, block, 0, st>>>(pb); break;
-    default: return cudaErrorInvalidValue;
+static const void* walkn_f32_fn(const DevProblem& pb) {
+  if (pb.mkind == kEuclid) return reinterpret_cast<const void*>(walkn_f32_kernel<kEuclid, 8>);
+  if (pb.mkind == kSphere) return reinterpret_cast<const void*>(walkn_f32_kernel<kSphere, 8>);
+  switch (walkn_dq(pb.d + 1)) {
+    case 8: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 8>);
+    case 16: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 16>);
+    case 24: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 24>);
+    default: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 32>);
   }
-  return cudaGetLastError();
+}
+
+cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere) return cudaErrorInvalidValue;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(walkn_f32_fn(pb), dim3(grid), dim3(block), args, 0, st);
 }
 
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
@@ -35,9 +43,7 @@ int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
        : pb.mkind == kSphere ? reinterpret_cast<const void*>(walk3_f32_kernel<kSphere>)
                              : reinterpret_cast<const void*>(walk3_f32_kernel<kTorus>);
   } else {
-    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walkn_f32_kernel<kEuclid>)
-       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walkn_f32_kernel<kSphere>)
-                             : reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere>);
+    fn = walkn_f32_fn(pb);
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
   return nb < 1 ? 1 : nb;
@@ -47,7 +53,7 @@ __global__ void green_radius32_kernel(const double* a, const double* U, double* 
                                       const float* tab32, int NA, int NS, double z_max) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= count) return;
-  float v = table_lookup<float>(tab32, NA, NS, z_max, static_cast<float>(a[q]), s_of_u32(static_cast<float>(U[q])));
+  float v = table_lookup<float>(tab32, NA, NS, z_max, static_cast<float>(a[q]), static_cast<float>(U[q]));
   t[q] = static_cast<double>(fminf(fmaxf(v, 0.0f), 1.0f));
 }
 

@@ -8,27 +8,30 @@
 namespace mpwos {
 
 // ---------------------------------------------------------------------------
-// Radius tables: t(s; z) with U = sin^2(pi s / 2); s uniform on [0, 1].
-// Bisection to a bracket, then the safeguarded Newton polish.
+// Radius tables (layout in green.cuh): one thread per node; bisection to a
+// bracket, then the safeguarded Newton polish, in FP64.
 // ---------------------------------------------------------------------------
 __global__ void build_table_kernel(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
                                    float* tab32) {
+  const int side_len = NS + 2;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= NA * NS) return;
-  const int ia = idx / NS, j = idx % NS;
+  if (idx >= NA * 2 * side_len) return;
+  const int ia = idx / (2 * side_len);
+  const int rem = idx - ia * 2 * side_len;
+  const int side = rem / side_len;
+  const int j = rem - side * side_len - 1;            // node index -1 .. NS
   const double a = (NA == 1) ? a_fixed : 2.0 * sqrt(z_max * static_cast<double>(ia) / static_cast<double>(NA - 1));
-  const double s = static_cast<double>(j) / static_cast<double>(NS - 1);
-  const double sn = sin(0.5 * kPi * s);
-  const double U = sn * sn;
+  const double v = static_cast<double>(j < 0 ? -j : j) * (kTableVmax / static_cast<double>(NS - 1));
+  const double U = side == 0 ? v * v : 1.0 - v * v;
   const GreenLaw L = green_law(n, a);
   double t;
-  if (j == 0) {
+  if (U <= 0.0) {
     t = 0.0;
-  } else if (j == NS - 1) {
+  } else if (U >= 1.0) {
     t = 1.0;
   } else {
     double lo = 0.0, hi = 1.0;
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < 12; ++it) {   // bracket to 2^-12, then Newton converges in a few steps
       const double mid = 0.5 * (lo + hi);
       double F, dF;
       green_cdf_pdf(L, mid, F, dF);
@@ -36,28 +39,15 @@ __global__ void build_table_kernel(int n, int NA, int NS, double z_max, double a
     }
     t = green_invert64(L, U, 0.5 * (lo + hi));
   }
-  const int rs = NS + 2;
-  tab64[static_cast<size_t>(ia) * rs + j + 1] = t;
-  tab32[static_cast<size_t>(ia) * rs + j + 1] = static_cast<float>(t);
-}
-
-// Ghost nodes: t is odd about s = 0 and 1 - t is odd about s = 1.
-__global__ void table_ghosts_kernel(int NA, int NS, double* tab64, float* tab32) {
-  const int ia = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ia >= NA) return;
-  double* row = tab64 + static_cast<size_t>(ia) * (NS + 2);
-  row[0] = -row[2];
-  row[NS + 1] = 2.0 - row[NS - 1];
-  float* rowf = tab32 + static_cast<size_t>(ia) * (NS + 2);
-  rowf[0] = static_cast<float>(row[0]);
-  rowf[NS + 1] = static_cast<float>(row[NS + 1]);
+  if (j < 0) t = side == 0 ? -t : 2.0 - t;
+  tab64[idx] = t;
+  tab32[idx] = static_cast<float>(t);
 }
 
 cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
                                float* tab32, cudaStream_t st) {
-  const int total = NA * NS;
+  const int total = NA * 2 * (NS + 2);
   build_table_kernel<<<(total + 127) / 128, 128, 0, st>>>(n, NA, NS, z_max, a_fixed, tab64, tab32);
-  table_ghosts_kernel<<<(NA + 63) / 64, 64, 0, st>>>(NA, NS, tab64, tab32);
   return cudaGetLastError();
 }
 
@@ -141,14 +131,22 @@ cudaError_t launch_walk3_f64(const DevProblem& pb, int grid, int block, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
-  switch (pb.mkind) {
-    case kEuclid: walkn_f64_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
-    case kSphere: walkn_f64_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
-    case kEmbeddedSphere: walkn_f64_kernel<kEmbeddedSphere><<<grid, block, 0, st>>>(pb); break;
-    default: return cudaErrorInvalidValue;
+static const void* walkn_f64_fn(const DevProblem& pb) {
+  if (pb.mkind == kEuclid) return reinterpret_cast<const void*>(walkn_f64_kernel<kEuclid, 8>);
+  if (pb.mkind == kSphere) return reinterpret_cast<const void*>(walkn_f64_kernel<kSphere, 8>);
+  switch (walkn_dq(pb.d + 1)) {
+    case 8: return reinterpret_cast<const void*>(walkn_f64_kernel<kEmbeddedSphere, 8>);
+    case 16: return reinterpret_cast<const void*>(walkn_f64_kernel<kEmbeddedSphere, 16>);
+    case 24: return reinterpret_cast<const void*>(walkn_f64_kernel<kEmbeddedSphere, 24>);
+    default: return reinterpret_cast<const void*>(walkn_f64_kernel<kEmbeddedSphere, 32>);
   }
-  return cudaGetLastError();
+}
+
+cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere) return cudaErrorInvalidValue;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(walkn_f64_fn(pb), dim3(grid), dim3(block), args, 0, st);
 }
 
 int occupancy_walk_f64(const DevProblem& pb, bool n3, int block) {
@@ -159,9 +157,7 @@ int occupancy_walk_f64(const DevProblem& pb, bool n3, int block) {
        : pb.mkind == kSphere ? reinterpret_cast<const void*>(walk3_f64_kernel<kSphere>)
                              : reinterpret_cast<const void*>(walk3_f64_kernel<kTorus>);
   } else {
-    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walkn_f64_kernel<kEuclid>)
-       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walkn_f64_kernel<kSphere>)
-                             : reinterpret_cast<const void*>(walkn_f64_kernel<kEmbeddedSphere>);
+    fn = walkn_f64_fn(pb);
   }
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
   return nb < 1 ? 1 : nb;
@@ -188,7 +184,7 @@ __global__ void green_radius64_kernel(int n, const double* a, const double* U, d
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= count) return;
   const GreenLaw L = green_law(n, a[q]);
-  const double guess = table_lookup<double>(tab64, NA, NS, z_max, a[q], s_of_u64(U[q]));
+  const double guess = table_lookup<double>(tab64, NA, NS, z_max, a[q], U[q]);
   t[q] = green_invert64(L, U[q], guess);
 }
 
@@ -216,26 +212,26 @@ cudaError_t launch_c_sigma_r(int n, const double* a, double* c, int64_t count, c
 namespace mpwos {
 
 // s0 = normalize(Q^T (y0 - b)) for each query point (embedded sphere start state).
-__global__ void intrinsic_start_kernel(const double* pts, const double* QT, const double* b, int n, int D,
-                                       int64_t P, double* s0) {
+__global__ void intrinsic_start_kernel(const double* pts, const double* QT, const double* b, int n, int npad,
+                                       int D, int64_t P, double* s0) {
   const int lane = threadIdx.x & 31;
   const int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (p >= P) return;
   double sj = 0.0;
   if (lane < D) {
     const double* y = pts + p * n;
-    const double* row = QT + static_cast<size_t>(lane) * n;
+    const double* row = QT + static_cast<size_t>(lane) * npad;
     for (int i = 0; i < n; ++i) sj += row[i] * (y[i] - b[i]);
   }
   const double nn = sqrt(warp_sum1(sj * sj));
   if (lane < D) s0[p * D + lane] = sj / nn;
 }
 
-cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const double* b, int n, int D, int64_t P,
+cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const double* b, int n, int npad, int D, int64_t P,
                                    double* s0, cudaStream_t st) {
   const int block = 128;
-  intrinsic_start_kernel<<<static_cast<unsigned>((P * 32 + block - 1) / block), block, 0, st>>>(pts, QT, b, n, D, P,
-                                                                                               s0);
+  intrinsic_start_kernel<<<static_cast<unsigned>((P * 32 + block - 1) / block), block, 0, st>>>(pts, QT, b, n, npad,
+                                                                                               D, P, s0);
   return cudaGetLastError();
 }
 

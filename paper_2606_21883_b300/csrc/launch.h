@@ -17,7 +17,7 @@ int occupancy_walk_f32(const DevProblem& pb, bool n3, int block);
 
 // Intrinsic start points s0 = normalize(Q^T (y0 - b)) of an embedded sphere
 // (QT: D x n device array), one warp per point.
-cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const double* b, int n, int D, int64_t P,
+cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const double* b, int n, int npad, int D, int64_t P,
                                    double* s0, cudaStream_t st);
 
 // Per-point mean, standard error and mean steps from per-walk scores.
@@ -26,7 +26,7 @@ cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flag
                           cudaStream_t st);
 
 // Inverse-CDF tables of the radial Green law: NA rows over z = a^2/4 in
-// [0, z_max] (NA == 1: the single law at a = a_fixed), NS nodes + 2 ghosts.
+// [0, z_max] (NA == 1: the single law at a = a_fixed); two sides of NS + 2 nodes per row.
 cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
                                float* tab32, cudaStream_t st);
 

@@ -130,7 +130,7 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       break;
     case MPWOS_EMBEDDED_SPHERE:
       if (m->n <= 3) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs n > 3");
-      if (m->d < 1 || m->d + 1 > kMaxQuadDim || m->d + 1 > m->n) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs 1 <= d < min(n, 32)");
+      if (m->d < 1 || m->d + 1 > kMaxQuadDim - 1 || m->d + 1 > m->n) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs 1 <= d <= min(n - 1, 30)");
       if (!m->Q || !m->b) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs Q and b");
       if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE supports the closed problem only");
       break;
@@ -181,6 +181,30 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
   return MPWOS_OK;
 }
 
+// Coefficients of the FP32 survival-weight polynomial em1(z) = sum_j k_j z^j,
+// k_j = 1/(j! (nu+1)_j) (Lemma 3.1), enough terms for 1e-9 relative
+// truncation at z_max; otherwise the FP32 walk falls back to the FP64 series.
+void fill_em1_poly(DevProblem& pb, int n, double z_max) {
+  const double nu = 0.5 * (n - 2);
+  double kj = 1.0, zj = 1.0, em = 0.0, last = 1.0;
+  int T = 0;
+  for (int j = 1; j <= 32; ++j) {
+    kj /= static_cast<double>(j) * (nu + j);
+    zj *= z_max;
+    pb.em1_k[j - 1] = static_cast<float>(kj);
+    last = kj * zj;
+    em += last;
+    T = j;
+    if (last <= 1e-9 * em) break;
+  }
+  pb.em1_terms = T;
+  pb.em1_fp64 = (z_max > 0.0 && last > 1e-9 * em) ? 1 : 0;
+}
+
+// Rows of a variable-radius table: the law's dependence on z = a^2/4 enters
+// through z/(nu + j); high dimensions need few rows.
+int table_rows(int n) { return n <= 8 ? kTableNA : 17; }
+
 void copy_func(const mpwos_func& f, DevFunc& d) {
   std::memset(&d, 0, sizeof d);
   d.kind = f.kind;
@@ -203,7 +227,7 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
 
 // The radius table for (n, law range): cached per context.
 int get_table(mpwos_ctx* ctx, int n, bool fixed, double a_or_zmax, Table** out) {
-  const int NA = fixed ? 1 : kTableNA;
+  const int NA = fixed ? 1 : table_rows(n);
   auto key = std::make_tuple(n, NA, a_or_zmax);
   auto it = ctx->tables.find(key);
   if (it != ctx->tables.end()) {
@@ -214,11 +238,11 @@ int get_table(mpwos_ctx* ctx, int n, bool fixed, double a_or_zmax, Table** out) 
   t.NA = NA;
   t.NS = kTableNS;
   t.z_max = fixed ? 0.25 * a_or_zmax * a_or_zmax : a_or_zmax;
-  const size_t cnt = static_cast<size_t>(NA) * (kTableNS + 2);
+  const size_t cnt = static_cast<size_t>(NA) * 2 * (kTableNS + 2);
   CK(cudaMalloc(&t.tab64, cnt * sizeof(double)));
   CK(cudaMalloc(&t.tab32, cnt * sizeof(float)));
   CK(launch_build_table(n, NA, kTableNS, t.z_max, fixed ? a_or_zmax : 0.0, t.tab64, t.tab32, ctx->stream));
-  ctx->launches += 2;
+  ctx->launches += 1;
   auto res = ctx->tables.emplace(key, t);
   *out = &res.first->second;
   return MPWOS_OK;
@@ -252,8 +276,10 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   if (!pr->closed) copy_func(pr->g, pb.g);
   const int n = m->n;
   if (!pr->closed) {
+    std::vector<float> ef(pr->bnd_normal, pr->bnd_normal + n);
     pb.e = sc.upload(pr->bnd_normal, n);
-    if (!pb.e) return fail(ctx, MPWOS_ENOMEM, "boundary normal");
+    pb.ef = sc.upload(ef.data(), n);
+    if (!pb.e || !pb.ef) return fail(ctx, MPWOS_ENOMEM, "boundary normal");
   }
   // SPHERE_QUAD coefficient arrays
   const int D = m->d + 1;
@@ -262,9 +288,12 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     if (df == &pb.g && pr->closed) continue;
     if (hf.kind == MPWOS_FUNC_SPHERE_QUAD) {
       const int Dq = (m->kind == MPWOS_SPHERE) ? 3 : D;
+      std::vector<float> vf(hf.v, hf.v + Dq), Af(hf.A, hf.A + static_cast<size_t>(Dq) * Dq);
       df->v = sc.upload(hf.v, Dq);
       df->A = sc.upload(hf.A, static_cast<size_t>(Dq) * Dq);
-      if (!df->v || !df->A) return fail(ctx, MPWOS_ENOMEM, "SPHERE_QUAD data");
+      df->vf = sc.upload(vf.data(), vf.size());
+      df->Af = sc.upload(Af.data(), Af.size());
+      if (!df->v || !df->A || !df->vf || !df->Af) return fail(ctx, MPWOS_ENOMEM, "SPHERE_QUAD data");
     }
   }
   // query points
@@ -275,12 +304,14 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     if (!pb.pts && P) return fail(ctx, MPWOS_ENOMEM, "query points");
   }
   if (m->kind == MPWOS_EMBEDDED_SPHERE) {
-    std::vector<double> qt(static_cast<size_t>(D) * n);
-    std::vector<float> qtf(qt.size());
+    // Q^T, D rows of stride npad = n rounded up to 4 (zero padded: 16-byte row slices)
+    const int npad = (n + 3) & ~3;
+    std::vector<double> qt(static_cast<size_t>(D) * npad, 0.0);
+    std::vector<float> qtf(qt.size(), 0.0f);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < D; ++j) {
-        qt[static_cast<size_t>(j) * n + i] = m->Q[static_cast<size_t>(i) * D + j];
-        qtf[static_cast<size_t>(j) * n + i] = static_cast<float>(m->Q[static_cast<size_t>(i) * D + j]);
+        qt[static_cast<size_t>(j) * npad + i] = m->Q[static_cast<size_t>(i) * D + j];
+        qtf[static_cast<size_t>(j) * npad + i] = static_cast<float>(m->Q[static_cast<size_t>(i) * D + j]);
       }
     double* qtd = sc.upload(qt.data(), qt.size());
     float* qtfd = sc.upload(qtf.data(), qtf.size());
@@ -292,7 +323,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     pb.b = bd;
     pb.s0 = s0;
     if (P) {
-      CK(launch_intrinsic_start(pb.pts, qtd, bd, n, D, P, s0, ctx->stream));
+      CK(launch_intrinsic_start(pb.pts, qtd, bd, n, npad, D, P, s0, ctx->stream));
       ctx->launches++;
     }
   }
@@ -302,6 +333,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   if (n > 3 && 0.25 * a_max * a_max > 0.5 * nu)
     return fail(ctx, MPWOS_EINVAL,
                 "sigma (theta rho_geo)^2 / 4 = %g exceeds (n-2)/4 = %g: outside the series evaluation range", 0.25 * a_max * a_max, 0.5 * nu);
+  fill_em1_poly(pb, n, 0.25 * a_max * a_max);
   Table* tab = nullptr;
   int rc = pr->closed ? get_table(ctx, n, true, a_max, &tab) : get_table(ctx, n, false, 0.25 * a_max * a_max, &tab);
   if (rc) return rc;
@@ -532,10 +564,10 @@ namespace {
 
 constexpr size_t kNoAllocBytes = size_t(32) << 20;   // 32 MiB per device
 constexpr size_t kNaHeader = 256;                      // max-steps counter
-constexpr size_t kNaNormal = 8192;                     // boundary normal, n <= 1024 doubles
+constexpr size_t kNaNormal = 8192 + 4096;              // boundary normal, n <= 1024 doubles + floats
 constexpr size_t kNaQuad = 256;                        // SPHERE_QUAD v, A on S^2 (12 doubles)
-constexpr size_t kNaTab64 = 534272;                    // 65 x 1027 doubles, rounded up to 256
-constexpr size_t kNaTab32 = 267264;                    // 65 x 1027 floats, rounded up to 256
+constexpr size_t kNaTab64 = 1068288;                   // 65 x 2 x 1027 doubles, rounded up to 256
+constexpr size_t kNaTab32 = 534272;                    // 65 x 2 x 1027 floats, rounded up to 256
 constexpr size_t kNaFixed = kNaHeader + kNaNormal + kNaQuad + kNaTab64 + kNaTab32;
 constexpr size_t kNaPerWalk = sizeof(double) + 2 * sizeof(int32_t);
 
@@ -626,8 +658,13 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   copy_func(prob->f, pb.f);
   if (!prob->closed) {
     copy_func(prob->g, pb.g);
+    float ef_host[1024];
+    for (int i = 0; i < m->n; ++i) ef_host[i] = static_cast<float>(prob->bnd_normal[i]);
+    float* ef_dev = reinterpret_cast<float*>(e_dev + 1024);
     CK(cudaMemcpyAsync(e_dev, prob->bnd_normal, sizeof(double) * m->n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ef_dev, ef_host, sizeof(float) * m->n, cudaMemcpyHostToDevice, ctx->stream));
     pb.e = e_dev;
+    pb.ef = ef_dev;
   }
   // SPHERE_QUAD data on S^2: v (3) then A (9)
   for (DevFunc* df : {&pb.f, &pb.g}) {
@@ -647,10 +684,11 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
     return fail(ctx, MPWOS_EINVAL, "sigma (theta rho_geo)^2 / 4 = %g exceeds (n-2)/4: outside the series range",
                 0.25 * a_max * a_max);
   pb.NS = kTableNS;
-  pb.NA = prob->closed ? 1 : kTableNA;
+  pb.NA = prob->closed ? 1 : table_rows(n);
   pb.z_max = 0.25 * a_max * a_max;
+  fill_em1_poly(pb, n, pb.z_max);
   CK(launch_build_table(n, pb.NA, pb.NS, pb.z_max, prob->closed ? a_max : 0.0, tab64, tab32, ctx->stream));
-  ctx->launches += 2;
+  ctx->launches += 1;
   pb.tab64 = tab64;
   pb.tab32 = tab32;
   pb.S_out = S;

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
-  const uint32_t k0 = static_cast<uint32_t>(pb.seed), k1 = static_cast<uint32_t>(pb.seed >> 32);
+  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
   const int nv = pb.n_v;
   const uint32_t ub = 2u * static_cast<uint32_t>(1 + nv);
 
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
     // Theta = Y + r g/|g|
     double g[3], gx;
     {
-      const U4 b0 = philox4x32_10(0u, kk, i, p, k0, k1);
-      const U4 b1 = philox4x32_10(1u, kk, i, p, k0, k1);
+      const U4 b0 = philox4x32_10(0u, kk, i, p, K);
+      const U4 b1 = philox4x32_10(1u, kk, i, p, K);
       box_muller64(u53(b0.x, b0.y), u53(b0.z, b0.w), g[0], g[1]);
       box_muller64(u53(b1.x, b1.y), u53(b1.z, b1.w), g[2], gx);
     }
@@ -93,13 +93,13 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
     // F_k over N_V interior samples
     double F = 0.0;
     for (int l = 0; l < nv; ++l) {
-      const U4 bu = philox4x32_10(ub + static_cast<uint32_t>(l), kk, i, p, k0, k1);
+      const U4 bu = philox4x32_10(ub + static_cast<uint32_t>(l), kk, i, p, K);
       const double U = u53(bu.x, bu.y);
-      const double guess = table_lookup<double>(pb.tab64, pb.NA, pb.NS, pb.z_max, a, s_of_u64(U));
+      const double guess = table_lookup<double>(pb.tab64, pb.NA, pb.NS, pb.z_max, a, U);
       const double t = green_invert64(law, U, guess);
       const uint32_t jb = 2u * static_cast<uint32_t>(1 + l);
-      const U4 b0 = philox4x32_10(jb, kk, i, p, k0, k1);
-      const U4 b1 = philox4x32_10(jb + 1u, kk, i, p, k0, k1);
+      const U4 b0 = philox4x32_10(jb, kk, i, p, K);
+      const U4 b1 = philox4x32_10(jb + 1u, kk, i, p, K);
       box_muller64(u53(b0.x, b0.y), u53(b0.z, b0.w), g[0], g[1]);
       box_muller64(u53(b1.x, b1.y), u53(b1.z, b1.w), g[2], gx);
       const double zn = sqrt(dot3(g, g));
@@ -117,25 +117,106 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
   }
 }
 
-// FP32 walk (FP64 weights and score).  Draws of a step are packed: the step's
-// 3(1+N_V) Gaussians come from consecutive uniform pairs (Box-Muller) of the
-// step's uniform stream (four 24-bit uniforms per block), U_l follows at
-// uniform index 2 ceil(3(1+N_V)/2) + l.  N_V = 1 uses two blocks per step.
+// FP32 walk.  Positions, projection and sampling in FP32; c_{sigma,r} and
+// omega from the FP64 series (once per radius value); each walk's weight W and
+// score S in float pairs (~2^-48 relative), so the step loop issues no FP64
+// instruction; per-point sums over walks are FP64 (reduce kernel).
+// Draws of a step are packed: the step's 3(1+N_V) Gaussians come from
+// consecutive uniform pairs (Box-Muller) of the step's uniform stream (four
+// 24-bit uniforms per block), U_l follows at uniform index 2 ceil(3(1+N_V)/2)
+// + l.  N_V = 1 uses two blocks per step.
 __device__ __forceinline__ float uniform_at32(uint32_t u, uint32_t kk, uint32_t i, uint32_t p,
-                                              uint32_t k0, uint32_t k1) {
-  const U4 b = philox4x32_10(u >> 2, kk, i, p, k0, k1);
+                                              const PhiloxKeys& K) {
+  const U4 b = philox4x32_10(u >> 2, kk, i, p, K);
   const uint32_t s = u & 3u;
-  return u24(s == 0 ? b.x : (s == 1 ? b.y : (s == 2 ? b.z : b.w)));
+  return u23(s == 0 ? b.x : (s == 1 ? b.y : (s == 2 ? b.z : b.w)));
 }
 
 __device__ __forceinline__ float gaussian_at32(uint32_t q, uint32_t kk, uint32_t i, uint32_t p,
-                                               uint32_t k0, uint32_t k1) {
+                                               const PhiloxKeys& K) {
   const uint32_t pair = q >> 1;
-  const U4 b = philox4x32_10(pair >> 1, kk, i, p, k0, k1);
+  const U4 b = philox4x32_10(pair >> 1, kk, i, p, K);
   const bool hi = pair & 1u;
   float g0, g1;
-  box_muller32(u24(hi ? b.z : b.x), u24(hi ? b.w : b.y), g0, g1);
+  box_muller32(u23(hi ? b.z : b.x), u23(hi ? b.w : b.y), g0, g1);
   return (q & 1u) ? g1 : g0;
+}
+
+// Torus angles of cp(x) (same as those of x about the centre circle).
+__device__ __forceinline__ void torus_angles32(float R, const float* x, float& ct, float& st, float& cph,
+                                               float& sph) {
+  const float rho2 = x[0] * x[0] + x[1] * x[1];
+  const float irho = rsqrtf(rho2);
+  const float dr = rho2 * irho - R;
+  const float iw = rsqrtf(dr * dr + x[2] * x[2]);
+  ct = dr * iw;
+  st = x[2] * iw;
+  cph = x[0] * irho;
+  sph = x[1] * irho;
+}
+
+// (-Delta_M + sigma) u or u itself for a torus Fourier series, from the angles.
+__device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevFunc& fn, float ct, float st,
+                                               float cph, float sph) {
+  const float R = static_cast<float>(pb.R), a = static_cast<float>(pb.a_tube);
+  const float ia = 1.0f / a;
+  const float irr = 1.0f / (R + a * ct);
+  const float sg = static_cast<float>(pb.sigma);
+  float total = 0.0f;
+  for (int t = 0; t < fn.n_terms; ++t) {
+    const int m = fn.modes[t][0], q = fn.modes[t][1];
+    float cm = 1.0f, sm = 0.0f, cq = 1.0f, sq = 0.0f;
+    for (int j = 0; j < m; ++j) { const float c2 = cm * ct - sm * st; sm = sm * ct + cm * st; cm = c2; }
+    for (int j = 0; j < q; ++j) { const float c2 = cq * cph - sq * sph; sq = sq * cph + cq * sph; cq = c2; }
+    const float Tv = fn.modes[t][2] == 0 ? cm : sm;
+    const float Pv = fn.modes[t][3] == 0 ? cq : sq;
+    float val;
+    if (!fn.apply_op) {
+      val = Tv * Pv;
+    } else {
+      const float Tp = fn.modes[t][2] == 0 ? -static_cast<float>(m) * sm : static_cast<float>(m) * cm;
+      const float lap = static_cast<float>(m * m) * Tv * ia * ia + st * Tp * ia * irr +
+                        static_cast<float>(q * q) * Tv * irr * irr;
+      val = Pv * (lap + sg * Tv);
+    }
+    total += static_cast<float>(fn.coef[t]) * val;
+  }
+  return total;
+}
+
+// cp(x) in FP32 with reciprocal square roots.
+template <int MK>
+__device__ __forceinline__ void cp3_f32(const DevProblem& pb, const float* x, float* out) {
+  if constexpr (MK == kEuclid) {
+    out[0] = x[0]; out[1] = x[1]; out[2] = x[2];
+  } else if constexpr (MK == kSphere) {
+    const float inv = rsqrtf(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    out[0] = x[0] * inv; out[1] = x[1] * inv; out[2] = x[2] * inv;
+  } else {
+    // cp = (R + s dr)/rho (x0, x1) + s x2 e_z, dr = rho - R, s = a / sqrt(dr^2 + x2^2)
+    const float R = static_cast<float>(pb.R);
+    const float rho2 = x[0] * x[0] + x[1] * x[1];
+    const float irho = rsqrtf(rho2);
+    const float dr = rho2 * irho - R;
+    const float s = static_cast<float>(pb.a_tube) * rsqrtf(dr * dr + x[2] * x[2]);
+    const float fac = (R + s * dr) * irho;
+    out[0] = x[0] * fac; out[1] = x[1] * fac; out[2] = s * x[2];
+  }
+}
+
+// f(cp(Z)) in FP32.
+template <int MK>
+__device__ __forceinline__ float source_at32(const DevProblem& pb, const float* Z) {
+  if constexpr (MK == kTorus) {
+    if (pb.f.kind == kTorusFourier) {
+      float ct, st, cph, sph;
+      torus_angles32(static_cast<float>(pb.R), Z, ct, st, cph, sph);
+      return torus_series32(pb, pb.f, ct, st, cph, sph);
+    }
+  }
+  float cZ[3];
+  cp3_f32<MK>(pb, Z, cZ);
+  return func3<MK, float>(pb, pb.f, cZ);
 }
 
 template <int MK>
@@ -144,15 +225,17 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
-  const uint32_t k0 = static_cast<uint32_t>(pb.seed), k1 = static_cast<uint32_t>(pb.seed >> 32);
+  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
   const int nv = pb.n_v;
   const float eps = static_cast<float>(pb.eps);
   const float theta = static_cast<float>(pb.theta);
   const float rgeo = static_cast<float>(pb.rho_geo);
   const float sqs = static_cast<float>(pb.sqrt_sigma);
+  const F2 tau = f2_from_double(pb.tau_w);
+  const float inv_sigma = static_cast<float>(1.0 / pb.sigma);
 
   float Y[3];
-  double W = 1.0, S = 0.0;
+  F2 W{1.0f, 0.0f}, S{0.0f, 0.0f};
   int64_t k = 0;
   uint32_t p = 0, i = 0;
   auto init = [&](int64_t ww) {
@@ -160,11 +243,11 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
     i = static_cast<uint32_t>(ww - static_cast<int64_t>(p) * pb.N);
     const double* y0 = pb.pts + static_cast<size_t>(p) * 3;
     Y[0] = static_cast<float>(y0[0]); Y[1] = static_cast<float>(y0[1]); Y[2] = static_cast<float>(y0[2]);
-    W = 1.0; S = 0.0; k = 0;
+    W = F2{1.0f, 0.0f}; S = F2{0.0f, 0.0f}; k = 0;
   };
   init(w);
   float r_prev = -1.0f;
-  double c = 1.0, omega = 0.0;
+  F2 c2{1.0f, 0.0f}, om2{0.0f, 0.0f};
 
   for (;;) {
     float dG = INFINITY;
@@ -174,17 +257,17 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
       float yg[3];
       dG = delta_gamma3<MK, float>(pb, Y, yg);
       if (dG < eps) {
-        S += W * static_cast<double>(func3<MK, float>(pb, pb.g, yg));
+        S = f2_add(S, f2_mul_f(W, func3<MK, float>(pb, pb.g, yg)));
         done = true;
-      } else if (W == 0.0) {
+      } else if (W.hi == 0.0f) {
         done = true;
       }
-    } else if (W < pb.tau_w) {
+    } else if (W.hi < tau.hi || (W.hi == tau.hi && W.lo < tau.lo)) {
       done = true;
     }
     if (!done && k >= pb.max_steps) { done = true; flag = 1; }
     if (done) {
-      pb.S_out[w] = S;
+      pb.S_out[w] = f2_to_double(S);
       pb.K_out[w] = static_cast<int32_t>(k);
       pb.flag_out[w] = flag;
       w += stride;
@@ -194,55 +277,58 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
     }
     const float r = theta * (dG < rgeo ? dG : rgeo);
     const float a = sqs * r;
-    if (r != r_prev) {   // constant-radius walks compute the weights once
-      const double ad = static_cast<double>(a);
-      const double em1 = em1_series(0.5, 0.25 * (ad * ad));
-      c = 1.0 / (1.0 + em1);
-      omega = one_minus_c(em1, c) / pb.sigma;
+    if (r != r_prev) {   // constant-radius walks evaluate the weights once
+      if (!pb.em1_fp64) {
+        weights_from_em1(em1_poly32(pb, 0.25f * a * a), inv_sigma, c2, om2);
+      } else {
+        const double ad = static_cast<double>(a);
+        const double em1 = em1_series(0.5, 0.25 * (ad * ad));
+        const double c = 1.0 / (1.0 + em1);
+        c2 = f2_from_double(c);
+        om2 = f2_from_double(one_minus_c(em1, c) / pb.sigma);
+      }
       r_prev = r;
     }
     const uint32_t kk = static_cast<uint32_t>(k);
     float Th[3], F = 0.0f;
     if (nv == 1) {
-      const U4 b0 = philox4x32_10(0u, kk, i, p, k0, k1);
-      const U4 b1 = philox4x32_10(1u, kk, i, p, k0, k1);
+      const U4 b0 = philox4x32_10(0u, kk, i, p, K);
+      const U4 b1 = philox4x32_10(1u, kk, i, p, K);
       float g[3], z[3];
-      box_muller32(u24(b0.x), u24(b0.y), g[0], g[1]);
-      box_muller32(u24(b0.z), u24(b0.w), g[2], z[0]);
-      box_muller32(u24(b1.x), u24(b1.y), z[1], z[2]);
-      const float U = u24(b1.z);
+      box_muller32(u23(b0.x), u23(b0.y), g[0], g[1]);
+      box_muller32(u23(b0.z), u23(b0.w), g[2], z[0]);
+      box_muller32(u23(b1.x), u23(b1.y), z[1], z[2]);
+      const float U = u23(b1.z);
       const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
       for (int q = 0; q < 3; ++q) Th[q] = Y[q] + sc * g[q];
-      float t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, s_of_u32(U));
+      float t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, U);
       t = fminf(fmaxf(t, 0.0f), 1.0f);
       const float zs = (r * t) * rsqrtf(fmaxf(dot3(z, z), 1e-30f));
-      float Z[3], cZ[3];
+      float Z[3];
       for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * z[q];
-      cp3<MK, float>(pb, Z, cZ);
-      F = func3<MK, float>(pb, pb.f, cZ);
+      F = source_at32<MK>(pb, Z);
     } else {
       float g[3];
-      for (int q = 0; q < 3; ++q) g[q] = gaussian_at32(static_cast<uint32_t>(q), kk, i, p, k0, k1);
+      for (int q = 0; q < 3; ++q) g[q] = gaussian_at32(static_cast<uint32_t>(q), kk, i, p, K);
       const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
       for (int q = 0; q < 3; ++q) Th[q] = Y[q] + sc * g[q];
       const uint32_t nu = 2u * ((3u * static_cast<uint32_t>(1 + nv) + 1u) / 2u);
       for (int l = 0; l < nv; ++l) {
-        const float U = uniform_at32(nu + static_cast<uint32_t>(l), kk, i, p, k0, k1);
-        float t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, s_of_u32(U));
+        const float U = uniform_at32(nu + static_cast<uint32_t>(l), kk, i, p, K);
+        float t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, U);
         t = fminf(fmaxf(t, 0.0f), 1.0f);
         for (int q = 0; q < 3; ++q)
-          g[q] = gaussian_at32(3u * static_cast<uint32_t>(1 + l) + static_cast<uint32_t>(q), kk, i, p, k0, k1);
+          g[q] = gaussian_at32(3u * static_cast<uint32_t>(1 + l) + static_cast<uint32_t>(q), kk, i, p, K);
         const float zs = (r * t) * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
-        float Z[3], cZ[3];
+        float Z[3];
         for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * g[q];
-        cp3<MK, float>(pb, Z, cZ);
-        F += func3<MK, float>(pb, pb.f, cZ);
+        F += source_at32<MK>(pb, Z);
       }
       F /= static_cast<float>(nv);
     }
-    S += (W * omega) * static_cast<double>(F);
-    W *= c;
-    cp3<MK, float>(pb, Th, Y);
+    S = f2_add(S, f2_mul_f(f2_mul(W, om2), F));
+    W = f2_mul(W, c2);
+    cp3_f32<MK>(pb, Th, Y);
     ++k;
   }
 }

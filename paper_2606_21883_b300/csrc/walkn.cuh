@@ -14,7 +14,7 @@
 // Draws of step k of walk (p, i), Philox counter (j, k, i, p), nb = ceil(n/G):
 //   Theta direction: blocks [0, nb);  Z_l direction: blocks [nb(1+l), nb(2+l));
 //   FP64: U_l = u53(x, y) of block nb(1+N_V) + l  (identical to the CPU oracle);
-//   FP32: U_l = u24(word l mod 4) of block nb(1+N_V) + l/4.
+//   FP32: U_l = u23(word l mod 4) of block nb(1+N_V) + l/4.
 #pragma once
 #include "dev_common.cuh"
 #include "green.cuh"
@@ -29,6 +29,34 @@ template <> struct Prec<double> {
 template <> struct Prec<float> {
   static constexpr int G = 4;
   static constexpr int MB = 8;    // n <= 32 * 4 * 8 = 1024
+};
+
+// Running weight W and score S of one walk: FP64 in the FP64 walk, float
+// pairs in the FP32 walk (no FP64 instruction in the FP32 step loop).
+template <typename T> struct WalkAcc;
+template <> struct WalkAcc<double> {
+  double W = 1.0, S = 0.0, c = 1.0, om = 0.0, tau = 0.0;
+  __device__ void set_tau(double t) { tau = t; }
+  __device__ void reset() { W = 1.0; S = 0.0; }
+  __device__ void set(double cc, double omega) { c = cc; om = omega; }
+  __device__ void set_from_em1(float, float) {}
+  __device__ void add_terminal(double g) { S += W * g; }
+  __device__ void add_step(double F) { S += (W * om) * F; W *= c; }
+  __device__ bool below() const { return W < tau; }
+  __device__ bool zero() const { return W == 0.0; }
+  __device__ double score() const { return S; }
+};
+template <> struct WalkAcc<float> {
+  F2 W{1.0f, 0.0f}, S{0.0f, 0.0f}, c{1.0f, 0.0f}, om{0.0f, 0.0f}, tau{0.0f, 0.0f};
+  __device__ void set_tau(double t) { tau = f2_from_double(t); }
+  __device__ void reset() { W = F2{1.0f, 0.0f}; S = F2{0.0f, 0.0f}; }
+  __device__ void set(double cc, double omega) { c = f2_from_double(cc); om = f2_from_double(omega); }
+  __device__ void set_from_em1(float em1, float inv_sigma) { weights_from_em1(em1, inv_sigma, c, om); }
+  __device__ void add_terminal(float g) { S = f2_add(S, f2_mul_f(W, g)); }
+  __device__ void add_step(float F) { S = f2_add(S, f2_mul_f(f2_mul(W, om), F)); W = f2_mul(W, c); }
+  __device__ bool below() const { return W.hi < tau.hi || (W.hi == tau.hi && W.lo < tau.lo); }
+  __device__ bool zero() const { return W.hi == 0.0f; }
+  __device__ double score() const { return f2_to_double(S); }
 };
 
 template <int NV, typename T>
@@ -49,13 +77,13 @@ __device__ __forceinline__ T warp_sum1(T v) {
 // The n-vector of Gaussians for blocks jb + b (b = lane + 32 m) of step kk.
 template <typename T>
 __device__ __forceinline__ void gen_vector(T (&g)[Prec<T>::G * Prec<T>::MB], int n, int lane, uint32_t jb,
-                                           uint32_t kk, uint32_t wi, uint32_t p, uint32_t k0, uint32_t k1) {
+                                           uint32_t kk, uint32_t wi, uint32_t p, const PhiloxKeys& K) {
   constexpr int G = Prec<T>::G, MB = Prec<T>::MB;
 #pragma unroll
   for (int m = 0; m < MB; ++m) {
     const int b = lane + 32 * m;
     if (G * b < n) {
-      const U4 r = philox4x32_10(jb + static_cast<uint32_t>(b), kk, wi, p, k0, k1);
+      const U4 r = philox4x32_10(jb + static_cast<uint32_t>(b), kk, wi, p, K);
       if constexpr (G == 2) {
         double g0, g1;
         box_muller64(u53(r.x, r.y), u53(r.z, r.w), g0, g1);
@@ -63,8 +91,8 @@ __device__ __forceinline__ void gen_vector(T (&g)[Prec<T>::G * Prec<T>::MB], int
         g[2 * m + 1] = (2 * b + 1 < n) ? g1 : 0.0;
       } else {
         float g0, g1, g2, g3;
-        box_muller32(u24(r.x), u24(r.y), g0, g1);
-        box_muller32(u24(r.z), u24(r.w), g2, g3);
+        box_muller32(u23(r.x), u23(r.y), g0, g1);
+        box_muller32(u23(r.z), u23(r.w), g2, g3);
         g[4 * m] = g0;
         g[4 * m + 1] = (4 * b + 1 < n) ? g1 : 0.0f;
         g[4 * m + 2] = (4 * b + 2 < n) ? g2 : 0.0f;
@@ -77,48 +105,36 @@ __device__ __forceinline__ void gen_vector(T (&g)[Prec<T>::G * Prec<T>::MB], int
   }
 }
 
-// Value of component v of a distributed vector, broadcast to all lanes.
-template <typename T, int L>
-__device__ __forceinline__ T gather(const T (&x)[L], int v, int G) {
+// Component v of a distributed vector, broadcast to all lanes (v is warp-
+// uniform).  Components v < 32 G live in register slot v mod G of lane v/G.
+template <typename T, int L, int G>
+__device__ __forceinline__ T gather(const T (&x)[L], int v) {
   const int blk = v / G;
   const int owner = blk & 31;
-  const int slot = (blk >> 5) * G + (v - blk * G);
-  T val = T(0);
+  T val = x[0];
+  if (blk < 32) {
+    const int slot = v - blk * G;
 #pragma unroll
-  for (int t = 0; t < L; ++t)
-    if (t == slot) val = x[t];
+    for (int t = 1; t < G; ++t)
+      if (t == slot) val = x[t];
+  } else {
+    const int slot = (blk >> 5) * G + (v - blk * G);
+#pragma unroll
+    for (int t = 1; t < L; ++t)
+      if (t == slot) val = x[t];
+  }
   return __shfl_sync(0xffffffffu, val, owner);
 }
 
-// POLY at the point whose component v is base_v + sc * dir_v, divided by den.
-template <typename T, int L>
-__device__ __forceinline__ T poly_at(const DevFunc& fn, const T (&base)[L], const T (&dir)[L], T sc, T inv_den,
-                                     bool use_dir, int G) {
+// POLY at the point X_v = (base_v + sc dir_v) inv.
+template <typename T, int L, int G>
+__device__ __forceinline__ T poly_at(const DevFunc& fn, const T (&base)[L], const T (&dir)[L], T sc, T inv) {
   T total = T(0);
   for (int t = 0; t < fn.n_terms; ++t) {
     T prod = T(fn.coef[t]);
     for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
       const int v = fn.var[q];
-      T xv = gather(base, v, G);
-      if (use_dir) xv += sc * gather(dir, v, G);
-      xv *= inv_den;
-      for (int e = 0; e < fn.pw[q]; ++e) prod *= xv;
-    }
-    total += prod;
-  }
-  return total;
-}
-
-// POLY at y_Gamma = yg_scale Y + yg_e e (e a host-copied device array).
-template <typename T, int L>
-__device__ __forceinline__ T poly_at_boundary(const DevFunc& fn, const T (&Y)[L], const double* e, T yg_scale,
-                                              T yg_e, int G) {
-  T total = T(0);
-  for (int t = 0; t < fn.n_terms; ++t) {
-    T prod = T(fn.coef[t]);
-    for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
-      const int v = fn.var[q];
-      const T xv = yg_scale * gather(Y, v, G) + yg_e * T(e[v]);
+      const T xv = (gather<T, L, G>(base, v) + sc * gather<T, L, G>(dir, v)) * inv;
       for (int ee = 0; ee < fn.pw[q]; ++ee) prod *= xv;
     }
     total += prod;
@@ -126,17 +142,50 @@ __device__ __forceinline__ T poly_at_boundary(const DevFunc& fn, const T (&Y)[L]
   return total;
 }
 
+// POLY at y_Gamma = yg_scale Y + yg_e e.
+template <typename T, int L, int G>
+__device__ __forceinline__ T poly_at_boundary(const DevFunc& fn, const T (&Y)[L], const T* e, T yg_scale, T yg_e) {
+  T total = T(0);
+  for (int t = 0; t < fn.n_terms; ++t) {
+    T prod = T(fn.coef[t]);
+    for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
+      const int v = fn.var[q];
+      const T xv = yg_scale * gather<T, L, G>(Y, v) + yg_e * e[v];
+      for (int ee = 0; ee < fn.pw[q]; ++ee) prod *= xv;
+    }
+    total += prod;
+  }
+  return total;
+}
+
+// Lane l receives the warp-wide sum of v[l] (recursive halving: 31 shuffles
+// for 32 values instead of 5 per value).
+template <typename T>
+__device__ __forceinline__ T reduce_scatter32(T (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const T send = up ? v[i] : v[i + o];
+      const T keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // SPHERE_QUAD at the unit vector s (lane j holds s_j, j < D; others 0).
 template <typename T>
-__device__ __forceinline__ T sphere_quad_at(const DevProblem& pb, const DevFunc& fn, T sj, int lane, int D) {
+__device__ __forceinline__ T sphere_quad_at(const DevProblem& pb, const DevFunc& fn, const T* vT, const T* AT,
+                                            T sj, int lane, int D) {
   const bool on = lane < D;
-  const T vj = on ? T(fn.v[lane]) : T(0);
   T As = T(0);
   for (int q = 0; q < D; ++q) {
     const T sq = __shfl_sync(0xffffffffu, sj, q);
-    if (on) As += T(fn.A[lane * D + q]) * sq;
+    if (on) As += AT[lane * D + q] * sq;
   }
-  T acc[3] = {vj * sj, sj * As, on ? T(fn.A[lane * D + lane]) : T(0)};
+  T acc[3] = {on ? vT[lane] * sj : T(0), sj * As, on ? AT[lane * D + lane] : T(0)};
   warp_sum<3>(acc);
   const T lin = acc[0], quad = acc[1], tr = acc[2];
   if (!fn.apply_op) return T(fn.c0) + lin + quad;
@@ -144,40 +193,53 @@ __device__ __forceinline__ T sphere_quad_at(const DevProblem& pb, const DevFunc&
   return sg * (T(fn.c0) + mean) + (d + sg) * lin + (T(2) * (d + T(1)) + sg) * (quad - mean);
 }
 
-// Per-lane partial of Q^T g (acc[j], j < D), reduced over the warp.
-template <typename T, int D_MAX>
-__device__ __forceinline__ void qt_times(const DevProblem& pb, const T* QT, const T (&g)[Prec<T>::G * Prec<T>::MB],
-                                         int lane, int D, T (&acc)[D_MAX]) {
+// (Q^T g)_lane and |g|^2 for one Gaussian vector: per-lane partial products
+// with 16-byte loads of the transposed, zero-padded Q^T (row stride npad),
+// then one reduce-scatter; |g|^2 rides in slot 31 (D <= 31).
+template <typename T, int DQ>
+__device__ __forceinline__ T qt_times(const T* QT, int npad, const T (&g)[Prec<T>::G * Prec<T>::MB], int n,
+                                      int lane, int D, T& gg) {
   constexpr int G = Prec<T>::G, MB = Prec<T>::MB;
-  const int n = pb.n;
+  T acc[32];
 #pragma unroll
-  for (int j = 0; j < D_MAX; ++j) acc[j] = T(0);
+  for (int j = 0; j < 32; ++j) acc[j] = T(0);
+  T g2 = T(0);
 #pragma unroll
   for (int m = 0; m < MB; ++m) {
     const int b = lane + 32 * m;
     if (G * b < n) {
 #pragma unroll
-      for (int j = 0; j < D_MAX; ++j) {
-        if (j < D) {
-          const T* row = QT + static_cast<size_t>(j) * n + G * b;
+      for (int q = 0; q < G; ++q) g2 += g[G * m + q] * g[G * m + q];
 #pragma unroll
-          for (int q = 0; q < G; ++q)
-            if (G * b + q < n) acc[j] += row[q] * g[G * m + q];
+      for (int j = 0; j < DQ; ++j) {
+        if (j < D) {
+          const T* row = QT + static_cast<size_t>(j) * npad + G * b;
+          if constexpr (G == 4) {
+            const float4 q4 = *reinterpret_cast<const float4*>(row);
+            acc[j] += q4.x * g[4 * m] + q4.y * g[4 * m + 1] + q4.z * g[4 * m + 2] + q4.w * g[4 * m + 3];
+          } else {
+            const double2 q2 = *reinterpret_cast<const double2*>(row);
+            acc[j] += q2.x * g[2 * m] + q2.y * g[2 * m + 1];
+          }
         }
       }
     }
   }
-  warp_sum<D_MAX>(acc);
+  acc[31] = g2;
+  const T mine = reduce_scatter32(acc, lane);
+  gg = __shfl_sync(0xffffffffu, mine, 31);
+  return mine;
 }
 
 // ---------------------------------------------------------------------------
 // The warp walk.  T = double: the FP64 walk (per-walk identical draws to the
-// CPU oracle); T = float: the FP32 walk with FP64 weights and score.
+// CPU oracle, explicit norms); T = float: the FP32 walk (norms of the updated
+// state from the reductions already done, float-pair W and S).
 // ---------------------------------------------------------------------------
-template <typename T, int MK>
+template <typename T, int MK, int DQ>
 __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
   constexpr int G = Prec<T>::G, MB = Prec<T>::MB, L = G * MB;
-  constexpr int DQ = 32;
+  constexpr bool kF64 = sizeof(T) == 8;
   const int lane = threadIdx.x & 31;
   const int64_t total = pb.P * pb.N;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
@@ -185,24 +247,54 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
   if (w >= total) return;
   const int n = pb.n;
   const int D = pb.d + 1;
-  const uint32_t k0 = static_cast<uint32_t>(pb.seed), k1 = static_cast<uint32_t>(pb.seed >> 32);
+  const int npad = (n + 3) & ~3;
+  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
   const int nv = pb.n_v;
   const uint32_t nb = static_cast<uint32_t>((n + G - 1) / G);
+  // loop-invariant parameters in the walk's precision
+  const T eps_t = T(pb.eps), h_t = T(pb.h), rgeo_t = T(pb.rho_geo), theta_t = T(pb.theta);
+  const T sqs_t = T(pb.sqrt_sigma);
+  const T sh_t = T(sqrt(1.0 - pb.h * pb.h));
+  const float inv_sigma_f = static_cast<float>(1.0 / pb.sigma);
+  const bool bnd = !pb.closed;
+  const T* eT = kF64 ? reinterpret_cast<const T*>(pb.e) : reinterpret_cast<const T*>(pb.ef);
   const T* QT = nullptr;
+  const T* vT = nullptr;
+  const T* AT = nullptr;
   if constexpr (MK == kEmbeddedSphere) {
-    if constexpr (sizeof(T) == 8) QT = reinterpret_cast<const T*>(pb.Q); else QT = reinterpret_cast<const T*>(pb.Qf);
+    QT = kF64 ? reinterpret_cast<const T*>(pb.Q) : reinterpret_cast<const T*>(pb.Qf);
+    vT = kF64 ? reinterpret_cast<const T*>(pb.f.v) : reinterpret_cast<const T*>(pb.f.vf);
+    AT = kF64 ? reinterpret_cast<const T*>(pb.f.A) : reinterpret_cast<const T*>(pb.f.Af);
   }
 
-  T Y[L];        // ambient state (sphere, R^n)
-  T sj = T(0);   // intrinsic state (embedded sphere), lane j < D
-  double W = 1.0, S = 0.0;
+  T Y[L];          // ambient state (sphere, R^n)
+  T sj = T(0);     // intrinsic state (embedded sphere), lane j < D
+  T al = T(0), yy = T(1);   // e.Y and |Y|^2 (boundary problems)
+  WalkAcc<T> wa;
+  wa.set_tau(pb.tau_w);
   int64_t k = 0;
   uint32_t p = 0, wi = 0;
 
+  auto state_dots = [&]() {
+    T acc[2] = {T(0), T(0)};
+#pragma unroll
+    for (int m = 0; m < MB; ++m)
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const int cc = G * (lane + 32 * m) + q;
+        const T ev = cc < n ? eT[cc] : T(0);
+        acc[0] += Y[G * m + q] * ev;
+        acc[1] += Y[G * m + q] * Y[G * m + q];
+      }
+    warp_sum<2>(acc);
+    al = acc[0];
+    yy = acc[1];
+  };
   auto init = [&](int64_t ww) {
     p = static_cast<uint32_t>(ww / pb.N);
     wi = static_cast<uint32_t>(ww - static_cast<int64_t>(p) * pb.N);
-    W = 1.0; S = 0.0; k = 0;
+    wa.reset();
+    k = 0;
     if constexpr (MK == kEmbeddedSphere) {
       sj = lane < D ? T(pb.s0[static_cast<size_t>(p) * D + lane]) : T(0);
     } else {
@@ -214,11 +306,11 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
           const int c = G * (lane + 32 * m) + q;
           Y[G * m + q] = c < n ? T(y0[c]) : T(0);
         }
+      if (bnd) state_dots();
     }
   };
   init(w);
   T r_prev = T(-1);
-  double c = 1.0, omega = 0.0;
   GreenLaw law{};
   T g[L];
 
@@ -228,56 +320,45 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
     bool done = false;
     int flag = 0;
     if constexpr (MK != kEmbeddedSphere) {
-      if (!pb.closed) {
-        T acc[2] = {T(0), T(0)};
-#pragma unroll
-        for (int m = 0; m < MB; ++m)
-#pragma unroll
-          for (int q = 0; q < G; ++q) {
-            const int cc = G * (lane + 32 * m) + q;
-            const T ev = cc < n ? T(pb.e[cc]) : T(0);
-            acc[0] += Y[G * m + q] * ev;
-            acc[1] += Y[G * m + q] * Y[G * m + q];
-          }
-        warp_sum<2>(acc);
-        const T al = acc[0], h = T(pb.h);
+      if (bnd) {
+        // FP64 recomputes e.Y and |Y|^2 every step; FP32 carries them from the
+        // last update and resynchronises every 64 steps (bounded rounding drift)
+        if (kF64 || (k & 63) == 0) state_dots();
         T yg_scale, yg_e;   // y_Gamma = yg_e e + yg_scale Y
-        if (MK == kEuclid) {
-          dG = (al <= h) ? T(0) : fabs(al - h);
+        if constexpr (MK == kEuclid) {
+          dG = (al <= h_t) ? T(0) : fabs(al - h_t);
           yg_scale = T(1);
-          yg_e = -(al - h);
+          yg_e = -(al - h_t);
         } else {
           // unit sphere, Omega = {e.x > h}: with alpha = e.Y, rho = |Y - alpha e|,
           // sh = sqrt(1 - h^2):  y_G = h e + sh (Y - alpha e)/rho,
           // |P_T r_G| = |rho h - alpha sh|,  |P_N r_G| = |1 - h alpha - sh rho|.
-          const T rho = sqrt(fmax(acc[1] - al * al, T(0)));
-          const T sh = sqrt(T(1) - h * h);
-          const T rt = rho * h - al * sh;
-          T ex = fabs(T(1) - h * al - sh * rho) - T(pb.rho_geo);
+          const T rho = sqrt(fmax(yy - al * al, T(0)));
+          const T rt = rho * h_t - al * sh_t;
+          T ex = fabs(T(1) - h_t * al - sh_t * rho) - rgeo_t;
           ex = ex < T(0) ? T(0) : ex;
-          dG = (al <= h) ? T(0) : sqrt(rt * rt + ex * ex);
-          yg_scale = sh / rho;
-          yg_e = h - al * yg_scale;
+          dG = (al <= h_t) ? T(0) : sqrt(rt * rt + ex * ex);
+          yg_scale = sh_t / rho;
+          yg_e = h_t - al * yg_scale;
         }
-        if (dG < T(pb.eps)) {
-          // g at y_Gamma = yg_e e + yg_scale Y
+        if (dG < eps_t) {
           T gv = T(0);
-          if (pb.g.kind == kPoly) gv = poly_at_boundary<T, L>(pb.g, Y, pb.e, yg_scale, yg_e, G);
-          S += W * static_cast<double>(gv);
+          if (pb.g.kind == kPoly) gv = poly_at_boundary<T, L, G>(pb.g, Y, eT, yg_scale, yg_e);
+          wa.add_terminal(gv);
           done = true;
-        } else if (W == 0.0) {
+        } else if (wa.zero()) {
           done = true;
         }
-      } else if (W < pb.tau_w) {
+      } else if (wa.below()) {
         done = true;
       }
     } else {
-      if (W < pb.tau_w) done = true;
+      if (wa.below()) done = true;
     }
     if (!done && k >= pb.max_steps) { done = true; flag = 1; }
     if (done) {
       if (lane == 0) {
-        pb.S_out[w] = S;
+        pb.S_out[w] = wa.score();
         pb.K_out[w] = static_cast<int32_t>(k);
         pb.flag_out[w] = flag;
       }
@@ -287,19 +368,19 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
       continue;
     }
     // ---- radius and weights -------------------------------------------------
-    const T rgeo = T(pb.rho_geo);
-    const T r = T(pb.theta) * (dG < rgeo ? dG : rgeo);
-    const T a = T(pb.sqrt_sigma) * r;
+    const T r = theta_t * (dG < rgeo_t ? dG : rgeo_t);
+    const T a = sqs_t * r;
     if (r != r_prev) {
-      if constexpr (sizeof(T) == 8) {
+      if constexpr (kF64) {
         law = green_law(n, a);
-        c = law.c;
-        omega = law.omc / pb.sigma;
+        wa.set(law.c, law.omc / pb.sigma);
+      } else if (!pb.em1_fp64) {
+        wa.set_from_em1(em1_poly32(pb, 0.25f * a * a), inv_sigma_f);
       } else {
         const double ad = static_cast<double>(a);
         const double em1 = em1_series(0.5 * static_cast<double>(n - 2), 0.25 * (ad * ad));
-        c = 1.0 / (1.0 + em1);
-        omega = one_minus_c(em1, c) / pb.sigma;
+        const double cc = 1.0 / (1.0 + em1);
+        wa.set(cc, one_minus_c(em1, cc) / pb.sigma);
       }
       r_prev = r;
     }
@@ -308,73 +389,57 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
     T F = T(0);
     for (int l = 0; l < nv; ++l) {
       T t;
-      {
-        T U;
-        if constexpr (G == 2) {
-          const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l), kk, wi, p, k0, k1);
-          U = u53(bu.x, bu.y);
-          const double guess = table_lookup<double>(pb.tab64, pb.NA, pb.NS, pb.z_max, a, s_of_u64(U));
-          t = green_invert64(law, U, guess);
-        } else {
-          const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l >> 2), kk, wi,
-                                      p, k0, k1);
-          const int s4 = l & 3;
-          U = u24(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
-          t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, s_of_u32(U));
-          t = fminf(fmaxf(t, 0.0f), 1.0f);
-        }
-      }
-      gen_vector<T>(g, n, lane, nb * static_cast<uint32_t>(1 + l), kk, wi, p, k0, k1);
-      if constexpr (MK == kEmbeddedSphere) {
-        T qg[DQ];
-        qt_times<T, DQ>(pb, QT, g, lane, D, qg);
-        T gg = T(0);
-#pragma unroll
-        for (int q = 0; q < L; ++q) gg += g[q] * g[q];
-        gg = fmax(warp_sum1(gg), T(1e-30));
-        const T zs = (r * t) / sqrt(gg);
-        T qgj = T(0);
-#pragma unroll
-        for (int j = 0; j < DQ; ++j)
-          if (j == lane) qgj = qg[j];
-        T zj = lane < D ? sj + zs * qgj : T(0);
-        const T zn = sqrt(warp_sum1(zj * zj));
-        F += sphere_quad_at<T>(pb, pb.f, zj / zn, lane, D);
+      if constexpr (kF64) {
+        const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l), kk, wi, p, K);
+        const double U = u53(bu.x, bu.y);
+        const double guess = table_lookup<double>(pb.tab64, pb.NA, pb.NS, pb.z_max, a, U);
+        t = green_invert64(law, U, guess);
       } else {
-        T gg = T(0);
+        const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l >> 2), kk, wi, p, K);
+        const int s4 = l & 3;
+        const float U = u23(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
+        t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, U);
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+      }
+      gen_vector<T>(g, n, lane, nb * static_cast<uint32_t>(1 + l), kk, wi, p, K);
+      if constexpr (MK == kEmbeddedSphere) {
+        T gg;
+        const T qgj = qt_times<T, DQ>(QT, npad, g, n, lane, D, gg);
+        const T zs = (r * t) / sqrt(fmax(gg, T(1e-30)));
+        const T zj = lane < D ? sj + zs * qgj : T(0);
+        const T zn = sqrt(warp_sum1(zj * zj));
+        F += sphere_quad_at<T>(pb, pb.f, vT, AT, zj / zn, lane, D);
+      } else {
+        T acc[2] = {T(0), T(0)};
 #pragma unroll
-        for (int q = 0; q < L; ++q) gg += g[q] * g[q];
-        gg = fmax(warp_sum1(gg), T(1e-30));
-        const T zs = (r * t) / sqrt(gg);
+        for (int q = 0; q < L; ++q) { acc[0] += g[q] * g[q]; acc[1] += Y[q] * g[q]; }
+        warp_sum<2>(acc);
+        const T zs = (r * t) / sqrt(fmax(acc[0], T(1e-30)));
         T inv = T(1);
-        if (MK == kSphere) {
-          T zz = T(0);
+        if constexpr (MK == kSphere) {
+          if constexpr (kF64) {
+            T zz = T(0);
 #pragma unroll
-          for (int q = 0; q < L; ++q) { const T zq = Y[q] + zs * g[q]; zz += zq * zq; }
-          inv = T(1) / sqrt(warp_sum1(zz));
+            for (int q = 0; q < L; ++q) { const T zq = Y[q] + zs * g[q]; zz += zq * zq; }
+            inv = T(1) / sqrt(warp_sum1(zz));
+          } else {
+            inv = rsqrtf(yy + zs * (T(2) * acc[1] + zs * acc[0]));
+          }
         }
-        if (pb.f.kind == kPoly) F += poly_at<T, L>(pb.f, Y, g, zs, inv, true, G);
+        if (pb.f.kind == kPoly) F += poly_at<T, L, G>(pb.f, Y, g, zs, inv);
       }
     }
     if (nv > 1) F /= T(nv);
     // ---- Theta = Y + r g/|g|, Y = cp(Theta) --------------------------------------
-    gen_vector<T>(g, n, lane, 0u, kk, wi, p, k0, k1);
+    gen_vector<T>(g, n, lane, 0u, kk, wi, p, K);
     if constexpr (MK == kEmbeddedSphere) {
-      T qg[DQ];
-      qt_times<T, DQ>(pb, QT, g, lane, D, qg);
-      T gg = T(0);
-#pragma unroll
-      for (int q = 0; q < L; ++q) gg += g[q] * g[q];
-      gg = fmax(warp_sum1(gg), T(1e-30));
-      const T sc = r / sqrt(gg);
-      T qgj = T(0);
-#pragma unroll
-      for (int j = 0; j < DQ; ++j)
-        if (j == lane) qgj = qg[j];
-      T tj = lane < D ? sj + sc * qgj : T(0);
+      T gg;
+      const T qgj = qt_times<T, DQ>(QT, npad, g, n, lane, D, gg);
+      const T sc = r / sqrt(fmax(gg, T(1e-30)));
+      const T tj = lane < D ? sj + sc * qgj : T(0);
       const T tn = sqrt(warp_sum1(tj * tj));
       sj = tj / tn;
-    } else {
+    } else if constexpr (kF64) {
       T gg = T(0);
 #pragma unroll
       for (int q = 0; q < L; ++q) gg += g[q] * g[q];
@@ -383,24 +448,51 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
 #pragma unroll
       for (int q = 0; q < L; ++q) Y[q] = Y[q] + sc * g[q];
       if (MK == kSphere) {
-        T yy = T(0);
+        T ys = T(0);
 #pragma unroll
-        for (int q = 0; q < L; ++q) yy += Y[q] * Y[q];
-        const T yn = sqrt(warp_sum1(yy));
+        for (int q = 0; q < L; ++q) ys += Y[q] * Y[q];
+        const T yn = sqrt(warp_sum1(ys));
 #pragma unroll
         for (int q = 0; q < L; ++q) Y[q] = Y[q] / yn;
       }
+    } else {
+      // FP32: one reduction gives |g|^2, Y.g and e.g; the updated e.Y and |Y|^2
+      // follow without another pass.
+      T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int m = 0; m < MB; ++m)
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          const T gq = g[G * m + q];
+          acc[0] += gq * gq;
+          acc[1] += Y[G * m + q] * gq;
+          if (bnd) {
+            const int cc = G * (lane + 32 * m) + q;
+            acc[2] += gq * (cc < n ? eT[cc] : T(0));
+          }
+        }
+      warp_sum<3>(acc);
+      const T sc = r * rsqrtf(fmaxf(acc[0], 1e-30f));
+      T inv = T(1);
+      const T tt = yy + sc * (T(2) * acc[1] + sc * acc[0]);
+      if (MK == kSphere) inv = rsqrtf(tt);
+#pragma unroll
+      for (int q = 0; q < L; ++q) Y[q] = (Y[q] + sc * g[q]) * inv;
+      al = (al + sc * acc[2]) * inv;
+      yy = tt * inv * inv;
     }
-    S += (W * omega) * static_cast<double>(F);
-    W *= c;
+    wa.add_step(F);
     ++k;
   }
 }
 
-template <int MK>
-__global__ void __launch_bounds__(128) walkn_f64_kernel(const DevProblem pb) { walkn_body<double, MK>(pb); }
+template <int MK, int DQ>
+__global__ void __launch_bounds__(128) walkn_f64_kernel(const DevProblem pb) { walkn_body<double, MK, DQ>(pb); }
 
-template <int MK>
-__global__ void __launch_bounds__(128) walkn_f32_kernel(const DevProblem pb) { walkn_body<float, MK>(pb); }
+template <int MK, int DQ>
+__global__ void __launch_bounds__(128, 4) walkn_f32_kernel(const DevProblem pb) { walkn_body<float, MK, DQ>(pb); }
+
+// Embedded-sphere dimension bucket (d + 1 <= DQ).
+inline int walkn_dq(int D) { return D <= 8 ? 8 : (D <= 16 ? 16 : (D <= 24 ? 24 : 32)); }
 
 }  // namespace mpwos
