@@ -46,6 +46,11 @@ extern "C" {
 #define MPWOS_SPHERE 1            /* unit sphere S^{n-1} in R^n, cp(x) = x/|x|    */
 #define MPWOS_TORUS 2             /* torus in R^3, centre radius R, tube radius a */
 #define MPWOS_EMBEDDED_SPHERE 3   /* Q S^d + b, Q (n x (d+1)) orthonormal columns */
+#define MPWOS_POINT_CLOUD 4       /* closed surface in R^3 given by points (Sec. 2.1 (iii)) */
+
+/* ---- closest point on a point cloud ------------------------------------ */
+#define MPWOS_CLOUD_CP_FIT 0      /* k nearest, PCA plane, quadratic height fit, projection */
+#define MPWOS_CLOUD_CP_NEAREST 1  /* nearest cloud point                                    */
 
 /* ---- function kinds for f and g (a C ABI cannot pass device code) ------- */
 #define MPWOS_FUNC_POLY 0          /* sum_t coef_t prod_j x[var]^pw (ambient coords)  */
@@ -59,7 +64,12 @@ extern "C" {
 typedef struct mpwos_ctx mpwos_ctx;
 
 /* Manifold M (Sec. 2.1).  Q, b are host arrays (embedded sphere only),
- * Q row-major n x (d+1) with orthonormal columns; copied at the call. */
+ * Q row-major n x (d+1) with orthonormal columns; copied at the call.
+ * Point cloud (n = 3, d = 2, closed problems): n_cloud x 3 host array; the
+ * context builds a search grid on first use and caches it by (pointer, size,
+ * k_nn, contents checksum) — keep the array unchanged while it is cached.
+ * rho_geo(y) = c_h h(y), h(y) the mean distance from y to its k_nn nearest
+ * cloud points (eq. rho_geo_spacing); cp by cp_mode. */
 typedef struct {
   int kind;
   int n;            /* ambient dimension                                  */
@@ -67,6 +77,11 @@ typedef struct {
   double R, a;      /* torus: centre-circle radius, tube radius           */
   const double* Q;  /* embedded sphere                                    */
   const double* b;  /* embedded sphere shift, length n                    */
+  const double* cloud;  /* point cloud, n_cloud x 3                       */
+  int64_t n_cloud;
+  int k_nn;         /* 1 .. 32                                            */
+  double c_h;
+  int cp_mode;      /* MPWOS_CLOUD_CP_FIT or MPWOS_CLOUD_CP_NEAREST        */
 } mpwos_manifold_desc;
 
 /* A function on M given as a small closed family of device-evaluable forms.
@@ -157,7 +172,8 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
  *   - pts (P x n) and the three outputs must be DEVICE pointers (EINVAL
  *     otherwise); problem data are host pointers as for mpwos_solve;
  *   - P * N must not exceed mpwos_noalloc_max_walks() (EINVAL with the limit
- *     in the message); EMBEDDED_SPHERE is not supported (EINVAL);
+ *     in the message); EMBEDDED_SPHERE and POINT_CLOUD are not supported
+ *     (EINVAL);
  *   - the first call on a device looks up the array's device address; make
  *     that first call before any stream capture;
  *   - every call shares the array: calls that overlap on the GPU (other

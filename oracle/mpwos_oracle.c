@@ -262,6 +262,8 @@ static double dot(const double* a, const double* b, int n) {
   return s;
 }
 
+static void cloud_cp(const orc_manifold* m, const double* x, double* out);
+
 void orc_cp(const orc_manifold* m, const double* x, double* out) {
   int n = m->n;
   if (m->kind == ORC_EUCLID) {
@@ -277,6 +279,8 @@ void orc_cp(const orc_manifold* m, const double* x, double* out) {
     double nw = sqrt(dot(w, w, 3));
     double s = m->a / nw;
     for (int i = 0; i < 3; ++i) out[i] = c[i] + s * w[i];
+  } else if (m->kind == ORC_POINT_CLOUD) {
+    cloud_cp(m, x, out);
   } else { /* embedded unit sphere: cp(x) = Q normalize(Q^T (x - b)) + b */
     int D = m->d + 1;
     double* s = (double*)malloc(sizeof(double) * (size_t)D);
@@ -294,6 +298,150 @@ void orc_cp(const orc_manifold* m, const double* x, double* out) {
     }
     free(s);
   }
+}
+
+/* ---- point cloud (Sec. 2.1 representation (iii); eq. rho_geo_spacing) ---- */
+/* k nearest cloud points of x by brute force, ordered by (distance^2, index);
+ * returns h(x), the mean distance to them. */
+double orc_cloud_knn(const orc_manifold* m, const double* x, int64_t* idx, double* d2) {
+  int k = m->k_nn;
+  for (int j = 0; j < k; ++j) { d2[j] = INFINITY; idx[j] = -1; }
+  for (int64_t i = 0; i < m->n_cloud; ++i) {
+    const double* p = m->cloud + 3 * i;
+    double dx = p[0] - x[0], dy = p[1] - x[1], dz = p[2] - x[2];
+    double dd = dx * dx + dy * dy + dz * dz;
+    if (dd < d2[k - 1]) {
+      int j = k - 1;
+      while (j > 0 && d2[j - 1] > dd) { d2[j] = d2[j - 1]; idx[j] = idx[j - 1]; --j; }
+      d2[j] = dd;
+      idx[j] = i;
+    }
+  }
+  double h = 0.0;
+  for (int j = 0; j < k; ++j) h += sqrt(d2[j]);
+  return h / (double)k;
+}
+
+/* Eigen-decomposition of a symmetric 3x3 matrix by cyclic Jacobi rotations;
+ * V's columns are the eigenvectors. */
+static void jacobi3(double A[3][3], double lam[3], double V[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = fabs(A[0][1]) + fabs(A[0][2]) + fabs(A[1][2]);
+    if (off < 1e-300) break;
+    for (int p = 0; p < 2; ++p)
+      for (int q = p + 1; q < 3; ++q) {
+        if (A[p][q] == 0.0) continue;
+        double th = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+        double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < 3; ++r) {          /* A <- A J */
+          double arp = A[r][p], arq = A[r][q];
+          A[r][p] = c * arp - s * arq;
+          A[r][q] = s * arp + c * arq;
+        }
+        for (int r = 0; r < 3; ++r) {          /* A <- J^T A */
+          double apr = A[p][r], aqr = A[q][r];
+          A[p][r] = c * apr - s * aqr;
+          A[q][r] = s * apr + c * aqr;
+        }
+        for (int r = 0; r < 3; ++r) {          /* V <- V J */
+          double vrp = V[r][p], vrq = V[r][q];
+          V[r][p] = c * vrp - s * vrq;
+          V[r][q] = s * vrp + c * vrq;
+        }
+      }
+  }
+  for (int i = 0; i < 3; ++i) lam[i] = A[i][i];
+}
+
+/* Solve the n x n system M a = b by Gaussian elimination with partial pivoting. */
+static void gauss_solve(int n, double M[6][6], double b[6], double a[6]) {
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
+    if (piv != c) {
+      for (int j = 0; j < n; ++j) { double t = M[c][j]; M[c][j] = M[piv][j]; M[piv][j] = t; }
+      double t = b[c]; b[c] = b[piv]; b[piv] = t;
+    }
+    for (int r = c + 1; r < n; ++r) {
+      double f = M[r][c] / M[c][c];
+      for (int j = c; j < n; ++j) M[r][j] -= f * M[c][j];
+      b[r] -= f * b[c];
+    }
+  }
+  for (int r = n - 1; r >= 0; --r) {
+    double s = b[r];
+    for (int j = r + 1; j < n; ++j) s -= M[r][j] * a[j];
+    a[r] = s / M[r][r];
+  }
+}
+
+/* cp on a point cloud: the k nearest points, their PCA plane at the centroid
+ * (normal = eigenvector of the smallest covariance eigenvalue), an unweighted
+ * least-squares quadratic height z = a0 + a1 u + a2 v + a3 u^2 + a4 uv + a5 v^2
+ * in plane coordinates scaled by h(x), and the projection of x onto that graph:
+ * the vertical foot point plus one Newton step on the squared distance.
+ * Nearest mode: the nearest cloud point. */
+static void cloud_cp(const orc_manifold* m, const double* x, double* out) {
+  int k = m->k_nn;
+  int64_t idx[64];
+  double d2[64];
+  double h = orc_cloud_knn(m, x, idx, d2);
+  if (m->cp_mode == ORC_CP_NEAREST) {
+    for (int i = 0; i < 3; ++i) out[i] = m->cloud[3 * idx[0] + i];
+    return;
+  }
+  double c[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < 3; ++i) c[i] += m->cloud[3 * idx[j] + i];
+  for (int i = 0; i < 3; ++i) c[i] /= (double)k;
+  double C[3][3] = {{0}};
+  for (int j = 0; j < k; ++j) {
+    double d[3];
+    for (int i = 0; i < 3; ++i) d[i] = m->cloud[3 * idx[j] + i] - c[i];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) C[a][b] += d[a] * d[b];
+  }
+  double lam[3], V[3][3];
+  jacobi3(C, lam, V);
+  int imin = 0, imax = 0;
+  for (int i = 1; i < 3; ++i) {
+    if (lam[i] < lam[imin]) imin = i;
+    if (lam[i] > lam[imax]) imax = i;
+  }
+  double nrm[3] = {V[0][imin], V[1][imin], V[2][imin]};
+  double u[3] = {V[0][imax], V[1][imax], V[2][imax]};
+  double v[3] = {nrm[1] * u[2] - nrm[2] * u[1], nrm[2] * u[0] - nrm[0] * u[2], nrm[0] * u[1] - nrm[1] * u[0]};
+  double s = h > 0.0 ? h : 1.0;
+  double M[6][6] = {{0}}, rhs[6] = {0}, a[6];
+  for (int j = 0; j < k; ++j) {
+    double d[3];
+    for (int i = 0; i < 3; ++i) d[i] = (m->cloud[3 * idx[j] + i] - c[i]) / s;
+    double xi = dot(d, u, 3), et = dot(d, v, 3), ze = dot(d, nrm, 3);
+    double row[6] = {1.0, xi, et, xi * xi, xi * et, et * et};
+    for (int p = 0; p < 6; ++p) {
+      rhs[p] += row[p] * ze;
+      for (int q = 0; q < 6; ++q) M[p][q] += row[p] * row[q];
+    }
+  }
+  gauss_solve(6, M, rhs, a);
+  double d[3];
+  for (int i = 0; i < 3; ++i) d[i] = (x[i] - c[i]) / s;
+  double xi0 = dot(d, u, 3), et0 = dot(d, v, 3), ze0 = dot(d, nrm, 3);
+  double hz = a[0] + a[1] * xi0 + a[2] * et0 + a[3] * xi0 * xi0 + a[4] * xi0 * et0 + a[5] * et0 * et0;
+  double hx = a[1] + 2.0 * a[3] * xi0 + a[4] * et0;
+  double hy = a[2] + a[4] * xi0 + 2.0 * a[5] * et0;
+  double e = hz - ze0;
+  double g0 = e * hx, g1 = e * hy;
+  double H00 = 1.0 + hx * hx + e * 2.0 * a[3], H01 = hx * hy + e * a[4], H11 = 1.0 + hy * hy + e * 2.0 * a[5];
+  double det = H00 * H11 - H01 * H01;
+  double xi1 = xi0 - (H11 * g0 - H01 * g1) / det;
+  double et1 = et0 - (H00 * g1 - H01 * g0) / det;
+  double z1 = a[0] + a[1] * xi1 + a[2] * et1 + a[3] * xi1 * xi1 + a[4] * xi1 * et1 + a[5] * et1 * et1;
+  for (int i = 0; i < 3; ++i) out[i] = c[i] + s * (xi1 * u[i] + et1 * v[i] + z1 * nrm[i]);
 }
 
 static double kappa_of(const orc_manifold* m) {
@@ -460,7 +608,14 @@ static int run_walk(const orc_manifold* m, const orc_problem* pb, const orc_para
       break;
     }
     if (k >= pr->max_steps) { flag = 1; break; }
-    double rgeo = pr->c_kappa / (1.0 + kappa_of(m));
+    double rgeo;
+    if (m->kind == ORC_POINT_CLOUD) {
+      int64_t idx[64];
+      double d2[64];
+      rgeo = m->c_h * orc_cloud_knn(m, w->Y, idx, d2);   /* eq. rho_geo_spacing */
+    } else {
+      rgeo = pr->c_kappa / (1.0 + kappa_of(m));
+    }
     double r = pr->theta * (dG < rgeo ? dG : rgeo);
     double a = sqs * r;
     double em1 = orc_em1(n, a);

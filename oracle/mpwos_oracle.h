@@ -25,7 +25,8 @@
 extern "C" {
 #endif
 
-enum { ORC_EUCLID = 0, ORC_SPHERE = 1, ORC_TORUS = 2, ORC_EMBEDDED_SPHERE = 3 };
+enum { ORC_EUCLID = 0, ORC_SPHERE = 1, ORC_TORUS = 2, ORC_EMBEDDED_SPHERE = 3, ORC_POINT_CLOUD = 4 };
+enum { ORC_CP_FIT = 0, ORC_CP_NEAREST = 1 };
 enum { ORC_POLY = 0, ORC_TORUS_FOURIER = 1, ORC_SPHERE_QUAD = 2 };
 
 typedef struct {
@@ -33,6 +34,11 @@ typedef struct {
   double R, a;            /* torus: centre-circle radius, tube radius          */
   const double* Q;        /* embedded sphere: n x (d+1) row-major, orthonormal */
   const double* b;        /* embedded sphere: shift, length n                  */
+  const double* cloud;    /* point cloud: n_cloud x 3                          */
+  int64_t n_cloud;
+  int k_nn;               /* neighbours for h(y) and the local fit             */
+  double c_h;             /* rho_geo = c_h h(y) (eq. rho_geo_spacing)          */
+  int cp_mode;            /* ORC_CP_FIT or ORC_CP_NEAREST                      */
 } orc_manifold;
 
 typedef struct {
@@ -82,6 +88,8 @@ void   orc_cp(const orc_manifold* m, const double* x, double* out);
 double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
                        const double* y, double* y_gamma);
 double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, const double* x);
+/* point cloud: k nearest (by distance^2, then index), mean distance h(x) */
+double orc_cloud_knn(const orc_manifold* m, const double* x, int64_t* idx, double* d2);
 
 /* the walk: per-walk score S, stopping index K, flag (1 = hit max_steps) */
 int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,

@@ -11,7 +11,7 @@ from .build import build
 
 __all__ = ["lib", "philox", "u53", "gaussians", "em1", "c_sigma_r", "green_cdf", "green_cdf_inv",
            "kt_minus_one", "cp", "delta_gamma", "func_eval", "walk_scores", "solve", "trace",
-           "OracleProblem"]
+           "OracleProblem", "cloud_knn"]
 
 _lib: Optional[C.CDLL] = None
 
@@ -21,7 +21,8 @@ _ip = C.POINTER(C.c_int)
 
 class _Manifold(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int), ("d", C.c_int), ("R", C.c_double),
-                ("a", C.c_double), ("Q", _dp), ("b", _dp)]
+                ("a", C.c_double), ("Q", _dp), ("b", _dp), ("cloud", _dp), ("n_cloud", C.c_int64),
+                ("k_nn", C.c_int), ("c_h", C.c_double), ("cp_mode", C.c_int)]
 
 
 class _Func(C.Structure):
@@ -68,6 +69,7 @@ def lib() -> C.CDLL:
         L.orc_delta_gamma.restype = C.c_double
         L.orc_func_eval.restype = C.c_double
         L.orc_trace.restype = C.c_int64
+        L.orc_cloud_knn.restype = C.c_double
         _lib = L
     return _lib
 
@@ -92,6 +94,13 @@ class OracleProblem:
             b = self._arr(m.b)
             self.man.Q = _dptr(Q)
             self.man.b = _dptr(b)
+        if m.cloud is not None:
+            cl = self._arr(m.cloud)
+            self.man.cloud = _dptr(cl)
+            self.man.n_cloud = cl.shape[0]
+            self.man.k_nn = m.k_nn
+            self.man.c_h = m.c_h
+            self.man.cp_mode = m.cp_mode
         self.prob = _Problem(sigma=problem.sigma, closed=int(problem.closed),
                              bnd_offset=problem.bnd_offset)
         if problem.bnd_normal is not None:
@@ -183,6 +192,16 @@ def delta_gamma(op: OracleProblem, y):
     yg = np.zeros_like(y)
     d = lib().orc_delta_gamma(C.byref(op.man), C.byref(op.prob), C.byref(op.params), _dptr(y), _dptr(yg))
     return d, yg
+
+
+def cloud_knn(op: OracleProblem, x):
+    """k nearest cloud points of x (indices ordered by distance^2, then index) and h(x)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    k = op.man.k_nn
+    idx = np.zeros(k, dtype=np.int64)
+    d2 = np.zeros(k)
+    h = lib().orc_cloud_knn(C.byref(op.man), _dptr(x), idx.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(d2))
+    return idx, d2, h
 
 
 def func_eval(op: OracleProblem, which: str, x):

@@ -35,7 +35,8 @@ class MpwosError(RuntimeError):
 
 class ManifoldDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int), ("d", C.c_int), ("R", C.c_double), ("a", C.c_double),
-                ("Q", _dp), ("b", _dp)]
+                ("Q", _dp), ("b", _dp), ("cloud", _dp), ("n_cloud", C.c_int64), ("k_nn", C.c_int),
+                ("c_h", C.c_double), ("cp_mode", C.c_int)]
 
 
 class Func(C.Structure):
@@ -127,6 +128,15 @@ class _Marshal:
         if m.Q is not None:
             md.Q = self.arr(m.Q).ctypes.data_as(_dp)
             md.b = self.arr(m.b).ctypes.data_as(_dp)
+        if m.cloud is not None:
+            # the same host array on every call, so the context's grid cache hits
+            if not (m.cloud.flags.c_contiguous and m.cloud.dtype == np.float64):
+                m.cloud = np.ascontiguousarray(m.cloud, dtype=np.float64)
+            md.cloud = m.cloud.ctypes.data_as(_dp)
+            md.n_cloud = m.cloud.shape[0]
+            md.k_nn = m.k_nn
+            md.c_h = m.c_h
+            md.cp_mode = m.cp_mode
         pd = ProblemDesc(sigma=problem.sigma, closed=int(problem.closed), bnd_offset=problem.bnd_offset)
         if problem.bnd_normal is not None:
             pd.bnd_normal = self.arr(problem.bnd_normal).ctypes.data_as(_dp)

@@ -10,7 +10,7 @@ constexpr int kMaxTerms = 32;       // terms of a POLY / TORUS function
 constexpr int kMaxPolyFactors = 64; // total (var, pow) factors of a POLY
 constexpr int kMaxQuadDim = 32;     // d + 1 of a SPHERE_QUAD / embedded sphere
 
-enum ManifoldKind : int { kEuclid = 0, kSphere = 1, kTorus = 2, kEmbeddedSphere = 3 };
+enum ManifoldKind : int { kEuclid = 0, kSphere = 1, kTorus = 2, kEmbeddedSphere = 3, kPointCloud = 4 };
 enum FuncKind : int { kPoly = 0, kTorusFourier = 1, kSphereQuad = 2 };
 
 // A function on M (f or g), copied by value into the kernel parameters.
@@ -37,6 +37,18 @@ struct DevProblem {
   const double* b;
   const float* Qf;
   const float* bf;
+  // point cloud: points sorted by grid cell (xyz interleaved), original
+  // indices, cell start offsets (cells + 1), grid origin / cell size / dims
+  const double* cl_pts64;
+  const float* cl_pts32;
+  const int* cl_orig;
+  const int* cl_start;
+  double cl_origin[3];
+  double cl_cell;
+  int cl_dims[3];
+  int cl_k;          // neighbours (k_nn)
+  double cl_c_h;     // rho_geo = c_h h(y)
+  int cl_mode;       // 0: quadratic fit projection, 1: nearest point
   // problem
   double sigma, sqrt_sigma;
   int closed;

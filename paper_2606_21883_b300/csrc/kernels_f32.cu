@@ -7,14 +7,25 @@
 
 namespace mpwos {
 
-cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+static const void* walk3_f32_fn(const DevProblem& pb) {
   switch (pb.mkind) {
-    case kEuclid: walk3_f32_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
-    case kSphere: walk3_f32_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
-    case kTorus: walk3_f32_kernel<kTorus><<<grid, block, 0, st>>>(pb); break;
-    default: return cudaErrorInvalidValue;
+    case kEuclid: return reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid, 1>);
+    case kSphere: return reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1>);
+    case kTorus: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1>);
+    case kPointCloud:
+      return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f32_kernel<kPointCloud, 8>)
+           : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_kernel<kPointCloud, 16>)
+                           : reinterpret_cast<const void*>(walk3_f32_kernel<kPointCloud, 32>);
+    default: return nullptr;
   }
-  return cudaGetLastError();
+}
+
+cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  const void* fn = walk3_f32_fn(pb);
+  if (!fn) return cudaErrorInvalidValue;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
 }
 
 static const void* walkn_f32_fn(const DevProblem& pb) {
@@ -39,9 +50,7 @@ int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
   int nb = 0;
   const void* fn = nullptr;
   if (n3) {
-    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid>)
-       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walk3_f32_kernel<kSphere>)
-                             : reinterpret_cast<const void*>(walk3_f32_kernel<kTorus>);
+    fn = walk3_f32_fn(pb);
   } else {
     fn = walkn_f32_fn(pb);
   }

@@ -4,6 +4,7 @@
 #include "launch.h"
 #include "walk3.cuh"
 #include "walkn.cuh"
+#include "cloud.cuh"
 
 namespace mpwos {
 
@@ -121,14 +122,25 @@ cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flag
 // ---------------------------------------------------------------------------
 // FP64 walks
 // ---------------------------------------------------------------------------
-cudaError_t launch_walk3_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+static const void* walk3_f64_fn(const DevProblem& pb) {
   switch (pb.mkind) {
-    case kEuclid: walk3_f64_kernel<kEuclid><<<grid, block, 0, st>>>(pb); break;
-    case kSphere: walk3_f64_kernel<kSphere><<<grid, block, 0, st>>>(pb); break;
-    case kTorus: walk3_f64_kernel<kTorus><<<grid, block, 0, st>>>(pb); break;
-    default: return cudaErrorInvalidValue;
+    case kEuclid: return reinterpret_cast<const void*>(walk3_f64_kernel<kEuclid, 1>);
+    case kSphere: return reinterpret_cast<const void*>(walk3_f64_kernel<kSphere, 1>);
+    case kTorus: return reinterpret_cast<const void*>(walk3_f64_kernel<kTorus, 1>);
+    case kPointCloud:
+      return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f64_kernel<kPointCloud, 8>)
+           : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f64_kernel<kPointCloud, 16>)
+                           : reinterpret_cast<const void*>(walk3_f64_kernel<kPointCloud, 32>);
+    default: return nullptr;
   }
-  return cudaGetLastError();
+}
+
+cudaError_t launch_walk3_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  const void* fn = walk3_f64_fn(pb);
+  if (!fn) return cudaErrorInvalidValue;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
 }
 
 static const void* walkn_f64_fn(const DevProblem& pb) {
@@ -153,9 +165,7 @@ int occupancy_walk_f64(const DevProblem& pb, bool n3, int block) {
   int nb = 0;
   const void* fn = nullptr;
   if (n3) {
-    fn = pb.mkind == kEuclid ? reinterpret_cast<const void*>(walk3_f64_kernel<kEuclid>)
-       : pb.mkind == kSphere ? reinterpret_cast<const void*>(walk3_f64_kernel<kSphere>)
-                             : reinterpret_cast<const void*>(walk3_f64_kernel<kTorus>);
+    fn = walk3_f64_fn(pb);
   } else {
     fn = walkn_f64_fn(pb);
   }
@@ -232,6 +242,96 @@ cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const do
   const int block = 128;
   intrinsic_start_kernel<<<static_cast<unsigned>((P * 32 + block - 1) / block), block, 0, st>>>(pts, QT, b, n, npad,
                                                                                                D, P, s0);
+  return cudaGetLastError();
+}
+
+}  // namespace mpwos
+
+// ---------------------------------------------------------------------------
+// Point-cloud grid: cell of each point, counts, exclusive scan, scatter into
+// cell order (original index kept), and h(p) at every cloud point (its max
+// sets the radius-table range).
+// ---------------------------------------------------------------------------
+namespace mpwos {
+
+__global__ void cloud_cell_kernel(const double* pts, int64_t N, double ox, double oy, double oz, double cs, int gx,
+                                  int gy, int gz, int* cell, int* counts) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  int c[3];
+  const double o[3] = {ox, oy, oz};
+  const int g[3] = {gx, gy, gz};
+  for (int a = 0; a < 3; ++a) {
+    int ci = static_cast<int>(floor((pts[3 * i + a] - o[a]) / cs));
+    c[a] = ci < 0 ? 0 : (ci >= g[a] ? g[a] - 1 : ci);
+  }
+  const int id = (c[2] * gy + c[1]) * gx + c[0];
+  cell[i] = id;
+  atomicAdd(&counts[id], 1);
+}
+
+// Exclusive scan of counts (ncells) into start (ncells + 1), one block.
+__global__ void cloud_scan_kernel(const int* counts, int ncells, int* start) {
+  __shared__ int partial[1024];
+  const int t = threadIdx.x, T = blockDim.x;
+  const int per = (ncells + T - 1) / T;
+  const int b = t * per, e = min(ncells, b + per);
+  int s = 0;
+  for (int q = b; q < e; ++q) s += counts[q];
+  partial[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    int run = 0;
+    for (int q = 0; q < T; ++q) { const int v = partial[q]; partial[q] = run; run += v; }
+    start[ncells] = run;
+  }
+  __syncthreads();
+  int run = partial[t];
+  for (int q = b; q < e; ++q) { start[q] = run; run += counts[q]; }
+}
+
+__global__ void cloud_scatter_kernel(const double* pts, int64_t N, const int* cell, const int* start, int* cursor,
+                                     double* spts64, float* spts32, int* orig) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int id = cell[i];
+  const int pos = start[id] + atomicAdd(&cursor[id], 1);
+  for (int a = 0; a < 3; ++a) {
+    spts64[3 * pos + a] = pts[3 * i + a];
+    spts32[3 * pos + a] = static_cast<float>(pts[3 * i + a]);
+  }
+  orig[pos] = static_cast<int>(i);
+}
+
+template <int KM>
+__global__ void cloud_hmax_kernel(const DevProblem pb, int64_t N, unsigned long long* hmax_bits) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= N) return;
+  const double x[3] = {pb.cl_pts64[3 * q], pb.cl_pts64[3 * q + 1], pb.cl_pts64[3 * q + 2]};
+  Knn<double, KM> R;
+  const double h = cloud_knn<double, KM>(pb, x, R);
+  atomicMax(hmax_bits, static_cast<unsigned long long>(__double_as_longlong(h)));
+}
+
+cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[3], double cs, const int dims[3],
+                              int* cell, int* counts, int* start, int* cursor, double* spts64, float* spts32,
+                              int* orig, cudaStream_t st) {
+  const int ncells = dims[0] * dims[1] * dims[2];
+  cudaMemsetAsync(counts, 0, sizeof(int) * ncells, st);
+  cudaMemsetAsync(cursor, 0, sizeof(int) * ncells, st);
+  const unsigned grid = static_cast<unsigned>((N + 255) / 256);
+  cloud_cell_kernel<<<grid, 256, 0, st>>>(pts, N, origin[0], origin[1], origin[2], cs, dims[0], dims[1], dims[2], cell,
+                                          counts);
+  cloud_scan_kernel<<<1, 1024, 0, st>>>(counts, ncells, start);
+  cloud_scatter_kernel<<<grid, 256, 0, st>>>(pts, N, cell, start, cursor, spts64, spts32, orig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cloud_hmax(const DevProblem& pb, int64_t N, unsigned long long* hmax_bits, cudaStream_t st) {
+  const unsigned grid = static_cast<unsigned>((N + 127) / 128);
+  if (pb.cl_k <= 8) cloud_hmax_kernel<8><<<grid, 128, 0, st>>>(pb, N, hmax_bits);
+  else if (pb.cl_k <= 16) cloud_hmax_kernel<16><<<grid, 128, 0, st>>>(pb, N, hmax_bits);
+  else cloud_hmax_kernel<32><<<grid, 128, 0, st>>>(pb, N, hmax_bits);
   return cudaGetLastError();
 }
 

@@ -30,6 +30,12 @@ cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flag
 cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
                                float* tab32, cudaStream_t st);
 
+// Point-cloud grid (counting sort by cell) and the largest h(p) over the cloud.
+cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[3], double cs, const int dims[3],
+                              int* cell, int* counts, int* start, int* cursor, double* spts64, float* spts32,
+                              int* orig, cudaStream_t st);
+cudaError_t launch_cloud_hmax(const DevProblem& pb, int64_t N, unsigned long long* hmax_bits, cudaStream_t st);
+
 // Verification primitives.
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t count,
                           cudaStream_t st);

@@ -31,6 +31,17 @@ struct Table {
   double z_max = 0.0;
 };
 
+struct CloudGrid {
+  double* pts64 = nullptr;
+  float* pts32 = nullptr;
+  int* orig = nullptr;
+  int* start = nullptr;
+  double origin[3] = {0, 0, 0};
+  double cell = 0.0;
+  int dims[3] = {0, 0, 0};
+  double h_max = 0.0;
+};
+
 }  // namespace
 
 struct mpwos_ctx {
@@ -41,6 +52,7 @@ struct mpwos_ctx {
   std::string err;
   long long launches = 0;
   std::map<std::tuple<int, int, double>, Table> tables;  // (n, NA, z_max or a) -> table
+  std::map<std::tuple<const void*, int64_t, int, double>, CloudGrid> clouds;  // (ptr, N, k, checksum) -> grid
 };
 
 namespace {
@@ -133,6 +145,16 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       if (m->d < 1 || m->d + 1 > kMaxQuadDim - 1 || m->d + 1 > m->n) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs 1 <= d <= min(n - 1, 30)");
       if (!m->Q || !m->b) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs Q and b");
       if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE supports the closed problem only");
+      break;
+    case MPWOS_POINT_CLOUD:
+      if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD lives in R^3 (n = 3, d = 2)");
+      if (!m->cloud) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD needs cloud");
+      if (m->k_nn < 1 || m->k_nn > 32) return fail(ctx, MPWOS_EINVAL, "k_nn must lie in [1, 32]");
+      if (m->cp_mode == MPWOS_CLOUD_CP_FIT && m->k_nn < 6) return fail(ctx, MPWOS_EINVAL, "the quadratic fit needs k_nn >= 6");
+      if (m->n_cloud < m->k_nn || m->n_cloud > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "need k_nn <= n_cloud < 2^31");
+      if (!(m->c_h > 0.0)) return fail(ctx, MPWOS_EINVAL, "c_h must be > 0");
+      if (m->cp_mode != MPWOS_CLOUD_CP_FIT && m->cp_mode != MPWOS_CLOUD_CP_NEAREST) return fail(ctx, MPWOS_EINVAL, "unknown cp_mode");
+      if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD supports the closed problem only");
       break;
     default:
       return fail(ctx, MPWOS_EINVAL, "unknown manifold kind %d", m->kind);
@@ -248,6 +270,98 @@ int get_table(mpwos_ctx* ctx, int n, bool fixed, double a_or_zmax, Table** out) 
   return MPWOS_OK;
 }
 
+// The search grid of a point cloud (cached per context).
+int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
+  const int64_t N = m->n_cloud;
+  const double* P = m->cloud;
+  double chk = 0.0;
+  for (int64_t i = 0; i < N; i += (N / 64 + 1)) chk += P[3 * i] * 1.0 + P[3 * i + 1] * 3.0 + P[3 * i + 2] * 7.0;
+  chk += P[3 * (N - 1)] + P[3 * (N - 1) + 2];
+  auto key = std::make_tuple(static_cast<const void*>(P), N, m->k_nn, chk);
+  auto it = ctx->clouds.find(key);
+  if (it != ctx->clouds.end()) {
+    *out = &it->second;
+    return MPWOS_OK;
+  }
+  CloudGrid G;
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < N; ++i)
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], P[3 * i + a]);
+      hi[a] = std::max(hi[a], P[3 * i + a]);
+    }
+  // cell size ~ the k-th neighbour distance, estimated on a sample of 32 points
+  const int k = m->k_nn;
+  double rk = 0.0;
+  int ns = 0;
+  std::vector<double> best(k);
+  for (int64_t sidx = 0; sidx < N && ns < 32; sidx += std::max<int64_t>(1, N / 32), ++ns) {
+    std::fill(best.begin(), best.end(), INFINITY);
+    for (int64_t i = 0; i < N; ++i) {
+      double dd = 0.0;
+      for (int a = 0; a < 3; ++a) dd += (P[3 * i + a] - P[3 * sidx + a]) * (P[3 * i + a] - P[3 * sidx + a]);
+      if (dd < best[k - 1]) {
+        int j = k - 1;
+        while (j > 0 && best[j - 1] > dd) { best[j] = best[j - 1]; --j; }
+        best[j] = dd;
+      }
+    }
+    rk += std::sqrt(best[k - 1]);
+  }
+  double cs = 1.25 * rk / ns;
+  const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  if (!(cs > 0.0)) cs = ext > 0.0 ? ext : 1.0;
+  for (;;) {
+    for (int a = 0; a < 3; ++a) G.dims[a] = static_cast<int>(std::floor((hi[a] - lo[a]) / cs)) + 1;
+    if (static_cast<int64_t>(G.dims[0]) * G.dims[1] * G.dims[2] <= (int64_t(1) << 24)) break;
+    cs *= 1.25;
+  }
+  const int ncells = G.dims[0] * G.dims[1] * G.dims[2];
+  for (int a = 0; a < 3; ++a) G.origin[a] = lo[a];
+  G.cell = cs;
+  double* dpts = nullptr;
+  int *cell = nullptr, *counts = nullptr, *cursor = nullptr;
+  CK(cudaMalloc(&G.pts64, sizeof(double) * 3 * N));
+  CK(cudaMalloc(&G.pts32, sizeof(float) * 3 * N));
+  CK(cudaMalloc(&G.orig, sizeof(int) * N));
+  CK(cudaMalloc(&G.start, sizeof(int) * (ncells + 1)));
+  CK(cudaMalloc(&dpts, sizeof(double) * 3 * N));
+  CK(cudaMalloc(&cell, sizeof(int) * N));
+  CK(cudaMalloc(&counts, sizeof(int) * ncells));
+  CK(cudaMalloc(&cursor, sizeof(int) * ncells));
+  CK(cudaMemcpyAsync(dpts, P, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_cloud_grid(dpts, N, G.origin, cs, G.dims, cell, counts, G.start, cursor, G.pts64, G.pts32, G.orig,
+                       ctx->stream));
+  ctx->launches += 3;
+  // largest h(p) over the cloud
+  DevProblem tmp;
+  std::memset(&tmp, 0, sizeof tmp);
+  tmp.cl_pts64 = G.pts64;
+  tmp.cl_pts32 = G.pts32;
+  tmp.cl_orig = G.orig;
+  tmp.cl_start = G.start;
+  for (int a = 0; a < 3; ++a) { tmp.cl_origin[a] = G.origin[a]; tmp.cl_dims[a] = G.dims[a]; }
+  tmp.cl_cell = cs;
+  tmp.cl_k = k;
+  unsigned long long* hbits = nullptr;
+  CK(cudaMalloc(&hbits, sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(hbits, 0, sizeof(unsigned long long), ctx->stream));
+  CK(launch_cloud_hmax(tmp, N, hbits, ctx->stream));
+  ctx->launches++;
+  unsigned long long hb = 0;
+  CK(cudaMemcpyAsync(&hb, hbits, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::memcpy(&G.h_max, &hb, sizeof(double));
+  cudaFree(dpts);
+  cudaFree(cell);
+  cudaFree(counts);
+  cudaFree(cursor);
+  cudaFree(hbits);
+  auto res = ctx->clouds.emplace(key, G);
+  *out = &res.first->second;
+  return MPWOS_OK;
+}
+
 // Everything a walk launch needs, built in `sc`.
 int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpwos_problem* pr,
             const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb) {
@@ -327,15 +441,34 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
       ctx->launches++;
     }
   }
+  // point cloud grid; rho_geo varies with h(y)
+  double rho_geo_max = pb.rho_geo;
+  if (m->kind == MPWOS_POINT_CLOUD) {
+    CloudGrid* G = nullptr;
+    int rc0 = get_cloud(ctx, m, &G);
+    if (rc0) return rc0;
+    pb.cl_pts64 = G->pts64;
+    pb.cl_pts32 = G->pts32;
+    pb.cl_orig = G->orig;
+    pb.cl_start = G->start;
+    for (int a = 0; a < 3; ++a) { pb.cl_origin[a] = G->origin[a]; pb.cl_dims[a] = G->dims[a]; }
+    pb.cl_cell = G->cell;
+    pb.cl_k = m->k_nn;
+    pb.cl_c_h = m->c_h;
+    pb.cl_mode = m->cp_mode;
+    // h at an off-cloud point stays near h at its neighbours; 1.5 x max over the cloud
+    rho_geo_max = m->c_h * 1.5 * G->h_max;
+  }
   // radius tables
-  const double a_max = pb.sqrt_sigma * pb.theta * pb.rho_geo;
+  const bool fixed_radius = pr->closed && m->kind != MPWOS_POINT_CLOUD;
+  const double a_max = pb.sqrt_sigma * pb.theta * rho_geo_max;
   const double nu = 0.5 * (n - 2);
   if (n > 3 && 0.25 * a_max * a_max > 0.5 * nu)
     return fail(ctx, MPWOS_EINVAL,
                 "sigma (theta rho_geo)^2 / 4 = %g exceeds (n-2)/4 = %g: outside the series evaluation range", 0.25 * a_max * a_max, 0.5 * nu);
   fill_em1_poly(pb, n, 0.25 * a_max * a_max);
   Table* tab = nullptr;
-  int rc = pr->closed ? get_table(ctx, n, true, a_max, &tab) : get_table(ctx, n, false, 0.25 * a_max * a_max, &tab);
+  int rc = fixed_radius ? get_table(ctx, n, true, a_max, &tab) : get_table(ctx, n, false, 0.25 * a_max * a_max, &tab);
   if (rc) return rc;
   pb.tab64 = tab->tab64;
   pb.tab32 = tab->tab32;
@@ -407,6 +540,12 @@ void mpwos_destroy(mpwos_ctx* ctx) {
   for (auto& kv : ctx->tables) {
     cudaFree(kv.second.tab64);
     cudaFree(kv.second.tab32);
+  }
+  for (auto& kv : ctx->clouds) {
+    cudaFree(kv.second.pts64);
+    cudaFree(kv.second.pts32);
+    cudaFree(kv.second.orig);
+    cudaFree(kv.second.start);
   }
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
@@ -607,8 +746,8 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   CK(cudaSetDevice(ctx->device));
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
-  if (m->kind == MPWOS_EMBEDDED_SPHERE)
-    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE is not supported (use mpwos_solve)");
+  if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD)
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE and POINT_CLOUD are not supported (use mpwos_solve)");
   if (P > 0 && (!is_device_ptr(pts) || !is_device_ptr(mean) || !is_device_ptr(stderr_) || !is_device_ptr(mean_steps)))
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: pts and the three outputs must be device pointers");
   const int64_t walks = P * N;

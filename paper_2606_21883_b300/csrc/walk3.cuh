@@ -13,13 +13,42 @@
 #include "dev_common.cuh"
 #include "geom3.cuh"
 #include "green.cuh"
+#include "cloud.cuh"
 
 namespace mpwos {
 
 // FP64 walk.  Draws of step k of walk (p, i), Philox counter (j, k, i, p):
 //   Theta direction: blocks 0, 1;  Z_l direction: blocks 2(1+l), 2(1+l)+1;
 //   U_l: block 2(1+N_V) + l (words x, y);  two Gaussians per block.
-template <int MK>
+// cp(x) for any R^3 manifold (point clouds through their k-nearest fit).
+template <int MK, int KM, typename T>
+__device__ __forceinline__ void cp_any(const DevProblem& pb, const T* x, T* out) {
+  if constexpr (MK == kPointCloud) {
+    Knn<T, KM> R;
+    const T h = cloud_knn<T, KM>(pb, x, R);
+    cloud_project<T, KM>(pb, x, R, h, out);
+  } else {
+    cp3<MK, T>(pb, x, out);
+  }
+}
+
+// rho_geo at y: c_kappa/(1 + kappa) (eq. rho_geo_curvature) or c_h h(y) (eq. rho_geo_spacing).
+template <int MK, int KM, typename T>
+__device__ __forceinline__ T rho_geo_at(const DevProblem& pb, const T* y) {
+  if constexpr (MK == kPointCloud) {
+    Knn<T, KM> R;
+    return T(pb.cl_c_h) * cloud_knn<T, KM>(pb, y, R);
+  } else {
+    return T(pb.rho_geo);
+  }
+}
+
+// f constant (a POLY without variables): F needs no projection of Z.
+__device__ __forceinline__ bool source_is_constant(const DevFunc& f) {
+  return f.kind == kPoly && f.term_off[f.n_terms] == 0;
+}
+
+template <int MK, int KM>
 __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
   const int64_t total = pb.P * pb.N;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -69,7 +98,7 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
       init(w);
       continue;
     }
-    const double rgeo = pb.rho_geo;
+    const double rgeo = rho_geo_at<MK, KM, double>(pb, Y);
     const double r = pb.theta * (dG < rgeo ? dG : rgeo);
     const double a = pb.sqrt_sigma * r;
     if (r != r_prev) {
@@ -106,13 +135,17 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
       const double zs = (r * t) / zn;
       double Z[3], cZ[3];
       for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * g[q];
-      cp3<MK, double>(pb, Z, cZ);
-      F += func3<MK, double>(pb, pb.f, cZ);
+      if (MK == kPointCloud && source_is_constant(pb.f)) {
+        F += func3<MK, double>(pb, pb.f, Z);
+      } else {
+        cp_any<MK, KM, double>(pb, Z, cZ);
+        F += func3<MK, double>(pb, pb.f, cZ);
+      }
     }
     if (nv > 1) F /= static_cast<double>(nv);
     S += (W * omega) * F;
     W *= law.c;
-    cp3<MK, double>(pb, Th, Y);
+    cp_any<MK, KM, double>(pb, Th, Y);
     ++k;
   }
 }
@@ -205,8 +238,14 @@ __device__ __forceinline__ void cp3_f32(const DevProblem& pb, const float* x, fl
 }
 
 // f(cp(Z)) in FP32.
-template <int MK>
+template <int MK, int KM>
 __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* Z) {
+  if constexpr (MK == kPointCloud) {
+    if (source_is_constant(pb.f)) return func3<MK, float>(pb, pb.f, Z);
+    float cZ[3];
+    cp_any<MK, KM, float>(pb, Z, cZ);
+    return func3<MK, float>(pb, pb.f, cZ);
+  }
   if constexpr (MK == kTorus) {
     if (pb.f.kind == kTorusFourier) {
       float ct, st, cph, sph;
@@ -219,7 +258,7 @@ __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* 
   return func3<MK, float>(pb, pb.f, cZ);
 }
 
-template <int MK>
+template <int MK, int KM>
 __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
   const int64_t total = pb.P * pb.N;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -275,7 +314,9 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
       init(w);
       continue;
     }
-    const float r = theta * (dG < rgeo ? dG : rgeo);
+    float rg = rgeo;
+    if constexpr (MK == kPointCloud) rg = rho_geo_at<MK, KM, float>(pb, Y);
+    const float r = theta * (dG < rg ? dG : rg);
     const float a = sqs * r;
     if (r != r_prev) {   // constant-radius walks evaluate the weights once
       if (!pb.em1_fp64) {
@@ -306,7 +347,7 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
       const float zs = (r * t) * rsqrtf(fmaxf(dot3(z, z), 1e-30f));
       float Z[3];
       for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * z[q];
-      F = source_at32<MK>(pb, Z);
+      F = source_at32<MK, KM>(pb, Z);
     } else {
       float g[3];
       for (int q = 0; q < 3; ++q) g[q] = gaussian_at32(static_cast<uint32_t>(q), kk, i, p, K);
@@ -322,13 +363,13 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
         const float zs = (r * t) * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
         float Z[3];
         for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * g[q];
-        F += source_at32<MK>(pb, Z);
+        F += source_at32<MK, KM>(pb, Z);
       }
       F /= static_cast<float>(nv);
     }
     S = f2_add(S, f2_mul_f(f2_mul(W, om2), F));
     W = f2_mul(W, c2);
-    cp3_f32<MK>(pb, Th, Y);
+    if constexpr (MK == kPointCloud) cp_any<MK, KM, float>(pb, Th, Y); else cp3_f32<MK>(pb, Th, Y);
     ++k;
   }
 }

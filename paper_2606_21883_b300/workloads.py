@@ -40,6 +40,10 @@ MANIFOLD_EUCLID = 0
 MANIFOLD_SPHERE = 1
 MANIFOLD_TORUS = 2
 MANIFOLD_EMBEDDED_SPHERE = 3
+MANIFOLD_POINT_CLOUD = 4
+
+CLOUD_CP_FIT = 0       # kNN + PCA plane + quadratic height fit + projection
+CLOUD_CP_NEAREST = 1   # nearest cloud point
 
 TRIG_COS = 0
 TRIG_SIN = 1
@@ -108,6 +112,10 @@ class Manifold:
     a: float = 0.0
     Q: Optional[np.ndarray] = None   # n x (d+1), row-major float64
     b: Optional[np.ndarray] = None   # n
+    cloud: Optional[np.ndarray] = None   # N_c x 3 float64 (point cloud)
+    k_nn: int = 16
+    c_h: float = 2.4
+    cp_mode: int = CLOUD_CP_FIT
 
 
 @dataclass
@@ -289,3 +297,50 @@ def euclid_halfspace(P: int = 16, walks: int = 2000, n: int = 3, sigma: float = 
     pts[:, 0] = g.uniform(0.05, 1.5, P)
     exact = np.exp(-math.sqrt(sigma) * pts[:, 0])
     return Workload("euclid_half", prob, pts, walks, Params(eps=1e-3), exact, "f64")
+
+
+# ----------------------------------------------------------------------------
+# point cloud on a radius-perturbed sphere
+# ----------------------------------------------------------------------------
+
+def _harmonics_l123(w: np.ndarray) -> np.ndarray:
+    """The 15 real spherical harmonics of degrees 1-3 (unnormalised polynomial
+    forms) at unit vectors w (M x 3)."""
+    x, y, z = w[:, 0], w[:, 1], w[:, 2]
+    return np.stack([x, y, z,
+                     x * y, y * z, 3 * z * z - 1, x * z, x * x - y * y,
+                     y * (3 * x * x - y * y), x * y * z, y * (5 * z * z - 1), z * (5 * z * z - 3),
+                     x * (5 * z * z - 1), z * (x * x - y * y), x * (x * x - 3 * y * y)], axis=1)
+
+
+def perturbed_sphere_coeffs(seed: int = 0) -> np.ndarray:
+    """alpha for r(w) = 1 + 0.2 sum alpha_i Y_i(w), scaled so max |sum| <= 1."""
+    a = _rng(seed).standard_normal(15)
+    probe = _rng(seed + 100).standard_normal((200000, 3))
+    probe /= np.linalg.norm(probe, axis=1, keepdims=True)
+    m = np.max(np.abs(_harmonics_l123(probe) @ a))
+    return a / (1.02 * m)
+
+
+def perturbed_sphere_radius(w: np.ndarray, alpha: np.ndarray) -> np.ndarray:
+    return 1.0 + 0.2 * (_harmonics_l123(w) @ alpha)
+
+
+def perturbed_sphere_cloud(N: int = 200_000, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
+    """N points r(w) w with w area-uniform on S^2 (seed), and the coefficients alpha."""
+    alpha = perturbed_sphere_coeffs(seed)
+    w = _rng(seed + 1).standard_normal((N, 3))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    return np.ascontiguousarray(perturbed_sphere_radius(w, alpha)[:, None] * w), alpha
+
+
+def point_cloud(P: int = 256, walks: int = 1000, N_cloud: int = 200_000, k_nn: int = 16, c_h: float = 2.4,
+                sigma: float = 100.0, seed: int = 0, cp_mode: int = CLOUD_CP_FIT) -> Workload:
+    """Closed point-cloud surface (radius-perturbed sphere), f = sigma: u = 1.
+
+    Query points are cloud points (on the sampled surface), chosen by seed."""
+    cloud, alpha = perturbed_sphere_cloud(N_cloud, seed)
+    man = Manifold(MANIFOLD_POINT_CLOUD, n=3, d=2, cloud=cloud, k_nn=k_nn, c_h=c_h, cp_mode=cp_mode)
+    prob = Problem(man, sigma=sigma, closed=True, f=Func.const(sigma), g=Func.const(0.0))
+    idx = _rng(seed + 7).choice(N_cloud, size=P, replace=False)
+    return Workload("point_cloud", prob, cloud[idx].copy(), walks, Params(), np.ones(P), "f32")

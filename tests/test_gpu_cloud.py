@@ -1,0 +1,55 @@
+"""GPU point-cloud walks against the oracle (Sec. 2.1 representation (iii)).
+
+FP64: identical k-nearest sets (exact distances, (distance^2, index) order),
+the same fit and projection, so each walk agrees with the oracle to 1e-12.
+The 200k-point cloud at full size: every f = sigma walk telescopes
+(S = 1 - W_K) in both precisions.  FP32 agrees with FP64 statistically."""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2606_21883_b300 as M
+from paper_2606_21883_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = M.Context(0)
+    yield c
+    c.close()
+
+
+def _smooth_source(w):
+    w.problem.f = W.Func.poly([(1.0, []), (1.0, [(0, 1)]), (2.0, [(1, 1), (2, 1)])])
+    return w
+
+
+@pytest.mark.parametrize("mode", [W.CLOUD_CP_FIT, W.CLOUD_CP_NEAREST])
+def test_cloud_walk_parity_fp64(ctx, mode):
+    w = _smooth_source(W.point_cloud(P=4, walks=1, N_cloud=20000, cp_mode=mode))
+    w.params.max_steps = 60
+    Sg, Kg, Fg = ctx.walk_scores(w.problem, w.params, w.points, 4, precision=M.FP64)
+    So, Ko, Fo = O.walk_scores(w.problem, w.params, w.points, 4)
+    ok = (np.abs(Sg - So) <= 1e-12 * np.maximum(1.0, np.abs(So))) & (Kg == Ko) & (Fg == Fo)
+    assert ok.all(), (np.argwhere(~ok)[:3].tolist(), Sg[~ok][:3], So[~ok][:3])
+
+
+@pytest.mark.parametrize("prec", [M.FP64, M.FP32])
+def test_cloud_full_size_telescoping(ctx, prec):
+    w = W.point_cloud(P=32, walks=1)                  # 200k points, k = 16, sigma = 100
+    w.params.tau_w = 1e-4
+    S, K, F = ctx.walk_scores(w.problem, w.params, w.points, 32 if prec == M.FP32 else 4, precision=prec)
+    assert not F.any() and np.all(K > 10)
+    # FP64: exact to rounding; FP32: omega carries ~1e-7 relative error per term
+    tol = 1e-9 if prec == M.FP64 else 1e-6
+    assert np.all((S > 1 - 1e-4 - tol) & (S <= 1 + tol))
+
+
+def test_cloud_fp32_vs_fp64(ctx):
+    w = _smooth_source(W.point_cloud(P=6, walks=1, N_cloud=50000))
+    w.params.tau_w = 1e-3
+    m32, s32, _, _ = ctx.solve(w.problem, w.params, w.points, 2048, precision=M.FP32)
+    m64, s64, _, _ = ctx.solve(w.problem, w.params, w.points, 512, precision=M.FP64)
+    assert np.all(np.abs(m32 - m64) < 4 * np.sqrt(s32 ** 2 + s64 ** 2))
