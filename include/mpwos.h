@@ -187,6 +187,50 @@ int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwo
 /* Largest P * N accepted by mpwos_solve_noalloc. */
 int64_t mpwos_noalloc_max_walks(void);
 
+/* ---- request serving (continuous batching) ------------------------------
+ * A request is one solve (same inputs as mpwos_solve; query points on the
+ * HOST, copied at submit) with a walk budget per point and an optional target
+ * standard error: walks per point start at min(256, budget) and double for the
+ * points whose standard error is still above the target, up to the budget
+ * (target 0: exactly `walk_budget` walks, as mpwos_solve).  Requests are
+ * admitted while a stream slot and serving memory are free (16 slots and a
+ * quarter of the free device memory by default), run concurrently on their
+ * own streams in bounded chunks, and are advanced by a scheduler thread of the
+ * context.  A walk's draws depend only on (seed, point, walk index), so a
+ * request's results do not depend on the other requests in flight; with
+ * target 0 they equal mpwos_solve's bit for bit.  Point clouds: the search
+ * grid is built at submit. */
+
+/* Serving limits: at most max_active requests in flight (<= 64; change only
+ * while idle), mem_bytes of device memory for their scratch, chunk_walks walks
+ * per launch.  Values <= 0 keep the current setting. */
+int mpwos_serve_config(mpwos_ctx* ctx, int max_active, size_t mem_bytes, int64_t chunk_walks);
+
+/* Queue a request; *request_id identifies it.  Fails with EINVAL on invalid
+ * inputs (as mpwos_solve) or device query points. */
+int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+                 const mpwos_params* prm, const double* pts, int64_t P, int64_t walk_budget,
+                 double target_stderr, uint64_t* request_id);
+
+/* *state: 0 queued, 1 running, 2 finished, 3 failed, 4 canceled. */
+int mpwos_poll(mpwos_ctx* ctx, uint64_t request_id, int* state);
+
+/* Block until the request leaves the queue/running states or timeout_s
+ * seconds pass (MPWOS_ETIMEDOUT; timeout_s < 0 waits without limit). */
+int mpwos_wait(mpwos_ctx* ctx, uint64_t request_id, double timeout_s);
+
+/* Cancel a queued or running request (a running one stops after its current
+ * round; mpwos_fetch then returns MPWOS_ECANCELED). */
+int mpwos_cancel(mpwos_ctx* ctx, uint64_t request_id);
+
+/* Copy a finished request's per-point mean, standard error, mean steps and
+ * walks used (host arrays of P; any may be NULL) and its latency (submit to
+ * completion, seconds), then release it.  Returns the request's status
+ * (MPWOS_OK, MPWOS_EMAXSTEPS, MPWOS_ECANCELED or the failure code);
+ * MPWOS_EBUSY if it has not finished. */
+int mpwos_fetch(mpwos_ctx* ctx, uint64_t request_id, double* mean, double* stderr_,
+                double* mean_steps, int64_t* walks, double* latency_s);
+
 /* ---- primitives exposed for verification ------------------------------ */
 
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4q..4q+3] =

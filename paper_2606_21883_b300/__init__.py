@@ -80,6 +80,14 @@ def lib() -> C.CDLL:
         L.mpwos_green_radius.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_int64, C.c_int]
         L.mpwos_c_sigma_r.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64]
+        L.mpwos_serve_config.argtypes = [C.c_void_p, C.c_int, C.c_size_t, C.c_int64]
+        L.mpwos_submit.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc), C.POINTER(Params),
+                                   C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_uint64)]
+        L.mpwos_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]
+        L.mpwos_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_double]
+        L.mpwos_cancel.argtypes = [C.c_void_p, C.c_uint64]
+        L.mpwos_fetch.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -226,6 +234,41 @@ class Context:
         rc = self.L.mpwos_walk_scores(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
                                       int(pts.shape[0]), int(N), _ptr(S), _ptr(K), _ptr(flags))
         return self._check(rc)
+
+    # -- serving ------------------------------------------------------------------
+    def serve_config(self, max_active=0, mem_bytes=0, chunk_walks=0):
+        return self._check(self.L.mpwos_serve_config(self.h, int(max_active), int(mem_bytes), int(chunk_walks)))
+
+    def submit(self, problem, params, pts, walk_budget, target_stderr=0.0, precision=FP32):
+        """mpwos_submit: returns the request id (query points copied at submit)."""
+        mar = _Marshal()
+        md, pd = mar.problem(problem)
+        prm = make_params(params, precision)
+        pts = mar.arr(pts)
+        rid = C.c_uint64(0)
+        self._check(self.L.mpwos_submit(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
+                                        int(pts.shape[0]), int(walk_budget), float(target_stderr), C.byref(rid)))
+        return int(rid.value)
+
+    def poll(self, rid):
+        st = C.c_int(0)
+        self._check(self.L.mpwos_poll(self.h, C.c_uint64(rid), C.byref(st)))
+        return int(st.value)
+
+    def wait(self, rid, timeout_s=-1.0):
+        return self._check(self.L.mpwos_wait(self.h, C.c_uint64(rid), float(timeout_s)), (MPWOS_OK, MPWOS_ETIMEDOUT))
+
+    def cancel(self, rid):
+        return self._check(self.L.mpwos_cancel(self.h, C.c_uint64(rid)))
+
+    def fetch(self, rid, P):
+        """mpwos_fetch: (mean, stderr, mean_steps, walks, latency_s, status)."""
+        mean, se, ms = np.zeros(P), np.zeros(P), np.zeros(P)
+        walks = np.zeros(P, dtype=np.int64)
+        lat = C.c_double(0.0)
+        rc = self.L.mpwos_fetch(self.h, C.c_uint64(rid), _ptr(mean), _ptr(se), _ptr(ms), _ptr(walks), C.byref(lat))
+        self._check(rc, (MPWOS_OK, MPWOS_EMAXSTEPS, MPWOS_ECANCELED))
+        return mean, se, ms, walks, float(lat.value), rc
 
     # -- primitives -------------------------------------------------------------
     def philox(self, ctr, key0, key1):

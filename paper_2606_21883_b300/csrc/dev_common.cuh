@@ -73,6 +73,11 @@ struct DevProblem {
   const float* tab32;
   int NA, NS;         // a-rows (uniform in z = a^2/4), s-nodes (+2 ghosts per row)
   double z_max;
+  // work map: walk (p, i) for p in wk_points (all points 0..P-1 when null),
+  // i in [wk_i0, wk_i1); this launch covers enumeration indices [wk_w0, wk_w1)
+  // of the wk_np * (wk_i1 - wk_i0) walks; outputs at p * out_stride + i
+  const int* wk_points;
+  int64_t wk_np, wk_i0, wk_i1, wk_w0, wk_w1, out_stride;
   // queries and outputs
   int64_t P, N;
   const double* pts;  // P x n
@@ -174,6 +179,22 @@ __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, floa
 // B300's FP64 pipe (about 1/64 of the FP32 rate) would otherwise co-limit the
 // step; per-point sums over walks stay in FP64.
 // ---------------------------------------------------------------------------
+// Walk enumeration index -> (point, walk index, output slot).
+struct WalkId {
+  uint32_t p, i;
+  int64_t o;
+};
+
+__device__ __forceinline__ WalkId walk_id(const DevProblem& pb, int64_t w) {
+  const int64_t nw = pb.wk_i1 - pb.wk_i0;
+  const int64_t r = w / nw;
+  WalkId id;
+  id.p = static_cast<uint32_t>(pb.wk_points ? pb.wk_points[r] : r);
+  id.i = static_cast<uint32_t>(pb.wk_i0 + (w - r * nw));
+  id.o = static_cast<int64_t>(id.p) * pb.out_stride + id.i;
+  return id;
+}
+
 struct F2 { float hi, lo; };
 
 // c = 1 / (1 + em1) as a float pair and omega = (1 - c)/sigma, from an FP32

@@ -74,20 +74,22 @@ __device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
   return KSum{s, a.c + b.c - err};
 }
 
-__global__ void reduce_kernel(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
-                              double* mean, double* se, double* msteps, unsigned long long* n_flagged) {
+__global__ void reduce_kernel(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t Nu,
+                              int64_t stride, const int64_t* n_per_point, double* mean, double* se, double* msteps,
+                              unsigned long long* n_flagged) {
   const int lane = threadIdx.x & 31;
   const int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (p >= P) return;
+  const int64_t N = n_per_point ? n_per_point[p] : Nu;
   KSum s1{0.0, 0.0}, s2{0.0, 0.0};
   long long ks = 0, nf = 0;
-  const double* Sp = S + p * N;
+  const double* Sp = S + p * stride;
   for (int64_t i = lane; i < N; i += 32) {
     const double v = Sp[i];
     kahan_add(s1, v);
     kahan_add(s2, v * v);
-    ks += K[p * N + i];
-    nf += flags[p * N + i];
+    ks += K[p * stride + i];
+    nf += flags[p * stride + i];
   }
   for (int off = 16; off > 0; off >>= 1) {
     KSum o1{__shfl_down_sync(0xffffffffu, s1.s, off), __shfl_down_sync(0xffffffffu, s1.c, off)};
@@ -113,9 +115,16 @@ __global__ void reduce_kernel(const double* S, const int32_t* K, const int32_t* 
 cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
                           double* mean, double* se, double* msteps, unsigned long long* n_flagged,
                           cudaStream_t st) {
+  return launch_reduce_strided(S, K, flags, P, N, N, nullptr, mean, se, msteps, n_flagged, st);
+}
+
+cudaError_t launch_reduce_strided(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                                  int64_t stride, const int64_t* n_per_point, double* mean, double* se,
+                                  double* msteps, unsigned long long* n_flagged, cudaStream_t st) {
   const int block = 256;
   const int64_t grid = (P * 32 + block - 1) / block;
-  reduce_kernel<<<static_cast<unsigned>(grid), block, 0, st>>>(S, K, flags, P, N, mean, se, msteps, n_flagged);
+  reduce_kernel<<<static_cast<unsigned>(grid), block, 0, st>>>(S, K, flags, P, N, stride, n_per_point, mean, se,
+                                                               msteps, n_flagged);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,12 @@ cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flag
                           double* mean, double* se, double* msteps, unsigned long long* n_flagged,
                           cudaStream_t st);
 
+// Same over a strided per-walk layout (row p at p * stride), each point with
+// n_per_point[p] walks (N walks for every point when n_per_point is null).
+cudaError_t launch_reduce_strided(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                                  int64_t stride, const int64_t* n_per_point, double* mean, double* se,
+                                  double* msteps, unsigned long long* n_flagged, cudaStream_t st);
+
 // Inverse-CDF tables of the radial Green law: NA rows over z = a^2/4 in
 // [0, z_max] (NA == 1: the single law at a = a_fixed); two sides of NS + 2 nodes per row.
 cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,

@@ -8,8 +8,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -44,7 +49,12 @@ struct CloudGrid {
 
 }  // namespace
 
+struct ServeEngine;
+void serve_shutdown(mpwos_ctx* ctx);
+
 struct mpwos_ctx {
+  std::recursive_mutex mu;           // public calls and the request scheduler
+  ServeEngine* serve = nullptr;
   int device = 0;
   int sm_count = 0;
   cudaStream_t own = nullptr;
@@ -89,19 +99,22 @@ double kappa_of(const mpwos_manifold_desc* m) {
   return 1.0;
 }
 
-// Stream-ordered device buffers released at the end of a call.
+// Stream-ordered device buffers released at the end of a call (or of a
+// served request), on the stream they were allocated on.
 struct Scratch {
   mpwos_ctx* ctx;
+  cudaStream_t stream;
   std::vector<void*> bufs;
-  explicit Scratch(mpwos_ctx* c) : ctx(c) {}
+  explicit Scratch(mpwos_ctx* c) : ctx(c), stream(c->stream) {}
+  Scratch(mpwos_ctx* c, cudaStream_t s) : ctx(c), stream(s) {}
   ~Scratch() {
-    for (void* b : bufs) cudaFreeAsync(b, ctx->stream);
+    for (void* b : bufs) cudaFreeAsync(b, stream);
   }
   template <typename T>
   T* alloc(size_t count) {
     void* p = nullptr;
     if (count == 0) count = 1;
-    if (cudaMallocAsync(&p, count * sizeof(T), ctx->stream) != cudaSuccess) {
+    if (cudaMallocAsync(&p, count * sizeof(T), stream) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -111,7 +124,7 @@ struct Scratch {
   template <typename T>
   T* upload(const T* host, size_t count) {
     T* d = alloc<T>(count);
-    if (d && count) cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream);
+    if (d && count) cudaMemcpyAsync(d, host, count * sizeof(T), cudaMemcpyHostToDevice, stream);
     return d;
   }
 };
@@ -364,7 +377,8 @@ int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
 
 // Everything a walk launch needs, built in `sc`.
 int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpwos_problem* pr,
-            const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb) {
+            const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb,
+            CloudGrid* cloud_pre = nullptr) {
   std::memset(&pb, 0, sizeof pb);
   pb.mkind = m->kind;
   pb.n = m->n;
@@ -386,6 +400,13 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   pb.seed = pa->seed;
   pb.P = P;
   pb.N = N;
+  pb.wk_points = nullptr;
+  pb.wk_np = P;
+  pb.wk_i0 = 0;
+  pb.wk_i1 = N;
+  pb.wk_w0 = 0;
+  pb.wk_w1 = P * N;
+  pb.out_stride = N;
   copy_func(pr->f, pb.f);
   if (!pr->closed) copy_func(pr->g, pb.g);
   const int n = m->n;
@@ -437,16 +458,18 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     pb.b = bd;
     pb.s0 = s0;
     if (P) {
-      CK(launch_intrinsic_start(pb.pts, qtd, bd, n, npad, D, P, s0, ctx->stream));
+      CK(launch_intrinsic_start(pb.pts, qtd, bd, n, npad, D, P, s0, sc.stream));
       ctx->launches++;
     }
   }
   // point cloud grid; rho_geo varies with h(y)
   double rho_geo_max = pb.rho_geo;
   if (m->kind == MPWOS_POINT_CLOUD) {
-    CloudGrid* G = nullptr;
-    int rc0 = get_cloud(ctx, m, &G);
-    if (rc0) return rc0;
+    CloudGrid* G = cloud_pre;
+    if (!G) {
+      int rc0 = get_cloud(ctx, m, &G);
+      if (rc0) return rc0;
+    }
     pb.cl_pts64 = G->pts64;
     pb.cl_pts32 = G->pts32;
     pb.cl_orig = G->orig;
@@ -478,18 +501,29 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   return MPWOS_OK;
 }
 
-int run_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64) {
-  if (pb.P == 0) return MPWOS_OK;
+int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid);
+
+int run_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64) { return run_walks_on(ctx, pb, fp64, ctx->stream, 0); }
+
+// Launch the walk kernel for pb's work range on st; max_grid > 0 caps the grid,
+// max_grid < 0 takes a 1/|max_grid| share of the full grid (served requests
+// leave SMs to the other requests in flight).
+int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid) {
+  if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
+  if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tab32)
+    return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
   const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
   const int block = n3 ? (fp64 ? 128 : 256) : 128;
   const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
   const int64_t per_block = n3 ? block : block / 32;
   int64_t grid = static_cast<int64_t>(ctx->sm_count) * occ;
-  const int64_t need = (pb.P * pb.N + per_block - 1) / per_block;
+  const int64_t need = (pb.wk_w1 - pb.wk_w0 + per_block - 1) / per_block;
+  if (max_grid < 0) grid = std::max<int64_t>(ctx->sm_count, grid / (-max_grid));
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
   if (grid > need) grid = need;
   cudaError_t e;
-  if (n3) e = fp64 ? launch_walk3_f64(pb, (int)grid, block, ctx->stream) : launch_walk3_f32(pb, (int)grid, block, ctx->stream);
-  else e = fp64 ? launch_walkn_f64(pb, (int)grid, block, ctx->stream) : launch_walkn_f32(pb, (int)grid, block, ctx->stream);
+  if (n3) e = fp64 ? launch_walk3_f64(pb, (int)grid, block, st) : launch_walk3_f32(pb, (int)grid, block, st);
+  else e = fp64 ? launch_walkn_f64(pb, (int)grid, block, st) : launch_walkn_f32(pb, (int)grid, block, st);
   if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "walk launch: %s", cudaGetErrorString(e));
   ctx->launches++;
   return MPWOS_OK;
@@ -535,6 +569,7 @@ int mpwos_create(int device, mpwos_ctx** out) {
 
 void mpwos_destroy(mpwos_ctx* ctx) {
   if (!ctx) return;
+  serve_shutdown(ctx);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->tables) {
@@ -565,6 +600,7 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
                       const mpwos_params* prm, const double* pts, int64_t P, int64_t N, double* S, int32_t* K,
                       int32_t* flags) {
   if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
@@ -591,6 +627,7 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
 int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob, const mpwos_params* prm,
                 const double* pts, int64_t P, int64_t N, double* mean, double* stderr_, double* mean_steps) {
   if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
@@ -629,6 +666,7 @@ int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_proble
 
 int mpwos_philox(mpwos_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t key1, uint32_t* out, int64_t count) {
   if (!ctx || !ctr || !out || count < 0) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Scratch sc(ctx);
   uint32_t* dc = sc.upload(ctr, static_cast<size_t>(count) * 4);
@@ -646,6 +684,7 @@ int mpwos_philox(mpwos_ctx* ctx, const uint32_t* ctr, uint32_t key0, uint32_t ke
 int mpwos_green_radius(mpwos_ctx* ctx, int n, double a_max, const double* a, const double* U, double* t,
                        int64_t count, int precision) {
   if (!ctx || !a || !U || !t || count < 0 || n < 3 || n > 1024 || !(a_max > 0.0)) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   if (n > 3 && 0.25 * a_max * a_max > 0.25 * (n - 2)) return fail(ctx, MPWOS_EINVAL, "a_max outside the series range");
   CK(cudaSetDevice(ctx->device));
   Table* tab = nullptr;
@@ -670,6 +709,7 @@ int mpwos_green_radius(mpwos_ctx* ctx, int n, double a_max, const double* a, con
 
 int mpwos_c_sigma_r(mpwos_ctx* ctx, int n, const double* a, double* c, int64_t count) {
   if (!ctx || !a || !c || count < 0 || n < 3) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   Scratch sc(ctx);
   double* da = sc.upload(a, count);
@@ -743,6 +783,7 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
                                    const mpwos_params* prm, const double* pts, int64_t P, int64_t N, double* mean,
                                    double* stderr_, double* mean_steps) {
   if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
@@ -793,6 +834,13 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   pb.seed = prm->seed;
   pb.P = P;
   pb.N = N;
+  pb.wk_points = nullptr;
+  pb.wk_np = P;
+  pb.wk_i0 = 0;
+  pb.wk_i1 = N;
+  pb.wk_w0 = 0;
+  pb.wk_w1 = P * N;
+  pb.out_stride = N;
   pb.pts = pts;
   copy_func(prob->f, pb.f);
   if (!prob->closed) {
@@ -846,3 +894,467 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   if (hflag) return fail(ctx, MPWOS_EMAXSTEPS, "%llu walks reached max_steps", hflag);
   return MPWOS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Request serving: continuous batching of solve requests.
+//
+// Requests are admitted while a stream slot and device memory are free; each
+// runs on its own stream in rounds (all points get n0 walks, then points whose
+// standard error is still above the target get their walk count doubled, up
+// to the budget), and each round's walks are launched in bounded chunks with a
+// capped grid so that requests in flight share the SMs.  A walk's result
+// depends only on (seed, point, walk index), so a request's results do not
+// depend on what else is in flight.  A host scheduler thread advances rounds
+// and admits queued requests.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct OwnedFunc {
+  mpwos_func f{};
+  std::vector<double> coef, v, A;
+  std::vector<int> off, var, pw, modes;
+  void take(const mpwos_func& src, int D) {
+    f = src;
+    coef.assign(src.coef, src.coef + (src.coef ? src.n_terms : 0));
+    f.coef = coef.data();
+    if (src.kind == MPWOS_FUNC_POLY) {
+      const int nf = src.n_terms ? src.term_off[src.n_terms] : 0;
+      off.assign(src.term_off, src.term_off + (src.term_off ? src.n_terms + 1 : 0));
+      var.assign(src.var, src.var + (src.var ? nf : 0));
+      pw.assign(src.pw, src.pw + (src.pw ? nf : 0));
+      f.term_off = off.data(); f.var = var.data(); f.pw = pw.data();
+    } else if (src.kind == MPWOS_FUNC_TORUS_FOURIER) {
+      modes.assign(src.modes, src.modes + (src.modes ? 4 * src.n_terms : 0));
+      f.modes = modes.data();
+    } else if (src.kind == MPWOS_FUNC_SPHERE_QUAD) {
+      v.assign(src.v, src.v + D);
+      A.assign(src.A, src.A + static_cast<size_t>(D) * D);
+      f.v = v.data(); f.A = A.data();
+    }
+  }
+};
+
+struct Request {
+  uint64_t id = 0;
+  int state = 0;                 // 0 queued, 1 running, 2 done, 3 failed, 4 canceled
+  int status = MPWOS_OK;
+  std::string err;
+  mpwos_manifold_desc man{};
+  mpwos_problem prob{};
+  mpwos_params prm{};
+  OwnedFunc f, g;
+  std::vector<double> Q, b, normal, pts;
+  CloudGrid* cloud = nullptr;
+  int64_t P = 0, budget = 0;
+  double target = 0.0;
+  size_t bytes = 0;
+  int slot = -1;
+  std::unique_ptr<Scratch> sc;
+  cudaEvent_t ev = nullptr;
+  DevProblem pb{};
+  double *S = nullptr, *mean = nullptr, *se = nullptr, *ms = nullptr;
+  int32_t *K = nullptr, *F = nullptr;
+  int64_t* nper = nullptr;
+  int* act = nullptr;
+  unsigned long long* nflag = nullptr;
+  double *h_mean = nullptr, *h_se = nullptr, *h_ms = nullptr;
+  int64_t* h_n = nullptr;
+  int* h_act = nullptr;
+  unsigned long long* h_flag = nullptr;
+  std::vector<int> active;
+  int64_t cur = 0;
+  bool cancel = false;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+}  // namespace
+
+struct ServeEngine {
+  std::map<uint64_t, std::unique_ptr<Request>> reqs;
+  std::deque<uint64_t> queue;
+  std::vector<cudaStream_t> streams;
+  std::vector<bool> slot_busy;
+  int max_active = 16;
+  size_t mem_budget = 0, mem_used = 0;
+  int64_t chunk_walks = int64_t(1) << 20;
+  uint64_t next_id = 1;
+  bool stop = false;
+  std::condition_variable_any cv;
+  std::thread thr;
+};
+
+namespace {
+
+constexpr int64_t kFirstRoundWalks = 256;
+
+void req_free_device(Request& r) {
+  r.sc.reset();   // stream-ordered frees on the request's stream
+}
+
+void req_finish(mpwos_ctx* ctx, Request& r, int state, int status, const std::string& err) {
+  ServeEngine& E = *ctx->serve;
+  r.state = state;
+  r.status = status;
+  r.err = err;
+  r.t_done = std::chrono::steady_clock::now();
+  req_free_device(r);
+  if (r.slot >= 0) {
+    E.slot_busy[r.slot] = false;
+    r.slot = -1;
+  }
+  E.mem_used -= std::min(E.mem_used, r.bytes);
+}
+
+int req_round(mpwos_ctx* ctx, Request& r, int64_t i1) {
+  ServeEngine& E = *ctx->serve;
+  const cudaStream_t st = E.streams[r.slot];
+  const int64_t i0 = r.cur;
+  for (size_t q = 0; q < r.active.size(); ++q) {
+    r.h_act[q] = r.active[q];
+    r.h_n[r.active[q]] = i1;
+  }
+  CK(cudaMemcpyAsync(r.act, r.h_act, sizeof(int) * r.active.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(r.nper, r.h_n, sizeof(int64_t) * r.P, cudaMemcpyHostToDevice, st));
+  r.pb.wk_points = r.act;
+  r.pb.wk_np = static_cast<int64_t>(r.active.size());
+  r.pb.wk_i0 = i0;
+  r.pb.wk_i1 = i1;
+  r.pb.out_stride = r.budget;
+  const int64_t total = r.pb.wk_np * (i1 - i0);
+  // requests in flight share the SMs: each launch takes a 1/running share of a full grid
+  int running = 0;
+  for (auto& kv : E.reqs) running += kv.second->state == 1;
+  const int64_t max_grid = running > 1 ? -static_cast<int64_t>(running) : 0;
+  for (int64_t w0 = 0; w0 < total; w0 += E.chunk_walks) {
+    r.pb.wk_w0 = w0;
+    r.pb.wk_w1 = std::min(total, w0 + E.chunk_walks);
+    int rc = run_walks_on(ctx, r.pb, r.prm.precision == MPWOS_FP64, st, max_grid);
+    if (rc) return rc;
+  }
+  CK(cudaMemsetAsync(r.nflag, 0, sizeof(unsigned long long), st));
+  CK(launch_reduce_strided(r.S, r.K, r.F, r.P, 0, r.budget, r.nper, r.mean, r.se, r.ms, r.nflag, st));
+  ctx->launches++;
+  CK(cudaMemcpyAsync(r.h_mean, r.mean, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(r.h_se, r.se, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(r.h_ms, r.ms, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(r.h_flag, r.nflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(r.ev, st));
+  r.cur = i1;
+  return MPWOS_OK;
+}
+
+int req_start(mpwos_ctx* ctx, Request& r) {
+  ServeEngine& E = *ctx->serve;
+  const cudaStream_t st = E.streams[r.slot];
+  r.sc.reset(new Scratch(ctx, st));
+  int rc = prepare(ctx, *r.sc, &r.man, &r.prob, &r.prm, r.pts.data(), r.P, r.budget, r.pb, r.cloud);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(ctx->stream));   // tables built on the context stream
+  const size_t W = static_cast<size_t>(r.P) * r.budget;
+  r.S = r.sc->alloc<double>(W);
+  r.K = r.sc->alloc<int32_t>(W);
+  r.F = r.sc->alloc<int32_t>(W);
+  r.mean = r.sc->alloc<double>(r.P);
+  r.se = r.sc->alloc<double>(r.P);
+  r.ms = r.sc->alloc<double>(r.P);
+  r.nper = r.sc->alloc<int64_t>(r.P);
+  r.act = r.sc->alloc<int>(r.P);
+  r.nflag = r.sc->alloc<unsigned long long>(1);
+  if (!r.S || !r.K || !r.F || !r.mean || !r.se || !r.ms || !r.nper || !r.act || !r.nflag)
+    return fail(ctx, MPWOS_ENOMEM, "request %llu: device memory", (unsigned long long)r.id);
+  r.pb.S_out = r.S;
+  r.pb.K_out = r.K;
+  r.pb.flag_out = r.F;
+  r.active.resize(r.P);
+  for (int64_t p = 0; p < r.P; ++p) { r.active[p] = static_cast<int>(p); r.h_n[p] = 0; }
+  r.cur = 0;
+  const int64_t n0 = r.target > 0.0 ? std::min(r.budget, kFirstRoundWalks) : r.budget;
+  return req_round(ctx, r, n0);
+}
+
+void req_advance(mpwos_ctx* ctx, Request& r) {
+  if (r.cancel) {
+    req_finish(ctx, r, 4, MPWOS_ECANCELED, "canceled");
+    return;
+  }
+  std::vector<int> next;
+  if (r.target > 0.0)
+    for (int p : r.active)
+      if (r.h_se[p] > r.target && r.h_n[p] < r.budget) next.push_back(p);
+  if (next.empty()) {
+    if (*r.h_flag) req_finish(ctx, r, 2, MPWOS_EMAXSTEPS, "some walks reached max_steps");
+    else req_finish(ctx, r, 2, MPWOS_OK, "");
+    return;
+  }
+  r.active.swap(next);
+  const int rc = req_round(ctx, r, std::min(r.budget, 2 * r.cur));
+  if (rc) req_finish(ctx, r, 3, rc, ctx->err);
+}
+
+void serve_admit(mpwos_ctx* ctx) {
+  ServeEngine& E = *ctx->serve;
+  while (!E.queue.empty()) {
+    Request& r = *E.reqs[E.queue.front()];
+    int active = 0, slot = -1;
+    for (int q = 0; q < E.max_active; ++q) {
+      if (E.slot_busy[q]) ++active;
+      else if (slot < 0) slot = q;
+    }
+    if (slot < 0) return;
+    if (E.mem_used + r.bytes > E.mem_budget) {
+      if (active > 0) return;   // wait for memory; a lone oversized request fails below
+      E.queue.pop_front();
+      req_finish(ctx, r, 3, MPWOS_ENOMEM, "request exceeds the serving memory budget");
+      continue;
+    }
+    E.queue.pop_front();
+    E.slot_busy[slot] = true;
+    r.slot = slot;
+    r.state = 1;
+    E.mem_used += r.bytes;
+    const int rc = req_start(ctx, r);
+    if (rc) req_finish(ctx, r, 3, rc, ctx->err);
+  }
+}
+
+void serve_loop(mpwos_ctx* ctx) {
+  cudaSetDevice(ctx->device);
+  ServeEngine& E = *ctx->serve;
+  std::unique_lock<std::recursive_mutex> lk(ctx->mu);
+  while (!E.stop) {
+    for (auto& kv : E.reqs) {
+      Request& r = *kv.second;
+      if (r.state != 1) continue;
+      const cudaError_t q = cudaEventQuery(r.ev);
+      if (q == cudaSuccess) req_advance(ctx, r);
+      else if (q != cudaErrorNotReady) req_finish(ctx, r, 3, MPWOS_ECUDA, cudaGetErrorString(q));
+    }
+    serve_admit(ctx);
+    bool running = false;   // after admission: a request started just now must be polled
+    for (auto& kv : E.reqs) running = running || kv.second->state == 1;
+    if (!running && E.queue.empty()) {
+      E.cv.wait_for(lk, std::chrono::milliseconds(100));
+    } else {
+      lk.unlock();
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      lk.lock();
+    }
+  }
+}
+
+int serve_init(mpwos_ctx* ctx) {
+  if (ctx->serve) return MPWOS_OK;
+  ServeEngine* E = new ServeEngine();
+  ctx->serve = E;
+  size_t free_b = 0, total_b = 0;
+  CK(cudaMemGetInfo(&free_b, &total_b));
+  E->mem_budget = free_b / 4;
+  E->streams.resize(E->max_active);
+  E->slot_busy.assign(E->max_active, false);
+  for (auto& st : E->streams) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  E->thr = std::thread(serve_loop, ctx);
+  return MPWOS_OK;
+}
+
+Request* find_req(mpwos_ctx* ctx, uint64_t id) {
+  if (!ctx->serve) return nullptr;
+  auto it = ctx->serve->reqs.find(id);
+  return it == ctx->serve->reqs.end() ? nullptr : it->second.get();
+}
+
+void req_release(mpwos_ctx* ctx, uint64_t id) {
+  Request* r = find_req(ctx, id);
+  if (!r) return;
+  cudaFreeHost(r->h_mean);
+  cudaFreeHost(r->h_se);
+  cudaFreeHost(r->h_ms);
+  cudaFreeHost(r->h_n);
+  cudaFreeHost(r->h_act);
+  cudaFreeHost(r->h_flag);
+  if (r->ev) cudaEventDestroy(r->ev);
+  ctx->serve->reqs.erase(id);
+}
+
+}  // namespace
+
+void serve_shutdown(mpwos_ctx* ctx) {
+  ServeEngine* E = ctx->serve;
+  if (!E) return;
+  {
+    std::lock_guard<std::recursive_mutex> lk(ctx->mu);
+    E->stop = true;
+  }
+  E->cv.notify_all();
+  if (E->thr.joinable()) E->thr.join();
+  cudaSetDevice(ctx->device);
+  for (auto& st : E->streams) cudaStreamSynchronize(st);
+  std::vector<uint64_t> ids;
+  for (auto& kv : E->reqs) ids.push_back(kv.first);
+  for (uint64_t id : ids) {
+    Request* r = find_req(ctx, id);
+    if (r) req_free_device(*r);
+    req_release(ctx, id);
+  }
+  for (auto& st : E->streams) cudaStreamDestroy(st);
+  delete E;
+  ctx->serve = nullptr;
+}
+
+extern "C" {
+
+int mpwos_serve_config(mpwos_ctx* ctx, int max_active, size_t mem_bytes, int64_t chunk_walks) {
+  if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  int rc = serve_init(ctx);
+  if (rc) return rc;
+  ServeEngine& E = *ctx->serve;
+  bool idle = true;
+  for (auto& kv : E.reqs) idle = idle && kv.second->state >= 2;
+  if (max_active > 0) {
+    if (!idle) return fail(ctx, MPWOS_EBUSY, "change max_active only while no request is queued or running");
+    if (max_active > 64) return fail(ctx, MPWOS_EINVAL, "max_active must be <= 64");
+    for (auto& st : E.streams) cudaStreamDestroy(st);
+    E.max_active = max_active;
+    E.streams.resize(max_active);
+    E.slot_busy.assign(max_active, false);
+    for (auto& st : E.streams) CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  }
+  if (mem_bytes > 0) E.mem_budget = mem_bytes;
+  if (chunk_walks > 0) E.chunk_walks = chunk_walks;
+  return MPWOS_OK;
+}
+
+int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob, const mpwos_params* prm,
+                 const double* pts, int64_t P, int64_t walk_budget, double target_stderr, uint64_t* request_id) {
+  if (!ctx || !request_id) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  int rc = validate(ctx, m, prob, prm, P, walk_budget);
+  if (rc) return rc;
+  if (P > 0 && (!pts || is_device_ptr(pts))) return fail(ctx, MPWOS_EINVAL, "mpwos_submit takes host query points");
+  if (!(target_stderr >= 0.0)) return fail(ctx, MPWOS_EINVAL, "target_stderr must be >= 0");
+  rc = serve_init(ctx);
+  if (rc) return rc;
+  ServeEngine& E = *ctx->serve;
+  std::unique_ptr<Request> r(new Request());
+  r->id = E.next_id++;
+  r->P = P;
+  r->budget = walk_budget;
+  r->target = target_stderr;
+  r->man = *m;
+  r->prob = *prob;
+  r->prm = *prm;
+  const int D = (m->kind == MPWOS_SPHERE && m->n == 3) ? 3 : m->d + 1;
+  r->f.take(prob->f, D);
+  r->prob.f = r->f.f;
+  if (!prob->closed) {
+    r->g.take(prob->g, D);
+    r->prob.g = r->g.f;
+    r->normal.assign(prob->bnd_normal, prob->bnd_normal + m->n);
+    r->prob.bnd_normal = r->normal.data();
+  }
+  if (m->kind == MPWOS_EMBEDDED_SPHERE) {
+    r->Q.assign(m->Q, m->Q + static_cast<size_t>(m->n) * (m->d + 1));
+    r->b.assign(m->b, m->b + m->n);
+    r->man.Q = r->Q.data();
+    r->man.b = r->b.data();
+  }
+  if (m->kind == MPWOS_POINT_CLOUD) {
+    rc = get_cloud(ctx, m, &r->cloud);   // grid built now, while the caller's array is valid
+    if (rc) return rc;
+    r->man.cloud = nullptr;
+  }
+  r->pts.assign(pts, pts + static_cast<size_t>(P) * m->n);
+  r->bytes = static_cast<size_t>(P) * walk_budget * 16 + static_cast<size_t>(P) * 48 + (64 << 10);
+  CK(cudaMallocHost(&r->h_mean, sizeof(double) * std::max<int64_t>(P, 1)));
+  CK(cudaMallocHost(&r->h_se, sizeof(double) * std::max<int64_t>(P, 1)));
+  CK(cudaMallocHost(&r->h_ms, sizeof(double) * std::max<int64_t>(P, 1)));
+  CK(cudaMallocHost(&r->h_n, sizeof(int64_t) * std::max<int64_t>(P, 1)));
+  CK(cudaMallocHost(&r->h_act, sizeof(int) * std::max<int64_t>(P, 1)));
+  CK(cudaMallocHost(&r->h_flag, sizeof(unsigned long long)));
+  *r->h_flag = 0;
+  CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+  r->t_submit = std::chrono::steady_clock::now();
+  const uint64_t id = r->id;
+  if (P == 0) {
+    r->state = 2;
+    r->t_done = r->t_submit;
+  } else {
+    E.queue.push_back(id);
+  }
+  E.reqs[id] = std::move(r);
+  *request_id = id;
+  E.cv.notify_all();
+  return MPWOS_OK;
+}
+
+int mpwos_poll(mpwos_ctx* ctx, uint64_t id, int* state) {
+  if (!ctx || !state) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  Request* r = find_req(ctx, id);
+  if (!r) return fail(ctx, MPWOS_ENOTFOUND, "unknown request %llu", (unsigned long long)id);
+  *state = r->state;
+  return MPWOS_OK;
+}
+
+int mpwos_wait(mpwos_ctx* ctx, uint64_t id, double timeout_s) {
+  if (!ctx) return MPWOS_EINVAL;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    {
+      std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+      Request* r = find_req(ctx, id);
+      if (!r) return fail(ctx, MPWOS_ENOTFOUND, "unknown request %llu", (unsigned long long)id);
+      if (r->state >= 2) return MPWOS_OK;
+    }
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (timeout_s >= 0.0 && el > timeout_s) {
+      std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+      return fail(ctx, MPWOS_ETIMEDOUT, "request %llu not finished after %.3f s", (unsigned long long)id, el);
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+
+int mpwos_cancel(mpwos_ctx* ctx, uint64_t id) {
+  if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  Request* r = find_req(ctx, id);
+  if (!r) return fail(ctx, MPWOS_ENOTFOUND, "unknown request %llu", (unsigned long long)id);
+  if (r->state == 0) {
+    auto& q = ctx->serve->queue;
+    for (auto it = q.begin(); it != q.end(); ++it)
+      if (*it == id) { q.erase(it); break; }
+    r->state = 4;
+    r->status = MPWOS_ECANCELED;
+    r->t_done = std::chrono::steady_clock::now();
+  } else if (r->state == 1) {
+    r->cancel = true;
+  }
+  return MPWOS_OK;
+}
+
+int mpwos_fetch(mpwos_ctx* ctx, uint64_t id, double* mean, double* stderr_, double* mean_steps,
+                int64_t* walks, double* latency_s) {
+  if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  Request* r = find_req(ctx, id);
+  if (!r) return fail(ctx, MPWOS_ENOTFOUND, "unknown request %llu", (unsigned long long)id);
+  if (r->state < 2) return fail(ctx, MPWOS_EBUSY, "request %llu has not finished", (unsigned long long)id);
+  const int status = r->status;
+  if (status != MPWOS_OK) fail(ctx, status, "request %llu: %s", (unsigned long long)id, r->err.c_str());
+  if (r->state == 2) {
+    for (int64_t p = 0; p < r->P; ++p) {
+      if (mean) mean[p] = r->h_mean[p];
+      if (stderr_) stderr_[p] = r->h_se[p];
+      if (mean_steps) mean_steps[p] = r->h_ms[p];
+      if (walks) walks[p] = r->h_n[p];
+    }
+  }
+  if (latency_s) *latency_s = std::chrono::duration<double>(r->t_done - r->t_submit).count();
+  req_release(ctx, id);
+  return status;
+}
+
+}  // extern "C"

@@ -50,20 +50,20 @@ __device__ __forceinline__ bool source_is_constant(const DevFunc& f) {
 
 template <int MK, int KM>
 __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
-  const int64_t total = pb.P * pb.N;
+  const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
   const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
   const int nv = pb.n_v;
   const uint32_t ub = 2u * static_cast<uint32_t>(1 + nv);
 
   double Y[3], W = 1.0, S = 0.0;
-  int64_t k = 0;
+  int64_t k = 0, o = 0;
   uint32_t p = 0, i = 0;
   auto init = [&](int64_t ww) {
-    p = static_cast<uint32_t>(ww / pb.N);
-    i = static_cast<uint32_t>(ww - static_cast<int64_t>(p) * pb.N);
+    const WalkId id = walk_id(pb, ww);
+    p = id.p; i = id.i; o = id.o;
     const double* y0 = pb.pts + static_cast<size_t>(p) * 3;
     Y[0] = y0[0]; Y[1] = y0[1]; Y[2] = y0[2];
     W = 1.0; S = 0.0; k = 0;
@@ -90,9 +90,9 @@ __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
     }
     if (!done && k >= pb.max_steps) { done = true; flag = 1; }
     if (done) {
-      pb.S_out[w] = S;
-      pb.K_out[w] = static_cast<int32_t>(k);
-      pb.flag_out[w] = flag;
+      pb.S_out[o] = S;
+      pb.K_out[o] = static_cast<int32_t>(k);
+      pb.flag_out[o] = flag;
       w += stride;
       if (w >= total) break;
       init(w);
@@ -260,9 +260,9 @@ __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* 
 
 template <int MK, int KM>
 __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
-  const int64_t total = pb.P * pb.N;
+  const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  int64_t w = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
   const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
   const int nv = pb.n_v;
@@ -275,11 +275,11 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
 
   float Y[3];
   F2 W{1.0f, 0.0f}, S{0.0f, 0.0f};
-  int64_t k = 0;
+  int64_t k = 0, o = 0;
   uint32_t p = 0, i = 0;
   auto init = [&](int64_t ww) {
-    p = static_cast<uint32_t>(ww / pb.N);
-    i = static_cast<uint32_t>(ww - static_cast<int64_t>(p) * pb.N);
+    const WalkId id = walk_id(pb, ww);
+    p = id.p; i = id.i; o = id.o;
     const double* y0 = pb.pts + static_cast<size_t>(p) * 3;
     Y[0] = static_cast<float>(y0[0]); Y[1] = static_cast<float>(y0[1]); Y[2] = static_cast<float>(y0[2]);
     W = F2{1.0f, 0.0f}; S = F2{0.0f, 0.0f}; k = 0;
@@ -306,9 +306,9 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
     }
     if (!done && k >= pb.max_steps) { done = true; flag = 1; }
     if (done) {
-      pb.S_out[w] = f2_to_double(S);
-      pb.K_out[w] = static_cast<int32_t>(k);
-      pb.flag_out[w] = flag;
+      pb.S_out[o] = f2_to_double(S);
+      pb.K_out[o] = static_cast<int32_t>(k);
+      pb.flag_out[o] = flag;
       w += stride;
       if (w >= total) break;
       init(w);

@@ -241,9 +241,9 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
   constexpr int G = Prec<T>::G, MB = Prec<T>::MB, L = G * MB;
   constexpr bool kF64 = sizeof(T) == 8;
   const int lane = threadIdx.x & 31;
-  const int64_t total = pb.P * pb.N;
+  const int64_t total = pb.wk_w1;
   const int64_t nwarps = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-  int64_t w = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  int64_t w = pb.wk_w0 + ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   if (w >= total) return;
   const int n = pb.n;
   const int D = pb.d + 1;
@@ -272,7 +272,7 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
   T al = T(0), yy = T(1);   // e.Y and |Y|^2 (boundary problems)
   WalkAcc<T> wa;
   wa.set_tau(pb.tau_w);
-  int64_t k = 0;
+  int64_t k = 0, o = 0;
   uint32_t p = 0, wi = 0;
 
   auto state_dots = [&]() {
@@ -291,8 +291,8 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
     yy = acc[1];
   };
   auto init = [&](int64_t ww) {
-    p = static_cast<uint32_t>(ww / pb.N);
-    wi = static_cast<uint32_t>(ww - static_cast<int64_t>(p) * pb.N);
+    const WalkId id = walk_id(pb, ww);
+    p = id.p; wi = id.i; o = id.o;
     wa.reset();
     k = 0;
     if constexpr (MK == kEmbeddedSphere) {
@@ -358,9 +358,9 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
     if (!done && k >= pb.max_steps) { done = true; flag = 1; }
     if (done) {
       if (lane == 0) {
-        pb.S_out[w] = wa.score();
-        pb.K_out[w] = static_cast<int32_t>(k);
-        pb.flag_out[w] = flag;
+        pb.S_out[o] = wa.score();
+        pb.K_out[o] = static_cast<int32_t>(k);
+        pb.flag_out[o] = flag;
       }
       w += nwarps;
       if (w >= total) break;
