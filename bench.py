@@ -37,11 +37,13 @@ from paper_2606_21883_b300 import workloads as W  # noqa: E402
 
 METRIC = "walk-steps/s at fixed RMSE (torus, FP32 walk + FP64 accumulation)"
 UNIT = "walk-steps/s"
-# Algorithmic lane-operations per walk-step of the FP32 torus walk (N_V = 1);
-# breakdown in the design notes: Philox 2 x 80, Box-Muller 3 x 16, sphere and
-# interior samples 20, radius table 32, torus cp 2 x 25, torus source 50,
-# FP64 weights/score 4, loop and stop test 6.
-OPS_PER_STEP = 370
+# Algorithmic lane-operations per walk-step of the FP32 torus walk (N_V = 1),
+# the minimal operation count of one step: 2 Philox4x32-10 blocks (10 rounds x
+# 2 wide multiplies + 2 three-input XORs) 80, 7 uniforms 14, 3 Box-Muller pairs
+# 27, sphere sample 8, radius table 25, interior sample 9, torus angles of Z 13,
+# torus source (-Delta_M + sigma) u 33, closest point of Theta 14, weight and
+# score (W omega F, S +=, W c) 4, stop test and loop 6.
+OPS_PER_STEP = 233
 
 
 def _peaks():
@@ -99,6 +101,84 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def _serving_mix(rng, n_req, cloud_w):
+    """Seeded request mix: (workload, points, walk budget, target stderr).
+
+    Points log-uniform in [1, P_max], budget log-uniform in [256, 65536], target
+    standard error log-uniform in [1e-3, 1e-2].  P_max: 4096 on the torus, 64
+    on the S^2 cap and the point cloud, 8 on S^999 (thousands of steps per
+    walk), 1 on S^20 in R^1000 (226,786 steps per walk; budget 256)."""
+    import math as _m
+    out = []
+    kinds = ["torus", "cap", "cloud", "s999", "s20"]
+    for q in range(n_req):
+        kind = kinds[int(rng.integers(len(kinds)))]
+        lo = lambda a, b: int(round(_m.exp(rng.uniform(_m.log(a), _m.log(b)))))
+        target = _m.exp(rng.uniform(_m.log(1e-3), _m.log(1e-2)))
+        budget = lo(256, 65536)
+        seed = int(rng.integers(1 << 30))
+        if kind == "torus":
+            w = W.torus_closed(P=lo(1, 4096), walks=1, seed=seed)
+        elif kind == "cap":
+            w = W.sphere_cap(P=lo(1, 64), walks=1, seed=seed)
+        elif kind == "cloud":
+            P = lo(1, 64)
+            idx = rng.choice(len(cloud_w.problem.manifold.cloud), size=P, replace=False)
+            w = W.Workload("cloud", cloud_w.problem, cloud_w.problem.manifold.cloud[idx].copy(), 1,
+                           cloud_w.params, np.ones(P), "f32")
+        elif kind == "s999":
+            w = W.hypersphere_half(P=lo(1, 8), walks=1, seed=seed)
+            budget = min(budget, 4096)
+        else:
+            w = W.embedded_s20(P=1, walks=1, seed=seed % 7)
+            budget, target = 256, 0.0
+        out.append((kind, w, budget, target))
+    return out
+
+
+def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7):
+    """p50/p99 latency of Poisson arrivals at ~70% of the measured capacity."""
+    import time as _t
+    rng = np.random.default_rng(seed)
+    cloud_w = W.point_cloud(P=1, walks=1)
+    cloud_w.params.tau_w = 1e-4
+
+    def run(reqs, rate):
+        ids, lat, steps = [], [], 0.0
+        t0 = _t.perf_counter()
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
+        pending = {}
+        q = 0
+        while q < len(reqs) or pending:
+            now = _t.perf_counter() - t0
+            while q < len(reqs) and arrivals[q] <= now:
+                kind, w, budget, target = reqs[q]
+                rid = ctx.submit(w.problem, w.params, w.points, budget, target, precision=M.FP32)
+                pending[rid] = len(w.points)
+                q += 1
+            for rid in list(pending):
+                if ctx.poll(rid) >= 2:
+                    mean, se, ms, walks, lt, rc = ctx.fetch(rid, pending.pop(rid))
+                    lat.append(lt)
+                    steps += float(np.sum(ms * walks))
+            _t.sleep(0.0005)
+        return np.array(lat), steps, _t.perf_counter() - t0
+
+    calib = _serving_mix(rng, n_calib, cloud_w)
+    _, st_c, T_c = run(calib, 0.0)                       # all at once: capacity
+    cap_rate = n_calib / T_c
+    rate = 0.7 * cap_rate
+    reqs = _serving_mix(rng, n_req, cloud_w)
+    lat, steps, T = run(reqs, rate)
+    kinds = {k: sum(1 for r in reqs if r[0] == k) for k in ["torus", "cap", "cloud", "s999", "s20"]}
+    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_ms": 1e3 * float(lat.mean()), "requests": int(len(lat)), "arrival_rate_hz": rate,
+            "capacity_hz": cap_rate, "walk_steps_per_s": steps / T, "mix": kinds,
+            "recipe": "Poisson arrivals at 0.7 x capacity (capacity from a burst of 24); points log-uniform "
+                      "(torus <=4096, cap/cloud <=64, S^999 <=8, S^20 1), budget log-uniform 256-65536, "
+                      "target stderr log-uniform 1e-3-1e-2, FP32 walks"}
+
+
 def cpu_baseline(target_s: float = 15.0):
     """The CPU oracle, as it stands, on a bounded sample of the torus workload."""
     import oracle as O
@@ -145,6 +225,7 @@ def main():
     ap.add_argument("--points", type=int, default=4096)
     ap.add_argument("--walks", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -260,6 +341,8 @@ def main():
                          "peak_source": f"148 SM x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz ({src} max clock)"},
             "clocks": clocks,
         }
+        if not args.no_serving and world == 1:
+            line["serving"] = serving_leg(M, ctx)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -54,12 +54,12 @@ __device__ __forceinline__ T cloud_knn(const DevProblem& pb, const T* x, Knn<T, 
   const T* P = cloud_pts<T>(pb);
 #pragma unroll
   for (int j = 0; j < KM; ++j) { R.d2[j] = T(INFINITY); R.idx[j] = -1; R.gid[j] = 0x7fffffff; }
-  const T cs = T(pb.cl_cell);
+  const T cs = pick<T>(pb.cl_cell, pb.cl_cell_f);
   int c[3];
   T lo[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    lo[a] = T(pb.cl_origin[a]);
+    lo[a] = pick<T>(pb.cl_origin[a], pb.cl_origin_f[a]);
     int ci = static_cast<int>(floor((x[a] - lo[a]) / cs));
     c[a] = ci < 0 ? 0 : (ci >= pb.cl_dims[a] ? pb.cl_dims[a] - 1 : ci);
   }

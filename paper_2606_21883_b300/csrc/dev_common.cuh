@@ -26,6 +26,16 @@ struct DevFunc {
   const double* A;                     // device, (d + 1)^2
   const float* vf;                     // float copies
   const float* Af;
+  float coef_f[kMaxTerms];             // FP32 copies of coef, c0 (the FP32 walks read no double)
+  float c0_f;
+};
+
+// FP32 copies of the loop-invariant scalars, filled on the host: a double read
+// in an FP32 walk costs a conversion on B300's narrow FP64 pipe every step.
+struct ScalarsF {
+  float eps, theta, rho_geo, sqrt_sigma, sigma, inv_sigma, R, a, inv_a, h, sh, c_h;
+  float tab_scale;   // (NS - 1) / sqrt(1/2): table abscissa per sqrt(U)
+  float z_scale;     // (NA - 1) / z_max (0 when NA == 1)
 };
 
 // Everything a walk kernel reads, passed by value (kernel parameter space).
@@ -45,6 +55,8 @@ struct DevProblem {
   const int* cl_start;
   double cl_origin[3];
   double cl_cell;
+  float cl_origin_f[3];
+  float cl_cell_f;
   int cl_dims[3];
   int cl_k;          // neighbours (k_nn)
   double cl_c_h;     // rho_geo = c_h h(y)
@@ -61,6 +73,7 @@ struct DevProblem {
   int n_v;
   int64_t max_steps;
   uint64_t seed;
+  ScalarsF sf;
   // FP32 survival weight: em1(z) = I~_nu(a) - 1 = sum_{j=1..T} k_j z^j (Lemma 3.1
   // series, coefficients k_j = 1/(j! (nu+1)_j) from FP64 on the host, T chosen
   // so the truncation is below 1e-9 relative at z_max); em1_fp64 = 1 when T
@@ -179,6 +192,11 @@ __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, floa
 // B300's FP64 pipe (about 1/64 of the FP32 rate) would otherwise co-limit the
 // step; per-point sums over walks stay in FP64.
 // ---------------------------------------------------------------------------
+// The double or the host-made float copy of a scalar, by walk precision.
+template <typename T> __device__ __forceinline__ T pick(double d, float f);
+template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
 // Walk enumeration index -> (point, walk index, output slot).
 struct WalkId {
   uint32_t p, i;

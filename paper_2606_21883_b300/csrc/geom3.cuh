@@ -28,7 +28,7 @@ __device__ __forceinline__ void cp3(const DevProblem& pb, const T* x, T* out) {
     const T nx = dsqrt<T>(dot3(x, x));
     out[0] = x[0] / nx; out[1] = x[1] / nx; out[2] = x[2] / nx;
   } else {  // torus: nearest point of the centre circle, then the tube around it
-    const T R = T(pb.R), a = T(pb.a_tube);
+    const T R = pick<T>(pb.R, pb.sf.R), a = pick<T>(pb.a_tube, pb.sf.a);
     const T rho = dsqrt<T>(x[0] * x[0] + x[1] * x[1]);
     const T c0 = R * x[0] / rho, c1 = R * x[1] / rho;
     T w[3] = {x[0] - c0, x[1] - c1, x[2] - T(0)};
@@ -45,8 +45,13 @@ __device__ __forceinline__ void cp3(const DevProblem& pb, const T* x, T* out) {
 // with e.y <= h is outside Omega: distance 0.
 template <int MK, typename T>
 __device__ __forceinline__ T delta_gamma3(const DevProblem& pb, const T* y, T* yg) {
-  const T e[3] = {T(pb.e[0]), T(pb.e[1]), T(pb.e[2])};
-  const T h = T(pb.h);
+  T e[3];
+  if constexpr (sizeof(T) == 4) {
+    e[0] = pb.ef[0]; e[1] = pb.ef[1]; e[2] = pb.ef[2];
+  } else {
+    e[0] = pb.e[0]; e[1] = pb.e[1]; e[2] = pb.e[2];
+  }
+  const T h = pick<T>(pb.h, pb.sf.h);
   const T ey = dot3(e, y);
   if constexpr (MK == kEuclid) {
     for (int i = 0; i < 3; ++i) yg[i] = y[i] - (ey - h) * e[i];
@@ -74,7 +79,7 @@ __device__ __forceinline__ T delta_gamma3(const DevProblem& pb, const T* y, T* y
     rt2 += rti * rti;
   }
   if (ey <= h) return T(0);
-  T ex = fabs(rn) - T(pb.rho_geo);
+  T ex = fabs(rn) - pick<T>(pb.rho_geo, pb.sf.rho_geo);
   if (ex < T(0)) ex = T(0);
   return dsqrt<T>(rt2 + ex * ex);
   }
@@ -86,7 +91,7 @@ __device__ __forceinline__ T func3(const DevProblem& pb, const DevFunc& fn, cons
   if (fn.kind == kPoly) {
     T total = T(0);
     for (int t = 0; t < fn.n_terms; ++t) {
-      T prod = T(fn.coef[t]);
+      T prod = pick<T>(fn.coef[t], fn.coef_f[t]);
       for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
         const T xv = x[fn.var[q]];
         for (int e = 0; e < fn.pw[q]; ++e) prod *= xv;
@@ -96,7 +101,7 @@ __device__ __forceinline__ T func3(const DevProblem& pb, const DevFunc& fn, cons
     return total;
   }
   if (fn.kind == kTorusFourier) {
-    const T R = T(pb.R), a = T(pb.a_tube);
+    const T R = pick<T>(pb.R, pb.sf.R), a = pick<T>(pb.a_tube, pb.sf.a);
     const T rho = dsqrt<T>(x[0] * x[0] + x[1] * x[1]);
     const T dr = rho - R;
     const T nr = dsqrt<T>(dr * dr + x[2] * x[2]);
@@ -119,9 +124,9 @@ __device__ __forceinline__ T func3(const DevProblem& pb, const DevFunc& fn, cons
         const T Tp = fn.modes[t][2] == 0 ? -T(m) * sm : T(m) * cm;
         const T rr = R + a * ct;
         const T lap = T(m * m) * Tv / (a * a) + st * Tp / (a * rr) + T(q * q) * Tv / (rr * rr);
-        val = Pv * (lap + T(pb.sigma) * Tv);
+        val = Pv * (lap + pick<T>(pb.sigma, pb.sf.sigma) * Tv);
       }
-      total += T(fn.coef[t]) * val;
+      total += pick<T>(fn.coef[t], fn.coef_f[t]) * val;
     }
     return total;
   }
@@ -134,10 +139,11 @@ __device__ __forceinline__ T func3(const DevProblem& pb, const DevFunc& fn, cons
     tr += T(fn.A[i * 3 + i]);
     for (int j = 0; j < 3; ++j) quad += T(fn.A[i * 3 + j]) * s[i] * s[j];
   }
-  if (!fn.apply_op) return T(fn.c0) + lin + quad;
+  const T c0 = pick<T>(fn.c0, fn.c0_f);
+  if (!fn.apply_op) return c0 + lin + quad;
   const T mean = tr / T(3);
-  const T sg = T(pb.sigma);
-  return sg * (T(fn.c0) + mean) + (T(2) + sg) * lin + (T(6) + sg) * (quad - mean);
+  const T sg = pick<T>(pb.sigma, pb.sf.sigma);
+  return sg * (c0 + mean) + (T(2) + sg) * lin + (T(6) + sg) * (quad - mean);
 }
 
 }  // namespace mpwos

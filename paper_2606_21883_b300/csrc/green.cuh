@@ -232,4 +232,25 @@ __host__ __device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS,
   return v0 + wa * (v1 - v0);
 }
 
+// FP32 lookup with the problem's precomputed scales (no double arithmetic).
+__device__ __forceinline__ float table_lookup32(const DevProblem& pb, float a, float U) {
+  const int NS = pb.NS, NA = pb.NA, side_len = NS + 2;
+  const bool upper = U > 0.5f;
+  const float v = sqrtf(upper ? 1.0f - U : U);
+  const float xs = v * pb.sf.tab_scale;
+  int j = static_cast<int>(xs);
+  j = j < 0 ? 0 : (j > NS - 2 ? NS - 2 : j);
+  const float f = xs - static_cast<float>(j);
+  const float* tab = pb.tab32 + (upper ? side_len : 0);
+  if (NA == 1) return catmull_rom(tab, j, f);
+  const float fa = a * a * 0.25f * pb.sf.z_scale;
+  int ia = static_cast<int>(fa);
+  ia = ia < 0 ? 0 : (ia > NA - 2 ? NA - 2 : ia);
+  const float wa = fminf(fa - static_cast<float>(ia), 1.0f);
+  const float* r0 = tab + static_cast<size_t>(ia) * (2 * side_len);
+  const float v0 = catmull_rom(r0, j, f);
+  const float v1 = catmull_rom(r0 + 2 * side_len, j, f);
+  return v0 + wa * (v1 - v0);
+}
+
 }  // namespace mpwos

@@ -13,9 +13,9 @@ static const void* walk3_f32_fn(const DevProblem& pb) {
     case kSphere: return reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1>);
     case kTorus: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1>);
     case kPointCloud:
-      return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f32_kernel<kPointCloud, 8>)
-           : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_kernel<kPointCloud, 16>)
-                           : reinterpret_cast<const void*>(walk3_f32_kernel<kPointCloud, 32>);
+      return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 8>)
+           : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 16>)
+                           : reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 32>);
     default: return nullptr;
   }
 }

@@ -236,6 +236,27 @@ void fill_em1_poly(DevProblem& pb, int n, double z_max) {
   pb.em1_fp64 = (z_max > 0.0 && last > 1e-9 * em) ? 1 : 0;
 }
 
+// FP32 copies of the loop-invariant scalars (after the table and cloud are set).
+void fill_scalars_f(DevProblem& pb) {
+  ScalarsF& f = pb.sf;
+  f.eps = static_cast<float>(pb.eps);
+  f.theta = static_cast<float>(pb.theta);
+  f.rho_geo = static_cast<float>(pb.rho_geo);
+  f.sqrt_sigma = static_cast<float>(pb.sqrt_sigma);
+  f.sigma = static_cast<float>(pb.sigma);
+  f.inv_sigma = static_cast<float>(1.0 / pb.sigma);
+  f.R = static_cast<float>(pb.R);
+  f.a = static_cast<float>(pb.a_tube);
+  f.inv_a = pb.a_tube != 0.0 ? static_cast<float>(1.0 / pb.a_tube) : 0.0f;
+  f.h = static_cast<float>(pb.h);
+  f.sh = static_cast<float>(std::sqrt(std::max(0.0, 1.0 - pb.h * pb.h)));
+  f.c_h = static_cast<float>(pb.cl_c_h);
+  f.tab_scale = static_cast<float>((pb.NS - 1) / 0.70710678118654752);
+  f.z_scale = (pb.NA > 1 && pb.z_max > 0.0) ? static_cast<float>((pb.NA - 1) / pb.z_max) : 0.0f;
+  for (int a = 0; a < 3; ++a) pb.cl_origin_f[a] = static_cast<float>(pb.cl_origin[a]);
+  pb.cl_cell_f = static_cast<float>(pb.cl_cell);
+}
+
 // Rows of a variable-radius table: the law's dependence on z = a^2/4 enters
 // through z/(nu + j); high dimensions need few rows.
 int table_rows(int n) { return n <= 8 ? kTableNA : 17; }
@@ -246,7 +267,11 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
   d.apply_op = f.apply_op;
   d.n_terms = f.n_terms;
   d.c0 = f.c0;
-  for (int t = 0; t < f.n_terms; ++t) d.coef[t] = f.coef[t];
+  d.c0_f = static_cast<float>(f.c0);
+  for (int t = 0; t < f.n_terms; ++t) {
+    d.coef[t] = f.coef[t];
+    d.coef_f[t] = static_cast<float>(f.coef[t]);
+  }
   if (f.kind == MPWOS_FUNC_POLY) {
     for (int t = 0; t <= f.n_terms; ++t) d.term_off[t] = static_cast<int16_t>(f.n_terms ? f.term_off[t] : 0);
     const int nf = f.n_terms ? f.term_off[f.n_terms] : 0;
@@ -498,6 +523,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   pb.NA = tab->NA;
   pb.NS = tab->NS;
   pb.z_max = tab->z_max;
+  fill_scalars_f(pb);
   return MPWOS_OK;
 }
 
@@ -513,7 +539,7 @@ int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tab32)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
   const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
-  const int block = n3 ? (fp64 ? 128 : 256) : 128;
+  const int block = n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256) : 128;
   const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
   const int64_t per_block = n3 ? block : block / 32;
   int64_t grid = static_cast<int64_t>(ctx->sm_count) * occ;
@@ -878,6 +904,7 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   ctx->launches += 1;
   pb.tab64 = tab64;
   pb.tab32 = tab32;
+  fill_scalars_f(pb);
   pb.S_out = S;
   pb.K_out = K;
   pb.flag_out = F;

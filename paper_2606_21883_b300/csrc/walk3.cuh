@@ -37,9 +37,9 @@ template <int MK, int KM, typename T>
 __device__ __forceinline__ T rho_geo_at(const DevProblem& pb, const T* y) {
   if constexpr (MK == kPointCloud) {
     Knn<T, KM> R;
-    return T(pb.cl_c_h) * cloud_knn<T, KM>(pb, y, R);
+    return pick<T>(pb.cl_c_h, pb.sf.c_h) * cloud_knn<T, KM>(pb, y, R);
   } else {
-    return T(pb.rho_geo);
+    return pick<T>(pb.rho_geo, pb.sf.rho_geo);
   }
 }
 
@@ -49,7 +49,7 @@ __device__ __forceinline__ bool source_is_constant(const DevFunc& f) {
 }
 
 template <int MK, int KM>
-__global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) {
+__device__ __forceinline__ void walk3_f64_body(const DevProblem& pb) {
   const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -191,10 +191,10 @@ __device__ __forceinline__ void torus_angles32(float R, const float* x, float& c
 // (-Delta_M + sigma) u or u itself for a torus Fourier series, from the angles.
 __device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevFunc& fn, float ct, float st,
                                                float cph, float sph) {
-  const float R = static_cast<float>(pb.R), a = static_cast<float>(pb.a_tube);
-  const float ia = 1.0f / a;
-  const float irr = 1.0f / (R + a * ct);
-  const float sg = static_cast<float>(pb.sigma);
+  const float R = pb.sf.R, a = pb.sf.a;
+  const float ia = pb.sf.inv_a;
+  const float irr = __fdividef(1.0f, R + a * ct);
+  const float sg = pb.sf.sigma;
   float total = 0.0f;
   for (int t = 0; t < fn.n_terms; ++t) {
     const int m = fn.modes[t][0], q = fn.modes[t][1];
@@ -212,7 +212,7 @@ __device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevF
                         static_cast<float>(q * q) * Tv * irr * irr;
       val = Pv * (lap + sg * Tv);
     }
-    total += static_cast<float>(fn.coef[t]) * val;
+    total += fn.coef_f[t] * val;
   }
   return total;
 }
@@ -227,11 +227,11 @@ __device__ __forceinline__ void cp3_f32(const DevProblem& pb, const float* x, fl
     out[0] = x[0] * inv; out[1] = x[1] * inv; out[2] = x[2] * inv;
   } else {
     // cp = (R + s dr)/rho (x0, x1) + s x2 e_z, dr = rho - R, s = a / sqrt(dr^2 + x2^2)
-    const float R = static_cast<float>(pb.R);
+    const float R = pb.sf.R;
     const float rho2 = x[0] * x[0] + x[1] * x[1];
     const float irho = rsqrtf(rho2);
     const float dr = rho2 * irho - R;
-    const float s = static_cast<float>(pb.a_tube) * rsqrtf(dr * dr + x[2] * x[2]);
+    const float s = pb.sf.a * rsqrtf(dr * dr + x[2] * x[2]);
     const float fac = (R + s * dr) * irho;
     out[0] = x[0] * fac; out[1] = x[1] * fac; out[2] = s * x[2];
   }
@@ -249,7 +249,7 @@ __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* 
   if constexpr (MK == kTorus) {
     if (pb.f.kind == kTorusFourier) {
       float ct, st, cph, sph;
-      torus_angles32(static_cast<float>(pb.R), Z, ct, st, cph, sph);
+      torus_angles32(pb.sf.R, Z, ct, st, cph, sph);
       return torus_series32(pb, pb.f, ct, st, cph, sph);
     }
   }
@@ -259,19 +259,19 @@ __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* 
 }
 
 template <int MK, int KM>
-__global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
+__device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
   const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
   const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
   const int nv = pb.n_v;
-  const float eps = static_cast<float>(pb.eps);
-  const float theta = static_cast<float>(pb.theta);
-  const float rgeo = static_cast<float>(pb.rho_geo);
-  const float sqs = static_cast<float>(pb.sqrt_sigma);
+  const float eps = pb.sf.eps;
+  const float theta = pb.sf.theta;
+  const float rgeo = pb.sf.rho_geo;
+  const float sqs = pb.sf.sqrt_sigma;
   const F2 tau = f2_from_double(pb.tau_w);
-  const float inv_sigma = static_cast<float>(1.0 / pb.sigma);
+  const float inv_sigma = pb.sf.inv_sigma;
 
   float Y[3];
   F2 W{1.0f, 0.0f}, S{0.0f, 0.0f};
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
       const float U = u23(b1.z);
       const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
       for (int q = 0; q < 3; ++q) Th[q] = Y[q] + sc * g[q];
-      float t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, U);
+      float t = table_lookup32(pb, a, U);
       t = fminf(fmaxf(t, 0.0f), 1.0f);
       const float zs = (r * t) * rsqrtf(fmaxf(dot3(z, z), 1e-30f));
       float Z[3];
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
       const uint32_t nu = 2u * ((3u * static_cast<uint32_t>(1 + nv) + 1u) / 2u);
       for (int l = 0; l < nv; ++l) {
         const float U = uniform_at32(nu + static_cast<uint32_t>(l), kk, i, p, K);
-        float t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, U);
+        float t = table_lookup32(pb, a, U);
         t = fminf(fmaxf(t, 0.0f), 1.0f);
         for (int q = 0; q < 3; ++q)
           g[q] = gaussian_at32(3u * static_cast<uint32_t>(1 + l) + static_cast<uint32_t>(q), kk, i, p, K);
@@ -373,5 +373,15 @@ __global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) {
     ++k;
   }
 }
+
+// Entry points: the analytic manifolds run 256-thread blocks (64 registers; a
+// 48-register bound measured slower on B300); the point-cloud walk uses
+// 128-thread blocks with a larger register budget.
+template <int MK, int KM>
+__global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) { walk3_f32_body<MK, KM>(pb); }
+template <int MK, int KM>
+__global__ void __launch_bounds__(128) walk3_f32_cloud_kernel(const DevProblem pb) { walk3_f32_body<MK, KM>(pb); }
+template <int MK, int KM>
+__global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) { walk3_f64_body<MK, KM>(pb); }
 
 }  // namespace mpwos

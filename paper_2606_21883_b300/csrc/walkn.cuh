@@ -131,7 +131,7 @@ template <typename T, int L, int G>
 __device__ __forceinline__ T poly_at(const DevFunc& fn, const T (&base)[L], const T (&dir)[L], T sc, T inv) {
   T total = T(0);
   for (int t = 0; t < fn.n_terms; ++t) {
-    T prod = T(fn.coef[t]);
+    T prod = pick<T>(fn.coef[t], fn.coef_f[t]);
     for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
       const int v = fn.var[q];
       const T xv = (gather<T, L, G>(base, v) + sc * gather<T, L, G>(dir, v)) * inv;
@@ -147,7 +147,7 @@ template <typename T, int L, int G>
 __device__ __forceinline__ T poly_at_boundary(const DevFunc& fn, const T (&Y)[L], const T* e, T yg_scale, T yg_e) {
   T total = T(0);
   for (int t = 0; t < fn.n_terms; ++t) {
-    T prod = T(fn.coef[t]);
+    T prod = pick<T>(fn.coef[t], fn.coef_f[t]);
     for (int q = fn.term_off[t]; q < fn.term_off[t + 1]; ++q) {
       const int v = fn.var[q];
       const T xv = yg_scale * gather<T, L, G>(Y, v) + yg_e * e[v];
@@ -188,9 +188,10 @@ __device__ __forceinline__ T sphere_quad_at(const DevProblem& pb, const DevFunc&
   T acc[3] = {on ? vT[lane] * sj : T(0), sj * As, on ? AT[lane * D + lane] : T(0)};
   warp_sum<3>(acc);
   const T lin = acc[0], quad = acc[1], tr = acc[2];
-  if (!fn.apply_op) return T(fn.c0) + lin + quad;
-  const T d = T(D - 1), sg = T(pb.sigma), mean = tr / T(D);
-  return sg * (T(fn.c0) + mean) + (d + sg) * lin + (T(2) * (d + T(1)) + sg) * (quad - mean);
+  const T c0 = pick<T>(fn.c0, fn.c0_f);
+  if (!fn.apply_op) return c0 + lin + quad;
+  const T d = T(D - 1), sg = pick<T>(pb.sigma, pb.sf.sigma), mean = tr / T(D);
+  return sg * (c0 + mean) + (d + sg) * lin + (T(2) * (d + T(1)) + sg) * (quad - mean);
 }
 
 // (Q^T g)_lane and |g|^2 for one Gaussian vector: per-lane partial products
@@ -252,10 +253,11 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
   const int nv = pb.n_v;
   const uint32_t nb = static_cast<uint32_t>((n + G - 1) / G);
   // loop-invariant parameters in the walk's precision
-  const T eps_t = T(pb.eps), h_t = T(pb.h), rgeo_t = T(pb.rho_geo), theta_t = T(pb.theta);
-  const T sqs_t = T(pb.sqrt_sigma);
-  const T sh_t = T(sqrt(1.0 - pb.h * pb.h));
-  const float inv_sigma_f = static_cast<float>(1.0 / pb.sigma);
+  const T eps_t = pick<T>(pb.eps, pb.sf.eps), h_t = pick<T>(pb.h, pb.sf.h);
+  const T rgeo_t = pick<T>(pb.rho_geo, pb.sf.rho_geo), theta_t = pick<T>(pb.theta, pb.sf.theta);
+  const T sqs_t = pick<T>(pb.sqrt_sigma, pb.sf.sqrt_sigma);
+  const T sh_t = pick<T>(sqrt(1.0 - pb.h * pb.h), pb.sf.sh);
+  const float inv_sigma_f = pb.sf.inv_sigma;
   const bool bnd = !pb.closed;
   const T* eT = kF64 ? reinterpret_cast<const T*>(pb.e) : reinterpret_cast<const T*>(pb.ef);
   const T* QT = nullptr;
@@ -398,7 +400,7 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
         const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l >> 2), kk, wi, p, K);
         const int s4 = l & 3;
         const float U = u23(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
-        t = table_lookup<float>(pb.tab32, pb.NA, pb.NS, pb.z_max, a, U);
+        t = table_lookup32(pb, a, U);
         t = fminf(fmaxf(t, 0.0f), 1.0f);
       }
       gen_vector<T>(g, n, lane, nb * static_cast<uint32_t>(1 + l), kk, wi, p, K);
