@@ -61,6 +61,13 @@ extern "C" {
 #define MPWOS_FP64 0   /* FP64 walk; per-walk identical draws to the CPU oracle         */
 #define MPWOS_FP32 1   /* FP32 positions/projection/sampling, FP64 weights and sums     */
 
+/* ---- the projection Q^T g of the FP32 embedded-sphere walk --------------- */
+#define MPWOS_PROJ_AUTO 0     /* tensor cores for n >= 128, CUDA cores below               */
+#define MPWOS_PROJ_TENSOR 1   /* tcgen05 split-BF16 product (hi hi + hi lo + lo hi), FP32
+                                 accumulator: ~2^-17 relative per component; FP32 precision
+                                 and EMBEDDED_SPHERE only (MPWOS_EINVAL otherwise)           */
+#define MPWOS_PROJ_CUDA 2     /* FP32 dot products on the CUDA cores                       */
+
 typedef struct mpwos_ctx mpwos_ctx;
 
 /* Manifold M (Sec. 2.1).  Q, b are host arrays (embedded sphere only),
@@ -123,10 +130,12 @@ typedef struct {
   int64_t max_steps; /* per-walk cap; walks reaching it are flagged (EMAXSTEPS) */
   uint64_t seed;     /* Philox key                                              */
   int precision;     /* MPWOS_FP64 or MPWOS_FP32                                */
+  int projection;    /* MPWOS_PROJ_*: embedded sphere in FP32 only; ignored elsewhere
+                        except that MPWOS_PROJ_TENSOR is rejected there             */
 } mpwos_params;
 
 /* Fill a params struct with the defaults: eps 1e-3, tau_w 1e-8, theta 0.95,
- * c_kappa 1.2, n_v 1, max_steps 1e7, seed 0, FP64. */
+ * c_kappa 1.2, n_v 1, max_steps 1e7, seed 0, FP64, MPWOS_PROJ_AUTO. */
 void mpwos_params_default(mpwos_params* p);
 
 /* Create a context on CUDA device `device` (owns device state, tables, a
@@ -248,6 +257,16 @@ int mpwos_green_radius(mpwos_ctx* ctx, int n, double a_max, const double* a, con
 /* c_{sigma,r} (Lemma 2.1 via the Lemma 3.1 series) for ambient dimension n at
  * a = sqrt(sigma) r, evaluated by the device code; host arrays. */
 int mpwos_c_sigma_r(mpwos_ctx* ctx, int n, const double* a, double* c, int64_t count);
+
+/* The embedded-sphere projection Q^T g (eq. projected_chain_update: the
+ * closest point of an embedded sphere needs Q^T (x - b)) on the tensor cores,
+ * exactly as the FP32 walk forms it: out[r][j] = sum_i G[r][i] Q[i][j] for the
+ * rows of G (rows x n, FP32, row-major), Q n x D row-major (host FP64, rounded
+ * to BF16 hi + lo), G rounded to BF16 hi + lo, three BF16 products accumulated
+ * in FP32; gg[r] = |G_r|^2 in FP32.  out is rows x D.  1 <= n <= 1024,
+ * 1 <= D <= 31.  Host arrays.  MPWOS_ETIMEDOUT if a bounded wait ran out. */
+int mpwos_tc_project(mpwos_ctx* ctx, const double* Q, int n, int D, const float* G, int64_t rows,
+                     float* out, float* gg);
 
 /* Number of the library's own kernel launches so far on this context. */
 int64_t mpwos_launch_count(const mpwos_ctx* ctx);

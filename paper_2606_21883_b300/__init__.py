@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(HERE, "libmpwos.so")
 MPWOS_OK, MPWOS_EINVAL, MPWOS_ENOMEM, MPWOS_ECUDA = 0, 1, 2, 3
 MPWOS_ETIMEDOUT, MPWOS_ECANCELED, MPWOS_EMAXSTEPS, MPWOS_ENOTFOUND, MPWOS_EBUSY = 4, 5, 6, 7, 8
 FP64, FP32 = 0, 1
+PROJ_AUTO, PROJ_TENSOR, PROJ_CUDA = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -52,7 +53,8 @@ class ProblemDesc(C.Structure):
 
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("tau_w", C.c_double), ("theta", C.c_double), ("c_kappa", C.c_double),
-                ("n_v", C.c_int), ("max_steps", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int)]
+                ("n_v", C.c_int), ("max_steps", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int),
+                ("projection", C.c_int)]
 
 
 _lib: Optional[C.CDLL] = None
@@ -80,6 +82,8 @@ def lib() -> C.CDLL:
         L.mpwos_green_radius.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_int64, C.c_int]
         L.mpwos_c_sigma_r.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int64]
+        L.mpwos_tc_project.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                                       C.c_void_p, C.c_void_p]
         L.mpwos_serve_config.argtypes = [C.c_void_p, C.c_int, C.c_size_t, C.c_int64]
         L.mpwos_submit.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc), C.POINTER(Params),
                                    C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_uint64)]
@@ -153,9 +157,10 @@ class _Marshal:
         return md, pd
 
 
-def make_params(params, precision) -> Params:
+def make_params(params, precision, projection=PROJ_AUTO) -> Params:
     return Params(eps=params.eps, tau_w=params.tau_w, theta=params.theta, c_kappa=params.c_kappa,
-                  n_v=params.n_v, max_steps=params.max_steps, seed=params.seed, precision=precision)
+                  n_v=params.n_v, max_steps=params.max_steps, seed=params.seed, precision=precision,
+                  projection=projection)
 
 
 class Context:
@@ -195,11 +200,11 @@ class Context:
         return self._check(self.L.mpwos_set_stream(self.h, C.c_void_p(stream_handle)))
 
     # -- the walk ---------------------------------------------------------------
-    def solve(self, problem, params, pts, N, precision=FP64, out=None):
+    def solve(self, problem, params, pts, N, precision=FP64, out=None, projection=PROJ_AUTO):
         """mpwos_solve: returns (mean, stderr, mean_steps, status); pts host or device."""
         mar = _Marshal()
         md, pd = mar.problem(problem)
-        prm = make_params(params, precision)
+        prm = make_params(params, precision, projection)
         P = int(pts.shape[0])
         if out is None:
             out = (np.zeros(P), np.zeros(P), np.zeros(P))
@@ -210,11 +215,11 @@ class Context:
         self._check(rc, (MPWOS_OK, MPWOS_EMAXSTEPS))
         return out[0], out[1], out[2], rc
 
-    def walk_scores(self, problem, params, pts, N, precision=FP64):
+    def walk_scores(self, problem, params, pts, N, precision=FP64, projection=PROJ_AUTO):
         """mpwos_walk_scores: per-walk S (P x N), K, flags."""
         mar = _Marshal()
         md, pd = mar.problem(problem)
-        prm = make_params(params, precision)
+        prm = make_params(params, precision, projection)
         P = int(pts.shape[0])
         if not hasattr(pts, "data_ptr"):
             pts = mar.arr(pts)
@@ -226,11 +231,11 @@ class Context:
         self._check(rc)
         return S, K, fl
 
-    def walk_scores_device(self, problem, params, pts, N, precision, S, K, flags):
+    def walk_scores_device(self, problem, params, pts, N, precision, S, K, flags, projection=PROJ_AUTO):
         """mpwos_walk_scores into caller-owned device tensors (no host copies)."""
         mar = _Marshal()
         md, pd = mar.problem(problem)
-        prm = make_params(params, precision)
+        prm = make_params(params, precision, projection)
         rc = self.L.mpwos_walk_scores(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
                                       int(pts.shape[0]), int(N), _ptr(S), _ptr(K), _ptr(flags))
         return self._check(rc)
@@ -239,11 +244,11 @@ class Context:
     def serve_config(self, max_active=0, mem_bytes=0, chunk_walks=0):
         return self._check(self.L.mpwos_serve_config(self.h, int(max_active), int(mem_bytes), int(chunk_walks)))
 
-    def submit(self, problem, params, pts, walk_budget, target_stderr=0.0, precision=FP32):
+    def submit(self, problem, params, pts, walk_budget, target_stderr=0.0, precision=FP32, projection=PROJ_AUTO):
         """mpwos_submit: returns the request id (query points copied at submit)."""
         mar = _Marshal()
         md, pd = mar.problem(problem)
-        prm = make_params(params, precision)
+        prm = make_params(params, precision, projection)
         pts = mar.arr(pts)
         rid = C.c_uint64(0)
         self._check(self.L.mpwos_submit(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
@@ -276,6 +281,19 @@ class Context:
         out = np.zeros_like(ctr)
         self._check(self.L.mpwos_philox(self.h, _ptr(ctr), key0, key1, _ptr(out), ctr.shape[0]))
         return out
+
+    def tc_project(self, Q, G):
+        """mpwos_tc_project: (G Q, |G_r|^2) through the tensor-core contraction (FP32)."""
+        Q = np.ascontiguousarray(Q, dtype=np.float64)
+        G = np.ascontiguousarray(G, dtype=np.float32)
+        n, D = Q.shape
+        rows = G.shape[0]
+        assert G.shape[1] == n
+        out = np.zeros((rows, D), dtype=np.float32)
+        gg = np.zeros(rows, dtype=np.float32)
+        self._check(self.L.mpwos_tc_project(self.h, _ptr(Q), int(n), int(D), _ptr(G), int(rows), _ptr(out),
+                                            _ptr(gg)))
+        return out, gg
 
     def green_radius(self, n, a_max, a, U, precision=FP64):
         a = np.ascontiguousarray(a, dtype=np.float64)

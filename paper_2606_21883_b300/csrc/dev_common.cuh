@@ -98,6 +98,10 @@ struct DevProblem {
   double* S_out;
   int32_t* K_out;
   int32_t* flag_out;
+  // tensor-core embedded walk: Q^T as BF16 hi + lo in the kernel's swizzled
+  // shared-memory image (128 KB), and a status word (bit 0: a wait ran out)
+  const uint4* tc_bimg;
+  unsigned* dev_status;
 };
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,498 @@
+// embed_tc.cuh — the FP32 walk on an embedded sphere Q S^d + b in R^n with the
+// projection Q^T g of every Gaussian vector on the 5th-generation tensor cores
+// (the dense contraction of the closest point Q normalize(Q^T (x - b)) + b of
+// the projected chain, Sec. 2, eq. projected_chain_update).
+//
+// One persistent CTA of 512 threads per SM walks tiles of 128 walkers in
+// lockstep: a closed embedded sphere has constant radius, so every walk of the
+// tile stops at the same index.  For each Gaussian vector of a step (the
+// interior samples Z_l, then the sphere sample Theta) the tile's components are
+// generated in K-chunks of 64 — four threads per walker, 16 components (4
+// Philox blocks) each, the same draws as the warp walk — split into BF16
+// hi + lo and stored into a 128-byte-swizzled K-major A tile (128 rows =
+// walkers; two stages).  One elected thread issues, per 16-wide K slice, three
+// tcgen05.mma kind::f16 products into one FP32 TMEM accumulator (128 x 32):
+//   A_hi B_hi + A_hi B_lo + A_lo B_hi,   B = Q^T (32 x K, BF16 hi and lo),
+// the two correction products refining the BF16 product to ~2^-17 relative.
+// B stays resident in shared memory for the whole launch.  tcgen05.commit
+// arrives on the stage's mbarrier; warps 0..3 read their 32 TMEM lanes
+// (walkers) with tcgen05.ld and finish the step in FP32 registers.  Every
+// mbarrier wait is bounded; on expiry the CTA records a status bit and stops.
+#pragma once
+#include "dev_common.cuh"
+#include "green.cuh"
+
+namespace mpwos {
+namespace tc {
+
+constexpr int kThreads = 512;
+constexpr int kM = 128;                   // walkers per tile = accumulator rows = TMEM lanes
+constexpr int kTPW = kThreads / kM;       // generator threads per walker
+constexpr int kN = 32;                    // accumulator columns (d + 1 <= 31, zero padded)
+constexpr int kChunkK = 64;               // BF16 elements per 128-byte row
+constexpr int kMaxChunks = 16;            // n <= 1024
+constexpr int kBChunk = kN * 128;         // one B chunk (4 KB)
+constexpr int kAHalf = kM * 128;          // one A chunk, hi or lo (16 KB)
+constexpr int kBBytes = 2 * kMaxChunks * kBChunk;   // B hi + lo: 128 KB
+constexpr int kABytes = 2 * 2 * kAHalf;              // 2 stages x (hi + lo): 64 KB
+constexpr int kMiscBytes = 8192;
+constexpr int kSStride = 33;                                 // walker state row (conflict-free)
+constexpr int kSBytes = kM * kSStride * 4;                   // intrinsic states s: 16.5 KB
+constexpr int kSmemBytes = kBBytes + kABytes + kMiscBytes + kSBytes + 1024;   // + 1 KB alignment slack
+constexpr uint32_t kStatusTimeout = 1u;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete; false when about one
+// second (2^31 SM cycles) passes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  if (mbar_try_wait(addr, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(addr, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem] B[smem]^T: BF16 operands, FP32 accumulator.
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Shared-memory matrix descriptor of a K-major, 128-byte-swizzled operand:
+// start address, stride between 8-row groups 1024 bytes, descriptor version 1,
+// swizzle mode 2 (128 B).  The leading-dimension offset is unused here.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major,
+// N = 32 (bits 17..22 hold N/8), M = 128 (bits 24..28 hold M/16).
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(kN) >> 3) << 17) |
+                            ((static_cast<uint32_t>(kM) >> 4) << 24);
+
+// Byte offset of 16-byte unit u of row r in a 128-byte-swizzled tile.
+__device__ __forceinline__ uint32_t sw128(uint32_t r, uint32_t u) { return r * 128u + ((u ^ (r & 7u)) << 4); }
+
+// Two FP32 values rounded to BF16; `first` lands in the low half (lower address).
+__device__ __forceinline__ uint32_t pack_bf16x2(float first, float second) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(second), "f"(first));
+  return r;
+}
+__device__ __forceinline__ float bf16_low(uint32_t packed) { return __uint_as_float(packed << 16); }
+__device__ __forceinline__ float bf16_high(uint32_t packed) { return __uint_as_float(packed & 0xFFFF0000u); }
+
+struct Smem {
+  unsigned char* B;   // Q^T hi chunks [0, 16), lo chunks [16, 32)
+  unsigned char* A;   // stage s: hi at 2 s kAHalf, lo at (2 s + 1) kAHalf
+  uint64_t* mbar;     // one per stage
+  uint32_t* tmem_slot;
+  float* gg_part;     // kThreads partial |g|^2
+  float* Af;          // 32 x 32, zero padded
+  float* vf;          // 32, zero padded
+  float* s;           // kM x kSStride: walker states (intrinsic unit vectors)
+};
+
+// The walk's Gaussian vector of blocks jb + b of step kk of walk (p, wi):
+// components 4 b .. 4 b + 3 (zero past n), the warp walk's draws.
+struct PhiloxSource {
+  const PhiloxKeys* K;
+  uint32_t jb, kk, wi, p;
+  int n;
+  __device__ __forceinline__ void operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
+    g0 = g1 = g2 = g3 = 0.0f;
+    if (4 * b < n) {
+      const U4 r = philox4x32_10(jb + static_cast<uint32_t>(b), kk, wi, p, *K);
+      box_muller32(u23(r.x), u23(r.y), g0, g1);
+      box_muller32(u23(r.z), u23(r.w), g2, g3);
+      if (4 * b + 1 >= n) g1 = 0.0f;
+      if (4 * b + 2 >= n) g2 = 0.0f;
+      if (4 * b + 3 >= n) g3 = 0.0f;
+    }
+  }
+};
+
+// Row `row` of a caller-given rows x n FP32 matrix (verification primitive).
+struct MatrixSource {
+  const float* G;
+  int64_t row, rows;
+  int n;
+  __device__ __forceinline__ void operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
+    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (row < rows)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (4 * b + q < n) v[q] = G[row * n + 4 * b + q];
+    g0 = v[0]; g1 = v[1]; g2 = v[2]; g3 = v[3];
+  }
+};
+
+// Q^T g (threads < 128: their row's 32 columns) and |g|^2 for the vector that
+// `src` generates.  Thread (row, part) generates blocks 16 c + 4 part + 0..3
+// of chunk c, i.e. components 64 c + 16 part + 0..15.
+template <class Src>
+__device__ __forceinline__ void project_vector(const Smem& sm, uint32_t taddr, int nchunks, const Src& src,
+                                               uint32_t (&ph)[2], bool& ok, float (&q)[32], float& gg) {
+  const int tid = threadIdx.x;
+  const uint32_t row = static_cast<uint32_t>(tid & (kM - 1));
+  const int part = tid / kM;
+  float acc = 0.0f;
+  for (int c = 0; c < nchunks; ++c) {
+    const int s = c & 1;
+    if (c >= 2) {   // the products of chunk c - 2 have left this stage
+      if (ok) ok = mbar_wait(smem_u32(&sm.mbar[s]), ph[s]);
+      ph[s] ^= 1u;
+    }
+    unsigned char* Ahi = sm.A + (2 * s) * kAHalf;
+    unsigned char* Alo = Ahi + kAHalf;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {   // a 16-byte unit = 8 components = 2 blocks of 4
+      uint32_t hw[4], lw[4];
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) {
+        float g0, g1, g2, g3;
+        src(16 * c + 4 * part + 2 * u + bb, g0, g1, g2, g3);
+        acc = fmaf(g0, g0, fmaf(g1, g1, fmaf(g2, g2, fmaf(g3, g3, acc))));
+        const uint32_t h01 = pack_bf16x2(g0, g1), h23 = pack_bf16x2(g2, g3);
+        hw[2 * bb] = h01;
+        hw[2 * bb + 1] = h23;
+        lw[2 * bb] = pack_bf16x2(g0 - bf16_low(h01), g1 - bf16_high(h01));
+        lw[2 * bb + 1] = pack_bf16x2(g2 - bf16_low(h23), g3 - bf16_high(h23));
+      }
+      const uint32_t off = sw128(row, static_cast<uint32_t>(2 * part + u));
+      *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+      *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+    }
+    fence_proxy_async();   // generic-proxy stores -> visible to the tensor core
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a_hi = smem_u32(Ahi), a_lo = smem_u32(Alo);
+      const uint32_t b_hi = smem_u32(sm.B + c * kBChunk), b_lo = smem_u32(sm.B + (kMaxChunks + c) * kBChunk);
+#pragma unroll
+      for (int k4 = 0; k4 < kChunkK / 16; ++k4) {   // 16 BF16 = 32 bytes per K slice
+        const uint32_t ko = static_cast<uint32_t>(k4 * 32);
+        mma_bf16(taddr, desc_sw128(a_hi + ko), desc_sw128(b_hi + ko), kIdesc, (c | k4) != 0 ? 1u : 0u);
+        mma_bf16(taddr, desc_sw128(a_hi + ko), desc_sw128(b_lo + ko), kIdesc, 1u);
+        mma_bf16(taddr, desc_sw128(a_lo + ko), desc_sw128(b_hi + ko), kIdesc, 1u);
+      }
+      mma_commit(smem_u32(&sm.mbar[s]));
+    }
+  }
+  for (int c = (nchunks >= 2 ? nchunks - 2 : 0); c < nchunks; ++c) {   // the last products
+    const int s = c & 1;
+    if (ok) ok = mbar_wait(smem_u32(&sm.mbar[s]), ph[s]);
+    ph[s] ^= 1u;
+  }
+  tc_fence_after();
+  sm.gg_part[tid] = acc;
+  __syncthreads();
+  gg = 0.0f;
+  if (tid < kM) {
+#pragma unroll
+    for (int t = 0; t < kTPW; ++t) gg += sm.gg_part[tid + t * kM];
+    tmem_ld32(taddr + ((static_cast<uint32_t>(tid >> 5) * 32u) << 16), q);
+  }
+  tc_fence_before();
+}
+
+// SPHERE_QUAD source at the point z / |z| (z with DQ components, zero padded).
+template <int DQ>
+__device__ __forceinline__ float sphere_quad_tc(const DevProblem& pb, const Smem& sm, const float (&z)[32], int D) {
+  float zz = 0.0f;
+#pragma unroll
+  for (int j = 0; j < DQ; ++j) zz += z[j] * z[j];
+  const float iz = rsqrtf(zz);
+  float lin = 0.0f, quad = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DQ; ++i) {
+    lin += sm.vf[i] * z[i];
+    float Az = 0.0f;
+    const float4* row = reinterpret_cast<const float4*>(sm.Af + 32 * i);
+#pragma unroll
+    for (int j4 = 0; j4 < DQ / 4; ++j4) {
+      const float4 a4 = row[j4];
+      Az += a4.x * z[4 * j4] + a4.y * z[4 * j4 + 1] + a4.z * z[4 * j4 + 2] + a4.w * z[4 * j4 + 3];
+    }
+    quad += z[i] * Az;
+  }
+  lin *= iz;
+  quad *= iz * iz;
+  const float c0 = pb.f.c0_f;
+  if (!pb.f.apply_op) return c0 + lin + quad;
+  float tr = 0.0f;
+#pragma unroll
+  for (int i = 0; i < DQ; ++i) tr += sm.Af[33 * i];
+  const float dm = static_cast<float>(D - 1), sg = pb.sf.sigma, mean = tr / static_cast<float>(D);
+  return sg * (c0 + mean) + (dm + sg) * lin + (2.0f * (dm + 1.0f) + sg) * (quad - mean);
+}
+
+// Shared-memory layout of both tensor-core kernels (base aligned to 1 KB, the
+// period of the 128-byte swizzle).
+__device__ __forceinline__ Smem smem_layout(unsigned char* raw) {
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  Smem sm;
+  sm.B = base;
+  sm.A = base + kBBytes;
+  unsigned char* misc = base + kBBytes + kABytes;
+  sm.mbar = reinterpret_cast<uint64_t*>(misc);
+  sm.tmem_slot = reinterpret_cast<uint32_t*>(misc + 16);
+  sm.gg_part = reinterpret_cast<float*>(misc + 64);
+  sm.Af = reinterpret_cast<float*>(misc + 64 + 4 * kThreads);
+  sm.vf = sm.Af + 32 * 32;
+  sm.s = reinterpret_cast<float*>(misc + kMiscBytes);
+  return sm;
+}
+
+// Copy the B image into shared memory, initialise the stage barriers and
+// allocate the 32-column TMEM accumulator (warp 0); all threads call this.
+__device__ __forceinline__ uint32_t tc_begin(const Smem& sm, const uint4* bimg) {
+  const int tid = threadIdx.x;
+  uint4* dst = reinterpret_cast<uint4*>(sm.B);
+  for (int q = tid; q < kBBytes / 16; q += kThreads) dst[q] = bimg[q];
+  if (tid == 0) {
+    mbar_init(smem_u32(&sm.mbar[0]), 1);
+    mbar_init(smem_u32(&sm.mbar[1]), 1);
+    fence_mbar_init();
+  }
+  if ((tid >> 5) == 0) {
+    tmem_alloc(smem_u32(sm.tmem_slot), 32);
+    tmem_relinquish();
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *sm.tmem_slot;
+}
+
+// Release TMEM; after a wait that ran out, first let products in flight land
+// (bounded) and record the status.
+__device__ __forceinline__ void tc_end(const Smem& sm, uint32_t taddr, bool ok, const uint32_t (&ph)[2],
+                                       unsigned* status) {
+  const int tid = threadIdx.x;
+  if (!ok && tid == 0) {
+    mbar_wait(smem_u32(&sm.mbar[0]), ph[0]);
+    mbar_wait(smem_u32(&sm.mbar[1]), ph[1]);
+    atomicOr(status, kStatusTimeout);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((tid >> 5) == 0) tmem_dealloc(taddr, 32);
+}
+
+template <int DQ>
+__global__ void __launch_bounds__(kThreads, 1) embed_tc_kernel(const DevProblem pb) {
+  extern __shared__ unsigned char smem_raw[];
+  const Smem sm = smem_layout(smem_raw);
+  const int tid = threadIdx.x;
+  const int n = pb.n, D = pb.d + 1;
+  const int nchunks = (n + kChunkK - 1) / kChunkK;
+  for (int q = tid; q < 32 * 32; q += kThreads) {
+    const int i = q >> 5, j = q & 31;
+    sm.Af[q] = (i < D && j < D) ? pb.f.Af[i * D + j] : 0.0f;
+  }
+  if (tid < 32) sm.vf[tid] = tid < D ? pb.f.vf[tid] : 0.0f;
+  const uint32_t taddr = tc_begin(sm, pb.tc_bimg);
+
+  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
+  const uint32_t nb = static_cast<uint32_t>((n + 3) / 4);
+  const int nv = pb.n_v;
+  // closed manifold of constant curvature: one radius and one weight pair
+  const float r = pb.sf.theta * pb.sf.rho_geo;
+  const float a = pb.sf.sqrt_sigma * r;
+  F2 c2, om2;
+  if (!pb.em1_fp64) {
+    weights_from_em1(em1_poly32(pb, 0.25f * a * a), pb.sf.inv_sigma, c2, om2);
+  } else {
+    const double ad = static_cast<double>(a);
+    const double em1 = em1_series(0.5 * static_cast<double>(n - 2), 0.25 * (ad * ad));
+    const double cc = 1.0 / (1.0 + em1);
+    c2 = f2_from_double(cc);
+    om2 = f2_from_double(one_minus_c(em1, cc) / pb.sigma);
+  }
+  const F2 tau = f2_from_double(pb.tau_w);
+  const int64_t tiles = (pb.wk_w1 - pb.wk_w0 + kM - 1) / kM;
+  uint32_t ph[2] = {0u, 0u};
+  bool ok = true;
+
+  for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    const int64_t w = pb.wk_w0 + tile * kM + (tid & (kM - 1));
+    const bool active = w < pb.wk_w1;
+    uint32_t p = 0, wi = 0;
+    int64_t o = 0;
+    if (active) {
+      const WalkId id = walk_id(pb, w);
+      p = id.p;
+      wi = id.i;
+      o = id.o;
+    }
+    float* s = sm.s + (tid & (kM - 1)) * kSStride;   // this walker's state (threads < kM)
+    if (tid < kM)
+#pragma unroll
+      for (int j = 0; j < DQ; ++j)
+        s[j] = (active && j < D) ? static_cast<float>(pb.s0[static_cast<size_t>(p) * D + j]) : 0.0f;
+    F2 W{1.0f, 0.0f}, S{0.0f, 0.0f};
+    bool running = active && tid < kM;
+    int flag = 0;
+    int64_t k = 0;      // the tile's step index: uniform over the CTA (it keys every draw)
+    int64_t kstop = 0;  // this walker's stopping index K
+    for (;;) {
+      if (running) {
+        if (W.hi < tau.hi || (W.hi == tau.hi && W.lo < tau.lo)) {
+          running = false;
+        } else if (k >= pb.max_steps) {
+          running = false;
+          flag = 1;
+        }
+        kstop = k;
+      }
+      if (!__syncthreads_or(running)) break;
+      const uint32_t kk = static_cast<uint32_t>(k);
+      float q[32], gg;
+      // interior samples Z_l = s + r t_l g_l / |g_l| and the source average F
+      float F = 0.0f;
+      for (int l = 0; l < nv; ++l) {
+        float t = 0.0f;
+        if (tid < kM) {
+          const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l >> 2), kk, wi, p, K);
+          const int s4 = l & 3;
+          const float U = u23(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
+          t = fminf(fmaxf(table_lookup32(pb, a, U), 0.0f), 1.0f);
+        }
+        const PhiloxSource src{&K, nb * static_cast<uint32_t>(1 + l), kk, wi, p, n};
+        project_vector(sm, taddr, nchunks, src, ph, ok, q, gg);
+        if (tid < kM) {
+          const float zs = (r * t) * rsqrtf(fmaxf(gg, 1e-30f));
+#pragma unroll
+          for (int j = 0; j < 32; ++j) q[j] = j < DQ ? s[j] + zs * q[j] : 0.0f;
+          F += sphere_quad_tc<DQ>(pb, sm, q, D);
+        }
+      }
+      if (nv > 1) F /= static_cast<float>(nv);
+      // Theta = s + r g / |g|, then the closest point: s = Theta / |Theta|
+      const PhiloxSource src{&K, 0u, kk, wi, p, n};
+      project_vector(sm, taddr, nchunks, src, ph, ok, q, gg);
+      if (running) {
+        const float sc = r * rsqrtf(fmaxf(gg, 1e-30f));
+        float tt = 0.0f;
+#pragma unroll
+        for (int j = 0; j < DQ; ++j) {
+          q[j] = s[j] + sc * q[j];
+          tt += q[j] * q[j];
+        }
+        const float it = rsqrtf(tt);
+#pragma unroll
+        for (int j = 0; j < DQ; ++j) s[j] = q[j] * it;
+        S = f2_add(S, f2_mul_f(f2_mul(W, om2), F));
+        W = f2_mul(W, c2);
+      }
+      ++k;
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+    }
+    if (tid < kM && active && ok) {
+      pb.S_out[o] = f2_to_double(S);
+      pb.K_out[o] = static_cast<int32_t>(kstop);
+      pb.flag_out[o] = flag;
+    }
+  }
+  tc_end(sm, taddr, ok, ph, pb.dev_status);
+}
+
+// Verification primitive: out[row][0..31] = (Q^T g_row) and gg[row] = |g_row|^2
+// for the rows of a rows x n FP32 matrix G, through the walk's contraction path.
+__global__ void __launch_bounds__(kThreads, 1) tc_project_kernel(const uint4* bimg, const float* G, int64_t rows,
+                                                                 int n, float* out, float* gg_out, unsigned* status) {
+  extern __shared__ unsigned char smem_raw[];
+  const Smem sm = smem_layout(smem_raw);
+  const int tid = threadIdx.x;
+  const int nchunks = (n + kChunkK - 1) / kChunkK;
+  const uint32_t taddr = tc_begin(sm, bimg);
+  uint32_t ph[2] = {0u, 0u};
+  bool ok = true;
+  const int64_t tiles = (rows + kM - 1) / kM;
+  for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+    const int64_t row = tile * kM + (tid & (kM - 1));
+    const MatrixSource src{G, row, rows, n};
+    float q[32], gg;
+    project_vector(sm, taddr, nchunks, src, ph, ok, q, gg);
+    if (tid < kM && row < rows) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[row * 32 + j] = q[j];
+      gg_out[row] = gg;
+    }
+    if (!__syncthreads_and(ok)) ok = false;
+  }
+  tc_end(sm, taddr, ok, ph, status);
+}
+
+}  // namespace tc
+}  // namespace mpwos

@@ -4,6 +4,7 @@
 #include "launch.h"
 #include "walk3.cuh"
 #include "walkn.cuh"
+#include "embed_tc.cuh"
 
 namespace mpwos {
 
@@ -44,6 +45,38 @@ cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStre
   DevProblem arg = pb;
   void* args[] = {&arg};
   return cudaLaunchKernel(walkn_f32_fn(pb), dim3(grid), dim3(block), args, 0, st);
+}
+
+static const void* embed_tc_fn(int D) {
+  switch (walkn_dq(D)) {
+    case 8: return reinterpret_cast<const void*>(tc::embed_tc_kernel<8>);
+    case 16: return reinterpret_cast<const void*>(tc::embed_tc_kernel<16>);
+    case 24: return reinterpret_cast<const void*>(tc::embed_tc_kernel<24>);
+    default: return reinterpret_cast<const void*>(tc::embed_tc_kernel<32>);
+  }
+}
+
+size_t embed_tc_bimg_bytes() { return static_cast<size_t>(tc::kBBytes); }
+
+cudaError_t launch_embed_tc(const DevProblem& pb, int grid, cudaStream_t st) {
+  if (pb.mkind != kEmbeddedSphere || !pb.tc_bimg || !pb.dev_status || pb.n > 64 * tc::kMaxChunks || pb.d + 1 > 31)
+    return cudaErrorInvalidValue;
+  const void* fn = embed_tc_fn(pb.d + 1);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(tc::kThreads), args, tc::kSmemBytes, st);
+}
+
+cudaError_t launch_tc_project(const uint4* bimg, const float* G, int64_t rows, int n, float* out, float* gg,
+                              unsigned* status, int grid, cudaStream_t st) {
+  if (n < 1 || n > 64 * tc::kMaxChunks || grid < 1) return cudaErrorInvalidValue;
+  const void* fn = reinterpret_cast<const void*>(tc::tc_project_kernel);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&bimg, &G, &rows, &n, &out, &gg, &status};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(tc::kThreads), args, tc::kSmemBytes, st);
 }
 
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {

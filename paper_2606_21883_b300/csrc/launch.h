@@ -11,6 +11,14 @@ cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStre
 // Walks for R^n manifolds (n > 3), one warp per walker.
 cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStream_t st);
 cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st);
+// FP32 embedded-sphere walk with the projection on the tensor cores (one
+// persistent 512-thread CTA per SM, 128 walkers per tile; pb.tc_bimg set).
+cudaError_t launch_embed_tc(const DevProblem& pb, int grid, cudaStream_t st);
+// Size in bytes of the tensor-core kernel's shared-memory image of Q^T.
+size_t embed_tc_bimg_bytes();
+// out (rows x 32) = G Q through the walk's tensor-core contraction, gg = |G_row|^2.
+cudaError_t launch_tc_project(const uint4* bimg, const float* G, int64_t rows, int n, float* out, float* gg,
+                              unsigned* status, int grid, cudaStream_t st);
 // Resident blocks per SM of the walk kernel chosen for pb.
 int occupancy_walk_f64(const DevProblem& pb, bool n3, int block);
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block);

@@ -140,6 +140,9 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
   if (pa->n_v < 1 || pa->n_v > 64) return fail(ctx, MPWOS_EINVAL, "n_v must lie in [1, 64]");
   if (pa->max_steps < 0 || pa->max_steps > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "max_steps must lie in [0, 2^31)");
   if (pa->precision != MPWOS_FP64 && pa->precision != MPWOS_FP32) return fail(ctx, MPWOS_EINVAL, "unknown precision %d", pa->precision);
+  if (pa->projection < MPWOS_PROJ_AUTO || pa->projection > MPWOS_PROJ_CUDA) return fail(ctx, MPWOS_EINVAL, "unknown projection %d", pa->projection);
+  if (pa->projection == MPWOS_PROJ_TENSOR && (m->kind != MPWOS_EMBEDDED_SPHERE || pa->precision != MPWOS_FP32))
+    return fail(ctx, MPWOS_EINVAL, "MPWOS_PROJ_TENSOR needs EMBEDDED_SPHERE and MPWOS_FP32");
   if (m->n < 3 || m->n > 1024) return fail(ctx, MPWOS_EINVAL, "ambient dimension must lie in [3, 1024] (got %d)", m->n);
   switch (m->kind) {
     case MPWOS_EUCLID:
@@ -400,6 +403,40 @@ int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
   return MPWOS_OK;
 }
 
+// BF16 round-to-nearest-even of an FP32 value (finite inputs).
+uint16_t bf16_rne(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, sizeof x);
+  x += 0x7FFFu + ((x >> 16) & 1u);
+  return static_cast<uint16_t>(x >> 16);
+}
+float bf16_value(uint16_t h) {
+  const uint32_t x = static_cast<uint32_t>(h) << 16;
+  float f;
+  std::memcpy(&f, &x, sizeof f);
+  return f;
+}
+
+// Shared-memory image of Q^T for the tensor-core walk: B operand rows j < 32
+// (d + 1 used, rest zero), K-chunks of 64 components, each chunk 32 rows of
+// 128 bytes with 16-byte unit u of row j stored at unit u ^ (j mod 8); hi =
+// bf16(Q), lo = bf16(Q - hi); hi chunks first, then lo chunks.
+void tc_bimage(const double* Q, int n, int D, std::vector<uint16_t>& img) {
+  const size_t half = embed_tc_bimg_bytes() / 4;   // uint16 elements in the hi (or lo) part
+  img.assign(2 * half, 0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < D; ++j) {
+      const double q = Q[static_cast<size_t>(i) * D + j];
+      const uint16_t hi = bf16_rne(static_cast<float>(q));
+      const uint16_t lo = bf16_rne(static_cast<float>(q - static_cast<double>(bf16_value(hi))));
+      const int c = i / 64, kk = i % 64, u = kk / 8, e = kk % 8;
+      const size_t byte = static_cast<size_t>(c) * 4096 + static_cast<size_t>(j) * 128 +
+                          static_cast<size_t>(((u ^ (j & 7)) << 4) + 2 * e);
+      img[byte / 2] = hi;
+      img[half + byte / 2] = lo;
+    }
+}
+
 // Everything a walk launch needs, built in `sc`.
 int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpwos_problem* pr,
             const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb,
@@ -486,6 +523,16 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
       CK(launch_intrinsic_start(pb.pts, qtd, bd, n, npad, D, P, s0, sc.stream));
       ctx->launches++;
     }
+    const bool tc = pa->precision == MPWOS_FP32 &&
+                    (pa->projection == MPWOS_PROJ_TENSOR || (pa->projection == MPWOS_PROJ_AUTO && n >= 128));
+    if (tc) {
+      std::vector<uint16_t> img;
+      tc_bimage(m->Q, n, D, img);
+      pb.tc_bimg = reinterpret_cast<const uint4*>(sc.upload(img.data(), img.size()));
+      pb.dev_status = sc.alloc<unsigned>(1);
+      if (!pb.tc_bimg || !pb.dev_status) return fail(ctx, MPWOS_ENOMEM, "tensor-core operand image");
+      CK(cudaMemsetAsync(pb.dev_status, 0, sizeof(unsigned), sc.stream));
+    }
   }
   // point cloud grid; rho_geo varies with h(y)
   double rho_geo_max = pb.rho_geo;
@@ -538,6 +585,18 @@ int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tab32)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
+  if (pb.tc_bimg && !fp64) {
+    // one persistent CTA per SM (or a share of them), 128 walkers per tile
+    const int64_t tiles = (pb.wk_w1 - pb.wk_w0 + 127) / 128;
+    int64_t grid = ctx->sm_count;
+    if (max_grid < 0) grid = std::max<int64_t>(1, grid / (-max_grid));
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
+    if (grid > tiles) grid = tiles;
+    const cudaError_t e = launch_embed_tc(pb, static_cast<int>(grid), st);
+    if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "tensor-core walk launch: %s", cudaGetErrorString(e));
+    ctx->launches++;
+    return MPWOS_OK;
+  }
   const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
   const int block = n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256) : 128;
   const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
@@ -569,6 +628,7 @@ void mpwos_params_default(mpwos_params* p) {
   p->max_steps = 10000000;
   p->seed = 0;
   p->precision = MPWOS_FP64;
+  p->projection = MPWOS_PROJ_AUTO;
 }
 
 int mpwos_create(int device, mpwos_ctx** out) {
@@ -646,7 +706,10 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
   if (!dS) CK(cudaMemcpyAsync(S, pb.S_out, W * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (!dK) CK(cudaMemcpyAsync(K, pb.K_out, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
   if (!dF) CK(cudaMemcpyAsync(flags, pb.flag_out, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned tcst = 0;
+  if (pb.dev_status) CK(cudaMemcpyAsync(&tcst, pb.dev_status, sizeof tcst, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (tcst) return fail(ctx, MPWOS_ETIMEDOUT, "tensor-core walk: a bounded mbarrier wait ran out (status %u)", tcst);
   return MPWOS_OK;
 }
 
@@ -685,8 +748,42 @@ int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_proble
   if (!dm) CK(cudaMemcpyAsync(mean, om, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (!ds) CK(cudaMemcpyAsync(stderr_, os, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (!dt) CK(cudaMemcpyAsync(mean_steps, ot, P * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned tcst = 0;
+  if (pb.dev_status) CK(cudaMemcpyAsync(&tcst, pb.dev_status, sizeof tcst, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  if (tcst) return fail(ctx, MPWOS_ETIMEDOUT, "tensor-core walk: a bounded mbarrier wait ran out (status %u)", tcst);
   if (hflag) return fail(ctx, MPWOS_EMAXSTEPS, "%llu walks reached max_steps", hflag);
+  return MPWOS_OK;
+}
+
+int mpwos_tc_project(mpwos_ctx* ctx, const double* Q, int n, int D, const float* G, int64_t rows, float* out,
+                     float* gg) {
+  if (!ctx || !Q || !G || !out || !gg || rows < 0 || n < 1 || n > 1024 || D < 1 || D > 31) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  Scratch sc(ctx);
+  std::vector<uint16_t> img;
+  tc_bimage(Q, n, D, img);
+  const uint4* dimg = reinterpret_cast<const uint4*>(sc.upload(img.data(), img.size()));
+  const float* dG = sc.upload(G, static_cast<size_t>(rows) * n);
+  float* dout = sc.alloc<float>(static_cast<size_t>(rows) * 32);
+  float* dgg = sc.alloc<float>(static_cast<size_t>(rows));
+  unsigned* dst = sc.alloc<unsigned>(1);
+  if (!dimg || !dG || !dout || !dgg || !dst) return fail(ctx, MPWOS_ENOMEM, "tc_project buffers");
+  CK(cudaMemsetAsync(dst, 0, sizeof(unsigned), ctx->stream));
+  if (rows) {
+    const int64_t tiles = (rows + 127) / 128;
+    const int grid = static_cast<int>(std::min<int64_t>(tiles, ctx->sm_count));
+    CK(launch_tc_project(dimg, dG, rows, n, dout, dgg, dst, grid, ctx->stream));
+    ctx->launches++;
+    CK(cudaMemcpy2DAsync(out, sizeof(float) * D, dout, sizeof(float) * 32, sizeof(float) * D, rows,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(gg, dgg, sizeof(float) * rows, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  unsigned hst = 0;
+  CK(cudaMemcpyAsync(&hst, dst, sizeof hst, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hst) return fail(ctx, MPWOS_ETIMEDOUT, "tensor-core projection: a bounded mbarrier wait ran out");
   return MPWOS_OK;
 }
 
@@ -1065,6 +1162,7 @@ int req_round(mpwos_ctx* ctx, Request& r, int64_t i1) {
   CK(cudaMemcpyAsync(r.h_se, r.se, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(r.h_ms, r.ms, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(r.h_flag, r.nflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  if (r.pb.dev_status) CK(cudaMemcpyAsync(r.h_flag + 1, r.pb.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
   CK(cudaEventRecord(r.ev, st));
   r.cur = i1;
   return MPWOS_OK;
@@ -1102,6 +1200,10 @@ int req_start(mpwos_ctx* ctx, Request& r) {
 void req_advance(mpwos_ctx* ctx, Request& r) {
   if (r.cancel) {
     req_finish(ctx, r, 4, MPWOS_ECANCELED, "canceled");
+    return;
+  }
+  if (r.h_flag[1]) {
+    req_finish(ctx, r, 3, MPWOS_ETIMEDOUT, "tensor-core walk: a bounded mbarrier wait ran out");
     return;
   }
   std::vector<int> next;
@@ -1299,8 +1401,9 @@ int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_probl
   CK(cudaMallocHost(&r->h_ms, sizeof(double) * std::max<int64_t>(P, 1)));
   CK(cudaMallocHost(&r->h_n, sizeof(int64_t) * std::max<int64_t>(P, 1)));
   CK(cudaMallocHost(&r->h_act, sizeof(int) * std::max<int64_t>(P, 1)));
-  CK(cudaMallocHost(&r->h_flag, sizeof(unsigned long long)));
-  *r->h_flag = 0;
+  CK(cudaMallocHost(&r->h_flag, 2 * sizeof(unsigned long long)));   // [0] flagged walks, [1] kernel status
+  r->h_flag[0] = 0;
+  r->h_flag[1] = 0;
   CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
   r->t_submit = std::chrono::steady_clock::now();
   const uint64_t id = r->id;
