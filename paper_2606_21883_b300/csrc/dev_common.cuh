@@ -28,6 +28,7 @@ struct DevFunc {
   const float* Af;
   float coef_f[kMaxTerms];             // FP32 copies of coef, c0 (the FP32 walks read no double)
   float c0_f;
+  float mode_f[kMaxTerms][4];          // TORUS_FOURIER: m, q, m^2, q^2 as floats
 };
 
 // FP32 copies of the loop-invariant scalars, filled on the host: a double read
@@ -37,6 +38,14 @@ struct ScalarsF {
   float tab_scale;   // (NS - 1) / sqrt(1/2): table abscissa per sqrt(U)
   float z_scale;     // (NA - 1) / z_max (0 when NA == 1)
 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+// Round keys of one seed: k_r = (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85), r = 0..9.
+struct PhiloxKeys { uint32_t a[10], b[10]; };
 
 // Everything a walk kernel reads, passed by value (kernel parameter space).
 struct DevProblem {
@@ -73,6 +82,7 @@ struct DevProblem {
   int n_v;
   int64_t max_steps;
   uint64_t seed;
+  PhiloxKeys keys;   // round keys of seed (host-made; read as constant operands)
   ScalarsF sf;
   // FP32 survival weight: em1(z) = I~_nu(a) - 1 = sum_{j=1..T} k_j z^j (Lemma 3.1
   // series, coefficients k_j = 1/(j! (nu+1)_j) from FP64 on the host, T chosen
@@ -83,7 +93,7 @@ struct DevProblem {
   int em1_fp64;
   // radius tables (inverse CDF of the Green law; layout in green.cuh)
   const double* tab64;
-  const float* tab32;
+  const float4* tabc;  // FP32 walks: per interval the cubic c0 + c1 f + c2 f^2 + c3 f^3 (NS - 1 per side)
   int NA, NS;         // a-rows (uniform in z = a^2/4), s-nodes (+2 ghosts per row)
   double z_max;
   // work map: walk (p, i) for p in wk_points (all points 0..P-1 when null),
@@ -104,15 +114,7 @@ struct DevProblem {
   unsigned* dev_status;
 };
 
-// ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
-// ---------------------------------------------------------------------------
-struct U4 { uint32_t x, y, z, w; };
-
-// Round keys of one seed: k_r = (k0 + r 0x9E3779B9, k1 + r 0xBB67AE85), r = 0..9.
-struct PhiloxKeys { uint32_t a[10], b[10]; };
-
-__device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
+__host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
   PhiloxKeys K;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
@@ -122,8 +124,8 @@ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
   return K;
 }
 
-__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
-                                             const PhiloxKeys& K) {
+__host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                                      const PhiloxKeys& K) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
     const uint64_t p0 = static_cast<uint64_t>(0xD2511F53u) * c0;
@@ -133,6 +135,64 @@ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c
     c0 = n0; c1 = static_cast<uint32_t>(p1); c2 = n2; c3 = static_cast<uint32_t>(p0);
   }
   return U4{c0, c1, c2, c3};
+}
+
+// The two blocks j = 0, 1 of counter (j, k, i, p) for every step k of one walk
+// (i, p), with the work that depends on (i, p) only done once per walk and
+// the work both blocks share done once per step.  Writing one Philox round as
+//   (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ a_r, lo(M1 c2), hi(M0 c0) ^ c3 ^ b_r, lo(M0 c0)),
+// round 0 of block j gives (hi(M1 i) ^ k ^ a_0, lo(M1 i), p ^ b_0, j M0) since
+// M0 j < 2^32; round 1 then has a per-walk c0, c1 and a per-step c3, and the
+// blocks differ only in c2 (by M0); round 2 shares c2, c3; rounds 3..9 run in
+// full.  Output is identical to philox4x32_10(j, k, i, p, K).
+struct PhiloxWalk {
+  uint32_t x0;    // hi(M1 i) ^ a_0 (round 0 c0 before the step index)
+  uint32_t A, L;  // round 1 c0, c1
+  uint32_t HA;    // hi(M0 A) ^ b_2
+  uint32_t LA;    // lo(M0 A)
+};
+
+__host__ __device__ __forceinline__ PhiloxWalk philox_walk(uint32_t i, uint32_t p, const PhiloxKeys& K) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  PhiloxWalk w;
+  const uint64_t pi = static_cast<uint64_t>(M1) * i;
+  w.x0 = static_cast<uint32_t>(pi >> 32) ^ K.a[0];
+  const uint64_t pp = static_cast<uint64_t>(M1) * (p ^ K.b[0]);
+  w.A = static_cast<uint32_t>(pp >> 32) ^ static_cast<uint32_t>(pi) ^ K.a[1];
+  w.L = static_cast<uint32_t>(pp);
+  const uint64_t pa = static_cast<uint64_t>(M0) * w.A;
+  w.HA = static_cast<uint32_t>(pa >> 32) ^ K.b[2];
+  w.LA = static_cast<uint32_t>(pa);
+  return w;
+}
+
+__host__ __device__ __forceinline__ void philox_step_pair(const PhiloxWalk& w, uint32_t k, const PhiloxKeys& K,
+                                                          U4& out0, U4& out1) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  // round 1 (shared product of the step)
+  const uint64_t P = static_cast<uint64_t>(M0) * (w.x0 ^ k);
+  const uint32_t c2_0 = static_cast<uint32_t>(P >> 32) ^ K.b[1];
+  const uint32_t c2_1 = c2_0 ^ M0;
+  // round 2
+  const uint64_t q0 = static_cast<uint64_t>(M1) * c2_0;
+  const uint64_t q1 = static_cast<uint64_t>(M1) * c2_1;
+  uint32_t a0 = static_cast<uint32_t>(q0 >> 32) ^ w.L ^ K.a[2], a1 = static_cast<uint32_t>(q0);
+  uint32_t b0 = static_cast<uint32_t>(q1 >> 32) ^ w.L ^ K.a[2], b1 = static_cast<uint32_t>(q1);
+  uint32_t a2 = w.HA ^ static_cast<uint32_t>(P), a3 = w.LA;
+  uint32_t b2 = a2, b3 = a3;
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    const uint64_t pa0 = static_cast<uint64_t>(M0) * a0, pa1 = static_cast<uint64_t>(M1) * a2;
+    const uint64_t pb0 = static_cast<uint64_t>(M0) * b0, pb1 = static_cast<uint64_t>(M1) * b2;
+    const uint32_t na0 = static_cast<uint32_t>(pa1 >> 32) ^ a1 ^ K.a[r];
+    const uint32_t na2 = static_cast<uint32_t>(pa0 >> 32) ^ a3 ^ K.b[r];
+    const uint32_t nb0 = static_cast<uint32_t>(pb1 >> 32) ^ b1 ^ K.a[r];
+    const uint32_t nb2 = static_cast<uint32_t>(pb0 >> 32) ^ b3 ^ K.b[r];
+    a0 = na0; a1 = static_cast<uint32_t>(pa1); a2 = na2; a3 = static_cast<uint32_t>(pa0);
+    b0 = nb0; b1 = static_cast<uint32_t>(pb1); b2 = nb2; b3 = static_cast<uint32_t>(pb0);
+  }
+  out0 = U4{a0, a1, a2, a3};
+  out1 = U4{b0, b1, b2, b3};
 }
 
 __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -162,9 +222,9 @@ __device__ __forceinline__ float u24(uint32_t x) {
 }
 
 // 23-bit uniform in (0, 1] from one word without an int->float conversion:
-// 2 - [1, 2) built from the top 23 bits as a float mantissa.
+// 2 - [1, 2) built from the low 23 bits as a float mantissa (one logic op).
 __device__ __forceinline__ float u23(uint32_t x) {
-  return 2.0f - __uint_as_float(0x3f800000u | (x >> 9));
+  return 2.0f - __uint_as_float(0x3f800000u | (x & 0x7FFFFFu));
 }
 
 constexpr double kTwoPi = 6.283185307179586;
@@ -182,7 +242,7 @@ __device__ __forceinline__ void box_muller64(double ua, double ub, double& g0, d
 
 // FP32 Box-Muller pair (hardware approximations: MUFU lg2 / sin / cos).
 __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, float& g1) {
-  const float rad = sqrtf(-2.0f * __logf(ua));
+  const float rad = sqrtf(-1.38629436111989061f * __log2f(ua));   // -2 ln(ua) = -2 ln2 log2(ua)
   float s, c;
   __sincosf(kTwoPiF * ub, &s, &c);
   g0 = rad * c;

@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) embed_tc_kernel(const DevProblem 
   if (tid < 32) sm.vf[tid] = tid < D ? pb.f.vf[tid] : 0.0f;
   const uint32_t taddr = tc_begin(sm, pb.tc_bimg);
 
-  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
+  const PhiloxKeys& K = pb.keys;
   const uint32_t nb = static_cast<uint32_t>((n + 3) / 4);
   const int nv = pb.n_v;
   // closed manifold of constant curvature: one radius and one weight pair

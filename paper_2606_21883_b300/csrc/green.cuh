@@ -232,25 +232,36 @@ __host__ __device__ __forceinline__ T table_lookup(const T* tab, int NA, int NS,
   return v0 + wa * (v1 - v0);
 }
 
-// FP32 lookup with the problem's precomputed scales (no double arithmetic).
-__device__ __forceinline__ float table_lookup32(const DevProblem& pb, float a, float U) {
-  const int NS = pb.NS, NA = pb.NA, side_len = NS + 2;
+// FP32 lookup in the coefficient table: the Catmull-Rom cubic of interval j
+// (nodes j-1 .. j+2 of the node table) stored as one float4 of monomial
+// coefficients computed in FP64, so a lookup is one 16-byte load and three
+// FMAs per row.  tab_scale = (NS - 1)/sqrt(1/2), z_scale = (NA - 1)/z_max.
+__device__ __forceinline__ float table_lookup32(const float4* tabc, int NA, int NS, float tab_scale, float z_scale,
+                                                float a, float U) {
+  const int NI = NS - 1;   // intervals per side
   const bool upper = U > 0.5f;
   const float v = sqrtf(upper ? 1.0f - U : U);
-  const float xs = v * pb.sf.tab_scale;
+  const float xs = v * tab_scale;
   int j = static_cast<int>(xs);
-  j = j < 0 ? 0 : (j > NS - 2 ? NS - 2 : j);
+  j = j > NI - 1 ? NI - 1 : j;
   const float f = xs - static_cast<float>(j);
-  const float* tab = pb.tab32 + (upper ? side_len : 0);
-  if (NA == 1) return catmull_rom(tab, j, f);
-  const float fa = a * a * 0.25f * pb.sf.z_scale;
+  const float4* tab = tabc + (upper ? NI : 0) + j;
+  const float4 c = tab[0];
+  const float t0 = fmaf(f, fmaf(f, fmaf(f, c.w, c.z), c.y), c.x);
+  if (NA == 1) return t0;
+  const float fa = a * a * 0.25f * z_scale;
   int ia = static_cast<int>(fa);
   ia = ia < 0 ? 0 : (ia > NA - 2 ? NA - 2 : ia);
   const float wa = fminf(fa - static_cast<float>(ia), 1.0f);
-  const float* r0 = tab + static_cast<size_t>(ia) * (2 * side_len);
-  const float v0 = catmull_rom(r0, j, f);
-  const float v1 = catmull_rom(r0 + 2 * side_len, j, f);
+  const float4 c0 = tab[static_cast<size_t>(ia) * (2 * NI)];
+  const float4 c1 = tab[static_cast<size_t>(ia + 1) * (2 * NI)];
+  const float v0 = fmaf(f, fmaf(f, fmaf(f, c0.w, c0.z), c0.y), c0.x);
+  const float v1 = fmaf(f, fmaf(f, fmaf(f, c1.w, c1.z), c1.y), c1.x);
   return v0 + wa * (v1 - v0);
+}
+
+__device__ __forceinline__ float table_lookup32(const DevProblem& pb, float a, float U) {
+  return table_lookup32(pb.tabc, pb.NA, pb.NS, pb.sf.tab_scale, pb.sf.z_scale, a, U);
 }
 
 }  // namespace mpwos

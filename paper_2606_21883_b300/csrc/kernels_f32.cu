@@ -10,9 +10,13 @@ namespace mpwos {
 
 static const void* walk3_f32_fn(const DevProblem& pb) {
   switch (pb.mkind) {
-    case kEuclid: return reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid, 1>);
-    case kSphere: return reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1>);
-    case kTorus: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1>);
+    case kEuclid:
+      return pb.closed ? reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid, 1, true>)
+                       : reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid, 1, false>);
+    case kSphere:
+      return pb.closed ? reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, true>)
+                       : reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, false>);
+    case kTorus: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true>);   // closed only
     case kPointCloud:
       return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 8>)
            : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 16>)
@@ -92,17 +96,19 @@ int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
 }
 
 __global__ void green_radius32_kernel(const double* a, const double* U, double* t, int64_t count,
-                                      const float* tab32, int NA, int NS, double z_max) {
+                                      const float4* tabc, int NA, int NS, float tab_scale, float z_scale) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= count) return;
-  float v = table_lookup<float>(tab32, NA, NS, z_max, static_cast<float>(a[q]), static_cast<float>(U[q]));
+  const float v = table_lookup32(tabc, NA, NS, tab_scale, z_scale, static_cast<float>(a[q]), static_cast<float>(U[q]));
   t[q] = static_cast<double>(fminf(fmaxf(v, 0.0f), 1.0f));
 }
 
-cudaError_t launch_green_radius32(const double* a, const double* U, double* t, int64_t count, const float* tab32,
+cudaError_t launch_green_radius32(const double* a, const double* U, double* t, int64_t count, const float4* tabc,
                                   int NA, int NS, double z_max, cudaStream_t st) {
-  green_radius32_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(a, U, t, count, tab32, NA, NS,
-                                                                                   z_max);
+  const float tab_scale = static_cast<float>((NS - 1) / 0.70710678118654752);
+  const float z_scale = (NA > 1 && z_max > 0.0) ? static_cast<float>((NA - 1) / z_max) : 0.0f;
+  green_radius32_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(a, U, t, count, tabc, NA, NS,
+                                                                                   tab_scale, z_scale);
   return cudaGetLastError();
 }
 

@@ -12,8 +12,7 @@ namespace mpwos {
 // Radius tables (layout in green.cuh): one thread per node; bisection to a
 // bracket, then the safeguarded Newton polish, in FP64.
 // ---------------------------------------------------------------------------
-__global__ void build_table_kernel(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
-                                   float* tab32) {
+__global__ void build_table_kernel(int n, int NA, int NS, double z_max, double a_fixed, double* tab64) {
   const int side_len = NS + 2;
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= NA * 2 * side_len) return;
@@ -42,13 +41,29 @@ __global__ void build_table_kernel(int n, int NA, int NS, double z_max, double a
   }
   if (j < 0) t = side == 0 ? -t : 2.0 - t;
   tab64[idx] = t;
-  tab32[idx] = static_cast<float>(t);
+}
+
+// Monomial coefficients of each interval's Catmull-Rom cubic, in FP64 from the
+// FP64 nodes p0..p3 (nodes j-1 .. j+2):
+//   t(f) = p1 + f (p2 - p0)/2 + f^2 (2 p0 - 5 p1 + 4 p2 - p3)/2 + f^3 (3 (p1 - p2) + p3 - p0)/2.
+__global__ void build_coef_kernel(int NA, int NS, const double* tab64, float4* tabc) {
+  const int NI = NS - 1, side_len = NS + 2;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NA * 2 * NI) return;
+  const int row = idx / NI, j = idx - row * NI;   // row = 2 ia + side
+  const double* nd = tab64 + static_cast<size_t>(row) * side_len + j;
+  const double p0 = nd[0], p1 = nd[1], p2 = nd[2], p3 = nd[3];
+  tabc[idx] = make_float4(static_cast<float>(p1), static_cast<float>(0.5 * (p2 - p0)),
+                          static_cast<float>(0.5 * (2.0 * p0 - 5.0 * p1 + 4.0 * p2 - p3)),
+                          static_cast<float>(0.5 * (3.0 * (p1 - p2) + p3 - p0)));
 }
 
 cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
-                               float* tab32, cudaStream_t st) {
+                               float4* tabc, cudaStream_t st) {
   const int total = NA * 2 * (NS + 2);
-  build_table_kernel<<<(total + 127) / 128, 128, 0, st>>>(n, NA, NS, z_max, a_fixed, tab64, tab32);
+  build_table_kernel<<<(total + 127) / 128, 128, 0, st>>>(n, NA, NS, z_max, a_fixed, tab64);
+  const int nint = NA * 2 * (NS - 1);
+  build_coef_kernel<<<(nint + 127) / 128, 128, 0, st>>>(NA, NS, tab64, tabc);
   return cudaGetLastError();
 }
 

@@ -40,9 +40,10 @@ cudaError_t launch_reduce_strided(const double* S, const int32_t* K, const int32
                                   double* msteps, unsigned long long* n_flagged, cudaStream_t st);
 
 // Inverse-CDF tables of the radial Green law: NA rows over z = a^2/4 in
-// [0, z_max] (NA == 1: the single law at a = a_fixed); two sides of NS + 2 nodes per row.
+// [0, z_max] (NA == 1: the single law at a = a_fixed); two sides of NS + 2
+// FP64 nodes per row, and NS - 1 float4 interval cubics per side for FP32.
 cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fixed, double* tab64,
-                               float* tab32, cudaStream_t st);
+                               float4* tabc, cudaStream_t st);
 
 // Point-cloud grid (counting sort by cell) and the largest h(p) over the cloud.
 cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[3], double cs, const int dims[3],
@@ -55,7 +56,7 @@ cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_
                           cudaStream_t st);
 cudaError_t launch_green_radius64(int n, const double* a, const double* U, double* t, int64_t count,
                                   const double* tab64, int NA, int NS, double z_max, cudaStream_t st);
-cudaError_t launch_green_radius32(const double* a, const double* U, double* t, int64_t count, const float* tab32,
+cudaError_t launch_green_radius32(const double* a, const double* U, double* t, int64_t count, const float4* tabc,
                                   int NA, int NS, double z_max, cudaStream_t st);
 cudaError_t launch_c_sigma_r(int n, const double* a, double* c, int64_t count, cudaStream_t st);
 

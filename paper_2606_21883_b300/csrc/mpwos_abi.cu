@@ -31,7 +31,7 @@ constexpr int kTableNA = 65;     // rows over z = a^2/4 for variable-radius prob
 
 struct Table {
   double* tab64 = nullptr;
-  float* tab32 = nullptr;
+  float4* tabc = nullptr;
   int NA = 0, NS = 0;
   double z_max = 0.0;
 };
@@ -283,8 +283,14 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
       d.pw[q] = static_cast<int8_t>(f.pw[q]);
     }
   } else if (f.kind == MPWOS_FUNC_TORUS_FOURIER) {
-    for (int t = 0; t < f.n_terms; ++t)
+    for (int t = 0; t < f.n_terms; ++t) {
       for (int q = 0; q < 4; ++q) d.modes[t][q] = static_cast<int8_t>(f.modes[4 * t + q]);
+      const float m = static_cast<float>(f.modes[4 * t]), qq = static_cast<float>(f.modes[4 * t + 1]);
+      d.mode_f[t][0] = m;
+      d.mode_f[t][1] = qq;
+      d.mode_f[t][2] = m * m;
+      d.mode_f[t][3] = qq * qq;
+    }
   }
 }
 
@@ -303,8 +309,8 @@ int get_table(mpwos_ctx* ctx, int n, bool fixed, double a_or_zmax, Table** out) 
   t.z_max = fixed ? 0.25 * a_or_zmax * a_or_zmax : a_or_zmax;
   const size_t cnt = static_cast<size_t>(NA) * 2 * (kTableNS + 2);
   CK(cudaMalloc(&t.tab64, cnt * sizeof(double)));
-  CK(cudaMalloc(&t.tab32, cnt * sizeof(float)));
-  CK(launch_build_table(n, NA, kTableNS, t.z_max, fixed ? a_or_zmax : 0.0, t.tab64, t.tab32, ctx->stream));
+  CK(cudaMalloc(&t.tabc, static_cast<size_t>(NA) * 2 * (kTableNS - 1) * sizeof(float4)));
+  CK(launch_build_table(n, NA, kTableNS, t.z_max, fixed ? a_or_zmax : 0.0, t.tab64, t.tabc, ctx->stream));
   ctx->launches += 1;
   auto res = ctx->tables.emplace(key, t);
   *out = &res.first->second;
@@ -460,6 +466,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   pb.n_v = pa->n_v;
   pb.max_steps = pa->max_steps;
   pb.seed = pa->seed;
+  pb.keys = philox_keys(static_cast<uint32_t>(pa->seed), static_cast<uint32_t>(pa->seed >> 32));
   pb.P = P;
   pb.N = N;
   pb.wk_points = nullptr;
@@ -566,7 +573,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   int rc = fixed_radius ? get_table(ctx, n, true, a_max, &tab) : get_table(ctx, n, false, 0.25 * a_max * a_max, &tab);
   if (rc) return rc;
   pb.tab64 = tab->tab64;
-  pb.tab32 = tab->tab32;
+  pb.tabc = tab->tabc;
   pb.NA = tab->NA;
   pb.NS = tab->NS;
   pb.z_max = tab->z_max;
@@ -583,7 +590,7 @@ int run_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64) { return run_walks_on(c
 // leave SMs to the other requests in flight).
 int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid) {
   if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
-  if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tab32)
+  if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tabc)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
   if (pb.tc_bimg && !fp64) {
     // one persistent CTA per SM (or a share of them), 128 walkers per tile
@@ -660,7 +667,7 @@ void mpwos_destroy(mpwos_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->tables) {
     cudaFree(kv.second.tab64);
-    cudaFree(kv.second.tab32);
+    cudaFree(kv.second.tabc);
   }
   for (auto& kv : ctx->clouds) {
     cudaFree(kv.second.pts64);
@@ -822,7 +829,7 @@ int mpwos_green_radius(mpwos_ctx* ctx, int n, double a_max, const double* a, con
     if (precision == MPWOS_FP64)
       CK(launch_green_radius64(n, da, dU, dt, count, tab->tab64, tab->NA, tab->NS, tab->z_max, ctx->stream));
     else
-      CK(launch_green_radius32(da, dU, dt, count, tab->tab32, tab->NA, tab->NS, tab->z_max, ctx->stream));
+      CK(launch_green_radius32(da, dU, dt, count, tab->tabc, tab->NA, tab->NS, tab->z_max, ctx->stream));
     ctx->launches++;
   }
   CK(cudaMemcpyAsync(t, dt, count * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
@@ -869,8 +876,8 @@ constexpr size_t kNaHeader = 256;                      // max-steps counter
 constexpr size_t kNaNormal = 8192 + 4096;              // boundary normal, n <= 1024 doubles + floats
 constexpr size_t kNaQuad = 256;                        // SPHERE_QUAD v, A on S^2 (12 doubles)
 constexpr size_t kNaTab64 = 1068288;                   // 65 x 2 x 1027 doubles, rounded up to 256
-constexpr size_t kNaTab32 = 534272;                    // 65 x 2 x 1027 floats, rounded up to 256
-constexpr size_t kNaFixed = kNaHeader + kNaNormal + kNaQuad + kNaTab64 + kNaTab32;
+constexpr size_t kNaTabc = 2129920;                    // 65 x 2 x 1024 float4 interval cubics
+constexpr size_t kNaFixed = kNaHeader + kNaNormal + kNaQuad + kNaTab64 + kNaTabc;
 constexpr size_t kNaPerWalk = sizeof(double) + 2 * sizeof(int32_t);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -929,8 +936,8 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   cur += kNaQuad;
   double* tab64 = reinterpret_cast<double*>(cur);
   cur += kNaTab64;
-  float* tab32 = reinterpret_cast<float*>(cur);
-  cur += kNaTab32;
+  float4* tabc = reinterpret_cast<float4*>(cur);
+  cur += kNaTabc;
   double* S = reinterpret_cast<double*>(cur);
   int32_t* K = reinterpret_cast<int32_t*>(cur + walks * sizeof(double));
   int32_t* F = K + walks;
@@ -955,6 +962,7 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   pb.n_v = prm->n_v;
   pb.max_steps = prm->max_steps;
   pb.seed = prm->seed;
+  pb.keys = philox_keys(static_cast<uint32_t>(prm->seed), static_cast<uint32_t>(prm->seed >> 32));
   pb.P = P;
   pb.N = N;
   pb.wk_points = nullptr;
@@ -997,10 +1005,10 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   pb.NA = prob->closed ? 1 : table_rows(n);
   pb.z_max = 0.25 * a_max * a_max;
   fill_em1_poly(pb, n, pb.z_max);
-  CK(launch_build_table(n, pb.NA, pb.NS, pb.z_max, prob->closed ? a_max : 0.0, tab64, tab32, ctx->stream));
+  CK(launch_build_table(n, pb.NA, pb.NS, pb.z_max, prob->closed ? a_max : 0.0, tab64, tabc, ctx->stream));
   ctx->launches += 1;
   pb.tab64 = tab64;
-  pb.tab32 = tab32;
+  pb.tabc = tabc;
   fill_scalars_f(pb);
   pb.S_out = S;
   pb.K_out = K;

@@ -54,7 +54,7 @@ __device__ __forceinline__ void walk3_f64_body(const DevProblem& pb) {
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
-  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
+  const PhiloxKeys& K = pb.keys;
   const int nv = pb.n_v;
   const uint32_t ub = 2u * static_cast<uint32_t>(1 + nv);
 
@@ -188,6 +188,34 @@ __device__ __forceinline__ void torus_angles32(float R, const float* x, float& c
   sph = x[1] * irho;
 }
 
+// cos(m x), sin(m x) from c = cos x, s = sin x: closed forms for m <= 4 (the
+// mode is uniform across the warp, so the switch does not diverge), repeated
+// rotation above.
+__device__ __forceinline__ void angle_multiple(int m, float c, float s, float& cm, float& sm) {
+  switch (m) {
+    case 0: cm = 1.0f; sm = 0.0f; return;
+    case 1: cm = c; sm = s; return;
+    case 2: cm = fmaf(2.0f * c, c, -1.0f); sm = 2.0f * s * c; return;
+    case 3: {
+      const float c2 = fmaf(2.0f * c, c, -1.0f);
+      cm = c * fmaf(2.0f, c2, -1.0f);
+      sm = s * fmaf(2.0f, c2, 1.0f);
+      return;
+    }
+    case 4: {
+      const float c2 = fmaf(2.0f * c, c, -1.0f), s2 = 2.0f * s * c;
+      cm = fmaf(2.0f * c2, c2, -1.0f);
+      sm = 2.0f * s2 * c2;
+      return;
+    }
+    default: {
+      float a = 1.0f, b = 0.0f;
+      for (int j = 0; j < m; ++j) { const float a2 = a * c - b * s; b = b * c + a * s; a = a2; }
+      cm = a; sm = b;
+    }
+  }
+}
+
 // (-Delta_M + sigma) u or u itself for a torus Fourier series, from the angles.
 __device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevFunc& fn, float ct, float st,
                                                float cph, float sph) {
@@ -197,19 +225,19 @@ __device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevF
   const float sg = pb.sf.sigma;
   float total = 0.0f;
   for (int t = 0; t < fn.n_terms; ++t) {
-    const int m = fn.modes[t][0], q = fn.modes[t][1];
-    float cm = 1.0f, sm = 0.0f, cq = 1.0f, sq = 0.0f;
-    for (int j = 0; j < m; ++j) { const float c2 = cm * ct - sm * st; sm = sm * ct + cm * st; cm = c2; }
-    for (int j = 0; j < q; ++j) { const float c2 = cq * cph - sq * sph; sq = sq * cph + cq * sph; cq = c2; }
-    const float Tv = fn.modes[t][2] == 0 ? cm : sm;
+    float cm, sm, cq, sq;
+    angle_multiple(fn.modes[t][0], ct, st, cm, sm);
+    angle_multiple(fn.modes[t][1], cph, sph, cq, sq);
+    const bool tcos = fn.modes[t][2] == 0;
+    const float Tv = tcos ? cm : sm;
     const float Pv = fn.modes[t][3] == 0 ? cq : sq;
     float val;
     if (!fn.apply_op) {
       val = Tv * Pv;
     } else {
-      const float Tp = fn.modes[t][2] == 0 ? -static_cast<float>(m) * sm : static_cast<float>(m) * cm;
-      const float lap = static_cast<float>(m * m) * Tv * ia * ia + st * Tp * ia * irr +
-                        static_cast<float>(q * q) * Tv * irr * irr;
+      const float mf = fn.mode_f[t][0];
+      const float Tp = tcos ? -mf * sm : mf * cm;
+      const float lap = fn.mode_f[t][2] * Tv * (ia * ia) + st * Tp * (ia * irr) + fn.mode_f[t][3] * Tv * (irr * irr);
       val = Pv * (lap + sg * Tv);
     }
     total += fn.coef_f[t] * val;
@@ -258,14 +286,22 @@ __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* 
   return func3<MK, float>(pb, pb.f, cZ);
 }
 
-template <int MK, int KM>
+// The FP32 step loop.  FIXED: closed problems on analytic manifolds, where the
+// radius, c and omega are constants of the launch; the loop then carries
+// V = W omega instead of W (stop at V < tau_W omega), adds V F_k to S with one
+// TwoSum whose low parts accumulate unnormalised (renormalised every 64 steps;
+// |S.lo| stays below 64 ulp(S.hi)), and updates V *= c without renormalising
+// (|V.lo| stays within a few ulp of V.hi).  Otherwise W, S and omega follow the
+// radius step by step.
+template <int MK, int KM, bool FIXED>
 __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
   const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
   int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (w >= total) return;
-  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
+  const PhiloxKeys& K = pb.keys;
   const int nv = pb.n_v;
+  const int max_steps = static_cast<int>(pb.max_steps);
   const float eps = pb.sf.eps;
   const float theta = pb.sf.theta;
   const float rgeo = pb.sf.rho_geo;
@@ -275,24 +311,67 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
 
   float Y[3];
   F2 W{1.0f, 0.0f}, S{0.0f, 0.0f};
-  int64_t k = 0, o = 0;
+  int k = 0;
+  int64_t o = 0;
   uint32_t p = 0, i = 0;
+  PhiloxWalk pw{};
+  float r_prev = -1.0f;
+  F2 c2{1.0f, 0.0f}, om2{0.0f, 0.0f}, thr{0.0f, 0.0f};
+  auto set_weights = [&](float a) {
+    if (!pb.em1_fp64) {
+      weights_from_em1(em1_poly32(pb, 0.25f * a * a), inv_sigma, c2, om2);
+    } else {
+      const double ad = static_cast<double>(a);
+      const double em1 = em1_series(0.5, 0.25 * (ad * ad));
+      const double c = 1.0 / (1.0 + em1);
+      c2 = f2_from_double(c);
+      om2 = f2_from_double(one_minus_c(em1, c) / pb.sigma);
+    }
+  };
+  int k_stop = max_steps;   // FIXED: the common stopping index of every walk
+  bool k_flag = true;       // FIXED: walks end at max_steps (flagged) rather than by V < tau omega
+  if constexpr (FIXED) {
+    const float r = theta * rgeo;
+    set_weights(sqs * r);
+    thr = f2_mul(tau, om2);
+    // V_k = omega c^k in the same float-pair recurrence as the step loop
+    F2 V = om2;
+    for (int kq = 0; kq < max_steps; ++kq) {
+      if ((V.hi - thr.hi) + (V.lo - thr.lo) < 0.0f) {
+        k_stop = kq;
+        k_flag = false;
+        break;
+      }
+      const float vh = __fmul_rn(V.hi, c2.hi);
+      float ve = __fmaf_rn(V.hi, c2.hi, -vh);
+      ve = __fmaf_rn(V.hi, c2.lo, ve);
+      ve = __fmaf_rn(V.lo, c2.hi, ve);
+      V = F2{vh, ve};
+    }
+    if (k_flag && (V.hi - thr.hi) + (V.lo - thr.lo) < 0.0f) k_flag = false;   // V falls below at k = max_steps
+  }
   auto init = [&](int64_t ww) {
     const WalkId id = walk_id(pb, ww);
     p = id.p; i = id.i; o = id.o;
     const double* y0 = pb.pts + static_cast<size_t>(p) * 3;
     Y[0] = static_cast<float>(y0[0]); Y[1] = static_cast<float>(y0[1]); Y[2] = static_cast<float>(y0[2]);
-    W = F2{1.0f, 0.0f}; S = F2{0.0f, 0.0f}; k = 0;
+    W = FIXED ? om2 : F2{1.0f, 0.0f};   // FIXED: W holds V = W omega
+    S = F2{0.0f, 0.0f};
+    k = 0;
+    pw = philox_walk(i, p, K);
   };
   init(w);
-  float r_prev = -1.0f;
-  F2 c2{1.0f, 0.0f}, om2{0.0f, 0.0f};
 
   for (;;) {
     float dG = INFINITY;
     bool done = false;
     int flag = 0;
-    if (!pb.closed) {
+    if constexpr (FIXED) {
+      if (k >= k_stop) {
+        done = true;
+        flag = k_flag ? 1 : 0;
+      }
+    } else if (!pb.closed) {
       float yg[3];
       dG = delta_gamma3<MK, float>(pb, Y, yg);
       if (dG < eps) {
@@ -304,37 +383,35 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
     } else if (W.hi < tau.hi || (W.hi == tau.hi && W.lo < tau.lo)) {
       done = true;
     }
-    if (!done && k >= pb.max_steps) { done = true; flag = 1; }
+    if (!FIXED && !done && k >= max_steps) { done = true; flag = 1; }
     if (done) {
       pb.S_out[o] = f2_to_double(S);
-      pb.K_out[o] = static_cast<int32_t>(k);
+      pb.K_out[o] = k;
       pb.flag_out[o] = flag;
       w += stride;
       if (w >= total) break;
       init(w);
       continue;
     }
-    float rg = rgeo;
-    if constexpr (MK == kPointCloud) rg = rho_geo_at<MK, KM, float>(pb, Y);
-    const float r = theta * (dG < rg ? dG : rg);
-    const float a = sqs * r;
-    if (r != r_prev) {   // constant-radius walks evaluate the weights once
-      if (!pb.em1_fp64) {
-        weights_from_em1(em1_poly32(pb, 0.25f * a * a), inv_sigma, c2, om2);
-      } else {
-        const double ad = static_cast<double>(a);
-        const double em1 = em1_series(0.5, 0.25 * (ad * ad));
-        const double c = 1.0 / (1.0 + em1);
-        c2 = f2_from_double(c);
-        om2 = f2_from_double(one_minus_c(em1, c) / pb.sigma);
+    float r, a;
+    if constexpr (FIXED) {
+      r = theta * rgeo;
+      a = sqs * r;
+    } else {
+      float rg = rgeo;
+      if constexpr (MK == kPointCloud) rg = rho_geo_at<MK, KM, float>(pb, Y);
+      r = theta * (dG < rg ? dG : rg);
+      a = sqs * r;
+      if (r != r_prev) {   // constant-radius stretches evaluate the weights once
+        set_weights(a);
+        r_prev = r;
       }
-      r_prev = r;
     }
     const uint32_t kk = static_cast<uint32_t>(k);
     float Th[3], F = 0.0f;
     if (nv == 1) {
-      const U4 b0 = philox4x32_10(0u, kk, i, p, K);
-      const U4 b1 = philox4x32_10(1u, kk, i, p, K);
+      U4 b0, b1;
+      philox_step_pair(pw, kk, K, b0, b1);
       float g[3], z[3];
       box_muller32(u23(b0.x), u23(b0.y), g[0], g[1]);
       box_muller32(u23(b0.z), u23(b0.w), g[2], z[0]);
@@ -367,20 +444,159 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
       }
       F /= static_cast<float>(nv);
     }
-    S = f2_add(S, f2_mul_f(f2_mul(W, om2), F));
-    W = f2_mul(W, c2);
+    if constexpr (FIXED) {
+      // S += V F: the product's error term and the TwoSum error join S.lo
+      const float ph = __fmul_rn(W.hi, F);
+      const float pl = __fmaf_rn(W.lo, F, __fmaf_rn(W.hi, F, -ph));
+      const float s = __fadd_rn(S.hi, ph);
+      const float bb = __fadd_rn(s, -S.hi);
+      const float err = __fadd_rn(__fadd_rn(S.hi, -__fadd_rn(s, -bb)), __fadd_rn(ph, -bb));
+      S = F2{s, __fadd_rn(S.lo, __fadd_rn(err, pl))};
+      if ((k & 63) == 63) S = f2_fast_two_sum(S.hi, S.lo);
+      // V *= c
+      const float vh = __fmul_rn(W.hi, c2.hi);
+      float ve = __fmaf_rn(W.hi, c2.hi, -vh);
+      ve = __fmaf_rn(W.hi, c2.lo, ve);
+      ve = __fmaf_rn(W.lo, c2.hi, ve);
+      W = F2{vh, ve};
+    } else {
+      S = f2_add(S, f2_mul_f(f2_mul(W, om2), F));
+      W = f2_mul(W, c2);
+    }
     if constexpr (MK == kPointCloud) cp_any<MK, KM, float>(pb, Th, Y); else cp3_f32<MK>(pb, Th, Y);
     ++k;
   }
 }
 
-// Entry points: the analytic manifolds run 256-thread blocks (64 registers; a
-// 48-register bound measured slower on B300); the point-cloud walk uses
+// One FP32 step of a constant-radius walk with N_V = 1: the draws of step kk,
+// Theta and Z from Y, F = f(cp(Z)) (returned), then Y = cp(Theta).
+template <int MK>
+__device__ __forceinline__ float fixed_step32(const DevProblem& pb, const PhiloxKeys& K, const PhiloxWalk& pw,
+                                              uint32_t kk, float r, float a, float (&Y)[3]) {
+  U4 b0, b1;
+  philox_step_pair(pw, kk, K, b0, b1);
+  float g[3], z[3];
+  box_muller32(u23(b0.x), u23(b0.y), g[0], g[1]);
+  box_muller32(u23(b0.z), u23(b0.w), g[2], z[0]);
+  box_muller32(u23(b1.x), u23(b1.y), z[1], z[2]);
+  const float U = u23(b1.z);
+  const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
+  float t = table_lookup32(pb, a, U);
+  t = fminf(fmaxf(t, 0.0f), 1.0f);
+  const float zs = (r * t) * rsqrtf(fmaxf(dot3(z, z), 1e-30f));
+  float Z[3], Th[3];
+  for (int q = 0; q < 3; ++q) {
+    Z[q] = Y[q] + zs * z[q];
+    Th[q] = Y[q] + sc * g[q];
+  }
+  const float F = source_at32<MK, 1>(pb, Z);
+  cp3_f32<MK>(pb, Th, Y);
+  return F;
+}
+
+// Closed problems on analytic manifolds with N_V = 1: the radius, c and omega
+// are constants of the launch, so every walk has the same weights V_k = W_k
+// omega = omega c^k and the same stopping index.  Each thread advances NW walks
+// in lockstep (NW independent dependency chains per warp; V and the loop are
+// shared), adding V F_k to each walk's S with one TwoSum whose low parts
+// accumulate unnormalised (renormalised every 64 steps, |S.lo| < 64 ulp(S.hi)).
+// V *= c runs without renormalisation (|V.lo| stays within a few ulp of V.hi).
+template <int MK, int NW>
+__device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
+  const int64_t total = pb.wk_w1;
+  const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int64_t tid = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const PhiloxKeys& K = pb.keys;
+  const int max_steps = static_cast<int>(pb.max_steps);
+  const float r = pb.sf.theta * pb.sf.rho_geo;
+  const float a = pb.sf.sqrt_sigma * r;
+  F2 c2, om2;
+  if (!pb.em1_fp64) {
+    weights_from_em1(em1_poly32(pb, 0.25f * a * a), pb.sf.inv_sigma, c2, om2);
+  } else {
+    const double ad = static_cast<double>(a);
+    const double em1 = em1_series(0.5, 0.25 * (ad * ad));
+    const double c = 1.0 / (1.0 + em1);
+    c2 = f2_from_double(c);
+    om2 = f2_from_double(one_minus_c(em1, c) / pb.sigma);
+  }
+  const F2 thr = f2_mul(f2_from_double(pb.tau_w), om2);   // W < tau_W  <=>  V < tau_W omega
+  // the common stopping index, in the same float-pair recurrence as the loop
+  int k_stop = max_steps;
+  int k_flag = 1;
+  {
+    F2 V = om2;
+    int kq = 0;
+    for (; kq < max_steps; ++kq) {
+      if ((V.hi - thr.hi) + (V.lo - thr.lo) < 0.0f) break;
+      const float vh = __fmul_rn(V.hi, c2.hi);
+      V = F2{vh, __fmaf_rn(V.lo, c2.hi, __fmaf_rn(V.hi, c2.lo, __fmaf_rn(V.hi, c2.hi, -vh)))};
+    }
+    if (kq < max_steps || (V.hi - thr.hi) + (V.lo - thr.lo) < 0.0f) {
+      k_stop = kq;
+      k_flag = 0;
+    }
+  }
+  for (int64_t base = pb.wk_w0 + tid; base < total; base += NW * nthreads) {
+    float Y[NW][3];
+    F2 S[NW];
+    PhiloxWalk pw[NW];
+    int64_t o[NW];
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      const int64_t w = base + j * nthreads;
+      const WalkId id = walk_id(pb, w < total ? w : base);   // a missing partner repeats walk `base`
+      o[j] = w < total ? id.o : -1;
+      const double* y0 = pb.pts + static_cast<size_t>(id.p) * 3;
+      Y[j][0] = static_cast<float>(y0[0]); Y[j][1] = static_cast<float>(y0[1]); Y[j][2] = static_cast<float>(y0[2]);
+      S[j] = F2{0.0f, 0.0f};
+      pw[j] = philox_walk(id.i, id.p, K);
+    }
+    F2 V = om2;
+    for (int k = 0; k < k_stop; ++k) {
+#pragma unroll
+      for (int j = 0; j < NW; ++j) {
+        const float F = fixed_step32<MK>(pb, K, pw[j], static_cast<uint32_t>(k), r, a, Y[j]);
+        // S += V F: the product's error term and the TwoSum error join S.lo
+        const float ph = __fmul_rn(V.hi, F);
+        const float pl = __fmaf_rn(V.lo, F, __fmaf_rn(V.hi, F, -ph));
+        const float sh = __fadd_rn(S[j].hi, ph);
+        const float bb = __fadd_rn(sh, -S[j].hi);
+        const float err = __fadd_rn(__fadd_rn(S[j].hi, -__fadd_rn(sh, -bb)), __fadd_rn(ph, -bb));
+        S[j] = F2{sh, __fadd_rn(S[j].lo, __fadd_rn(err, pl))};
+        if ((k & 63) == 63) S[j] = f2_fast_two_sum(S[j].hi, S[j].lo);
+      }
+      const float vh = __fmul_rn(V.hi, c2.hi);
+      V = F2{vh, __fmaf_rn(V.lo, c2.hi, __fmaf_rn(V.hi, c2.lo, __fmaf_rn(V.hi, c2.hi, -vh)))};
+    }
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+      if (o[j] < 0) continue;
+      pb.S_out[o[j]] = f2_to_double(S[j]);
+      pb.K_out[o[j]] = k_stop;
+      pb.flag_out[o[j]] = k_flag;
+    }
+  }
+}
+
+// Entry points: the analytic manifolds run 256-thread blocks; the
+// fixed-radius loop fits 48 registers (5 blocks, 40 warps per SM: measured
+// fastest on B300), the general loop 64 (4 blocks); the point-cloud walk uses
 // 128-thread blocks with a larger register budget.
+template <int MK, int KM, bool FIXED>
+__global__ void __launch_bounds__(256, FIXED ? 5 : 4) walk3_f32_kernel(const DevProblem pb) {
+  if constexpr (FIXED) {
+    if (pb.n_v == 1) {
+      walk3_fixed_body<MK, 1>(pb);
+      return;
+    }
+  }
+  walk3_f32_body<MK, KM, FIXED>(pb);
+}
 template <int MK, int KM>
-__global__ void __launch_bounds__(256) walk3_f32_kernel(const DevProblem pb) { walk3_f32_body<MK, KM>(pb); }
-template <int MK, int KM>
-__global__ void __launch_bounds__(128) walk3_f32_cloud_kernel(const DevProblem pb) { walk3_f32_body<MK, KM>(pb); }
+__global__ void __launch_bounds__(128) walk3_f32_cloud_kernel(const DevProblem pb) {
+  walk3_f32_body<MK, KM, false>(pb);
+}
 template <int MK, int KM>
 __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) { walk3_f64_body<MK, KM>(pb); }
 

@@ -249,7 +249,7 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
   const int n = pb.n;
   const int D = pb.d + 1;
   const int npad = (n + 3) & ~3;
-  const PhiloxKeys K = philox_keys(static_cast<uint32_t>(pb.seed), static_cast<uint32_t>(pb.seed >> 32));
+  const PhiloxKeys& K = pb.keys;
   const int nv = pb.n_v;
   const uint32_t nb = static_cast<uint32_t>((n + G - 1) / G);
   // loop-invariant parameters in the walk's precision

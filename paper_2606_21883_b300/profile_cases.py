@@ -1,0 +1,67 @@
+"""Small seeded cases that launch one walk kernel each, for profiler captures.
+
+    python -m paper_2606_21883_b300.profile_cases torus     # walk3_f32_kernel<torus>
+    python -m paper_2606_21883_b300.profile_cases s20_tc    # embed_tc_kernel (tensor cores)
+    python -m paper_2606_21883_b300.profile_cases s20_cuda  # walkn_f32_kernel<embedded> (CUDA cores)
+    python -m paper_2606_21883_b300.profile_cases s999      # walkn_f32_kernel<sphere>
+
+Each case runs `--reps` walk launches into device buffers (the first one
+warms tables and caches) and prints one line with the walk-steps and the
+wall time of the last launch.  Inputs are the same seeded workloads the
+tests and the benchmark use, at sizes a profiler replays in seconds.
+"""
+from __future__ import annotations
+
+import argparse
+import time
+
+import numpy as np
+
+from . import FP32, PROJ_CUDA, PROJ_TENSOR, Context
+from . import workloads as W
+
+
+def _case(name):
+    if name == "torus":   # 64 points x 2048 walks x 525 steps = 6.9e7 walk-steps
+        w = W.torus_closed(P=64, walks=2048)
+        return w, 2048, {}
+    if name in ("s20_tc", "s20_cuda"):   # S^20 in R^1000, 4 tiles per SM, walks capped at 16 steps
+        w = W.embedded_s20(P=148, walks=1)
+        w.params.max_steps = 16
+        return w, 512, {"projection": PROJ_TENSOR if name == "s20_tc" else PROJ_CUDA}
+    if name == "s999":   # S^999 in R^1000, walks capped at 16 steps
+        w = W.hypersphere_half(P=148, walks=1)
+        w.params.max_steps = 16
+        return w, 128, {}
+    raise SystemExit(f"unknown case {name}")
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999"])
+    ap.add_argument("--reps", type=int, default=2)
+    args = ap.parse_args(argv)
+    import torch
+
+    w, N, kw = _case(args.case)
+    ctx = Context(0)
+    P = w.points.shape[0]
+    pts = torch.from_numpy(np.ascontiguousarray(w.points)).cuda()
+    S = torch.empty((P, N), dtype=torch.float64, device="cuda")
+    K = torch.empty((P, N), dtype=torch.int32, device="cuda")
+    F = torch.empty((P, N), dtype=torch.int32, device="cuda")
+    dt = 0.0
+    for _ in range(max(1, args.reps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.walk_scores_device(w.problem, w.params, pts, N, FP32, S, K, F, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    steps = int(K.sum().item())
+    print(f"{args.case}: {P} points x {N} walks, {steps} walk-steps, last launch {dt * 1e3:.2f} ms wall, "
+          f"{steps / dt:.3e} walk-steps/s")
+    ctx.close()
+
+
+if __name__ == "__main__":
+    main()
