@@ -37,13 +37,15 @@ from paper_2606_21883_b300 import workloads as W  # noqa: E402
 
 METRIC = "walk-steps/s at fixed RMSE (torus, FP32 walk + FP64 accumulation)"
 UNIT = "walk-steps/s"
-# Algorithmic lane-operations per walk-step of the FP32 torus walk (N_V = 1),
-# the minimal operation count of one step: 2 Philox4x32-10 blocks (10 rounds x
-# 2 wide multiplies + 2 three-input XORs) 80, 7 uniforms 14, 3 Box-Muller pairs
-# 27, sphere sample 8, radius table 25, interior sample 9, torus angles of Z 13,
-# torus source (-Delta_M + sigma) u 33, closest point of Theta 14, weight and
-# score (W omega F, S +=, W c) 4, stop test and loop 6.
-OPS_PER_STEP = 233
+# Algorithmic lane-operations per walk-step of the FP32 torus walk (N_V = 1):
+# the minimal operation count of one step, one wide multiply, three-input XOR
+# or MUFU op counting as one: 2 Philox4x32-10 blocks whose rounds 0..2 share
+# the per-walk and per-step work 64, 7 uniforms 14, 3 Box-Muller pairs 27,
+# sphere sample 9, radius table (side, sqrt, index, one 16-byte load, 3 FMA,
+# clamp) 17, interior sample 10, torus angles of cp(Z) 11, torus source
+# (-Delta_M + sigma) u for one mode 16, closest point of Theta 13, weight and
+# score in float pairs (S += V F by TwoSum, V *= c) 15, loop 3.
+OPS_PER_STEP = 199
 
 
 def _peaks():
@@ -184,12 +186,13 @@ def cpu_baseline(target_s: float = 15.0):
     import oracle as O
     w = W.torus_closed(P=64, walks=1)
     cores = os.cpu_count() or 1
-    # calibrate on a short run, then size the sample for ~target_s of CPU work
+    # load and warm the oracle, calibrate on 64 x 16 walks, then size the sample
+    # for ~target_s of wall time on all cores
+    O.solve(w.problem, w.params, w.points[:2], 2, n_threads=cores)
     t0 = time.perf_counter()
-    O.solve(w.problem, w.params, w.points[:8], 8, n_threads=cores)
-    dt = max(time.perf_counter() - t0, 1e-3)
-    per_walk = dt / 64.0
-    walks = int(max(8, min(4000, target_s / per_walk / 64)))
+    O.solve(w.problem, w.params, w.points, 16, n_threads=cores)
+    per_walk = max(time.perf_counter() - t0, 1e-3) / (64 * 16)
+    walks = int(max(16, min(8000, target_s / per_walk / 64)))
     t0 = time.perf_counter()
     m, se, ms, nf = O.solve(w.problem, w.params, w.points, walks, n_threads=cores)
     dt = time.perf_counter() - t0
@@ -326,7 +329,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "torus_closed R=1 a=0.4 sigma=2 u=sin(th)cos(2ph)", "points": P,
                        "walks_per_point": N, "steps_per_walk": 525, "walk_steps_per_step": steps_per_solve,
-                       "precision": "FP32 walk, FP64 weights + Kahan sums", "parallelism": f"dp{world} (points)",
+                       "precision": "FP32 walk; per-walk weight and score in float pairs (~2^-46); per-point FP64 Kahan sums", "parallelism": f"dp{world} (points)",
                        "l2": "flushed between timed steps (256 MB write)", "rmse": rmse,
                        "query_pts_per_s": P * args.steps * world / tmax},
             "rmse": rmse,
