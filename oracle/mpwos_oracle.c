@@ -499,6 +499,27 @@ double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_p
 /* ------------------------------------------------------------------------- */
 /* Problem data f, g evaluated at a point x of M.                              */
 /* ------------------------------------------------------------------------- */
+/* SPHERE_QUAD at the direction of s in R^{d+1} (normalised here):
+ * u = c0 + v.s + s^T A s, or (-Delta_{S^d} + sigma) u when apply_op. */
+static double quad_at(const orc_func* f, int d_dim, double sigma, const double* s_in) {
+  int D = d_dim + 1;   /* <= 32 */
+  double s[32];
+  double ns = sqrt(dot(s_in, s_in, D));
+  for (int j = 0; j < D; ++j) s[j] = s_in[j] / ns;
+  double lin = dot(f->v, s, D);
+  double quad = 0.0, tr = 0.0;
+  for (int i = 0; i < D; ++i) {
+    tr += f->A[(size_t)i * D + i];
+    for (int j = 0; j < D; ++j) quad += f->A[(size_t)i * D + j] * s[i] * s[j];
+  }
+  if (!f->apply_op) return f->c0 + lin + quad;
+  /* on S^d: degree-k harmonics have -Delta eigenvalue k(k+d-1); s^T A s splits
+   * into its trace-free part (k = 2) and the constant tr(A)/(d+1). */
+  double d = (double)d_dim;
+  double mean = tr / (double)D;
+  return sigma * (f->c0 + mean) + (d + sigma) * lin + (2.0 * (d + 1.0) + sigma) * (quad - mean);
+}
+
 static double trig(int kind, double v) { return kind == 0 ? cos(v) : sin(v); }
 
 double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, const double* x) {
@@ -551,21 +572,9 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
   } else {
     for (int j = 0; j < D; ++j) s[j] = x[j];
   }
-  double ns = sqrt(dot(s, s, D));
-  for (int j = 0; j < D; ++j) s[j] /= ns;
-  double lin = dot(f->v, s, D);
-  double quad = 0.0, tr = 0.0;
-  for (int i = 0; i < D; ++i) {
-    tr += f->A[(size_t)i * D + i];
-    for (int j = 0; j < D; ++j) quad += f->A[(size_t)i * D + j] * s[i] * s[j];
-  }
+  double val = quad_at(f, m->d, sigma, s);
   free(s);
-  if (!f->apply_op) return f->c0 + lin + quad;
-  /* on S^d: degree-k harmonics have -Delta eigenvalue k(k+d-1); s^T A s splits
-   * into its trace-free part (k = 2) and the constant tr(A)/(d+1). */
-  double d = (double)m->d;
-  double mean = tr / (double)D;
-  return sigma * (f->c0 + mean) + (d + sigma) * lin + (2.0 * (d + 1.0) + sigma) * (quad - mean);
+  return val;
 }
 
 /* ------------------------------------------------------------------------- */
@@ -658,6 +667,192 @@ static int run_walk(const orc_manifold* m, const orc_problem* pb, const orc_para
   return flag;
 }
 
+/* ------------------------------------------------------------------------- */
+/* Dimension-reduced exact sampler (an exact reformulation of the same walk;  */
+/* the paper draws full n-dimensional directions).  A step uses the n        */
+/* Gaussians g of a direction only through                                    */
+/*   - embedded sphere Q S^d + b: Q^T g (the intrinsic step) and |g|^2;       */
+/*   - sphere / R^n: the coordinates T that f, g and the boundary normal      */
+/*     read, |g|^2, and (sphere) the component of g along Y's part outside T. */
+/* For g ~ N(0, I_n) these are independent N(0,1) variables and a chi^2 with  */
+/* the remaining number of dimensions (n - D, n - |T| - 1 or n - |T|), so     */
+/* drawing them directly gives the same law of the walk.  The state kept is   */
+/* s (embedded sphere), or Y with T coordinates and, for the sphere, the norm */
+/* of the rest in one spare coordinate (which keeps |Y| and e.Y exact).       */
+/*   draws of vector v (0: Theta, 1 + l: Z_l) at step k:                      */
+/*     Gaussians: blocks 64 v, 64 v + 1, ... (two per block, orc_gaussians)   */
+/*     chi^2:     from block 64 v + 32 (orc_chi2)                             */
+/*     U_l:       block 64 (1 + N_V) + l, u53(words 0, 1)                     */
+/* ------------------------------------------------------------------------- */
+#define ORC_CHI2_ATTEMPTS 16
+
+double orc_chi2(uint64_t seed, uint32_t j0, uint32_t k, uint32_t i, uint32_t p, int m) {
+  if (m <= 0) return 0.0;
+  double x;
+  if (m == 1) {
+    orc_gaussians(seed, j0, k, i, p, 1, &x);
+    return x * x;
+  }
+  /* Marsaglia & Tsang (ACM TOMS 26, 2000): Gamma(alpha) for alpha = m/2 >= 1 by
+   * squeezing (1 + c x)^3, x ~ N(0,1), with the exact log acceptance test; an
+   * attempt that finds v <= 0 is rejected.  chi^2_m = 2 Gamma(m/2).  After 16
+   * rejections (probability below 1e-20 for every m >= 2) the last candidate
+   * is returned. */
+  double d = 0.5 * (double)m - 1.0 / 3.0, c = 1.0 / sqrt(9.0 * d);
+  double cand = d;
+  for (uint32_t a = 0; a < ORC_CHI2_ATTEMPTS; ++a) {
+    orc_gaussians(seed, j0 + 2u * a, k, i, p, 1, &x);
+    double v = 1.0 + c * x;
+    if (v <= 0.0) continue;
+    v = v * v * v;
+    cand = d * v;
+    double U = uniform_at(seed, j0 + 2u * a + 1u, k, i, p);
+    if (log(U) < 0.5 * x * x + d - d * v + d * log(v)) return 2.0 * d * v;
+  }
+  return 2.0 * cand;
+}
+
+static void mark_poly(const orc_func* f, int* used) {
+  if (f->kind != ORC_POLY) return;
+  for (int t = 0; t < f->n_terms; ++t)
+    for (int q = f->term_off[t]; q < f->term_off[t + 1]; ++q) used[f->var[q]] = 1;
+}
+
+int orc_tracked_set(const orc_manifold* m, const orc_problem* pb, int* T) {
+  if (pb->f.kind != ORC_POLY || (!pb->closed && pb->g.kind != ORC_POLY)) return -1;
+  int* used = (int*)calloc((size_t)m->n, sizeof(int));
+  mark_poly(&pb->f, used);
+  if (!pb->closed) {
+    mark_poly(&pb->g, used);
+    for (int q = 0; q < m->n; ++q)
+      if (pb->bnd_normal[q] != 0.0) used[q] = 1;
+  }
+  int nT = 0;
+  for (int q = 0; q < m->n; ++q)
+    if (used[q]) {
+      if (nT == 32) { free(used); return -1; }
+      T[nT++] = q;
+    }
+  free(used);
+  return nT;
+}
+
+static int run_walk_reduced(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
+                            const double* y0, uint32_t p, uint32_t i, work_t* w,
+                            double* S_out, int64_t* K_out) {
+  int n = m->n;
+  int emb = m->kind == ORC_EMBEDDED_SPHERE, sph = m->kind == ORC_SPHERE;
+  int D = m->d + 1;
+  int T[32], nT, spare = -1;
+  if (emb) {
+    nT = D;
+  } else {
+    nT = orc_tracked_set(m, pb, T);
+    if (sph)
+      for (int q = 0; q < n && spare < 0; ++q) {
+        int inT = 0;
+        for (int t = 0; t < nT; ++t) inT |= (T[t] == q);
+        if (!inT) spare = q;
+      }
+  }
+  int ng = nT + (sph ? 1 : 0);                      /* Gaussians per direction */
+  int rest = emb ? n - D : (sph ? n - nT - 1 : n - nT);   /* chi^2 degrees of freedom */
+  double sqs = sqrt(pb->sigma);
+  double g[33], s[32], th[32], z[32];
+  /* state: embedded sphere s = normalize(Q^T (y0 - b)); otherwise Y canonical */
+  memset(w->Y, 0, sizeof(double) * (size_t)n);
+  if (emb) {
+    double ns = 0.0;
+    for (int j = 0; j < D; ++j) {
+      double acc = 0.0;
+      for (int q = 0; q < n; ++q) acc += m->Q[(size_t)q * D + j] * (y0[q] - m->b[q]);
+      s[j] = acc;
+      ns += acc * acc;
+    }
+    for (int j = 0; j < D; ++j) s[j] /= sqrt(ns);
+  } else {
+    double tt = 0.0;
+    for (int t = 0; t < nT; ++t) {
+      w->Y[T[t]] = y0[T[t]];
+      tt += y0[T[t]] * y0[T[t]];
+    }
+    if (sph) {
+      double yy = dot(y0, y0, n);
+      w->Y[spare] = sqrt(yy - tt > 0.0 ? yy - tt : 0.0);
+    }
+  }
+  double W = 1.0, S = 0.0;
+  int64_t k = 0;
+  int flag = 0;
+  for (;;) {
+    double dG = INFINITY;
+    if (!pb->closed) {
+      dG = orc_delta_gamma(m, pb, pr, w->Y, w->yg);
+      if (dG < pr->eps) {
+        S += W * orc_func_eval(m, &pb->g, pb->sigma, w->yg);
+        break;
+      }
+      if (W == 0.0) break;
+    } else if (W < pr->tau_w) {
+      break;
+    }
+    if (k >= pr->max_steps) { flag = 1; break; }
+    double rgeo = pr->c_kappa / (1.0 + kappa_of(m));
+    double r = pr->theta * (dG < rgeo ? dG : rgeo);
+    double a = sqs * r;
+    double em1 = orc_em1(n, a);
+    double c = 1.0 / (1.0 + em1);
+    double omega = ((em1 <= 1.0) ? em1 * c : 1.0 - c) / pb->sigma;
+    /* F_k: N_V interior samples Z_l = Y + R_l g_l/|g_l| */
+    double F = 0.0;
+    for (int l = 0; l < pr->n_v; ++l) {
+      uint32_t jv = 64u * (uint32_t)(1 + l);
+      double U = uniform_at(pr->seed, 64u * (uint32_t)(1 + pr->n_v) + (uint32_t)l, (uint32_t)k, i, p);
+      double t = orc_green_cdf_inv(n, a, U);
+      orc_gaussians(pr->seed, jv, (uint32_t)k, i, p, ng, g);
+      double X = orc_chi2(pr->seed, jv + 32u, (uint32_t)k, i, p, rest);
+      double zs = (r * t) / sqrt(dot(g, g, ng) + X);
+      if (emb) {
+        for (int j = 0; j < D; ++j) z[j] = s[j] + zs * g[j];
+        F += quad_at(&pb->f, m->d, pb->sigma, z);
+      } else {
+        memcpy(w->Z, w->Y, sizeof(double) * (size_t)n);
+        for (int q = 0; q < nT; ++q) w->Z[T[q]] += zs * g[q];
+        if (sph) {
+          double zr = w->Y[spare] + zs * g[nT];
+          w->Z[spare] = sqrt(zr * zr + zs * zs * X);
+        }
+        orc_cp(m, w->Z, w->cZ);
+        F += orc_func_eval(m, &pb->f, pb->sigma, w->cZ);
+      }
+    }
+    if (pr->n_v > 1) F /= (double)pr->n_v;
+    /* Theta = Y + r g/|g|, Y = cp(Theta) */
+    orc_gaussians(pr->seed, 0u, (uint32_t)k, i, p, ng, g);
+    double X = orc_chi2(pr->seed, 32u, (uint32_t)k, i, p, rest);
+    double sc = r / sqrt(dot(g, g, ng) + X);
+    if (emb) {
+      for (int j = 0; j < D; ++j) th[j] = s[j] + sc * g[j];
+      double tn = sqrt(dot(th, th, D));
+      for (int j = 0; j < D; ++j) s[j] = th[j] / tn;
+    } else {
+      memcpy(w->Th, w->Y, sizeof(double) * (size_t)n);
+      for (int q = 0; q < nT; ++q) w->Th[T[q]] += sc * g[q];
+      if (sph) {
+        double tr_ = w->Y[spare] + sc * g[nT];
+        w->Th[spare] = sqrt(tr_ * tr_ + sc * sc * X);
+      }
+    }
+    S += (W * omega) * F;
+    W *= c;
+    if (!emb) orc_cp(m, w->Th, w->Y);
+    k++;
+  }
+  *S_out = S;
+  *K_out = k;
+  return flag;
+}
+
 int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
                     const double* pts, int64_t P, int64_t N, double* S, int64_t* K,
                     int32_t* flags, int n_threads) {
@@ -673,8 +868,11 @@ int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_para
     for (int64_t q = 0; q < total; ++q) {
       int64_t p = q / N, i = q % N;
       int64_t nrec = 0;
-      flags[q] = run_walk(m, pb, pr, pts + (size_t)p * (size_t)m->n, (uint32_t)p, (uint32_t)i, &w,
-                          &S[q], &K[q], NULL, 0, &nrec);
+      const double* y0 = pts + (size_t)p * (size_t)m->n;
+      if (pr->sampler == ORC_SAMPLER_REDUCED)
+        flags[q] = run_walk_reduced(m, pb, pr, y0, (uint32_t)p, (uint32_t)i, &w, &S[q], &K[q]);
+      else
+        flags[q] = run_walk(m, pb, pr, y0, (uint32_t)p, (uint32_t)i, &w, &S[q], &K[q], NULL, 0, &nrec);
     }
     work_free(&w);
   }

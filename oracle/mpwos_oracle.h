@@ -61,11 +61,17 @@ typedef struct {
   orc_func f, g;
 } orc_problem;
 
+enum { ORC_SAMPLER_FULL = 0, ORC_SAMPLER_REDUCED = 1 };
+
 typedef struct {
   double eps, tau_w, theta, c_kappa;
   int n_v;
   int64_t max_steps;
   uint64_t seed;
+  int sampler;            /* ORC_SAMPLER_FULL: n Gaussians per direction;
+                             ORC_SAMPLER_REDUCED: the dimension-reduced exact
+                             sampler (spheres and R^n with POLY data, embedded
+                             spheres); see orc_chi2 */
 } orc_params;
 
 /* One trace record per step of one walk (tiny-case pins). */
@@ -84,6 +90,13 @@ double orc_c_sigma_r(int n, double a);    /* 1 / I~_nu(a)                       
 double orc_green_cdf(int n, double a, double t);
 double orc_green_cdf_inv(int n, double a, double U);
 double orc_kt_minus_one(double mu, double x);
+/* chi^2 with m degrees of freedom from the counter stream at block j0 of step k
+ * (Marsaglia-Tsang gamma sampling for m >= 2, attempt a at blocks j0 + 2a and
+ * j0 + 2a + 1; x^2 of one Gaussian for m = 1; 0 for m <= 0). */
+double orc_chi2(uint64_t seed, uint32_t j0, uint32_t k, uint32_t i, uint32_t p, int m);
+/* tracked coordinates of the reduced sampler (ascending; returns their count,
+ * -1 if more than 32 or the data are not POLY) */
+int    orc_tracked_set(const orc_manifold* m, const orc_problem* pb, int* T);
 void   orc_cp(const orc_manifold* m, const double* x, double* out);
 double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
                        const double* y, double* y_gamma);

@@ -9,7 +9,7 @@ import numpy as np
 
 from .build import build
 
-__all__ = ["lib", "philox", "u53", "gaussians", "em1", "c_sigma_r", "green_cdf", "green_cdf_inv",
+__all__ = ["lib", "philox", "u53", "gaussians", "chi2", "tracked_set", "em1", "c_sigma_r", "green_cdf", "green_cdf_inv",
            "kt_minus_one", "cp", "delta_gamma", "func_eval", "walk_scores", "solve", "trace",
            "OracleProblem", "cloud_knn"]
 
@@ -39,7 +39,7 @@ class _Problem(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("tau_w", C.c_double), ("theta", C.c_double),
                 ("c_kappa", C.c_double), ("n_v", C.c_int), ("max_steps", C.c_int64),
-                ("seed", C.c_uint64)]
+                ("seed", C.c_uint64), ("sampler", C.c_int)]
 
 
 class _Trace(C.Structure):
@@ -70,6 +70,8 @@ def lib() -> C.CDLL:
         L.orc_func_eval.restype = C.c_double
         L.orc_trace.restype = C.c_int64
         L.orc_cloud_knn.restype = C.c_double
+        L.orc_chi2.restype = C.c_double
+        L.orc_chi2.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
         _lib = L
     return _lib
 
@@ -113,7 +115,8 @@ class OracleProblem:
     def set_params(self, params):
         self.params = _Params(eps=params.eps, tau_w=params.tau_w, theta=params.theta,
                               c_kappa=params.c_kappa, n_v=params.n_v,
-                              max_steps=params.max_steps, seed=params.seed)
+                              max_steps=params.max_steps, seed=params.seed,
+                              sampler=getattr(params, "sampler", 0))
 
     def _arr(self, a, dtype=np.float64):
         a = np.ascontiguousarray(a, dtype=dtype)
@@ -158,6 +161,18 @@ def gaussians(seed, j0, k, i, p, n):
     lib().orc_gaussians(C.c_uint64(seed), C.c_uint32(j0), C.c_uint32(k), C.c_uint32(i),
                         C.c_uint32(p), C.c_int(n), _dptr(g))
     return g
+
+
+def chi2(seed, j0, k, i, p, m):
+    """chi^2_m from the reduced sampler's counter stream at block j0 of step k."""
+    return lib().orc_chi2(seed, j0, k, i, p, m)
+
+
+def tracked_set(problem, params):
+    op = OracleProblem(problem, params)
+    T = (C.c_int * 32)()
+    nT = lib().orc_tracked_set(C.byref(op.man), C.byref(op.prob), T)
+    return list(T[:nT]) if nT >= 0 else None
 
 
 def em1(n, a):

@@ -42,6 +42,9 @@ MANIFOLD_TORUS = 2
 MANIFOLD_EMBEDDED_SPHERE = 3
 MANIFOLD_POINT_CLOUD = 4
 
+SAMPLER_FULL = 0      # n Gaussians per direction
+SAMPLER_REDUCED = 1   # dimension-reduced exact sampler (tracked coordinates + chi^2 remainder)
+
 CLOUD_CP_FIT = 0       # kNN + PCA plane + quadratic height fit + projection
 CLOUD_CP_NEAREST = 1   # nearest cloud point
 
@@ -138,6 +141,7 @@ class Params:
     n_v: int = 1
     max_steps: int = 10_000_000
     seed: int = 0
+    sampler: int = 0   # SAMPLER_FULL or SAMPLER_REDUCED (dimension-reduced exact sampler)
 
 
 # ----------------------------------------------------------------------------
