@@ -68,6 +68,17 @@ extern "C" {
                                  and EMBEDDED_SPHERE only (MPWOS_EINVAL otherwise)           */
 #define MPWOS_PROJ_CUDA 2     /* FP32 dot products on the CUDA cores                       */
 
+/* ---- direction sampler (not in the paper; same law of the walk) --------- */
+#define MPWOS_SAMPLER_FULL 0     /* n Gaussians per direction (the paper's form)               */
+#define MPWOS_SAMPLER_REDUCED 1  /* dimension-reduced exact sampler: the walk reads a direction
+                                    only through the coordinates T that f, g and the boundary
+                                    normal use (the intrinsic Q^T g on an embedded sphere),
+                                    on a sphere the component along Y's part outside T, and
+                                    |g|^2; those are drawn directly (normals and a chi^2 of the
+                                    remaining dimensions).  SPHERE and EUCLID with n > 3 and
+                                    POLY data (|T| <= 32), EMBEDDED_SPHERE; its own Philox
+                                    stream layout (the CPU oracle has the same mode).        */
+
 typedef struct mpwos_ctx mpwos_ctx;
 
 /* Manifold M (Sec. 2.1).  Q, b are host arrays (embedded sphere only),
@@ -132,10 +143,12 @@ typedef struct {
   int precision;     /* MPWOS_FP64 or MPWOS_FP32                                */
   int projection;    /* MPWOS_PROJ_*: embedded sphere in FP32 only; ignored elsewhere
                         except that MPWOS_PROJ_TENSOR is rejected there             */
+  int sampler;       /* MPWOS_SAMPLER_FULL or MPWOS_SAMPLER_REDUCED               */
 } mpwos_params;
 
 /* Fill a params struct with the defaults: eps 1e-3, tau_w 1e-8, theta 0.95,
- * c_kappa 1.2, n_v 1, max_steps 1e7, seed 0, FP64, MPWOS_PROJ_AUTO. */
+ * c_kappa 1.2, n_v 1, max_steps 1e7, seed 0, FP64, MPWOS_PROJ_AUTO,
+ * MPWOS_SAMPLER_FULL. */
 void mpwos_params_default(mpwos_params* p);
 
 /* Create a context on CUDA device `device` (owns device state, tables, a

@@ -680,7 +680,8 @@ static int run_walk(const orc_manifold* m, const orc_problem* pb, const orc_para
 /* s (embedded sphere), or Y with T coordinates and, for the sphere, the norm */
 /* of the rest in one spare coordinate (which keeps |Y| and e.Y exact).       */
 /*   draws of vector v (0: Theta, 1 + l: Z_l) at step k:                      */
-/*     Gaussians: blocks 64 v, 64 v + 1, ... (two per block, orc_gaussians)   */
+/*     Gaussians: blocks 64 v, 64 v + 1, ... (two per block, orc_gaussians);  */
+/*       on a sphere the first is the component along Y's rest, then T's      */
 /*     chi^2:     from block 64 v + 32 (orc_chi2)                             */
 /*     U_l:       block 64 (1 + N_V) + l, u53(words 0, 1)                     */
 /* ------------------------------------------------------------------------- */
@@ -812,14 +813,15 @@ static int run_walk_reduced(const orc_manifold* m, const orc_problem* pb, const 
       orc_gaussians(pr->seed, jv, (uint32_t)k, i, p, ng, g);
       double X = orc_chi2(pr->seed, jv + 32u, (uint32_t)k, i, p, rest);
       double zs = (r * t) / sqrt(dot(g, g, ng) + X);
+      const double* gT = g + (sph ? 1 : 0);   /* sphere: g[0] is the component along Y's rest */
       if (emb) {
-        for (int j = 0; j < D; ++j) z[j] = s[j] + zs * g[j];
+        for (int j = 0; j < D; ++j) z[j] = s[j] + zs * gT[j];
         F += quad_at(&pb->f, m->d, pb->sigma, z);
       } else {
         memcpy(w->Z, w->Y, sizeof(double) * (size_t)n);
-        for (int q = 0; q < nT; ++q) w->Z[T[q]] += zs * g[q];
+        for (int q = 0; q < nT; ++q) w->Z[T[q]] += zs * gT[q];
         if (sph) {
-          double zr = w->Y[spare] + zs * g[nT];
+          double zr = w->Y[spare] + zs * g[0];
           w->Z[spare] = sqrt(zr * zr + zs * zs * X);
         }
         orc_cp(m, w->Z, w->cZ);
@@ -831,15 +833,16 @@ static int run_walk_reduced(const orc_manifold* m, const orc_problem* pb, const 
     orc_gaussians(pr->seed, 0u, (uint32_t)k, i, p, ng, g);
     double X = orc_chi2(pr->seed, 32u, (uint32_t)k, i, p, rest);
     double sc = r / sqrt(dot(g, g, ng) + X);
+    const double* gT = g + (sph ? 1 : 0);
     if (emb) {
-      for (int j = 0; j < D; ++j) th[j] = s[j] + sc * g[j];
+      for (int j = 0; j < D; ++j) th[j] = s[j] + sc * gT[j];
       double tn = sqrt(dot(th, th, D));
       for (int j = 0; j < D; ++j) s[j] = th[j] / tn;
     } else {
       memcpy(w->Th, w->Y, sizeof(double) * (size_t)n);
-      for (int q = 0; q < nT; ++q) w->Th[T[q]] += sc * g[q];
+      for (int q = 0; q < nT; ++q) w->Th[T[q]] += sc * gT[q];
       if (sph) {
-        double tr_ = w->Y[spare] + sc * g[nT];
+        double tr_ = w->Y[spare] + sc * g[0];
         w->Th[spare] = sqrt(tr_ * tr_ + sc * sc * X);
       }
     }

@@ -23,6 +23,7 @@ MPWOS_OK, MPWOS_EINVAL, MPWOS_ENOMEM, MPWOS_ECUDA = 0, 1, 2, 3
 MPWOS_ETIMEDOUT, MPWOS_ECANCELED, MPWOS_EMAXSTEPS, MPWOS_ENOTFOUND, MPWOS_EBUSY = 4, 5, 6, 7, 8
 FP64, FP32 = 0, 1
 PROJ_AUTO, PROJ_TENSOR, PROJ_CUDA = 0, 1, 2
+SAMPLER_FULL, SAMPLER_REDUCED = 0, 1
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -54,7 +55,7 @@ class ProblemDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("eps", C.c_double), ("tau_w", C.c_double), ("theta", C.c_double), ("c_kappa", C.c_double),
                 ("n_v", C.c_int), ("max_steps", C.c_int64), ("seed", C.c_uint64), ("precision", C.c_int),
-                ("projection", C.c_int)]
+                ("projection", C.c_int), ("sampler", C.c_int)]
 
 
 _lib: Optional[C.CDLL] = None
@@ -160,7 +161,7 @@ class _Marshal:
 def make_params(params, precision, projection=PROJ_AUTO) -> Params:
     return Params(eps=params.eps, tau_w=params.tau_w, theta=params.theta, c_kappa=params.c_kappa,
                   n_v=params.n_v, max_steps=params.max_steps, seed=params.seed, precision=precision,
-                  projection=projection)
+                  projection=projection, sampler=getattr(params, "sampler", SAMPLER_FULL))
 
 
 class Context:

@@ -112,6 +112,14 @@ struct DevProblem {
   // shared-memory image (128 KB), and a status word (bit 0: a wait ran out)
   const uint4* tc_bimg;
   unsigned* dev_status;
+  // dimension-reduced exact sampler: tracked coordinates (count, normal on
+  // them), chi^2 degrees of freedom of the rest, per-point start states
+  // (row p: y_T in kMaxQuadDim slots, then |y_rest|; host-made from the points)
+  int reduced;
+  int red_nT, red_rest;
+  double red_e[kMaxQuadDim];
+  float red_ef[kMaxQuadDim];
+  const double* red_y0;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {

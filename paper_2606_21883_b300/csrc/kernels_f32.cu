@@ -5,6 +5,7 @@
 #include "walk3.cuh"
 #include "walkn.cuh"
 #include "embed_tc.cuh"
+#include "walkr.cuh"
 
 namespace mpwos {
 
@@ -81,6 +82,38 @@ cudaError_t launch_tc_project(const uint4* bimg, const float* G, int64_t rows, i
   if (e != cudaSuccess) return e;
   void* args[] = {&bimg, &G, &rows, &n, &out, &gg, &status};
   return cudaLaunchKernel(fn, dim3(grid), dim3(tc::kThreads), args, tc::kSmemBytes, st);
+}
+
+static const void* walkr32_fn(const DevProblem& pb) {
+  const int nt = walkr_nt(pb.red_nT);
+#define MPWOS_WALKR(MK)                                                              \
+  switch (nt) {                                                                      \
+    case 4: return reinterpret_cast<const void*>(walkr_kernel<float, MK, 4>);        \
+    case 8: return reinterpret_cast<const void*>(walkr_kernel<float, MK, 8>);        \
+    case 16: return reinterpret_cast<const void*>(walkr_kernel<float, MK, 16>);      \
+    case 24: return reinterpret_cast<const void*>(walkr_kernel<float, MK, 24>);      \
+    default: return reinterpret_cast<const void*>(walkr_kernel<float, MK, 32>);      \
+  }
+  if (pb.mkind == kEuclid) { MPWOS_WALKR(kEuclid) }
+  if (pb.mkind == kSphere) { MPWOS_WALKR(kSphere) }
+  MPWOS_WALKR(kEmbeddedSphere)
+#undef MPWOS_WALKR
+}
+
+cudaError_t launch_walkr_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere) return cudaErrorInvalidValue;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(walkr32_fn(pb), dim3(grid), dim3(block), args, 0, st);
+}
+
+int occupancy_walkr_f64(const DevProblem& pb, int block);
+
+int occupancy_walkr(const DevProblem& pb, bool fp64, int block) {
+  if (fp64) return occupancy_walkr_f64(pb, block);
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walkr32_fn(pb), block, 0);
+  return nb < 1 ? 1 : nb;
 }
 
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {

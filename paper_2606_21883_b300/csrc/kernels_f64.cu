@@ -5,6 +5,7 @@
 #include "walk3.cuh"
 #include "walkn.cuh"
 #include "cloud.cuh"
+#include "walkr.cuh"
 
 namespace mpwos {
 
@@ -183,6 +184,65 @@ cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStre
   DevProblem arg = pb;
   void* args[] = {&arg};
   return cudaLaunchKernel(walkn_f64_fn(pb), dim3(grid), dim3(block), args, 0, st);
+}
+
+template <typename T>
+static const void* walkr_fn(const DevProblem& pb) {
+  const int nt = walkr_nt(pb.red_nT);
+#define MPWOS_WALKR(MK)                                                              \
+  switch (nt) {                                                                      \
+    case 4: return reinterpret_cast<const void*>(walkr_kernel<T, MK, 4>);            \
+    case 8: return reinterpret_cast<const void*>(walkr_kernel<T, MK, 8>);            \
+    case 16: return reinterpret_cast<const void*>(walkr_kernel<T, MK, 16>);          \
+    case 24: return reinterpret_cast<const void*>(walkr_kernel<T, MK, 24>);          \
+    default: return reinterpret_cast<const void*>(walkr_kernel<T, MK, 32>);          \
+  }
+  if (pb.mkind == kEuclid) { MPWOS_WALKR(kEuclid) }
+  if (pb.mkind == kSphere) { MPWOS_WALKR(kSphere) }
+  MPWOS_WALKR(kEmbeddedSphere)
+#undef MPWOS_WALKR
+}
+
+cudaError_t launch_walkr_f64(const DevProblem& pb, int grid, int block, cudaStream_t st) {
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere) return cudaErrorInvalidValue;
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(walkr_fn<double>(pb), dim3(grid), dim3(block), args, 0, st);
+}
+
+// Per point: y_T and rho = sqrt(|y|^2 - |y_T|^2) (sphere) of the reduced state,
+// row p of red_y0 = [y_T (kMaxQuadDim slots), rho].
+__global__ void reduced_start_kernel(const double* pts, int n, const int* T, int nT, int64_t P, int sphere,
+                                     double* out) {
+  const int64_t p = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (p >= P) return;
+  const double* y = pts + static_cast<size_t>(p) * n;
+  double* o = out + static_cast<size_t>(p) * (kMaxQuadDim + 1);
+  double tt = 0.0;
+  for (int q = 0; q < kMaxQuadDim; ++q) {
+    const double v = q < nT ? y[T[q]] : 0.0;
+    o[q] = v;
+    tt += v * v;
+  }
+  double rho = 0.0;
+  if (sphere) {
+    double yy = 0.0;
+    for (int q = 0; q < n; ++q) yy += y[q] * y[q];
+    rho = sqrt(yy - tt > 0.0 ? yy - tt : 0.0);
+  }
+  o[kMaxQuadDim] = rho;
+}
+
+cudaError_t launch_reduced_start(const double* pts, int n, const int* T, int nT, int64_t P, int sphere, double* out,
+                                 cudaStream_t st) {
+  reduced_start_kernel<<<static_cast<unsigned>((P + 127) / 128), 128, 0, st>>>(pts, n, T, nT, P, sphere, out);
+  return cudaGetLastError();
+}
+
+int occupancy_walkr_f64(const DevProblem& pb, int block) {
+  int nb = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walkr_fn<double>(pb), block, 0);
+  return nb < 1 ? 1 : nb;
 }
 
 int occupancy_walk_f64(const DevProblem& pb, bool n3, int block) {

@@ -19,6 +19,13 @@ size_t embed_tc_bimg_bytes();
 // out (rows x 32) = G Q through the walk's tensor-core contraction, gg = |G_row|^2.
 cudaError_t launch_tc_project(const uint4* bimg, const float* G, int64_t rows, int n, float* out, float* gg,
                               unsigned* status, int grid, cudaStream_t st);
+// Walks with the dimension-reduced sampler, one thread per walker.
+cudaError_t launch_walkr_f64(const DevProblem& pb, int grid, int block, cudaStream_t st);
+cudaError_t launch_walkr_f32(const DevProblem& pb, int grid, int block, cudaStream_t st);
+int occupancy_walkr(const DevProblem& pb, bool fp64, int block);
+// Reduced start states (y_T, |y_rest|) of the query points.
+cudaError_t launch_reduced_start(const double* pts, int n, const int* T, int nT, int64_t P, int sphere, double* out,
+                                 cudaStream_t st);
 // Resident blocks per SM of the walk kernel chosen for pb.
 int occupancy_walk_f64(const DevProblem& pb, bool n3, int block);
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block);

@@ -129,6 +129,29 @@ struct Scratch {
   }
 };
 
+// Coordinates the reduced sampler tracks on SPHERE / EUCLID: the variables of f
+// (and g) and the support of the boundary normal, ascending; -1 if more than
+// kMaxQuadDim or the data are not POLY.
+int tracked_set(const mpwos_manifold_desc* m, const mpwos_problem* pr, int* T) {
+  if (pr->f.kind != MPWOS_FUNC_POLY || (!pr->closed && pr->g.kind != MPWOS_FUNC_POLY)) return -1;
+  std::vector<char> used(static_cast<size_t>(m->n), 0);
+  for (const mpwos_func* f : {&pr->f, &pr->g}) {
+    if (f == &pr->g && pr->closed) continue;
+    const int nf = f->n_terms ? f->term_off[f->n_terms] : 0;
+    for (int q = 0; q < nf; ++q) used[f->var[q]] = 1;
+  }
+  if (!pr->closed)
+    for (int q = 0; q < m->n; ++q)
+      if (pr->bnd_normal[q] != 0.0) used[q] = 1;
+  int nT = 0;
+  for (int q = 0; q < m->n; ++q)
+    if (used[q]) {
+      if (nT == kMaxQuadDim) return -1;
+      T[nT++] = q;
+    }
+  return nT;
+}
+
 int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* pr, const mpwos_params* pa,
              int64_t P, int64_t N) {
   if (!m || !pr || !pa) return fail(ctx, MPWOS_EINVAL, "null manifold, problem or params");
@@ -216,6 +239,19 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
   }
   if (m->kind == MPWOS_EMBEDDED_SPHERE && pr->f.kind != MPWOS_FUNC_SPHERE_QUAD)
     return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE source must be SPHERE_QUAD");
+  if (pa->sampler != MPWOS_SAMPLER_FULL && pa->sampler != MPWOS_SAMPLER_REDUCED)
+    return fail(ctx, MPWOS_EINVAL, "unknown sampler %d", pa->sampler);
+  if (pa->sampler == MPWOS_SAMPLER_REDUCED) {
+    if (m->kind == MPWOS_EUCLID || m->kind == MPWOS_SPHERE) {
+      if (m->n <= 3) return fail(ctx, MPWOS_EINVAL, "the reduced sampler needs n > 3 on SPHERE / EUCLID");
+      int T[kMaxQuadDim];
+      const int nT = tracked_set(m, pr, T);
+      if (nT < 0) return fail(ctx, MPWOS_EINVAL, "the reduced sampler needs POLY data reading at most %d coordinates", kMaxQuadDim);
+      if (m->kind == MPWOS_SPHERE && nT >= m->n) return fail(ctx, MPWOS_EINVAL, "the reduced sampler needs a coordinate outside the tracked set");
+    } else if (m->kind != MPWOS_EMBEDDED_SPHERE) {
+      return fail(ctx, MPWOS_EINVAL, "the reduced sampler supports SPHERE, EUCLID and EMBEDDED_SPHERE");
+    }
+  }
   return MPWOS_OK;
 }
 
@@ -530,7 +566,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
       CK(launch_intrinsic_start(pb.pts, qtd, bd, n, npad, D, P, s0, sc.stream));
       ctx->launches++;
     }
-    const bool tc = pa->precision == MPWOS_FP32 &&
+    const bool tc = pa->precision == MPWOS_FP32 && pa->sampler == MPWOS_SAMPLER_FULL &&
                     (pa->projection == MPWOS_PROJ_TENSOR || (pa->projection == MPWOS_PROJ_AUTO && n >= 128));
     if (tc) {
       std::vector<uint16_t> img;
@@ -539,6 +575,38 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
       pb.dev_status = sc.alloc<unsigned>(1);
       if (!pb.tc_bimg || !pb.dev_status) return fail(ctx, MPWOS_ENOMEM, "tensor-core operand image");
       CK(cudaMemsetAsync(pb.dev_status, 0, sizeof(unsigned), sc.stream));
+    }
+  }
+  // reduced sampler: tracked coordinates, remapped POLY variables, start states
+  if (pa->sampler == MPWOS_SAMPLER_REDUCED) {
+    pb.reduced = 1;
+    if (m->kind == MPWOS_EMBEDDED_SPHERE) {
+      pb.red_nT = D;
+      pb.red_rest = n - D;
+    } else {
+      int T[kMaxQuadDim];
+      const int nT = tracked_set(m, pr, T);
+      std::vector<int> pos(static_cast<size_t>(n), -1);
+      for (int q = 0; q < nT; ++q) pos[T[q]] = q;
+      for (DevFunc* df : {&pb.f, &pb.g}) {
+        if (df->kind != kPoly) continue;
+        const int nf = df->term_off[df->n_terms];
+        for (int q = 0; q < nf; ++q) df->var[q] = static_cast<int16_t>(pos[df->var[q]]);
+      }
+      pb.red_nT = nT;
+      pb.red_rest = (m->kind == MPWOS_SPHERE) ? n - nT - 1 : n - nT;
+      for (int q = 0; q < nT; ++q) {
+        pb.red_e[q] = pr->closed ? 0.0 : pr->bnd_normal[T[q]];
+        pb.red_ef[q] = static_cast<float>(pb.red_e[q]);
+      }
+      int* dT = sc.upload(T, static_cast<size_t>(nT > 0 ? nT : 1));
+      double* y0 = sc.alloc<double>(static_cast<size_t>(P > 0 ? P : 1) * (kMaxQuadDim + 1));
+      if (!dT || !y0) return fail(ctx, MPWOS_ENOMEM, "reduced start states");
+      if (P) {
+        CK(launch_reduced_start(pb.pts, n, dT, nT, P, m->kind == MPWOS_SPHERE, y0, sc.stream));
+        ctx->launches++;
+      }
+      pb.red_y0 = y0;
     }
   }
   // point cloud grid; rho_geo varies with h(y)
@@ -592,6 +660,19 @@ int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tabc)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
+  if (pb.reduced) {
+    const int blk = 128;
+    int64_t grid = static_cast<int64_t>(ctx->sm_count) * occupancy_walkr(pb, fp64, blk);
+    const int64_t need = (pb.wk_w1 - pb.wk_w0 + blk - 1) / blk;
+    if (max_grid < 0) grid = std::max<int64_t>(ctx->sm_count, grid / (-max_grid));
+    if (max_grid > 0 && grid > max_grid) grid = max_grid;
+    if (grid > need) grid = need;
+    const cudaError_t e = fp64 ? launch_walkr_f64(pb, static_cast<int>(grid), blk, st)
+                               : launch_walkr_f32(pb, static_cast<int>(grid), blk, st);
+    if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "reduced walk launch: %s", cudaGetErrorString(e));
+    ctx->launches++;
+    return MPWOS_OK;
+  }
   if (pb.tc_bimg && !fp64) {
     // one persistent CTA per SM (or a share of them), 128 walkers per tile
     const int64_t tiles = (pb.wk_w1 - pb.wk_w0 + 127) / 128;
@@ -636,6 +717,7 @@ void mpwos_params_default(mpwos_params* p) {
   p->seed = 0;
   p->precision = MPWOS_FP64;
   p->projection = MPWOS_PROJ_AUTO;
+  p->sampler = MPWOS_SAMPLER_FULL;
 }
 
 int mpwos_create(int device, mpwos_ctx** out) {
@@ -919,6 +1001,8 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   if (rc) return rc;
   if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD)
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE and POINT_CLOUD are not supported (use mpwos_solve)");
+  if (prm->sampler != MPWOS_SAMPLER_FULL)
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: the reduced sampler is not supported (use mpwos_solve)");
   if (P > 0 && (!is_device_ptr(pts) || !is_device_ptr(mean) || !is_device_ptr(stderr_) || !is_device_ptr(mean_steps)))
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: pts and the three outputs must be device pointers");
   const int64_t walks = P * N;
