@@ -108,8 +108,9 @@ def _serving_mix(rng, n_req, cloud_w):
 
     Points log-uniform in [1, P_max], budget log-uniform in [256, 65536], target
     standard error log-uniform in [1e-3, 1e-2].  P_max: 4096 on the torus, 64
-    on the S^2 cap and the point cloud, 8 on S^999 (thousands of steps per
-    walk), 1 on S^20 in R^1000 (226,786 steps per walk; budget 256)."""
+    on the S^2 cap, the point cloud and S^999 (thousands of steps per walk;
+    budget <= 4096), 4 on S^20 in R^1000 (226,786 steps per walk; budget
+    <= 1024); S^999 and S^20 use the dimension-reduced sampler."""
     import math as _m
     out = []
     kinds = ["torus", "cap", "cloud", "s999", "s20"]
@@ -129,11 +130,13 @@ def _serving_mix(rng, n_req, cloud_w):
             w = W.Workload("cloud", cloud_w.problem, cloud_w.problem.manifold.cloud[idx].copy(), 1,
                            cloud_w.params, np.ones(P), "f32")
         elif kind == "s999":
-            w = W.hypersphere_half(P=lo(1, 8), walks=1, seed=seed)
+            w = W.hypersphere_half(P=lo(1, 64), walks=1, seed=seed)
+            w.params.sampler = W.SAMPLER_REDUCED
             budget = min(budget, 4096)
         else:
-            w = W.embedded_s20(P=1, walks=1, seed=seed % 7)
-            budget, target = 256, 0.0
+            w = W.embedded_s20(P=lo(1, 4), walks=1, seed=seed % 7)
+            w.params.sampler = W.SAMPLER_REDUCED
+            budget = min(budget, 1024)
         out.append((kind, w, budget, target))
     return out
 
@@ -177,8 +180,41 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7):
             "mean_ms": 1e3 * float(lat.mean()), "requests": int(len(lat)), "arrival_rate_hz": rate,
             "capacity_hz": cap_rate, "walk_steps_per_s": steps / T, "mix": kinds,
             "recipe": "Poisson arrivals at 0.7 x capacity (capacity from a burst of 24); points log-uniform "
-                      "(torus <=4096, cap/cloud <=64, S^999 <=8, S^20 1), budget log-uniform 256-65536, "
-                      "target stderr log-uniform 1e-3-1e-2, FP32 walks"}
+                      "(torus <=4096, cap/cloud/S^999 <=64, S^20 <=4), budget log-uniform 256-65536 (S^999 <=4096, "
+                      "S^20 <=1024), target stderr log-uniform 1e-3-1e-2, FP32 walks, reduced sampler on S^999/S^20"}
+
+
+def secondary_leg(M, ctx):
+    """Short runs of the other configurations (not the headline metric): each is
+    one mpwos_solve timed by wall clock around device synchronisation, after a
+    warm call that builds its tables."""
+    import torch
+    cases = [
+        ("s999_half_reduced_fp32", lambda: W.hypersphere_half(P=16384, walks=1), 64, M.FP32, W.SAMPLER_REDUCED,
+         "S^999 in R^1000, x_1 > 0, 16384 pts x 64 walks to completion, dimension-reduced sampler, FP32"),
+        ("s20_in_r1000_reduced_fp32", lambda: W.embedded_s20(P=4096, walks=1), 16, M.FP32, W.SAMPLER_REDUCED,
+         "S^20 in R^1000, 4096 pts x 16 walks of 226,786 steps, dimension-reduced sampler, FP32"),
+        ("s2_cap_fp64", lambda: W.sphere_cap(P=64, walks=1), 1000, M.FP64, W.SAMPLER_FULL,
+         "S^2 cap, 64 pts x 1000 walks, FP64 (per-walk parity mode)"),
+    ]
+    out = {}
+    for name, make, N, prec, sampler, desc in cases:
+        w = make()
+        w.params.sampler = sampler
+        P = len(w.points)
+        pts = torch.tensor(w.points, dtype=torch.float64, device="cuda")
+        outs = tuple(torch.zeros(P, dtype=torch.float64, device="cuda") for _ in range(3))
+        ctx.solve(w.problem, w.params, pts[:8], 4, precision=prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.solve(w.problem, w.params, pts, N, precision=prec, out=outs)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        mean, ms = outs[0].cpu().numpy(), outs[2].cpu().numpy()
+        out[name] = {"workload": desc, "walk_steps_per_s": float(ms.sum() * N) / dt, "query_pts_per_s": P / dt,
+                     "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))), "seconds": dt,
+                     "mean_steps_per_walk": float(ms.mean())}
+    return out
 
 
 def cpu_baseline(target_s: float = 15.0):
@@ -219,6 +255,26 @@ def run_reference(args):
     return 0
 
 
+def rank_workload(points, walks, rank):
+    """Weak scaling: every rank solves its own batch of the torus workload (seed = rank)."""
+    return W.torus_closed(P=points, walks=walks, seed=rank)
+
+
+def max_over_ranks(dist, device, *values):
+    """The max of each value over all ranks (the timed region's slowest rank)."""
+    if dist is None:
+        return tuple(float(v) for v in values)
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return tuple(float(v) for v in t.tolist())
+
+
+def aggregate_rate(steps_per_rank_step, steps, world, tmax):
+    """Whole-job walk-steps/s: the units all ranks processed over the slowest rank's time."""
+    return steps_per_rank_step * steps * world / tmax
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -246,7 +302,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # weak scaling: every rank solves its own 4096-point batch (seed = rank)
-    w = W.torus_closed(P=args.points, walks=args.walks, seed=rank)
+    w = rank_workload(args.points, args.walks, rank)
     ctx = M.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
@@ -308,14 +364,8 @@ def main():
     clocks = sampler.stop()
 
     steps_per_solve = float(msteps.sum() * N)
-    tmax = t_dev
-    e2e_mean = float(np.mean(e2e_t))
-    if dist:
-        tt = torch.tensor([t_dev, e2e_mean], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tmax, e2e_mean = float(tt[0]), float(tt[1])
-    total_steps = steps_per_solve * args.steps * world
-    value = total_steps / tmax
+    tmax, e2e_mean = max_over_ranks(dist, "cuda", t_dev, float(np.mean(e2e_t)))
+    value = aggregate_rate(steps_per_solve, args.steps, world, tmax)
     rmse = float(np.sqrt(np.mean((mean - w.exact) ** 2)))
 
     if rank == 0:
@@ -346,6 +396,7 @@ def main():
         }
         if not args.no_serving and world == 1:
             line["serving"] = serving_leg(M, ctx)
+            line["secondary"] = secondary_leg(M, ctx)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)
