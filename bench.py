@@ -217,7 +217,7 @@ def secondary_leg(M, ctx):
     return out
 
 
-def cpu_baseline(target_s: float = 15.0):
+def cpu_baseline(target_s: float = 25.0):
     """The CPU oracle, as it stands, on a bounded sample of the torus workload."""
     import oracle as O
     w = W.torus_closed(P=64, walks=1)

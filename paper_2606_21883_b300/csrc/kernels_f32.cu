@@ -17,7 +17,16 @@ static const void* walk3_f32_fn(const DevProblem& pb) {
     case kSphere:
       return pb.closed ? reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, true>)
                        : reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, false>);
-    case kTorus: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true>);   // closed only
+    case kTorus: {   // closed only
+      const int mq = (pb.n_v == 1 && pb.f.kind == kTorusFourier) ? pb.f.single_mq : -1;
+      switch (mq) {
+#define MPWOS_MQ(c) case c: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true, c>);
+        MPWOS_MQ(0) MPWOS_MQ(1) MPWOS_MQ(2) MPWOS_MQ(3) MPWOS_MQ(4) MPWOS_MQ(5) MPWOS_MQ(6) MPWOS_MQ(7)
+        MPWOS_MQ(8) MPWOS_MQ(9) MPWOS_MQ(10) MPWOS_MQ(11) MPWOS_MQ(12) MPWOS_MQ(13) MPWOS_MQ(14) MPWOS_MQ(15)
+#undef MPWOS_MQ
+        default: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true>);
+      }
+    }
     case kPointCloud:
       return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 8>)
            : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 16>)

@@ -302,6 +302,7 @@ int table_rows(int n) { return n <= 8 ? kTableNA : 17; }
 
 void copy_func(const mpwos_func& f, DevFunc& d) {
   std::memset(&d, 0, sizeof d);
+  d.single_mq = -1;
   d.kind = f.kind;
   d.apply_op = f.apply_op;
   d.n_terms = f.n_terms;
@@ -327,6 +328,7 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
       d.mode_f[t][2] = m * m;
       d.mode_f[t][3] = qq * qq;
     }
+    if (f.n_terms == 1 && f.modes[0] <= 3 && f.modes[1] <= 3) d.single_mq = 4 * f.modes[0] + f.modes[1];
   }
 }
 

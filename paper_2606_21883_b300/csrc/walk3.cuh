@@ -245,6 +245,27 @@ __device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevF
   return total;
 }
 
+// The single torus Fourier term with compile-time mode numbers M, Q (the
+// launch picks the instance once; the angle multiples become straight-line
+// code): the same value as torus_series32 for that term.
+template <int M, int Q>
+__device__ __forceinline__ float torus_term32(const DevProblem& pb, const DevFunc& fn, float ct, float st, float cph,
+                                              float sph) {
+  float cm, sm, cq, sq;
+  angle_multiple(M, ct, st, cm, sm);
+  angle_multiple(Q, cph, sph, cq, sq);
+  const bool tcos = fn.modes[0][2] == 0;
+  const float Tv = tcos ? cm : sm;
+  const float Pv = fn.modes[0][3] == 0 ? cq : sq;
+  if (!fn.apply_op) return fn.coef_f[0] * (Tv * Pv);
+  const float ia = pb.sf.inv_a;
+  const float irr = __fdividef(1.0f, pb.sf.R + pb.sf.a * ct);
+  const float Tp = tcos ? -static_cast<float>(M) * sm : static_cast<float>(M) * cm;
+  const float lap = static_cast<float>(M * M) * Tv * (ia * ia) + st * Tp * (ia * irr) +
+                    static_cast<float>(Q * Q) * Tv * (irr * irr);
+  return fn.coef_f[0] * (Pv * (lap + pb.sf.sigma * Tv));
+}
+
 // cp(x) in FP32 with reciprocal square roots.
 template <int MK>
 __device__ __forceinline__ void cp3_f32(const DevProblem& pb, const float* x, float* out) {
@@ -469,8 +490,9 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
 }
 
 // One FP32 step of a constant-radius walk with N_V = 1: the draws of step kk,
-// Theta and Z from Y, F = f(cp(Z)) (returned), then Y = cp(Theta).
-template <int MK>
+// Theta and Z from Y, F = f(cp(Z)) (returned), then Y = cp(Theta).  MQ >= 0:
+// the torus source is one Fourier term with modes (MQ / 4, MQ % 4).
+template <int MK, int MQ>
 __device__ __forceinline__ float fixed_step32(const DevProblem& pb, const PhiloxKeys& K, const PhiloxWalk& pw,
                                               uint32_t kk, float r, float a, float (&Y)[3]) {
   U4 b0, b1;
@@ -489,7 +511,14 @@ __device__ __forceinline__ float fixed_step32(const DevProblem& pb, const Philox
     Z[q] = Y[q] + zs * z[q];
     Th[q] = Y[q] + sc * g[q];
   }
-  const float F = source_at32<MK, 1>(pb, Z);
+  float F;
+  if constexpr (MK == kTorus && MQ >= 0) {
+    float ct, st, cph, sph;
+    torus_angles32(pb.sf.R, Z, ct, st, cph, sph);
+    F = torus_term32<MQ / 4, MQ % 4>(pb, pb.f, ct, st, cph, sph);
+  } else {
+    F = source_at32<MK, 1>(pb, Z);
+  }
   cp3_f32<MK>(pb, Th, Y);
   return F;
 }
@@ -499,9 +528,10 @@ __device__ __forceinline__ float fixed_step32(const DevProblem& pb, const Philox
 // omega = omega c^k and the same stopping index.  Each thread advances NW walks
 // in lockstep (NW independent dependency chains per warp; V and the loop are
 // shared), adding V F_k to each walk's S with one TwoSum whose low parts
-// accumulate unnormalised (renormalised every 64 steps, |S.lo| < 64 ulp(S.hi)).
+// accumulate unnormalised (renormalised after every block of 64 steps,
+// |S.lo| < 64 ulp(S.hi)).
 // V *= c runs without renormalisation (|V.lo| stays within a few ulp of V.hi).
-template <int MK, int NW>
+template <int MK, int NW, int MQ>
 __device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
   const int64_t total = pb.wk_w1;
   const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -553,21 +583,25 @@ __device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
       pw[j] = philox_walk(id.i, id.p, K);
     }
     F2 V = om2;
-    for (int k = 0; k < k_stop; ++k) {
+    for (int k0 = 0; k0 < k_stop; k0 += 64) {   // blocks of 64 steps, S renormalised after each
+      const int k1 = k0 + 64 < k_stop ? k0 + 64 : k_stop;
+      for (int k = k0; k < k1; ++k) {
 #pragma unroll
-      for (int j = 0; j < NW; ++j) {
-        const float F = fixed_step32<MK>(pb, K, pw[j], static_cast<uint32_t>(k), r, a, Y[j]);
-        // S += V F: the product's error term and the TwoSum error join S.lo
-        const float ph = __fmul_rn(V.hi, F);
-        const float pl = __fmaf_rn(V.lo, F, __fmaf_rn(V.hi, F, -ph));
-        const float sh = __fadd_rn(S[j].hi, ph);
-        const float bb = __fadd_rn(sh, -S[j].hi);
-        const float err = __fadd_rn(__fadd_rn(S[j].hi, -__fadd_rn(sh, -bb)), __fadd_rn(ph, -bb));
-        S[j] = F2{sh, __fadd_rn(S[j].lo, __fadd_rn(err, pl))};
-        if ((k & 63) == 63) S[j] = f2_fast_two_sum(S[j].hi, S[j].lo);
+        for (int j = 0; j < NW; ++j) {
+          const float F = fixed_step32<MK, MQ>(pb, K, pw[j], static_cast<uint32_t>(k), r, a, Y[j]);
+          // S += V F: the product's error term and the TwoSum error join S.lo
+          const float ph = __fmul_rn(V.hi, F);
+          const float pl = __fmaf_rn(V.lo, F, __fmaf_rn(V.hi, F, -ph));
+          const float sh = __fadd_rn(S[j].hi, ph);
+          const float bb = __fadd_rn(sh, -S[j].hi);
+          const float err = __fadd_rn(__fadd_rn(S[j].hi, -__fadd_rn(sh, -bb)), __fadd_rn(ph, -bb));
+          S[j] = F2{sh, __fadd_rn(S[j].lo, __fadd_rn(err, pl))};
+        }
+        const float vh = __fmul_rn(V.hi, c2.hi);
+        V = F2{vh, __fmaf_rn(V.lo, c2.hi, __fmaf_rn(V.hi, c2.lo, __fmaf_rn(V.hi, c2.hi, -vh)))};
       }
-      const float vh = __fmul_rn(V.hi, c2.hi);
-      V = F2{vh, __fmaf_rn(V.lo, c2.hi, __fmaf_rn(V.hi, c2.lo, __fmaf_rn(V.hi, c2.hi, -vh)))};
+#pragma unroll
+      for (int j = 0; j < NW; ++j) S[j] = f2_fast_two_sum(S[j].hi, S[j].lo);
     }
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
@@ -582,12 +616,14 @@ __device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
 // Entry points: the analytic manifolds run 256-thread blocks; the
 // fixed-radius loop fits 48 registers (5 blocks, 40 warps per SM: measured
 // fastest on B300), the general loop 64 (4 blocks); the point-cloud walk uses
-// 128-thread blocks with a larger register budget.
-template <int MK, int KM, bool FIXED>
+// 128-thread blocks with a larger register budget.  MQ >= 0 (torus, one
+// Fourier term with modes m = MQ / 4, q = MQ % 4, N_V = 1): the host launches
+// the instance with those modes built in.
+template <int MK, int KM, bool FIXED, int MQ = -1>
 __global__ void __launch_bounds__(256, FIXED ? 5 : 4) walk3_f32_kernel(const DevProblem pb) {
   if constexpr (FIXED) {
     if (pb.n_v == 1) {
-      walk3_fixed_body<MK, 1>(pb);
+      walk3_fixed_body<MK, 1, MQ>(pb);
       return;
     }
   }
