@@ -4,6 +4,8 @@
     python -m paper_2606_21883_b300.profile_cases s20_tc    # embed_tc_kernel (tensor cores)
     python -m paper_2606_21883_b300.profile_cases s20_cuda  # walkn_f32_kernel<embedded> (CUDA cores)
     python -m paper_2606_21883_b300.profile_cases s999      # walkn_f32_kernel<sphere>
+    python -m paper_2606_21883_b300.profile_cases s999_red  # walkr_kernel<float, sphere> (reduced sampler)
+    python -m paper_2606_21883_b300.profile_cases s20_red   # walkr_kernel<float, embedded> (reduced sampler)
 
 Each case runs `--reps` walk launches into device buffers (the first one
 warms tables and caches) and prints one line with the walk-steps and the
@@ -33,12 +35,21 @@ def _case(name):
         w = W.hypersphere_half(P=148, walks=1)
         w.params.max_steps = 16
         return w, 128, {}
+    if name == "s999_red":   # S^999 half to completion (~4900 steps per walk), reduced sampler
+        w = W.hypersphere_half(P=2048, walks=1)
+        w.params.sampler = W.SAMPLER_REDUCED
+        return w, 32, {}
+    if name == "s20_red":   # S^20 in R^1000, reduced sampler, walks capped at 20000 steps
+        w = W.embedded_s20(P=1184, walks=1)
+        w.params.sampler = W.SAMPLER_REDUCED
+        w.params.max_steps = 20000
+        return w, 16, {}
     raise SystemExit(f"unknown case {name}")
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999"])
+    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999", "s999_red", "s20_red"])
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     import torch
