@@ -196,6 +196,10 @@ def secondary_leg(M, ctx):
          "S^20 in R^1000, 4096 pts x 16 walks of 226,786 steps, dimension-reduced sampler, FP32"),
         ("s2_cap_fp64", lambda: W.sphere_cap(P=64, walks=1), 1000, M.FP64, W.SAMPLER_FULL,
          "S^2 cap, 64 pts x 1000 walks, FP64 (per-walk parity mode)"),
+        ("torus_fp64", lambda: W.torus_closed(P=4096, walks=1), 50, M.FP64, W.SAMPLER_FULL,
+         "torus, 4096 pts x 50 walks, FP64 walk (per-walk parity mode)"),
+        ("torus_fp32", lambda: W.torus_closed(P=4096, walks=1), 50, M.FP32, W.SAMPLER_FULL,
+         "torus, 4096 pts x 50 walks, FP32 walk (same walks and RMSE scale as torus_fp64)"),
     ]
     out = {}
     for name, make, N, prec, sampler, desc in cases:
@@ -214,6 +218,7 @@ def secondary_leg(M, ctx):
         out[name] = {"workload": desc, "walk_steps_per_s": float(ms.sum() * N) / dt, "query_pts_per_s": P / dt,
                      "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))), "seconds": dt,
                      "mean_steps_per_walk": float(ms.mean())}
+    out["torus_fp32_over_fp64"] = out["torus_fp32"]["walk_steps_per_s"] / out["torus_fp64"]["walk_steps_per_s"]
     return out
 
 

@@ -21,8 +21,8 @@
 //     (normal) and 64 v + 33 + 2a (U = u53 of words 0, 1); U_l at block
 //     64 (1 + N_V) + l, u53 of words 0, 1.
 //   FP32: normals four per block (u23 words); chi^2 attempt a at block
-//     64 v + 32 + a (normal from words 0, 1, U from word 2); U_l at block
-//     64 (1 + N_V) + l / 4, word l mod 4.
+//     64 v + 32 + a (normal from words 0, 1, U from word 2); U_l = word 3 of
+//     block 64 (1 + l) + 32 (the first chi^2 block of Z_l, drawn anyway).
 // chi^2_m: 0 (m = 0), x^2 (m = 1), else 2 Gamma(m/2) by Marsaglia-Tsang
 // (ACM TOMS 26, 2000) with the exact log acceptance test, at most 16 attempts.
 #pragma once
@@ -100,32 +100,40 @@ __device__ __forceinline__ double red_chi2(const PhiloxKeys& K, uint32_t j0, uin
   return 2.0 * cand;
 }
 
-// FP32: the same test written as d (3 log1p(t) - 3t - 3t^2 - t^3), t = c x
-// (identical to d - d v + d log v for v = (1 + t)^3), which avoids the
-// cancellation of d - d v in single precision.
+// 3 log1p(t) - 3t - 3t^2 - t^3: its Taylor series about 0 for |t| < 1/4
+// (-9/2 t^2 - 3/4 t^4 + 3/5 t^5 - 1/2 t^6 + 3/7 t^7 - 3/8 t^8 + 1/3 t^9 - 3/10 t^10,
+// the t^3 terms cancel; relative error < 3e-7 there), log1pf beyond.
+__device__ __forceinline__ float mt_log_term(float t) {
+  if (fabsf(t) < 0.25f)
+    return t * t *
+           (-4.5f + t * t * (-0.75f + t * (0.6f + t * (-0.5f + t * (0.42857143f + t * (-0.375f + t * (0.33333333f +
+                                                                                                     t * -0.3f)))))));
+  return 3.0f * log1pf(t) - t * (3.0f + t * (3.0f + t));
+}
+
+// FP32: the same acceptance test written as d (3 log1p(t) - 3t - 3t^2 - t^3),
+// t = c x (identical to d - d v + d log v for v = (1 + t)^3), which avoids the
+// cancellation of d - d v in single precision.  `first` is attempt 0's block
+// (j0), which the caller also uses for the radius uniform.
 __device__ __forceinline__ float red_chi2(const PhiloxKeys& K, uint32_t j0, uint32_t kk, uint32_t i, uint32_t p,
-                                          int m, float) {
+                                          int m, const U4& first) {
   if (m <= 0) return 0.0f;
   if (m == 1) {
-    const U4 r = philox4x32_10(j0, kk, i, p, K);
     float x, y;
-    box_muller32(u23(r.x), u23(r.y), x, y);
+    box_muller32(u23(first.x), u23(first.y), x, y);
     return x * x;
   }
   const float d = 0.5f * static_cast<float>(m) - 1.0f / 3.0f, c = rsqrtf(9.0f * d);
   float cand = d;
   for (uint32_t a = 0; a < kChi2Attempts; ++a) {
-    const U4 r = philox4x32_10(j0 + a, kk, i, p, K);
+    const U4 r = a == 0 ? first : philox4x32_10(j0 + a, kk, i, p, K);
     float x, y;
     box_muller32(u23(r.x), u23(r.y), x, y);
     const float t = c * x;
     if (t <= -1.0f) continue;
     const float v = (1.0f + t) * (1.0f + t) * (1.0f + t);
     cand = d * v;
-    const float U = u23(r.z);
-    const float lhs = __logf(U);
-    const float rhs = 0.5f * x * x + d * (3.0f * log1pf(t) - t * (3.0f + t * (3.0f + t)));
-    if (lhs < rhs) return 2.0f * d * v;
+    if (__logf(u23(r.z)) < 0.5f * x * x + d * mt_log_term(t)) return 2.0f * d * v;
   }
   return 2.0f * cand;
 }
@@ -301,21 +309,20 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
     // ---- interior samples Z_l and F_k ----------------------------------------
     T F = T(0);
     for (int l = 0; l < nv; ++l) {
-      T t;
+      const uint32_t jv = 64u * static_cast<uint32_t>(1 + l);
+      T t, X;
       if constexpr (kF64) {
         const U4 bu = philox4x32_10(64u * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l), kk, wi, p, K);
         const double U = u53(bu.x, bu.y);
         const double guess = table_lookup<double>(pb.tab64, pb.NA, pb.NS, pb.z_max, a, U);
         t = green_invert64(law, U, guess);
+        X = red_chi2(K, jv + 32u, kk, wi, p, rest, 0.0);
       } else {
-        const U4 bu = philox4x32_10(64u * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l >> 2), kk, wi, p, K);
-        const int s4 = l & 3;
-        const float U = u23(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
-        t = fminf(fmaxf(table_lookup32(pb, a, U), 0.0f), 1.0f);
+        const U4 c0 = philox4x32_10(jv + 32u, kk, wi, p, K);
+        t = fminf(fmaxf(table_lookup32(pb, a, u23(c0.w)), 0.0f), 1.0f);
+        X = red_chi2(K, jv + 32u, kk, wi, p, rest, c0);
       }
-      const uint32_t jv = 64u * static_cast<uint32_t>(1 + l);
       red_normals<NG>(K, jv, kk, wi, p, ng, g);
-      const T X = red_chi2(K, jv + 32u, kk, wi, p, rest, T(0));
       T gg = X;
 #pragma unroll
       for (int q = 0; q < NG; ++q) gg += g[q] * g[q];
@@ -341,7 +348,12 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
     if (nv > 1) F /= T(nv);
     // ---- Theta = Y + r g/|g|, Y = cp(Theta) ------------------------------------
     red_normals<NG>(K, 0u, kk, wi, p, ng, g);
-    const T X = red_chi2(K, 32u, kk, wi, p, rest, T(0));
+    T X;
+    if constexpr (kF64) {
+      X = red_chi2(K, 32u, kk, wi, p, rest, 0.0);
+    } else {
+      X = red_chi2(K, 32u, kk, wi, p, rest, philox4x32_10(32u, kk, wi, p, K));
+    }
     T gg = X;
 #pragma unroll
     for (int q = 0; q < NG; ++q) gg += g[q] * g[q];
