@@ -46,6 +46,10 @@ UNIT = "walk-steps/s"
 # (-Delta_M + sigma) u for one mode 16, closest point of Theta 13, weight and
 # score in float pairs (S += V F by TwoSum, V *= c) 15, loop 3.
 OPS_PER_STEP = 199
+# DRAM bytes (read + write) of one bench launch of the walk kernel, measured
+# by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the
+# kernel as built now; the profile summary gives the command.
+TRAFFIC_BYTES = 21.42e6 + 603.81e6
 
 
 def _peaks():
@@ -393,7 +397,8 @@ def main():
                     "h2d_bytes_per_step": int(P * 3 * 8), "d2h_bytes_per_step": int(3 * P * 8)},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak_ops, "traffic": None,
+                         "frac": achieved / peak_ops, "traffic": TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
+                         "traffic_source": "profiles/walk3_f32_torus_bench_traffic.md",
                          "kernel": "walk3_f32_kernel<torus>", "kernel_ms": 1e3 * t_kernel,
                          "ops_per_walk_step": OPS_PER_STEP,
                          "peak_source": f"148 SM x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz ({src} max clock)"},
