@@ -348,3 +348,35 @@ def point_cloud(P: int = 256, walks: int = 1000, N_cloud: int = 200_000, k_nn: i
     prob = Problem(man, sigma=sigma, closed=True, f=Func.const(sigma), g=Func.const(0.0))
     idx = _rng(seed + 7).choice(N_cloud, size=P, replace=False)
     return Workload("point_cloud", prob, cloud[idx].copy(), walks, Params(), np.ones(P), "f32")
+
+
+# ----------------------------------------------------------------------------
+# Example 4: the unit sphere given only by a point cloud
+# ----------------------------------------------------------------------------
+
+def _legendre_poly_in_z(coef_by_degree: Sequence[float]) -> List[Tuple[float, List[Tuple[int, int]]]]:
+    """sum_l c_l P_l(x_3) as monomial terms in x_3 (index 2)."""
+    mono = np.polynomial.legendre.leg2poly(np.asarray(coef_by_degree, dtype=np.float64))
+    return [(float(c), [(2, p)] if p else []) for p, c in enumerate(mono) if c != 0.0]
+
+
+def sphere_cloud_legendre(P: int = 100, walks: int = 2000, N_cloud: int = 8000, k_nn: int = 6, c_h: float = 2.4,
+                          sigma: float = 10.0, seed: int = 0) -> Workload:
+    """Example 4: closed S^2 known only through N_cloud area-uniform points, k_nn = 6, c_h = 2.4,
+    closest point = nearest cloud point, m_* = 0;
+    u = P_1(x_3) + 0.2 P_3(x_3) + 0.1 P_5(x_3), f = sum_l c_l (l(l+1) + sigma) P_l(x_3).
+
+    sigma is not given for this example; 10 keeps a walk near 10^3 steps at tau_W = 1e-8.
+    Query points are P cloud points chosen by seed (the walk only visits cloud points)."""
+    g = _rng(seed)
+    cloud = g.standard_normal((N_cloud, 3))
+    cloud /= np.linalg.norm(cloud, axis=1, keepdims=True)
+    cloud = np.ascontiguousarray(cloud)
+    cu = [0.0, 1.0, 0.0, 0.2, 0.0, 0.1]
+    cf = [c * (l * (l + 1) + sigma) for l, c in enumerate(cu)]
+    man = Manifold(MANIFOLD_POINT_CLOUD, n=3, d=2, cloud=cloud, k_nn=k_nn, c_h=c_h, cp_mode=CLOUD_CP_NEAREST)
+    prob = Problem(man, sigma=sigma, closed=True, f=Func.poly(_legendre_poly_in_z(cf)), g=Func.const(0.0))
+    idx = _rng(seed + 7).choice(N_cloud, size=P, replace=False)
+    pts = cloud[idx].copy()
+    exact = np.polynomial.legendre.legval(pts[:, 2], cu)
+    return Workload("sphere_cloud_e4", prob, pts, walks, Params(), exact, "f32")

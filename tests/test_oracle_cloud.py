@@ -66,3 +66,46 @@ def test_cloud_telescoping(cloud):
     assert not fl.any()
     # closed case, f = sigma: S = 1 - W_K with W_K < tau_W <= W_{K-1}
     assert np.all((S > 1 - 1e-3) & (S <= 1 + 1e-12))
+
+
+# ---------------------------------------------------------------- Example 4
+@pytest.fixture(scope="module")
+def e4():
+    w = W.sphere_cloud_legendre(P=6, walks=1)
+    return w, O.OracleProblem(w.problem, w.params)
+
+
+def test_e4_source_is_the_screened_laplacian_of_u():
+    """f = (-Delta_S + sigma) u on S^2, checked by finite differences of u in the polar angle
+    (u depends on x_3 = cos t only: Delta_S u = u'' + cot t u')."""
+    w = W.sphere_cloud_legendre(P=1, walks=1, N_cloud=100)
+    cu = [0.0, 1.0, 0.0, 0.2, 0.0, 0.1]
+    u = lambda t: np.polynomial.legendre.legval(np.cos(t), cu)
+    op = O.OracleProblem(w.problem, w.params)
+    for t in [0.3, 1.1, 1.9, 2.7]:
+        h = 1e-4
+        d1 = (u(t + h) - u(t - h)) / (2 * h)
+        d2 = (u(t + h) - 2 * u(t) + u(t - h)) / h ** 2
+        x = np.array([np.sin(t), 0.0, np.cos(t)])
+        want = -(d2 + d1 / np.tan(t)) + w.problem.sigma * u(t)
+        assert O.func_eval(op, "f", x) == pytest.approx(want, rel=1e-6, abs=1e-6)
+
+
+def test_e4_nearest_cp_is_the_nearest_cloud_point(e4):
+    w, op = e4
+    cl = w.problem.manifold.cloud
+    tree = cKDTree(cl)
+    rng = np.random.default_rng(3)
+    for _ in range(30):
+        x = cl[rng.integers(len(cl))] + 0.05 * rng.standard_normal(3)
+        _, j = tree.query(x, k=1)
+        assert np.array_equal(O.cp(op, x), cl[j])
+
+
+def test_e4_walk_mean_matches_legendre_solution(e4):
+    """Example 4 at 300 walks per point: mean within 4 standard errors (+0.02 for the bias of the
+    nearest-point projection) of u = P_1 + 0.2 P_3 + 0.1 P_5."""
+    w, _ = e4
+    m, se, ms, nf = O.solve(w.problem, w.params, w.points, 300)
+    assert nf == 0 and np.all(ms > 500)
+    assert np.all(np.abs(m - w.exact) <= 4 * se + 0.02), (m, w.exact, se)
