@@ -467,6 +467,50 @@ double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_p
     double d = fabs(ey - h);
     return (ey <= h) ? 0.0 : d;
   }
+  if (m->kind == ORC_TORUS) {
+    /* a plane through the torus axis (e_3 = 0, h = 0), as in Example 1's cut:
+     * Gamma is the two meridian circles c_b + a (cos t u_b + sin t e_3), with
+     * centres c_b = R u_b, u_0 = (-e_2, e_1, 0), u_1 = -u_0.  The nearest point
+     * of circle b to y is c_b + a w/|w|, w = the part of y - c_b in the
+     * circle's plane span(u_b, e_3); the nearer circle wins (circle 0 on a tie).
+     * The torus normal at y_Gamma is w/|w|. */
+    double best = INFINITY, nrm[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 2; ++b) {
+      double sgn = (b == 0) ? 1.0 : -1.0;
+      double u[3] = {-sgn * e[1], sgn * e[0], 0.0};
+      double c[3] = {m->R * u[0], m->R * u[1], 0.0};
+      double wu = (y[0] - c[0]) * u[0] + (y[1] - c[1]) * u[1];
+      double wz = y[2];
+      double w[3] = {wu * u[0], wu * u[1], wz};
+      double nw = sqrt(wu * wu + wz * wz);
+      double nb[3];
+      if (nw > 0.0) {
+        for (int i = 0; i < 3; ++i) nb[i] = w[i] / nw;
+      } else {   /* y on the circle's axis: every point of the circle is nearest; take t = 0 */
+        for (int i = 0; i < 3; ++i) nb[i] = u[i];
+      }
+      double q[3], d2 = 0.0;
+      for (int i = 0; i < 3; ++i) {
+        q[i] = c[i] + m->a * nb[i];
+        d2 += (q[i] - y[i]) * (q[i] - y[i]);
+      }
+      if (d2 < best) {
+        best = d2;
+        for (int i = 0; i < 3; ++i) { yg[i] = q[i]; nrm[i] = nb[i]; }
+      }
+    }
+    double rn = 0.0;
+    for (int i = 0; i < 3; ++i) rn += (yg[i] - y[i]) * nrm[i];
+    double rt2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      double rti = (yg[i] - y[i]) - rn * nrm[i];
+      rt2 += rti * rti;
+    }
+    if (ey <= h) return 0.0;
+    double ex = fabs(rn) - ell;
+    if (ex < 0.0) ex = 0.0;
+    return sqrt(rt2 + ex * ex);
+  }
   /* unit sphere: y_Gamma = h e + sqrt(1-h^2) w/|w|, w = y - (e.y) e */
   double* w = (double*)malloc(sizeof(double) * (size_t)n);
   for (int i = 0; i < n; ++i) w[i] = y[i] - ey * e[i];
@@ -578,6 +622,99 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
 }
 
 /* ------------------------------------------------------------------------- */
+/* Compensation term (Sec. 2.3.3).  For x near M write x = y + eta n(y), y =   */
+/* cp(x), eta the signed normal distance (n the outward unit normal).  With a  */
+/* predictor u_*,                                                             */
+/*   R_*(s; y) = -Delta(E u_*)(y + s n(y)) + sigma u_*(y) - f(y),             */
+/*   m1 = (R_*(h) - R_*(-h)) / (2h),  m2 = (R_*(h) - 2 R_*(0) + R_*(-h)) / h^2, */
+/*   m_*(x) = eta m1(y) + eta^2 m2(y) / 2,                                     */
+/* and the source of a step becomes f(cp(Z)) + m_*(Z).  E u_* = u_* o cp is   */
+/* constant along normals, so its ambient Laplacian at y + s n(y) is the      */
+/* Laplacian of a function of the tangential coordinates alone:               */
+/*   unit sphere of R^3 (normal coordinate rho = 1 + s):                      */
+/*     -Delta(E u)(rho y) = (-Delta_S u)(y) / rho^2;                          */
+/*   torus (rho = a + s the distance from the centre circle, angles th, ph):  */
+/*     -Delta(E u) = -[u_thth / rho^2 - sin th u_th / (rho (R + rho cos th))  */
+/*                     + u_phph / (R + rho cos th)^2]                         */
+/*   (the Laplacian in the coordinates (rho, th, ph), whose metric is         */
+/*   d rho^2 + rho^2 d th^2 + (R + rho cos th)^2 d ph^2).                     */
+/* ------------------------------------------------------------------------- */
+double orc_normal_coord(const orc_manifold* m, const double* x) {
+  if (m->kind == ORC_TORUS) {
+    double rxy = sqrt(x[0] * x[0] + x[1] * x[1]);
+    double dr = rxy - m->R;
+    return sqrt(dr * dr + x[2] * x[2]) - m->a;
+  }
+  return sqrt(dot(x, x, 3)) - 1.0;   /* unit sphere of R^3 */
+}
+
+/* -Delta(E u_*) at y + s n(y), y on M */
+static double ext_neg_lap(const orc_manifold* m, const orc_func* u, const double* y, double s) {
+  if (m->kind == ORC_TORUS) {
+    double R = m->R;
+    double rxy = sqrt(y[0] * y[0] + y[1] * y[1]);
+    double dr = rxy - R;
+    double nr = sqrt(dr * dr + y[2] * y[2]);
+    double ct = dr / nr, st = y[2] / nr;
+    double th = atan2(y[2], dr), ph = atan2(y[1], y[0]);
+    double utt = 0.0, ut = 0.0, upp = 0.0;
+    for (int t = 0; t < u->n_terms; ++t) {
+      int mm = u->modes[4 * t], q = u->modes[4 * t + 1];
+      int tk = u->modes[4 * t + 2], pk = u->modes[4 * t + 3];
+      double T = trig(tk, mm * th);
+      double Tp = (tk == 0) ? -(double)mm * sin(mm * th) : (double)mm * cos(mm * th);
+      double P = trig(pk, q * ph);
+      utt += u->coef[t] * (-(double)(mm * mm) * T * P);
+      ut += u->coef[t] * (Tp * P);
+      upp += u->coef[t] * (-(double)(q * q) * T * P);
+    }
+    double rho = m->a + s;
+    double rr = R + rho * ct;
+    return -(utt / (rho * rho) - st * ut / (rho * rr) + upp / (rr * rr));
+  }
+  /* unit sphere of R^3, quadratic u = c0 + v.y + y^T A y: the degree-1 part is
+   * an eigenfunction of -Delta_S with eigenvalue 2, the trace-free quadratic
+   * part with eigenvalue 6 (the constant tr(A)/3 with 0) */
+  double ny = sqrt(dot(y, y, 3));
+  double w[3] = {y[0] / ny, y[1] / ny, y[2] / ny};
+  double lin = dot(u->v, w, 3), quad = 0.0, tr = 0.0;
+  for (int i = 0; i < 3; ++i) {
+    tr += u->A[i * 3 + i];
+    for (int j = 0; j < 3; ++j) quad += u->A[i * 3 + j] * w[i] * w[j];
+  }
+  double lam = 2.0 * lin + 6.0 * (quad - tr / 3.0);
+  double rho = 1.0 + s;
+  return lam / (rho * rho);
+}
+
+static double comp_R(const orc_manifold* m, const orc_problem* pb, const double* y, double s, double fy) {
+  return (ext_neg_lap(m, &pb->u_star, y, s) + pb->sigma * orc_func_eval(m, &pb->u_star, pb->sigma, y)) - fy;
+}
+
+/* m_*(x) with y = cp(x) and fy = f(y) already known */
+static double comp_m(const orc_manifold* m, const orc_problem* pb, const double* x, const double* y, double fy) {
+  double eta = orc_normal_coord(m, x);
+  if (pb->comp == ORC_COMP_EXACT) return comp_R(m, pb, y, eta, fy);
+  double h = pb->h_eta;
+  double Rp = comp_R(m, pb, y, h, fy);
+  double R0 = comp_R(m, pb, y, 0.0, fy);
+  double Rm = comp_R(m, pb, y, -h, fy);
+  double m1 = (Rp - Rm) / (2.0 * h);
+  double m2 = (Rp - 2.0 * R0 + Rm) / (h * h);
+  return eta * m1 + 0.5 * eta * eta * m2;
+}
+
+double orc_comp_R(const orc_manifold* m, const orc_problem* pb, const double* y, double s) {
+  return comp_R(m, pb, y, s, orc_func_eval(m, &pb->f, pb->sigma, y));
+}
+
+double orc_comp_m(const orc_manifold* m, const orc_problem* pb, const double* x) {
+  double y[3];
+  orc_cp(m, x, y);
+  return comp_m(m, pb, x, y, orc_func_eval(m, &pb->f, pb->sigma, y));
+}
+
+/* ------------------------------------------------------------------------- */
 /* One walk (Algorithm 1 + eq. path_score_definition).                          */
 /*   blocks of step k: Theta direction [0, nb); Z_l direction                   */
 /*   [nb(1+l), nb(2+l)); U_l at nb(1+N_V) + l;  nb = ceil(n/2).                 */
@@ -647,7 +784,9 @@ static int run_walk(const orc_manifold* m, const orc_problem* pb, const orc_para
       double zs = (r * t) / zn;
       for (int q = 0; q < n; ++q) w->Z[q] = w->Y[q] + zs * w->g[q];
       orc_cp(m, w->Z, w->cZ);
-      F += orc_func_eval(m, &pb->f, pb->sigma, w->cZ);
+      double fz = orc_func_eval(m, &pb->f, pb->sigma, w->cZ);
+      if (pb->comp != ORC_COMP_NONE) fz = fz + comp_m(m, pb, w->Z, w->cZ, fz);   /* f + m_* */
+      F += fz;
     }
     if (pr->n_v > 1) F /= (double)pr->n_v;
     S += (W * omega) * F;
@@ -856,9 +995,23 @@ static int run_walk_reduced(const orc_manifold* m, const orc_problem* pb, const 
   return flag;
 }
 
+/* The forms this oracle implements: a torus boundary is a plane through the
+ * axis; compensation runs on the torus (TORUS_FOURIER predictor) and the unit
+ * sphere of R^3 (SPHERE_QUAD predictor).  Returns -1 for anything else. */
+static int check_problem(const orc_manifold* m, const orc_problem* pb) {
+  if (m->kind == ORC_TORUS && !pb->closed && (pb->bnd_normal[2] != 0.0 || pb->bnd_offset != 0.0)) return -1;
+  if (pb->comp == ORC_COMP_NONE) return 0;
+  if (pb->comp != ORC_COMP_NORMAL2 && pb->comp != ORC_COMP_EXACT) return -1;
+  if ((pb->comp == ORC_COMP_NORMAL2 && !(pb->h_eta > 0.0)) || pb->u_star.apply_op) return -1;
+  if (m->kind == ORC_TORUS && pb->u_star.kind == ORC_TORUS_FOURIER) return 0;
+  if (m->kind == ORC_SPHERE && m->n == 3 && pb->u_star.kind == ORC_SPHERE_QUAD) return 0;
+  return -1;
+}
+
 int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
                     const double* pts, int64_t P, int64_t N, double* S, int64_t* K,
                     int32_t* flags, int n_threads) {
+  if (check_problem(m, pb) != 0) return -1;
 #ifdef _OPENMP
   if (n_threads > 0) omp_set_num_threads(n_threads);
 #endif
@@ -889,7 +1042,10 @@ int orc_solve(const orc_manifold* m, const orc_problem* pb, const orc_params* pr
   double* S = (double*)malloc(sizeof(double) * (size_t)(P * N));
   int64_t* K = (int64_t*)malloc(sizeof(int64_t) * (size_t)(P * N));
   int32_t* fl = (int32_t*)malloc(sizeof(int32_t) * (size_t)(P * N));
-  orc_walk_scores(m, pb, pr, pts, P, N, S, K, fl, n_threads);
+  if (orc_walk_scores(m, pb, pr, pts, P, N, S, K, fl, n_threads) != 0) {
+    free(S); free(K); free(fl);
+    return -1;
+  }
   int64_t nf = 0;
   for (int64_t p = 0; p < P; ++p) {
     double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, ks = 0.0;
@@ -915,6 +1071,7 @@ int orc_solve(const orc_manifold* m, const orc_problem* pb, const orc_params* pr
 int64_t orc_trace(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
                   const double* y0, int64_t p, int64_t i, orc_trace_rec* rec, int64_t cap,
                   double* S_out, int64_t* K_out) {
+  if (check_problem(m, pb) != 0) return -1;
   work_t w;
   work_alloc(&w, m->n);
   int64_t nrec = 0;

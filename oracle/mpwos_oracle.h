@@ -53,12 +53,24 @@ typedef struct {
   const double* A;        /* (d+1)^2 row-major                                 */
 } orc_func;
 
+enum { ORC_COMP_NONE = 0, ORC_COMP_NORMAL2 = 1, ORC_COMP_EXACT = 2 };
+
 typedef struct {
   double sigma;
   int closed;
   const double* bnd_normal;   /* unit normal e of the half-space {e.x > h}  */
   double bnd_offset;          /* h                                          */
   orc_func f, g;
+  /* compensation term (Sec. 2.3.3; m of eq. mismatch_definition):
+   * ORC_COMP_NONE: m_* = 0; ORC_COMP_NORMAL2: the second-order normal
+   * expansion m_* = eta m1 + eta^2 m2 / 2 from central differences of
+   * R_*(s; y) at s = -h_eta, 0, h_eta, with predictor u_star (TORUS_FOURIER
+   * on the torus, SPHERE_QUAD on the unit sphere of R^3; apply_op = 0);
+   * ORC_COMP_EXACT: m_*(x) = R_*(eta(x); y), the mismatch of eq.
+   * mismatch_definition with u_star in place of u (exact when u_star = u). */
+  int comp;
+  orc_func u_star;
+  double h_eta;
 } orc_problem;
 
 enum { ORC_SAMPLER_FULL = 0, ORC_SAMPLER_REDUCED = 1 };
@@ -101,6 +113,11 @@ void   orc_cp(const orc_manifold* m, const double* x, double* out);
 double orc_delta_gamma(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
                        const double* y, double* y_gamma);
 double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, const double* x);
+/* compensation: eta(x) the signed normal distance of x, R_*(s; y) at the
+ * closest point y, and m_*(x) (f evaluated at y = cp(x) inside) */
+double orc_normal_coord(const orc_manifold* m, const double* x);
+double orc_comp_R(const orc_manifold* m, const orc_problem* pb, const double* y, double s);
+double orc_comp_m(const orc_manifold* m, const orc_problem* pb, const double* x);
 /* point cloud: k nearest (by distance^2, then index), mean distance h(x) */
 double orc_cloud_knn(const orc_manifold* m, const double* x, int64_t* idx, double* d2);
 

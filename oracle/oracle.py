@@ -10,7 +10,7 @@ import numpy as np
 from .build import build
 
 __all__ = ["lib", "philox", "u53", "gaussians", "chi2", "tracked_set", "em1", "c_sigma_r", "green_cdf", "green_cdf_inv",
-           "kt_minus_one", "cp", "delta_gamma", "func_eval", "walk_scores", "solve", "trace",
+           "kt_minus_one", "cp", "delta_gamma", "func_eval", "normal_coord", "comp_R", "comp_m", "walk_scores", "solve", "trace",
            "OracleProblem", "cloud_knn"]
 
 _lib: Optional[C.CDLL] = None
@@ -33,7 +33,8 @@ class _Func(C.Structure):
 
 class _Problem(C.Structure):
     _fields_ = [("sigma", C.c_double), ("closed", C.c_int), ("bnd_normal", _dp),
-                ("bnd_offset", C.c_double), ("f", _Func), ("g", _Func)]
+                ("bnd_offset", C.c_double), ("f", _Func), ("g", _Func),
+                ("comp", C.c_int), ("u_star", _Func), ("h_eta", C.c_double)]
 
 
 class _Params(C.Structure):
@@ -70,6 +71,10 @@ def lib() -> C.CDLL:
         L.orc_func_eval.restype = C.c_double
         L.orc_trace.restype = C.c_int64
         L.orc_cloud_knn.restype = C.c_double
+        L.orc_normal_coord.restype = C.c_double
+        L.orc_comp_R.restype = C.c_double
+        L.orc_comp_R.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_double]
+        L.orc_comp_m.restype = C.c_double
         L.orc_chi2.restype = C.c_double
         L.orc_chi2.argtypes = [C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int]
         _lib = L
@@ -109,6 +114,10 @@ class OracleProblem:
             self.prob.bnd_normal = _dptr(self._arr(problem.bnd_normal))
         self.prob.f = self._func(problem.f)
         self.prob.g = self._func(problem.g)
+        if getattr(problem, "comp", 0):
+            self.prob.comp = problem.comp
+            self.prob.u_star = self._func(problem.u_star)
+            self.prob.h_eta = problem.h_eta
         self.n = m.n
         self.set_params(params)
 
@@ -221,8 +230,26 @@ def cloud_knn(op: OracleProblem, x):
 
 def func_eval(op: OracleProblem, which: str, x):
     x = np.ascontiguousarray(x, dtype=np.float64)
-    f = op.prob.f if which == "f" else op.prob.g
+    f = {"f": op.prob.f, "g": op.prob.g, "u_star": op.prob.u_star}[which]
     return lib().orc_func_eval(C.byref(op.man), C.byref(f), C.c_double(op.prob.sigma), _dptr(x))
+
+
+def normal_coord(op: OracleProblem, x):
+    """Signed normal distance eta of x from M (torus, unit sphere of R^3)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_normal_coord(C.byref(op.man), _dptr(x))
+
+
+def comp_R(op: OracleProblem, y, s):
+    """R_*(s; y) of the compensation term at y on M."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return lib().orc_comp_R(C.byref(op.man), C.byref(op.prob), _dptr(y), s)
+
+
+def comp_m(op: OracleProblem, x):
+    """m_*(x), the second-order normal expansion of the compensation term."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_comp_m(C.byref(op.man), C.byref(op.prob), _dptr(x))
 
 
 def walk_scores(problem, params, pts, N, n_threads=0):
@@ -232,9 +259,11 @@ def walk_scores(problem, params, pts, N, n_threads=0):
     S = np.zeros(P * N)
     K = np.zeros(P * N, dtype=np.int64)
     fl = np.zeros(P * N, dtype=np.int32)
-    lib().orc_walk_scores(C.byref(op.man), C.byref(op.prob), C.byref(op.params), _dptr(pts),
-                          C.c_int64(P), C.c_int64(N), _dptr(S), K.ctypes.data_as(C.POINTER(C.c_int64)),
-                          fl.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int(n_threads))
+    rc = lib().orc_walk_scores(C.byref(op.man), C.byref(op.prob), C.byref(op.params), _dptr(pts),
+                               C.c_int64(P), C.c_int64(N), _dptr(S), K.ctypes.data_as(C.POINTER(C.c_int64)),
+                               fl.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int(n_threads))
+    if rc != 0:
+        raise ValueError("the oracle does not implement this problem form")
     return S.reshape(P, N), K.reshape(P, N), fl.reshape(P, N)
 
 
@@ -246,9 +275,11 @@ def solve(problem, params, pts, N, n_threads=0):
     se = np.zeros(P)
     ms = np.zeros(P)
     nf = C.c_int64(0)
-    lib().orc_solve(C.byref(op.man), C.byref(op.prob), C.byref(op.params), _dptr(pts),
-                    C.c_int64(P), C.c_int64(N), _dptr(mean), _dptr(se), _dptr(ms), C.byref(nf),
-                    C.c_int(n_threads))
+    rc = lib().orc_solve(C.byref(op.man), C.byref(op.prob), C.byref(op.params), _dptr(pts),
+                         C.c_int64(P), C.c_int64(N), _dptr(mean), _dptr(se), _dptr(ms), C.byref(nf),
+                         C.c_int(n_threads))
+    if rc != 0:
+        raise ValueError("the oracle does not implement this problem form")
     return mean, se, ms, int(nf.value)
 
 

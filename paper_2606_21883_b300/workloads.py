@@ -45,6 +45,10 @@ MANIFOLD_POINT_CLOUD = 4
 SAMPLER_FULL = 0      # n Gaussians per direction
 SAMPLER_REDUCED = 1   # dimension-reduced exact sampler (tracked coordinates + chi^2 remainder)
 
+COMP_NONE = 0      # compensation term m_* = 0 (the baseline method)
+COMP_NORMAL2 = 1   # second-order normal expansion of m from a predictor u_* (Sec. 2.3.3)
+COMP_EXACT = 2     # m from its definition with u_* in place of u (exact when u_* = u)
+
 CLOUD_CP_FIT = 0       # kNN + PCA plane + quadratic height fit + projection
 CLOUD_CP_NEAREST = 1   # nearest cloud point
 
@@ -130,6 +134,9 @@ class Problem:
     g: Func
     bnd_normal: Optional[np.ndarray] = None
     bnd_offset: float = 0.0
+    comp: int = COMP_NONE           # COMP_NORMAL2: source f + m_* with predictor u_star
+    u_star: Optional[Func] = None   # torus Fourier (torus) or sphere quad (unit S^2), apply_op = 0
+    h_eta: float = 1e-2             # normal finite-difference step of m_*
 
 
 @dataclass
@@ -380,3 +387,56 @@ def sphere_cloud_legendre(P: int = 100, walks: int = 2000, N_cloud: int = 8000, 
     pts = cloud[idx].copy()
     exact = np.polynomial.legendre.legval(pts[:, 2], cu)
     return Workload("sphere_cloud_e4", prob, pts, walks, Params(), exact, "f32")
+
+
+# ----------------------------------------------------------------------------
+# Example 1: the torus with a planar cut (effect of the compensation term)
+# ----------------------------------------------------------------------------
+
+E1_PHI_C = 0.35 * math.pi
+
+
+def torus_cut_terms(phi_c: float = E1_PHI_C) -> List[Tuple[float, int, int, int, int]]:
+    """u = sin(s) A(theta) + sin(2s) B(theta) + sin(3s) C(theta), s = phi - phi_c, as torus
+    Fourier terms (coef, m, q, theta trig, phi trig); sin(q s) = sin(q phi) cos(q phi_c) -
+    cos(q phi) sin(q phi_c).
+    A = 1 + 0.9 cos t + 0.6 sin 2t + 0.35 cos 3t, B = 0.45 cos 2t, C = 0.3 (0.5 + sin t)."""
+    theta_parts = {1: [(1.0, 0, TRIG_COS), (0.9, 1, TRIG_COS), (0.6, 2, TRIG_SIN), (0.35, 3, TRIG_COS)],
+                   2: [(0.45, 2, TRIG_COS)],
+                   3: [(0.15, 0, TRIG_COS), (0.3, 1, TRIG_SIN)]}
+    terms = []
+    for q, parts in theta_parts.items():
+        for c, m, tk in parts:
+            terms.append((c * math.cos(q * phi_c), m, q, tk, TRIG_SIN))
+            terms.append((-c * math.sin(q * phi_c), m, q, tk, TRIG_COS))
+    return terms
+
+
+def torus_series_value(terms, theta: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """sum_t coef_t T_t(m_t theta) P_t(q_t phi) at parameter values."""
+    trig = (np.cos, np.sin)
+    out = np.zeros(np.broadcast(theta, phi).shape)
+    for c, m, q, tk, pk in terms:
+        out = out + c * trig[tk](m * theta) * trig[pk](q * phi)
+    return out
+
+
+def torus_cut(P: int = 100, walks: int = 2000, seed: int = 0, R: float = 1.0, a: float = 0.45,
+              sigma: float = 4.0, comp: int = COMP_NONE, u_star: Optional[Func] = None) -> Workload:
+    """Example 1: torus R = 1, a = 0.45 cut by the plane -sin(phi_c) x + cos(phi_c) y = 0,
+    Omega = {phi - phi_c in (0, pi)}, sigma = 4, the three-mode u above (u = 0 on Gamma), eps = 1e-5.
+    comp: COMP_NORMAL2 / COMP_EXACT with predictor u_star (the exact u when None)."""
+    man = Manifold(MANIFOLD_TORUS, n=3, d=2, R=R, a=a)
+    terms = torus_cut_terms()
+    e = np.array([-math.sin(E1_PHI_C), math.cos(E1_PHI_C), 0.0])
+    prob = Problem(man, sigma=sigma, closed=False, f=Func.torus(terms, apply_op=True), g=Func.const(0.0),
+                   bnd_normal=e, bnd_offset=0.0)
+    if comp:
+        prob.comp = int(comp)
+        prob.u_star = u_star if u_star is not None else Func.torus(terms, apply_op=False)
+    g = _rng(seed)
+    th = g.uniform(0.0, 2 * math.pi, P)
+    ph = E1_PHI_C + g.uniform(0.0, math.pi, P)
+    pts = torus_points(th, ph, R, a)
+    exact = torus_series_value(terms, th, ph)
+    return Workload("torus_cut_e1", prob, pts, walks, Params(eps=1e-5), exact, "f32")
