@@ -204,6 +204,14 @@ def secondary_leg(M, ctx):
          "torus, 4096 pts x 50 walks, FP64 walk (per-walk parity mode)"),
         ("torus_fp32", lambda: W.torus_closed(P=4096, walks=1), 50, M.FP32, W.SAMPLER_FULL,
          "torus, 4096 pts x 50 walks, FP32 walk (same walks and RMSE scale as torus_fp64)"),
+        ("torus_cut_e1_baseline_fp32", lambda: W.torus_cut(P=100, walks=1), 100000, M.FP32, W.SAMPLER_FULL,
+         "Example 1 cut torus, 100 pts x 1e5 walks, m_* = 0, FP32"),
+        ("torus_cut_e1_comp2_fp32", lambda: W.torus_cut(P=100, walks=1, comp=W.COMP_NORMAL2), 100000, M.FP32,
+         W.SAMPLER_FULL, "Example 1 cut torus, 100 pts x 1e5 walks, second-order m_* (predictor u), FP32"),
+        ("torus_cut_e1_exact_fp32", lambda: W.torus_cut(P=100, walks=1, comp=W.COMP_EXACT), 100000, M.FP32,
+         W.SAMPLER_FULL, "Example 1 cut torus, 100 pts x 1e5 walks, exact mismatch m (predictor u), FP32"),
+        ("sphere_cloud_e4_fp32", lambda: W.sphere_cloud_legendre(P=100, walks=1), 8000, M.FP32, W.SAMPLER_FULL,
+         "Example 4 S^2 as 8000 points, k_nn = 6, nearest-point cp, 100 pts x 8000 walks, FP32"),
     ]
     out = {}
     for name, make, N, prec, sampler, desc in cases:

@@ -57,6 +57,15 @@ extern "C" {
 #define MPWOS_FUNC_TORUS_FOURIER 1 /* sum_t coef_t T(m theta) P(q phi); T,P in {cos,sin} */
 #define MPWOS_FUNC_SPHERE_QUAD 2   /* c0 + v.s + s^T A s, s = intrinsic unit vector   */
 
+/* ---- compensation term m_* (Sec. 2.3.3; m of eq. mismatch_definition) ---- */
+#define MPWOS_COMP_NONE 0      /* m_* = 0: the baseline method                              */
+#define MPWOS_COMP_NORMAL2 1   /* m_*(x) = eta m1(y) + eta^2 m2(y)/2, y = cp(x), eta the signed
+                                  normal distance of x; m1, m2 central differences of
+                                  R_*(s; y) = -Delta(E u_*)(y + s n(y)) + sigma u_*(y) - f(y)
+                                  at s = -h_eta, 0, h_eta (E u_* = u_* o cp)                 */
+#define MPWOS_COMP_EXACT 2     /* m_*(x) = R_*(eta; y): the mismatch itself with u_* for u
+                                  (exact when u_* is the solution)                            */
+
 /* ---- precision of the walk --------------------------------------------- */
 #define MPWOS_FP64 0   /* FP64 walk; per-walk identical draws to the CPU oracle         */
 #define MPWOS_FP32 1   /* FP32 positions/projection/sampling, FP64 weights and sums     */
@@ -121,14 +130,23 @@ typedef struct {
 } mpwos_func;
 
 /* The screened Poisson problem (eqs. surface_pde, surface_bc).  Boundary:
- * Omega = M intersected with the half-space {x : e.x > h} (EUCLID, SPHERE),
- * or closed = 1 (Omega = M). */
+ * Omega = M intersected with the half-space {x : e.x > h} (EUCLID, SPHERE;
+ * TORUS with a plane through its axis, e_3 = 0 and h = 0, as in Example 1),
+ * or closed = 1 (Omega = M).
+ * Compensation (comp != MPWOS_COMP_NONE): the step's source becomes
+ * f(cp(Z)) + m_*(Z) with the predictor u_star, a TORUS_FOURIER series on the
+ * torus (at most 64 terms) or a SPHERE_QUAD on the sphere of R^3, apply_op = 0;
+ * walks in R^3 (TORUS, SPHERE with n = 3) with the full sampler only
+ * (MPWOS_EINVAL otherwise).  h_eta: the normal difference step (0: 1e-2). */
 typedef struct {
   double sigma;               /* screening, > 0                         */
   int closed;
   const double* bnd_normal;   /* unit e, length n (host)                */
   double bnd_offset;          /* h                                      */
   mpwos_func f, g;
+  int comp;                   /* MPWOS_COMP_*                           */
+  mpwos_func u_star;          /* predictor u_* (comp != NONE)           */
+  double h_eta;
 } mpwos_problem;
 
 /* Walk parameters (Algorithm 1; radius rule eq. radius_rule_unified). */
@@ -194,8 +212,8 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
  *   - pts (P x n) and the three outputs must be DEVICE pointers (EINVAL
  *     otherwise); problem data are host pointers as for mpwos_solve;
  *   - P * N must not exceed mpwos_noalloc_max_walks() (EINVAL with the limit
- *     in the message); EMBEDDED_SPHERE and POINT_CLOUD are not supported
- *     (EINVAL);
+ *     in the message); EMBEDDED_SPHERE, POINT_CLOUD, the reduced sampler and
+ *     compensation are not supported (EINVAL);
  *   - the first call on a device looks up the array's device address; make
  *     that first call before any stream capture;
  *   - every call shares the array: calls that overlap on the GPU (other

@@ -24,6 +24,7 @@ MPWOS_ETIMEDOUT, MPWOS_ECANCELED, MPWOS_EMAXSTEPS, MPWOS_ENOTFOUND, MPWOS_EBUSY 
 FP64, FP32 = 0, 1
 PROJ_AUTO, PROJ_TENSOR, PROJ_CUDA = 0, 1, 2
 SAMPLER_FULL, SAMPLER_REDUCED = 0, 1
+COMP_NONE, COMP_NORMAL2, COMP_EXACT = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int)
@@ -49,7 +50,7 @@ class Func(C.Structure):
 
 class ProblemDesc(C.Structure):
     _fields_ = [("sigma", C.c_double), ("closed", C.c_int), ("bnd_normal", _dp), ("bnd_offset", C.c_double),
-                ("f", Func), ("g", Func)]
+                ("f", Func), ("g", Func), ("comp", C.c_int), ("u_star", Func), ("h_eta", C.c_double)]
 
 
 class Params(C.Structure):
@@ -155,6 +156,10 @@ class _Marshal:
             pd.bnd_normal = self.arr(problem.bnd_normal).ctypes.data_as(_dp)
         pd.f = self.func(problem.f)
         pd.g = self.func(problem.g)
+        if getattr(problem, "comp", COMP_NONE) != COMP_NONE:
+            pd.comp = problem.comp
+            pd.u_star = self.func(problem.u_star)
+            pd.h_eta = problem.h_eta
         return md, pd
 
 

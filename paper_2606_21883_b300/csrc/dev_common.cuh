@@ -32,6 +32,25 @@ struct DevFunc {
   int single_mq;                       // TORUS_FOURIER with one term, m, q <= 3: 4 m + q; else -1
 };
 
+// Compensation term m_* (Sec. 2.3.3): the predictor u_* and the difference
+// step.  Torus: a Fourier series (m, q, theta trig, phi trig per term); unit
+// sphere of R^3: u_* = c0 + v.y + y^T A y.  FP32 walks read the float copies
+// and the launch constants sd1, sd2 (sphere: the central differences of
+// (1 + s)^-2 at s = 0 with step h, from FP64 on the host).
+constexpr int kMaxPredTerms = 64;
+constexpr int kCompNone = 0, kCompNormal2 = 1, kCompExact = 2;
+struct DevPredictor {
+  int comp, kind, n_terms;
+  double h;
+  double coef[kMaxPredTerms];
+  int8_t modes[kMaxPredTerms][4];
+  double c0, v[3], A[9];
+  float coef_f[kMaxPredTerms];
+  float mode_f[kMaxPredTerms][2];   // m, q
+  float c0_f, v_f[3], A_f[9];
+  float hf, sd1, sd2;
+};
+
 // FP32 copies of the loop-invariant scalars, filled on the host: a double read
 // in an FP32 walk costs a conversion on B300's narrow FP64 pipe every step.
 struct ScalarsF {
@@ -121,6 +140,8 @@ struct DevProblem {
   double red_e[kMaxQuadDim];
   float red_ef[kMaxQuadDim];
   const double* red_y0;
+  // compensation term (last, so the fields above keep their offsets)
+  DevPredictor pred;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {

@@ -57,6 +57,49 @@ __device__ __forceinline__ T delta_gamma3(const DevProblem& pb, const T* y, T* y
     for (int i = 0; i < 3; ++i) yg[i] = y[i] - (ey - h) * e[i];
     const T d = fabs(ey - h);
     return (ey <= h) ? T(0) : d;
+  } else if constexpr (MK == kTorus) {
+    // a plane through the axis (e_3 = 0, h = 0): Gamma is the two meridian
+    // circles c_b + a (cos t u_b + sin t e_3), c_b = R u_b, u_0 = (-e_2, e_1, 0),
+    // u_1 = -u_0.  Nearest point of circle b: c_b + a w/|w|, w the part of
+    // y - c_b in span(u_b, e_3); the nearer circle wins (circle 0 on a tie); the
+    // torus normal at y_G is w/|w|.
+    const T R = pick<T>(pb.R, pb.sf.R), a = pick<T>(pb.a_tube, pb.sf.a);
+    T best = T(INFINITY), nrm[3] = {T(0), T(0), T(0)};
+    for (int b = 0; b < 2; ++b) {
+      const T sgn = (b == 0) ? T(1) : T(-1);
+      const T u[3] = {-sgn * e[1], sgn * e[0], T(0)};
+      const T c[3] = {R * u[0], R * u[1], T(0)};
+      const T wu = (y[0] - c[0]) * u[0] + (y[1] - c[1]) * u[1];
+      const T wz = y[2];
+      const T w[3] = {wu * u[0], wu * u[1], wz};
+      const T nw = dsqrt<T>(wu * wu + wz * wz);
+      T nb[3];
+      if (nw > T(0)) {
+        for (int i = 0; i < 3; ++i) nb[i] = w[i] / nw;
+      } else {   // y on the circle's axis: take t = 0
+        for (int i = 0; i < 3; ++i) nb[i] = u[i];
+      }
+      T q[3], d2 = T(0);
+      for (int i = 0; i < 3; ++i) {
+        q[i] = c[i] + a * nb[i];
+        d2 += (q[i] - y[i]) * (q[i] - y[i]);
+      }
+      if (d2 < best) {
+        best = d2;
+        for (int i = 0; i < 3; ++i) { yg[i] = q[i]; nrm[i] = nb[i]; }
+      }
+    }
+    T rn = T(0);
+    for (int i = 0; i < 3; ++i) rn += (yg[i] - y[i]) * nrm[i];
+    T rt2 = T(0);
+    for (int i = 0; i < 3; ++i) {
+      const T rti = (yg[i] - y[i]) - rn * nrm[i];
+      rt2 += rti * rti;
+    }
+    if (ey <= h) return T(0);
+    T ex = fabs(rn) - pick<T>(pb.rho_geo, pb.sf.rho_geo);
+    if (ex < T(0)) ex = T(0);
+    return dsqrt<T>(rt2 + ex * ex);
   } else {
   // unit sphere: y_G = h e + sqrt(1 - h^2) w/|w|, w = y - (e.y) e
   T w[3];
@@ -82,6 +125,34 @@ __device__ __forceinline__ T delta_gamma3(const DevProblem& pb, const T* y, T* y
   T ex = fabs(rn) - pick<T>(pb.rho_geo, pb.sf.rho_geo);
   if (ex < T(0)) ex = T(0);
   return dsqrt<T>(rt2 + ex * ex);
+  }
+}
+
+// cos(m x), sin(m x) from c = cos x, s = sin x: closed forms for m <= 4 (the
+// mode is uniform across the warp, so the switch does not diverge), repeated
+// rotation above.
+__device__ __forceinline__ void angle_multiple(int m, float c, float s, float& cm, float& sm) {
+  switch (m) {
+    case 0: cm = 1.0f; sm = 0.0f; return;
+    case 1: cm = c; sm = s; return;
+    case 2: cm = fmaf(2.0f * c, c, -1.0f); sm = 2.0f * s * c; return;
+    case 3: {
+      const float c2 = fmaf(2.0f * c, c, -1.0f);
+      cm = c * fmaf(2.0f, c2, -1.0f);
+      sm = s * fmaf(2.0f, c2, 1.0f);
+      return;
+    }
+    case 4: {
+      const float c2 = fmaf(2.0f * c, c, -1.0f), s2 = 2.0f * s * c;
+      cm = fmaf(2.0f * c2, c2, -1.0f);
+      sm = 2.0f * s2 * c2;
+      return;
+    }
+    default: {
+      float a = 1.0f, b = 0.0f;
+      for (int j = 0; j < m; ++j) { const float a2 = a * c - b * s; b = b * c + a * s; a = a2; }
+      cm = a; sm = b;
+    }
   }
 }
 

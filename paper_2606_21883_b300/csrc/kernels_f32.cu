@@ -15,9 +15,12 @@ static const void* walk3_f32_fn(const DevProblem& pb) {
       return pb.closed ? reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid, 1, true>)
                        : reinterpret_cast<const void*>(walk3_f32_kernel<kEuclid, 1, false>);
     case kSphere:
+      if (pb.pred.comp != kCompNone) return reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, false, -1, true>);
       return pb.closed ? reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, true>)
                        : reinterpret_cast<const void*>(walk3_f32_kernel<kSphere, 1, false>);
-    case kTorus: {   // closed only
+    case kTorus: {
+      if (pb.pred.comp != kCompNone) return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, false, -1, true>);
+      if (!pb.closed) return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, false>);
       const int mq = (pb.n_v == 1 && pb.f.kind == kTorusFourier) ? pb.f.single_mq : -1;
       switch (mq) {
 #define MPWOS_MQ(c) case c: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true, c>);

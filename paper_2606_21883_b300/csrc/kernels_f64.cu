@@ -150,8 +150,12 @@ cudaError_t launch_reduce_strided(const double* S, const int32_t* K, const int32
 static const void* walk3_f64_fn(const DevProblem& pb) {
   switch (pb.mkind) {
     case kEuclid: return reinterpret_cast<const void*>(walk3_f64_kernel<kEuclid, 1>);
-    case kSphere: return reinterpret_cast<const void*>(walk3_f64_kernel<kSphere, 1>);
-    case kTorus: return reinterpret_cast<const void*>(walk3_f64_kernel<kTorus, 1>);
+    case kSphere:
+      return pb.pred.comp != kCompNone ? reinterpret_cast<const void*>(walk3_f64_kernel<kSphere, 1, true>)
+                                       : reinterpret_cast<const void*>(walk3_f64_kernel<kSphere, 1>);
+    case kTorus:
+      return pb.pred.comp != kCompNone ? reinterpret_cast<const void*>(walk3_f64_kernel<kTorus, 1, true>)
+                                       : reinterpret_cast<const void*>(walk3_f64_kernel<kTorus, 1>);
     case kPointCloud:
       return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f64_kernel<kPointCloud, 8>)
            : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f64_kernel<kPointCloud, 16>)

@@ -177,7 +177,8 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
     case MPWOS_TORUS:
       if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "TORUS lives in R^3 (n = 3, d = 2)");
       if (!(m->R > m->a && m->a > 0.0)) return fail(ctx, MPWOS_EINVAL, "TORUS needs R > a > 0");
-      if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "TORUS supports the closed problem only");
+      if (!pr->closed && pr->bnd_normal && (pr->bnd_normal[2] != 0.0 || pr->bnd_offset != 0.0))
+        return fail(ctx, MPWOS_EINVAL, "a TORUS boundary must be a plane through the axis (e_3 = 0, h = 0)");
       break;
     case MPWOS_EMBEDDED_SPHERE:
       if (m->n <= 3) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs n > 3");
@@ -199,7 +200,8 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       return fail(ctx, MPWOS_EINVAL, "unknown manifold kind %d", m->kind);
   }
   if (!pr->closed) {
-    if (m->kind != MPWOS_EUCLID && m->kind != MPWOS_SPHERE) return fail(ctx, MPWOS_EINVAL, "boundary needs EUCLID or SPHERE");
+    if (m->kind != MPWOS_EUCLID && m->kind != MPWOS_SPHERE && m->kind != MPWOS_TORUS)
+      return fail(ctx, MPWOS_EINVAL, "boundary needs EUCLID, SPHERE or TORUS");
     if (!pr->bnd_normal) return fail(ctx, MPWOS_EINVAL, "boundary problem needs bnd_normal");
     double nn = 0.0;
     for (int i = 0; i < m->n; ++i) nn += pr->bnd_normal[i] * pr->bnd_normal[i];
@@ -241,6 +243,25 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
     return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE source must be SPHERE_QUAD");
   if (pa->sampler != MPWOS_SAMPLER_FULL && pa->sampler != MPWOS_SAMPLER_REDUCED)
     return fail(ctx, MPWOS_EINVAL, "unknown sampler %d", pa->sampler);
+  if (pr->comp != MPWOS_COMP_NONE) {
+    const mpwos_func& u = pr->u_star;
+    if (pr->comp != MPWOS_COMP_NORMAL2 && pr->comp != MPWOS_COMP_EXACT) return fail(ctx, MPWOS_EINVAL, "unknown comp %d", pr->comp);
+    if (!(m->kind == MPWOS_TORUS || (m->kind == MPWOS_SPHERE && m->n == 3)))
+      return fail(ctx, MPWOS_EINVAL, "compensation needs TORUS or the sphere in R^3");
+    if (pa->sampler != MPWOS_SAMPLER_FULL) return fail(ctx, MPWOS_EINVAL, "compensation needs the full sampler");
+    if (!(pr->h_eta >= 0.0 && pr->h_eta < 0.5)) return fail(ctx, MPWOS_EINVAL, "h_eta must lie in [0, 0.5)");
+    if (u.apply_op) return fail(ctx, MPWOS_EINVAL, "the predictor u_star takes apply_op = 0");
+    if (m->kind == MPWOS_TORUS) {
+      if (u.kind != MPWOS_FUNC_TORUS_FOURIER) return fail(ctx, MPWOS_EINVAL, "on the TORUS u_star must be TORUS_FOURIER");
+      if (u.n_terms < 0 || u.n_terms > kMaxPredTerms) return fail(ctx, MPWOS_EINVAL, "u_star takes at most %d terms", kMaxPredTerms);
+      if (u.n_terms && (!u.coef || !u.modes)) return fail(ctx, MPWOS_EINVAL, "u_star needs coef and modes");
+      for (int t = 0; t < u.n_terms; ++t)
+        if (u.modes[4 * t] < 0 || u.modes[4 * t] > 64 || u.modes[4 * t + 1] < 0 || u.modes[4 * t + 1] > 64)
+          return fail(ctx, MPWOS_EINVAL, "u_star mode numbers must lie in [0, 64]");
+    } else {
+      if (u.kind != MPWOS_FUNC_SPHERE_QUAD || !u.v || !u.A) return fail(ctx, MPWOS_EINVAL, "on the sphere u_star must be SPHERE_QUAD with v and A");
+    }
+  }
   if (pa->sampler == MPWOS_SAMPLER_REDUCED) {
     if (m->kind == MPWOS_EUCLID || m->kind == MPWOS_SPHERE) {
       if (m->n <= 3) return fail(ctx, MPWOS_EINVAL, "the reduced sampler needs n > 3 on SPHERE / EUCLID");
@@ -329,6 +350,37 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
       d.mode_f[t][3] = qq * qq;
     }
     if (f.n_terms == 1 && f.modes[0] <= 3 && f.modes[1] <= 3) d.single_mq = 4 * f.modes[0] + f.modes[1];
+  }
+}
+
+// The compensation predictor (validated): coefficients, modes, the step and,
+// for the sphere, the central differences of (1 + s)^-2 at 0 with step h.
+void copy_pred(const mpwos_problem& pr, DevPredictor& d) {
+  std::memset(&d, 0, sizeof d);
+  d.comp = pr.comp;
+  if (pr.comp == MPWOS_COMP_NONE) return;
+  const mpwos_func& u = pr.u_star;
+  const double h = pr.h_eta > 0.0 ? pr.h_eta : 1e-2;
+  d.kind = u.kind;
+  d.h = h;
+  d.hf = static_cast<float>(h);
+  if (u.kind == MPWOS_FUNC_TORUS_FOURIER) {
+    d.n_terms = u.n_terms;
+    for (int t = 0; t < u.n_terms; ++t) {
+      d.coef[t] = u.coef[t];
+      d.coef_f[t] = static_cast<float>(u.coef[t]);
+      for (int q = 0; q < 4; ++q) d.modes[t][q] = static_cast<int8_t>(u.modes[4 * t + q]);
+      d.mode_f[t][0] = static_cast<float>(u.modes[4 * t]);
+      d.mode_f[t][1] = static_cast<float>(u.modes[4 * t + 1]);
+    }
+  } else {
+    d.c0 = u.c0;
+    d.c0_f = static_cast<float>(u.c0);
+    for (int i = 0; i < 3; ++i) { d.v[i] = u.v[i]; d.v_f[i] = static_cast<float>(u.v[i]); }
+    for (int i = 0; i < 9; ++i) { d.A[i] = u.A[i]; d.A_f[i] = static_cast<float>(u.A[i]); }
+    const double gp = 1.0 / ((1.0 + h) * (1.0 + h)), gm = 1.0 / ((1.0 - h) * (1.0 - h));
+    d.sd1 = static_cast<float>((gp - gm) / (2.0 * h));
+    d.sd2 = static_cast<float>((gp - 2.0 + gm) / (h * h));
   }
 }
 
@@ -516,6 +568,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   pb.out_stride = N;
   copy_func(pr->f, pb.f);
   if (!pr->closed) copy_func(pr->g, pb.g);
+  copy_pred(*pr, pb.pred);
   const int n = m->n;
   if (!pr->closed) {
     std::vector<float> ef(pr->bnd_normal, pr->bnd_normal + n);
@@ -1005,6 +1058,8 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE and POINT_CLOUD are not supported (use mpwos_solve)");
   if (prm->sampler != MPWOS_SAMPLER_FULL)
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: the reduced sampler is not supported (use mpwos_solve)");
+  if (prob->comp != MPWOS_COMP_NONE)
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: compensation is not supported (use mpwos_solve)");
   if (P > 0 && (!is_device_ptr(pts) || !is_device_ptr(mean) || !is_device_ptr(stderr_) || !is_device_ptr(mean_steps)))
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: pts and the three outputs must be device pointers");
   const int64_t walks = P * N;
@@ -1160,7 +1215,7 @@ struct Request {
   mpwos_manifold_desc man{};
   mpwos_problem prob{};
   mpwos_params prm{};
-  OwnedFunc f, g;
+  OwnedFunc f, g, u_star;
   std::vector<double> Q, b, normal, pts;
   CloudGrid* cloud = nullptr;
   int64_t P = 0, budget = 0;
@@ -1476,6 +1531,10 @@ int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_probl
     r->prob.g = r->g.f;
     r->normal.assign(prob->bnd_normal, prob->bnd_normal + m->n);
     r->prob.bnd_normal = r->normal.data();
+  }
+  if (prob->comp != MPWOS_COMP_NONE) {
+    r->u_star.take(prob->u_star, D);
+    r->prob.u_star = r->u_star.f;
   }
   if (m->kind == MPWOS_EMBEDDED_SPHERE) {
     r->Q.assign(m->Q, m->Q + static_cast<size_t>(m->n) * (m->d + 1));

@@ -14,6 +14,7 @@
 #include "geom3.cuh"
 #include "green.cuh"
 #include "cloud.cuh"
+#include "comp.cuh"
 
 namespace mpwos {
 
@@ -48,7 +49,8 @@ __device__ __forceinline__ bool source_is_constant(const DevFunc& f) {
   return f.kind == kPoly && f.term_off[f.n_terms] == 0;
 }
 
-template <int MK, int KM>
+// COMP: the step's source is f(cp(Z)) + m_*(Z) (compensation term, comp.cuh).
+template <int MK, int KM, bool COMP>
 __device__ __forceinline__ void walk3_f64_body(const DevProblem& pb) {
   const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -139,7 +141,9 @@ __device__ __forceinline__ void walk3_f64_body(const DevProblem& pb) {
         F += func3<MK, double>(pb, pb.f, Z);
       } else {
         cp_any<MK, KM, double>(pb, Z, cZ);
-        F += func3<MK, double>(pb, pb.f, cZ);
+        double fz = func3<MK, double>(pb, pb.f, cZ);
+        if constexpr (COMP) fz = fz + comp_m64<MK>(pb, Z, cZ, fz);
+        F += fz;
       }
     }
     if (nv > 1) F /= static_cast<double>(nv);
@@ -186,34 +190,6 @@ __device__ __forceinline__ void torus_angles32(float R, const float* x, float& c
   st = x[2] * iw;
   cph = x[0] * irho;
   sph = x[1] * irho;
-}
-
-// cos(m x), sin(m x) from c = cos x, s = sin x: closed forms for m <= 4 (the
-// mode is uniform across the warp, so the switch does not diverge), repeated
-// rotation above.
-__device__ __forceinline__ void angle_multiple(int m, float c, float s, float& cm, float& sm) {
-  switch (m) {
-    case 0: cm = 1.0f; sm = 0.0f; return;
-    case 1: cm = c; sm = s; return;
-    case 2: cm = fmaf(2.0f * c, c, -1.0f); sm = 2.0f * s * c; return;
-    case 3: {
-      const float c2 = fmaf(2.0f * c, c, -1.0f);
-      cm = c * fmaf(2.0f, c2, -1.0f);
-      sm = s * fmaf(2.0f, c2, 1.0f);
-      return;
-    }
-    case 4: {
-      const float c2 = fmaf(2.0f * c, c, -1.0f), s2 = 2.0f * s * c;
-      cm = fmaf(2.0f * c2, c2, -1.0f);
-      sm = 2.0f * s2 * c2;
-      return;
-    }
-    default: {
-      float a = 1.0f, b = 0.0f;
-      for (int j = 0; j < m; ++j) { const float a2 = a * c - b * s; b = b * c + a * s; a = a2; }
-      cm = a; sm = b;
-    }
-  }
 }
 
 // (-Delta_M + sigma) u or u itself for a torus Fourier series, from the angles.
@@ -314,7 +290,7 @@ __device__ __forceinline__ float source_at32(const DevProblem& pb, const float* 
 // |S.lo| stays below 64 ulp(S.hi)), and updates V *= c without renormalising
 // (|V.lo| stays within a few ulp of V.hi).  Otherwise W, S and omega follow the
 // radius step by step.
-template <int MK, int KM, bool FIXED>
+template <int MK, int KM, bool FIXED, bool COMP = false>
 __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
   const int64_t total = pb.wk_w1;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -446,6 +422,7 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
       float Z[3];
       for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * z[q];
       F = source_at32<MK, KM>(pb, Z);
+      if constexpr (COMP) F += comp_m32<MK>(pb, Z, F);
     } else {
       float g[3];
       for (int q = 0; q < 3; ++q) g[q] = gaussian_at32(static_cast<uint32_t>(q), kk, i, p, K);
@@ -461,7 +438,8 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
         const float zs = (r * t) * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
         float Z[3];
         for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * g[q];
-        F += source_at32<MK, KM>(pb, Z);
+        const float fz = source_at32<MK, KM>(pb, Z);
+        F += COMP ? fz + comp_m32<MK>(pb, Z, fz) : fz;
       }
       F /= static_cast<float>(nv);
     }
@@ -618,8 +596,9 @@ __device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
 // fastest on B300), the general loop 64 (4 blocks); the point-cloud walk uses
 // 128-thread blocks with a larger register budget.  MQ >= 0 (torus, one
 // Fourier term with modes m = MQ / 4, q = MQ % 4, N_V = 1): the host launches
-// the instance with those modes built in.
-template <int MK, int KM, bool FIXED, int MQ = -1>
+// the instance with those modes built in.  COMP: with the compensation term
+// (general loop only).
+template <int MK, int KM, bool FIXED, int MQ = -1, bool COMP = false>
 __global__ void __launch_bounds__(256, FIXED ? 5 : 4) walk3_f32_kernel(const DevProblem pb) {
   if constexpr (FIXED) {
     if (pb.n_v == 1) {
@@ -627,13 +606,13 @@ __global__ void __launch_bounds__(256, FIXED ? 5 : 4) walk3_f32_kernel(const Dev
       return;
     }
   }
-  walk3_f32_body<MK, KM, FIXED>(pb);
+  walk3_f32_body<MK, KM, FIXED, COMP>(pb);
 }
 template <int MK, int KM>
 __global__ void __launch_bounds__(128) walk3_f32_cloud_kernel(const DevProblem pb) {
   walk3_f32_body<MK, KM, false>(pb);
 }
-template <int MK, int KM>
-__global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) { walk3_f64_body<MK, KM>(pb); }
+template <int MK, int KM, bool COMP = false>
+__global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) { walk3_f64_body<MK, KM, COMP>(pb); }
 
 }  // namespace mpwos
