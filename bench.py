@@ -49,7 +49,7 @@ OPS_PER_STEP = 199
 # DRAM bytes (read + write) of one bench launch of the walk kernel, measured
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the
 # kernel as built now; the profile summary gives the command.
-TRAFFIC_BYTES = 21.42e6 + 603.81e6
+TRAFFIC_BYTES = 20.37e6 + 602.73e6
 
 
 def _peaks():
