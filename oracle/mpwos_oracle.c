@@ -264,6 +264,44 @@ static double dot(const double* a, const double* b, int n) {
 
 static void cloud_cp(const orc_manifold* m, const double* x, double* out);
 
+/* ---- hypersurface of revolution (Example 2) ----------------------------- */
+/* Profile R(t) = w(s) q(s), s = t/k, w = sqrt(1 - s^2), q = 1 - al + 2 al s^2,
+ * and its first two t-derivatives (w' = -s/w, w'' = -1/w^3 in s). */
+void orc_profile(const orc_manifold* m, double t, double* R, double* R1, double* R2) {
+  double k = m->prof_kappa, al = m->prof_alpha;
+  double s = t / k;
+  double w = sqrt(1.0 - s * s);
+  double q = 1.0 - al + 2.0 * al * s * s;
+  double dw = -s / w, ddw = -1.0 / (w * w * w);
+  double dq = 4.0 * al * s, ddq = 4.0 * al;
+  *R = w * q;
+  *R1 = (dw * q + w * dq) / k;
+  *R2 = (ddw * q + 2.0 * dw * dq + w * ddq) / (k * k);
+}
+
+/* The closest point of M to x lies in x's meridian half-plane: minimise
+ * D(t) = (R(t) - rho0)^2 + (t - t0)^2 (rho0 = |xh|, t0 = x_{n-1}) by Newton's
+ * method on D'(t)/2 = (R - rho0) R' + (t - t0) from t = t0, kept inside
+ * |t| <= k (1 - 1e-6); where the Newton derivative R'^2 + (R - rho0) R'' + 1
+ * falls below 0.1 the Gauss-Newton one R'^2 + 1 is used.  Stops when a step
+ * changes t by at most 1e-15 (1 + |t|), or after 60 steps. */
+static double rev_cp_t(const orc_manifold* m, double rho0, double t0) {
+  double lim = m->prof_kappa * (1.0 - 1e-6);
+  double t = t0 < -lim ? -lim : (t0 > lim ? lim : t0);
+  for (int it = 0; it < 60; ++it) {
+    double R, R1, R2;
+    orc_profile(m, t, &R, &R1, &R2);
+    double F = (R - rho0) * R1 + (t - t0);
+    double J = R1 * R1 + (R - rho0) * R2 + 1.0;
+    if (!(J > 0.1)) J = R1 * R1 + 1.0;
+    double tn = t - F / J;
+    tn = tn < -lim ? -lim : (tn > lim ? lim : tn);
+    if (fabs(tn - t) <= 1e-15 * (1.0 + fabs(t))) { t = tn; break; }
+    t = tn;
+  }
+  return t;
+}
+
 void orc_cp(const orc_manifold* m, const double* x, double* out) {
   int n = m->n;
   if (m->kind == ORC_EUCLID) {
@@ -281,6 +319,19 @@ void orc_cp(const orc_manifold* m, const double* x, double* out) {
     for (int i = 0; i < 3; ++i) out[i] = c[i] + s * w[i];
   } else if (m->kind == ORC_POINT_CLOUD) {
     cloud_cp(m, x, out);
+  } else if (m->kind == ORC_REVOLUTION) {
+    double rho0 = 0.0;
+    for (int i = 0; i < n - 1; ++i) rho0 += x[i] * x[i];
+    rho0 = sqrt(rho0);
+    double t = rev_cp_t(m, rho0, x[n - 1]);
+    double R, R1, R2;
+    orc_profile(m, t, &R, &R1, &R2);
+    if (rho0 > 0.0) {
+      for (int i = 0; i < n - 1; ++i) out[i] = x[i] * (R / rho0);
+    } else {   /* on the axis: every direction is nearest; take e_1 */
+      for (int i = 0; i < n - 1; ++i) out[i] = (i == 0) ? R : 0.0;
+    }
+    out[n - 1] = t;
   } else { /* embedded unit sphere: cp(x) = Q normalize(Q^T (x - b)) + b */
     int D = m->d + 1;
     double* s = (double*)malloc(sizeof(double) * (size_t)D);
@@ -444,11 +495,25 @@ static void cloud_cp(const orc_manifold* m, const double* x, double* out) {
   for (int i = 0; i < 3; ++i) out[i] = c[i] + s * (xi1 * u[i] + et1 * v[i] + z1 * nrm[i]);
 }
 
+/* largest absolute principal curvature at y on a hypersurface of revolution:
+ * the meridian |R''| / (1 + R'^2)^{3/2} and the n-2 parallel ones
+ * 1 / (R (1 + R'^2)^{1/2}) */
+double orc_kappa_at(const orc_manifold* m, const double* y);
+
 static double kappa_of(const orc_manifold* m) {
   /* largest absolute principal curvature (constant on these manifolds) */
   if (m->kind == ORC_EUCLID) return 0.0;
   if (m->kind == ORC_TORUS) return 1.0 / m->a;
   return 1.0; /* unit sphere, embedded unit sphere */
+}
+
+double orc_kappa_at(const orc_manifold* m, const double* y) {
+  if (m->kind != ORC_REVOLUTION) return kappa_of(m);
+  double R, R1, R2;
+  orc_profile(m, y[m->n - 1], &R, &R1, &R2);
+  double G = sqrt(1.0 + R1 * R1);
+  double km = fabs(R2) / (G * G * G), kp = 1.0 / (R * G);
+  return km > kp ? km : kp;
 }
 
 /* delta_Gamma(y) = ( |P_T r_Gamma|^2 + (|P_N r_Gamma| - ell)_+^2 )^{1/2},
@@ -603,6 +668,40 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
       total += f->coef[t] * val;
     }
     return total;
+  }
+  if (f->kind == ORC_REVOLUTION_QUAD) {
+    /* u = c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on |xh| = R(t).  With xh = R w
+     * (w on the unit sphere S^{n-2}), u = h0(t) + R (v.w) + R^2 (w^T A w - mA),
+     * h0 = c1 t + c2 t^2 + mA R^2, mA = tr(A)/(n-1): degree-0, 1 and 2 spherical
+     * harmonics with -Delta_{S^{n-2}} eigenvalues 0, n-2 and 2(n-1).  On the
+     * surface of revolution (metric (1 + R'^2) dt^2 + R^2 dw^2),
+     *   Delta_M (h(t) Y_k) = [ (h'' + (n-2) R' h'/R - h' R' R''/(1+R'^2)) / (1+R'^2)
+     *                          - lambda_k h / R^2 ] Y_k. */
+    int n = m->n;
+    double t = x[n - 1];
+    double R, R1, R2;
+    orc_profile(m, t, &R, &R1, &R2);
+    double rh = 0.0, vw = 0.0, aw = 0.0, trA = 0.0;
+    for (int i = 0; i < n - 1; ++i) rh += x[i] * x[i];
+    rh = sqrt(rh);
+    for (int i = 0; i < n - 1; ++i) {
+      double wi = x[i] / rh;
+      vw += f->v[i] * wi;
+      aw += f->A[i] * wi * wi;
+      trA += f->A[i];
+    }
+    double c1 = f->coef[0], c2 = f->coef[1];
+    double mA = trA / (double)(n - 1);
+    double u = c1 * t + c2 * t * t + R * vw + R * R * aw;
+    if (!f->apply_op) return u;
+    double md = (double)(n - 2), G2 = 1.0 + R1 * R1;
+    double h0p = c1 + 2.0 * c2 * t + 2.0 * mA * R * R1;
+    double h0pp = 2.0 * c2 + 2.0 * mA * (R1 * R1 + R * R2);
+    double L0 = (h0pp + md * R1 * h0p / R - h0p * R1 * R2 / G2) / G2;
+    double L1 = (R2 + md * R1 * R1 / R - R1 * R1 * R2 / G2) / G2 - md / R;
+    double h2p = 2.0 * R * R1, h2pp = 2.0 * R1 * R1 + 2.0 * R * R2;
+    double L2 = (h2pp + md * R1 * h2p / R - h2p * R1 * R2 / G2) / G2 - 2.0 * (md + 1.0);
+    return -L0 - L1 * vw - L2 * (aw - mA) + sigma * u;
   }
   /* sphere quad: intrinsic unit vector s of the round sphere S^d */
   int D = m->d + 1;
@@ -760,7 +859,7 @@ static int run_walk(const orc_manifold* m, const orc_problem* pb, const orc_para
       double d2[64];
       rgeo = m->c_h * orc_cloud_knn(m, w->Y, idx, d2);   /* eq. rho_geo_spacing */
     } else {
-      rgeo = pr->c_kappa / (1.0 + kappa_of(m));
+      rgeo = pr->c_kappa / (1.0 + orc_kappa_at(m, w->Y));   /* eq. rho_geo_curvature */
     }
     double r = pr->theta * (dG < rgeo ? dG : rgeo);
     double a = sqs * r;
@@ -999,6 +1098,8 @@ static int run_walk_reduced(const orc_manifold* m, const orc_problem* pb, const 
  * axis; compensation runs on the torus (TORUS_FOURIER predictor) and the unit
  * sphere of R^3 (SPHERE_QUAD predictor).  Returns -1 for anything else. */
 static int check_problem(const orc_manifold* m, const orc_problem* pb) {
+  if (m->kind == ORC_REVOLUTION && (!pb->closed || m->n < 4 || pb->f.kind != ORC_REVOLUTION_QUAD || pb->comp))
+    return -1;
   if (m->kind == ORC_TORUS && !pb->closed && (pb->bnd_normal[2] != 0.0 || pb->bnd_offset != 0.0)) return -1;
   if (pb->comp == ORC_COMP_NONE) return 0;
   if (pb->comp != ORC_COMP_NORMAL2 && pb->comp != ORC_COMP_EXACT) return -1;

@@ -25,9 +25,10 @@
 extern "C" {
 #endif
 
-enum { ORC_EUCLID = 0, ORC_SPHERE = 1, ORC_TORUS = 2, ORC_EMBEDDED_SPHERE = 3, ORC_POINT_CLOUD = 4 };
+enum { ORC_EUCLID = 0, ORC_SPHERE = 1, ORC_TORUS = 2, ORC_EMBEDDED_SPHERE = 3, ORC_POINT_CLOUD = 4,
+       ORC_REVOLUTION = 5 };
 enum { ORC_CP_FIT = 0, ORC_CP_NEAREST = 1 };
-enum { ORC_POLY = 0, ORC_TORUS_FOURIER = 1, ORC_SPHERE_QUAD = 2 };
+enum { ORC_POLY = 0, ORC_TORUS_FOURIER = 1, ORC_SPHERE_QUAD = 2, ORC_REVOLUTION_QUAD = 3 };
 
 typedef struct {
   int kind, n, d;
@@ -39,6 +40,9 @@ typedef struct {
   int k_nn;               /* neighbours for h(y) and the local fit             */
   double c_h;             /* rho_geo = c_h h(y) (eq. rho_geo_spacing)          */
   int cp_mode;            /* ORC_CP_FIT or ORC_CP_NEAREST                      */
+  /* hypersurface of revolution about the last axis (Example 2):
+   * M = {x = (xh, t) : |xh| = R(t)}, R(t) = sqrt(1 - (t/k)^2) (1 - al + 2 al (t/k)^2) */
+  double prof_alpha, prof_kappa;
 } orc_manifold;
 
 typedef struct {
@@ -49,8 +53,9 @@ typedef struct {
   const int* pw;
   const int* modes;       /* torus: 4 ints per term (m, q, theta trig, phi trig) */
   double c0;              /* sphere quad: u = c0 + v.s + s^T A s               */
-  const double* v;        /* d+1                                               */
-  const double* A;        /* (d+1)^2 row-major                                 */
+  const double* v;        /* d+1 (revolution quad: n-1)                        */
+  const double* A;        /* (d+1)^2 row-major (revolution quad: the n-1 diagonal entries) */
+  /* revolution quad: u = coef[0] t + coef[1] t^2 + v.xh + sum_j A_j xh_j^2, t = x_{n-1} */
 } orc_func;
 
 enum { ORC_COMP_NONE = 0, ORC_COMP_NORMAL2 = 1, ORC_COMP_EXACT = 2 };
@@ -118,6 +123,10 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
 double orc_normal_coord(const orc_manifold* m, const double* x);
 double orc_comp_R(const orc_manifold* m, const orc_problem* pb, const double* y, double s);
 double orc_comp_m(const orc_manifold* m, const orc_problem* pb, const double* x);
+/* hypersurface of revolution: the profile R(t), R'(t), R''(t); the curvature
+ * indicator (largest absolute principal curvature) at a point of M */
+void   orc_profile(const orc_manifold* m, double t, double* R, double* R1, double* R2);
+double orc_kappa_at(const orc_manifold* m, const double* y);
 /* point cloud: k nearest (by distance^2, then index), mean distance h(x) */
 double orc_cloud_knn(const orc_manifold* m, const double* x, int64_t* idx, double* d2);
 

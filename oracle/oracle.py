@@ -10,7 +10,7 @@ import numpy as np
 from .build import build
 
 __all__ = ["lib", "philox", "u53", "gaussians", "chi2", "tracked_set", "em1", "c_sigma_r", "green_cdf", "green_cdf_inv",
-           "kt_minus_one", "cp", "delta_gamma", "func_eval", "normal_coord", "comp_R", "comp_m", "walk_scores", "solve", "trace",
+           "kt_minus_one", "cp", "delta_gamma", "func_eval", "profile", "kappa_at", "normal_coord", "comp_R", "comp_m", "walk_scores", "solve", "trace",
            "OracleProblem", "cloud_knn"]
 
 _lib: Optional[C.CDLL] = None
@@ -22,7 +22,8 @@ _ip = C.POINTER(C.c_int)
 class _Manifold(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int), ("d", C.c_int), ("R", C.c_double),
                 ("a", C.c_double), ("Q", _dp), ("b", _dp), ("cloud", _dp), ("n_cloud", C.c_int64),
-                ("k_nn", C.c_int), ("c_h", C.c_double), ("cp_mode", C.c_int)]
+                ("k_nn", C.c_int), ("c_h", C.c_double), ("cp_mode", C.c_int),
+                ("prof_alpha", C.c_double), ("prof_kappa", C.c_double)]
 
 
 class _Func(C.Structure):
@@ -72,6 +73,7 @@ def lib() -> C.CDLL:
         L.orc_trace.restype = C.c_int64
         L.orc_cloud_knn.restype = C.c_double
         L.orc_normal_coord.restype = C.c_double
+        L.orc_kappa_at.restype = C.c_double
         L.orc_comp_R.restype = C.c_double
         L.orc_comp_R.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_double]
         L.orc_comp_m.restype = C.c_double
@@ -95,7 +97,8 @@ class OracleProblem:
     def __init__(self, problem, params):
         self._keep = []
         m = problem.manifold
-        self.man = _Manifold(kind=m.kind, n=m.n, d=m.d, R=m.R, a=m.a)
+        self.man = _Manifold(kind=m.kind, n=m.n, d=m.d, R=m.R, a=m.a,
+                             prof_alpha=getattr(m, "prof_alpha", 0.0), prof_kappa=getattr(m, "prof_kappa", 0.0))
         if m.Q is not None:
             Q = self._arr(m.Q)
             b = self._arr(m.b)
@@ -146,6 +149,8 @@ class OracleProblem:
             cf.coef = _dptr(self._arr(coef))
             cf.modes = _iptr(self._arr(modes, np.int32))
         else:
+            if f.kind == W.FUNC_REVOLUTION_QUAD:
+                cf.coef = _dptr(self._arr(np.asarray(f.coef, dtype=np.float64)))
             cf.v = _dptr(self._arr(f.v))
             cf.A = _dptr(self._arr(f.A))
         return cf
@@ -232,6 +237,19 @@ def func_eval(op: OracleProblem, which: str, x):
     x = np.ascontiguousarray(x, dtype=np.float64)
     f = {"f": op.prob.f, "g": op.prob.g, "u_star": op.prob.u_star}[which]
     return lib().orc_func_eval(C.byref(op.man), C.byref(f), C.c_double(op.prob.sigma), _dptr(x))
+
+
+def profile(op: OracleProblem, t):
+    """R(t), R'(t), R''(t) of a hypersurface of revolution's profile."""
+    R, R1, R2 = C.c_double(), C.c_double(), C.c_double()
+    lib().orc_profile(C.byref(op.man), C.c_double(t), C.byref(R), C.byref(R1), C.byref(R2))
+    return R.value, R1.value, R2.value
+
+
+def kappa_at(op: OracleProblem, y):
+    """The curvature indicator (largest absolute principal curvature) at y on M."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return lib().orc_kappa_at(C.byref(op.man), _dptr(y))
 
 
 def normal_coord(op: OracleProblem, x):

@@ -35,12 +35,14 @@ import numpy as np
 FUNC_POLY = 0
 FUNC_TORUS_FOURIER = 1
 FUNC_SPHERE_QUAD = 2
+FUNC_REVOLUTION_QUAD = 3   # c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on a hypersurface of revolution
 
 MANIFOLD_EUCLID = 0
 MANIFOLD_SPHERE = 1
 MANIFOLD_TORUS = 2
 MANIFOLD_EMBEDDED_SPHERE = 3
 MANIFOLD_POINT_CLOUD = 4
+MANIFOLD_REVOLUTION = 5    # {(xh, t): |xh| = R(t)} about the last axis, dumbbell profile (Example 2)
 
 SAMPLER_FULL = 0      # n Gaussians per direction
 SAMPLER_REDUCED = 1   # dimension-reduced exact sampler (tracked coordinates + chi^2 remainder)
@@ -86,6 +88,11 @@ class Func:
                     modes=[(int(t[1]), int(t[2]), int(t[3]), int(t[4])) for t in terms])
 
     @staticmethod
+    def revolution_quad(c1: float, c2: float, v: np.ndarray, a_diag: np.ndarray, apply_op: bool) -> "Func":
+        return Func(kind=FUNC_REVOLUTION_QUAD, apply_op=int(apply_op), coef=[float(c1), float(c2)],
+                    v=np.ascontiguousarray(v, dtype=np.float64), A=np.ascontiguousarray(a_diag, dtype=np.float64))
+
+    @staticmethod
     def sphere_quad(c0: float, v: np.ndarray, A: np.ndarray, apply_op: bool) -> "Func":
         return Func(kind=FUNC_SPHERE_QUAD, apply_op=int(apply_op), c0=float(c0),
                     v=np.ascontiguousarray(v, dtype=np.float64),
@@ -123,6 +130,8 @@ class Manifold:
     k_nn: int = 16
     c_h: float = 2.4
     cp_mode: int = CLOUD_CP_FIT
+    prof_alpha: float = 0.0   # hypersurface of revolution: R(t) = sqrt(1 - (t/k)^2) (1 - al + 2 al (t/k)^2)
+    prof_kappa: float = 0.0
 
 
 @dataclass
@@ -440,3 +449,40 @@ def torus_cut(P: int = 100, walks: int = 2000, seed: int = 0, R: float = 1.0, a:
     pts = torus_points(th, ph, R, a)
     exact = torus_series_value(terms, th, ph)
     return Workload("torus_cut_e1", prob, pts, walks, Params(eps=1e-5), exact, "f32")
+
+
+# ----------------------------------------------------------------------------
+# Example 2: the dumbbell hypersurface of revolution in R^1001
+# ----------------------------------------------------------------------------
+
+def dumbbell_profile(t: np.ndarray, alpha: float = 0.35, kappa: float = 1.2) -> np.ndarray:
+    """R(t) = sqrt(1 - (t/kappa)^2) (1 - alpha + 2 alpha (t/kappa)^2) (Example 2's profile)."""
+    s = np.asarray(t) / kappa
+    return np.sqrt(1.0 - s * s) * (1.0 - alpha + 2.0 * alpha * s * s)
+
+
+def dumbbell(P: int = 100, walks: int = 1000, n: int = 1001, seed: int = 0, alpha: float = 0.35,
+             kappa: float = 1.2) -> Workload:
+    """Example 2: M = {x = (xh, t) in R^n : |xh| = R(t)}, closed, d = n - 1, sigma = 2d,
+    u = 0.15 t + 0.05 t^2 + v1.xh + 0.2 xh^T diag(a) xh, v1 = (1, ..., 1)/sqrt(n-1),
+    sum_j a_j = 0 (a seeded: centred normal draws); theta = 0.95, c_kappa = 1.2.
+
+    Query points: t = kappa s with s uniform in [-0.9, 0.9] (away from the two tips),
+    xh = R(t) w with w uniform on S^{n-2}."""
+    g = _rng(seed)
+    m = n - 1
+    a = g.standard_normal(m)
+    a -= a.mean()
+    v = np.full(m, 1.0 / math.sqrt(m))
+    A = 0.2 * a
+    man = Manifold(MANIFOLD_REVOLUTION, n=n, d=n - 1, prof_alpha=alpha, prof_kappa=kappa)
+    sigma = 2.0 * (n - 1)
+    prob = Problem(man, sigma=sigma, closed=True, f=Func.revolution_quad(0.15, 0.05, v, A, apply_op=True),
+                   g=Func.const(0.0))
+    t = kappa * g.uniform(-0.9, 0.9, P)
+    w = g.standard_normal((P, m))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    xh = dumbbell_profile(t, alpha, kappa)[:, None] * w
+    pts = np.ascontiguousarray(np.concatenate([xh, t[:, None]], axis=1))
+    exact = 0.15 * t + 0.05 * t * t + xh @ v + (xh * xh) @ A
+    return Workload("dumbbell_e2", prob, pts, walks, Params(theta=0.95, c_kappa=1.2), exact, "f32")
