@@ -212,6 +212,8 @@ def secondary_leg(M, ctx):
          W.SAMPLER_FULL, "Example 1 cut torus, 100 pts x 1e5 walks, exact mismatch m (predictor u), FP32"),
         ("sphere_cloud_e4_fp32", lambda: W.sphere_cloud_legendre(P=100, walks=1), 8000, M.FP32, W.SAMPLER_FULL,
          "Example 4 S^2 as 8000 points, k_nn = 6, nearest-point cp, 100 pts x 8000 walks, FP32"),
+        ("dumbbell_e2_fp32", lambda: W.dumbbell(P=100, walks=1), 1000, M.FP32, W.SAMPLER_FULL,
+         "Example 2 dumbbell in R^1001 (sigma = 2000, Newton cp), 100 pts x 1000 walks, full sampler, FP32"),
     ]
     out = {}
     for name, make, N, prec, sampler, desc in cases:

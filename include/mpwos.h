@@ -47,6 +47,10 @@ extern "C" {
 #define MPWOS_TORUS 2             /* torus in R^3, centre radius R, tube radius a */
 #define MPWOS_EMBEDDED_SPHERE 3   /* Q S^d + b, Q (n x (d+1)) orthonormal columns */
 #define MPWOS_POINT_CLOUD 4       /* closed surface in R^3 given by points (Sec. 2.1 (iii)) */
+#define MPWOS_REVOLUTION 5        /* implicit hypersurface of revolution about the last axis,
+                                     {(xh, t) : |xh| = R(t)}, Example 2's dumbbell profile
+                                     R(t) = sqrt(1 - (t/k)^2) (1 - al + 2 al (t/k)^2);
+                                     cp by Newton's method in the profile parameter         */
 
 /* ---- closest point on a point cloud ------------------------------------ */
 #define MPWOS_CLOUD_CP_FIT 0      /* k nearest, PCA plane, quadratic height fit, projection */
@@ -56,6 +60,8 @@ extern "C" {
 #define MPWOS_FUNC_POLY 0          /* sum_t coef_t prod_j x[var]^pw (ambient coords)  */
 #define MPWOS_FUNC_TORUS_FOURIER 1 /* sum_t coef_t T(m theta) P(q phi); T,P in {cos,sin} */
 #define MPWOS_FUNC_SPHERE_QUAD 2   /* c0 + v.s + s^T A s, s = intrinsic unit vector   */
+#define MPWOS_FUNC_REVOLUTION_QUAD 3 /* c0 + coef[0] t + coef[1] t^2 + v.xh + sum_j A_j xh_j^2 on
+                                        MPWOS_REVOLUTION (v, A: n - 1 entries, A diagonal) */
 
 /* ---- compensation term m_* (Sec. 2.3.3; m of eq. mismatch_definition) ---- */
 #define MPWOS_COMP_NONE 0      /* m_* = 0: the baseline method                              */
@@ -109,6 +115,7 @@ typedef struct {
   int k_nn;         /* 1 .. 32                                            */
   double c_h;
   int cp_mode;      /* MPWOS_CLOUD_CP_FIT or MPWOS_CLOUD_CP_NEAREST        */
+  double prof_alpha, prof_kappa;   /* REVOLUTION: al in (0, 1/2), k > 0   */
 } mpwos_manifold_desc;
 
 /* A function on M given as a small closed family of device-evaluable forms.

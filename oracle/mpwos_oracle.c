@@ -670,9 +670,9 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
     return total;
   }
   if (f->kind == ORC_REVOLUTION_QUAD) {
-    /* u = c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on |xh| = R(t).  With xh = R w
+    /* u = c0 + c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on |xh| = R(t).  With xh = R w
      * (w on the unit sphere S^{n-2}), u = h0(t) + R (v.w) + R^2 (w^T A w - mA),
-     * h0 = c1 t + c2 t^2 + mA R^2, mA = tr(A)/(n-1): degree-0, 1 and 2 spherical
+     * h0 = c0 + c1 t + c2 t^2 + mA R^2, mA = tr(A)/(n-1): degree-0, 1 and 2 spherical
      * harmonics with -Delta_{S^{n-2}} eigenvalues 0, n-2 and 2(n-1).  On the
      * surface of revolution (metric (1 + R'^2) dt^2 + R^2 dw^2),
      *   Delta_M (h(t) Y_k) = [ (h'' + (n-2) R' h'/R - h' R' R''/(1+R'^2)) / (1+R'^2)
@@ -692,7 +692,7 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
     }
     double c1 = f->coef[0], c2 = f->coef[1];
     double mA = trA / (double)(n - 1);
-    double u = c1 * t + c2 * t * t + R * vw + R * R * aw;
+    double u = f->c0 + c1 * t + c2 * t * t + R * vw + R * R * aw;
     if (!f->apply_op) return u;
     double md = (double)(n - 2), G2 = 1.0 + R1 * R1;
     double h0p = c1 + 2.0 * c2 * t + 2.0 * mA * R * R1;

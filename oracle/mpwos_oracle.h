@@ -55,7 +55,7 @@ typedef struct {
   double c0;              /* sphere quad: u = c0 + v.s + s^T A s               */
   const double* v;        /* d+1 (revolution quad: n-1)                        */
   const double* A;        /* (d+1)^2 row-major (revolution quad: the n-1 diagonal entries) */
-  /* revolution quad: u = coef[0] t + coef[1] t^2 + v.xh + sum_j A_j xh_j^2, t = x_{n-1} */
+  /* revolution quad: u = c0 + coef[0] t + coef[1] t^2 + v.xh + sum_j A_j xh_j^2, t = x_{n-1} */
 } orc_func;
 
 enum { ORC_COMP_NONE = 0, ORC_COMP_NORMAL2 = 1, ORC_COMP_EXACT = 2 };

@@ -39,7 +39,8 @@ class MpwosError(RuntimeError):
 class ManifoldDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int), ("d", C.c_int), ("R", C.c_double), ("a", C.c_double),
                 ("Q", _dp), ("b", _dp), ("cloud", _dp), ("n_cloud", C.c_int64), ("k_nn", C.c_int),
-                ("c_h", C.c_double), ("cp_mode", C.c_int)]
+                ("c_h", C.c_double), ("cp_mode", C.c_int), ("prof_alpha", C.c_double),
+                ("prof_kappa", C.c_double)]
 
 
 class Func(C.Structure):
@@ -132,13 +133,16 @@ class _Marshal:
             cf.coef = self.arr(coef).ctypes.data_as(_dp)
             cf.modes = self.arr(modes, np.int32).ctypes.data_as(_ip)
         else:
+            if f.kind == W.FUNC_REVOLUTION_QUAD:
+                cf.coef = self.arr(np.asarray(f.coef, dtype=np.float64)).ctypes.data_as(_dp)
             cf.v = self.arr(f.v).ctypes.data_as(_dp)
             cf.A = self.arr(f.A).ctypes.data_as(_dp)
         return cf
 
     def problem(self, problem):
         m = problem.manifold
-        md = ManifoldDesc(kind=m.kind, n=m.n, d=m.d, R=m.R, a=m.a)
+        md = ManifoldDesc(kind=m.kind, n=m.n, d=m.d, R=m.R, a=m.a, prof_alpha=getattr(m, "prof_alpha", 0.0),
+                          prof_kappa=getattr(m, "prof_kappa", 0.0))
         if m.Q is not None:
             md.Q = self.arr(m.Q).ctypes.data_as(_dp)
             md.b = self.arr(m.b).ctypes.data_as(_dp)

@@ -10,8 +10,8 @@ constexpr int kMaxTerms = 32;       // terms of a POLY / TORUS function
 constexpr int kMaxPolyFactors = 64; // total (var, pow) factors of a POLY
 constexpr int kMaxQuadDim = 32;     // d + 1 of a SPHERE_QUAD / embedded sphere
 
-enum ManifoldKind : int { kEuclid = 0, kSphere = 1, kTorus = 2, kEmbeddedSphere = 3, kPointCloud = 4 };
-enum FuncKind : int { kPoly = 0, kTorusFourier = 1, kSphereQuad = 2 };
+enum ManifoldKind : int { kEuclid = 0, kSphere = 1, kTorus = 2, kEmbeddedSphere = 3, kPointCloud = 4, kRevolution = 5 };
+enum FuncKind : int { kPoly = 0, kTorusFourier = 1, kSphereQuad = 2, kRevolutionQuad = 3 };
 
 // A function on M (f or g), copied by value into the kernel parameters.
 struct DevFunc {
@@ -142,6 +142,9 @@ struct DevProblem {
   const double* red_y0;
   // compensation term (last, so the fields above keep their offsets)
   DevPredictor pred;
+  // hypersurface of revolution: profile parameters, c_kappa, tr(A)/(n-1) of f
+  double rv_alpha, rv_kappa, rv_mA;
+  float rv_alpha_f, rv_kappa_f, rv_mA_f, rv_ck_f;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {

@@ -21,6 +21,7 @@
 
 #include "../../include/mpwos.h"
 #include "launch.h"
+#include "revolution.cuh"
 
 using namespace mpwos;
 
@@ -186,6 +187,14 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       if (!m->Q || !m->b) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs Q and b");
       if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE supports the closed problem only");
       break;
+    case MPWOS_REVOLUTION:
+      if (m->n < 4 || m->d != m->n - 1) return fail(ctx, MPWOS_EINVAL, "REVOLUTION needs n >= 4 and d == n - 1");
+      if (!(m->prof_alpha > 0.0 && m->prof_alpha < 0.5 && m->prof_kappa > 0.0))
+        return fail(ctx, MPWOS_EINVAL, "REVOLUTION needs 0 < prof_alpha < 1/2 and prof_kappa > 0");
+      if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "REVOLUTION supports the closed problem only");
+      if (pr->f.kind != MPWOS_FUNC_REVOLUTION_QUAD) return fail(ctx, MPWOS_EINVAL, "REVOLUTION source must be REVOLUTION_QUAD");
+      if (pa->sampler != MPWOS_SAMPLER_FULL) return fail(ctx, MPWOS_EINVAL, "REVOLUTION needs the full sampler");
+      break;
     case MPWOS_POINT_CLOUD:
       if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD lives in R^3 (n = 3, d = 2)");
       if (!m->cloud) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD needs cloud");
@@ -231,6 +240,9 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       for (int t = 0; t < f->n_terms; ++t)
         if (f->modes[4 * t] < 0 || f->modes[4 * t] > 64 || f->modes[4 * t + 1] < 0 || f->modes[4 * t + 1] > 64)
           return fail(ctx, MPWOS_EINVAL, "torus mode numbers must lie in [0, 64]");
+    } else if (f->kind == MPWOS_FUNC_REVOLUTION_QUAD) {
+      if (m->kind != MPWOS_REVOLUTION) return fail(ctx, MPWOS_EINVAL, "REVOLUTION_QUAD needs the REVOLUTION manifold");
+      if (f->n_terms != 2 || !f->coef || !f->v || !f->A) return fail(ctx, MPWOS_EINVAL, "REVOLUTION_QUAD needs 2 coef, v and A");
     } else if (f->kind == MPWOS_FUNC_SPHERE_QUAD) {
       if (!(m->kind == MPWOS_EMBEDDED_SPHERE || (m->kind == MPWOS_SPHERE && m->n == 3)))
         return fail(ctx, MPWOS_EINVAL, "SPHERE_QUAD needs EMBEDDED_SPHERE or the sphere in R^3");
@@ -591,6 +603,25 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
       if (!df->v || !df->A || !df->vf || !df->Af) return fail(ctx, MPWOS_ENOMEM, "SPHERE_QUAD data");
     }
   }
+  // hypersurface of revolution: f's v and diag(A) (n - 1 entries), profile, tr(A)/(n-1)
+  if (m->kind == MPWOS_REVOLUTION) {
+    const int nh = n - 1;
+    std::vector<float> vf(pr->f.v, pr->f.v + nh), Af(pr->f.A, pr->f.A + nh);
+    pb.f.v = sc.upload(pr->f.v, nh);
+    pb.f.A = sc.upload(pr->f.A, nh);
+    pb.f.vf = sc.upload(vf.data(), nh);
+    pb.f.Af = sc.upload(Af.data(), nh);
+    if (!pb.f.v || !pb.f.A || !pb.f.vf || !pb.f.Af) return fail(ctx, MPWOS_ENOMEM, "REVOLUTION_QUAD data");
+    double trA = 0.0;
+    for (int i = 0; i < nh; ++i) trA += pr->f.A[i];
+    pb.rv_alpha = m->prof_alpha;
+    pb.rv_kappa = m->prof_kappa;
+    pb.rv_mA = trA / nh;
+    pb.rv_alpha_f = static_cast<float>(m->prof_alpha);
+    pb.rv_kappa_f = static_cast<float>(m->prof_kappa);
+    pb.rv_mA_f = static_cast<float>(pb.rv_mA);
+    pb.rv_ck_f = static_cast<float>(pa->c_kappa);
+  }
   // query points
   if (is_device_ptr(pts)) {
     pb.pts = pts;
@@ -684,8 +715,19 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     // h at an off-cloud point stays near h at its neighbours; 1.5 x max over the cloud
     rho_geo_max = m->c_h * 1.5 * G->h_max;
   }
+  // hypersurface of revolution: rho_geo = c_kappa / (1 + kappa(y)) varies; its
+  // largest value from the smallest curvature over a dense scan of the profile
+  if (m->kind == MPWOS_REVOLUTION) {
+    double kmin = INFINITY;
+    const double lim = m->prof_kappa * (1.0 - 1e-6);
+    for (int j = 0; j <= 20000; ++j) {
+      const double t = -lim + 2.0 * lim * j / 20000.0;
+      kmin = std::min(kmin, rev_kappa<double>(rev_profile<double>(t, m->prof_alpha, m->prof_kappa)));
+    }
+    rho_geo_max = pa->c_kappa / (1.0 + 0.99 * kmin);
+  }
   // radius tables
-  const bool fixed_radius = pr->closed && m->kind != MPWOS_POINT_CLOUD;
+  const bool fixed_radius = pr->closed && m->kind != MPWOS_POINT_CLOUD && m->kind != MPWOS_REVOLUTION;
   const double a_max = pb.sqrt_sigma * pb.theta * rho_geo_max;
   const double nu = 0.5 * (n - 2);
   if (n > 3 && 0.25 * a_max * a_max > 0.5 * nu)
@@ -1054,8 +1096,8 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   CK(cudaSetDevice(ctx->device));
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
-  if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD)
-    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE and POINT_CLOUD are not supported (use mpwos_solve)");
+  if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD || m->kind == MPWOS_REVOLUTION)
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE, POINT_CLOUD and REVOLUTION are not supported (use mpwos_solve)");
   if (prm->sampler != MPWOS_SAMPLER_FULL)
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: the reduced sampler is not supported (use mpwos_solve)");
   if (prob->comp != MPWOS_COMP_NONE)
@@ -1202,6 +1244,10 @@ struct OwnedFunc {
     } else if (src.kind == MPWOS_FUNC_SPHERE_QUAD) {
       v.assign(src.v, src.v + D);
       A.assign(src.A, src.A + static_cast<size_t>(D) * D);
+      f.v = v.data(); f.A = A.data();
+    } else if (src.kind == MPWOS_FUNC_REVOLUTION_QUAD) {   // D = n - 1: v and diag(A)
+      v.assign(src.v, src.v + D);
+      A.assign(src.A, src.A + D);
       f.v = v.data(); f.A = A.data();
     }
   }
@@ -1523,7 +1569,7 @@ int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_probl
   r->man = *m;
   r->prob = *prob;
   r->prm = *prm;
-  const int D = (m->kind == MPWOS_SPHERE && m->n == 3) ? 3 : m->d + 1;
+  const int D = (m->kind == MPWOS_SPHERE && m->n == 3) ? 3 : (m->kind == MPWOS_REVOLUTION ? m->n - 1 : m->d + 1);
   r->f.take(prob->f, D);
   r->prob.f = r->f.f;
   if (!prob->closed) {

@@ -15,9 +15,13 @@
 //   Theta direction: blocks [0, nb);  Z_l direction: blocks [nb(1+l), nb(2+l));
 //   FP64: U_l = u53(x, y) of block nb(1+N_V) + l  (identical to the CPU oracle);
 //   FP32: U_l = u23(word l mod 4) of block nb(1+N_V) + l/4.
+// The hypersurface of revolution (revolution.cuh) keeps Y in the ambient layout;
+// its closest point needs |Yh|^2 and Y_{n-1} (one reduction), then the same
+// Newton iteration in every lane.
 #pragma once
 #include "dev_common.cuh"
 #include "green.cuh"
+#include "revolution.cuh"
 
 namespace mpwos {
 
@@ -268,6 +272,23 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
     vT = kF64 ? reinterpret_cast<const T*>(pb.f.v) : reinterpret_cast<const T*>(pb.f.vf);
     AT = kF64 ? reinterpret_cast<const T*>(pb.f.A) : reinterpret_cast<const T*>(pb.f.Af);
   }
+  // hypersurface of revolution: v and diag(A) of f (n - 1 entries), profile, c_kappa
+  const T* vR = nullptr;
+  const T* aR = nullptr;
+  T rv_al = T(0), rv_k = T(1), rv_mA = T(0), ck_t = T(0), c0_t = T(0), c1_t = T(0), c2_t = T(0);
+  const T sig_t = pick<T>(pb.sigma, pb.sf.sigma);
+  if constexpr (MK == kRevolution) {
+    vR = kF64 ? reinterpret_cast<const T*>(pb.f.v) : reinterpret_cast<const T*>(pb.f.vf);
+    aR = kF64 ? reinterpret_cast<const T*>(pb.f.A) : reinterpret_cast<const T*>(pb.f.Af);
+    rv_al = pick<T>(pb.rv_alpha, pb.rv_alpha_f);
+    rv_k = pick<T>(pb.rv_kappa, pb.rv_kappa_f);
+    rv_mA = pick<T>(pb.rv_mA, pb.rv_mA_f);
+    ck_t = pick<T>(pb.c_kappa, pb.rv_ck_f);
+    c0_t = pick<T>(pb.f.c0, pb.f.c0_f);
+    c1_t = pick<T>(pb.f.coef[0], pb.f.coef_f[0]);
+    c2_t = pick<T>(pb.f.coef[1], pb.f.coef_f[1]);
+  }
+  T ty = T(0);   // revolution: the axis coordinate Y_{n-1}
 
   T Y[L];          // ambient state (sphere, R^n)
   T sj = T(0);     // intrinsic state (embedded sphere), lane j < D
@@ -308,6 +329,7 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
           const int c = G * (lane + 32 * m) + q;
           Y[G * m + q] = c < n ? T(y0[c]) : T(0);
         }
+      if constexpr (MK == kRevolution) ty = T(y0[n - 1]);
       if (bnd) state_dots();
     }
   };
@@ -370,7 +392,9 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
       continue;
     }
     // ---- radius and weights -------------------------------------------------
-    const T r = theta_t * (dG < rgeo_t ? dG : rgeo_t);
+    T rg = rgeo_t;   // rho_geo = c_kappa / (1 + kappa(Y)) (eq. rho_geo_curvature)
+    if constexpr (MK == kRevolution) rg = ck_t / (T(1) + rev_kappa<T>(rev_profile<T>(ty, rv_al, rv_k)));
+    const T r = theta_t * (dG < rg ? dG : rg);
     const T a = sqs_t * r;
     if (r != r_prev) {
       if constexpr (kF64) {
@@ -417,6 +441,33 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
         for (int q = 0; q < L; ++q) { acc[0] += g[q] * g[q]; acc[1] += Y[q] * g[q]; }
         warp_sum<2>(acc);
         const T zs = (r * t) / sqrt(fmax(acc[0], T(1e-30)));
+        if constexpr (MK == kRevolution) {
+          // Z = Y + zs g; |Zh|^2, v.Zh, Zh^T diag(A) Zh and Z_{n-1} in one reduction
+          T za[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+          for (int m = 0; m < MB; ++m)
+#pragma unroll
+            for (int q = 0; q < G; ++q) {
+              const int cc = G * (lane + 32 * m) + q;
+              const T zc = Y[G * m + q] + zs * g[G * m + q];
+              if (cc < n - 1) {
+                za[0] += zc * zc;
+                za[1] += vR[cc] * zc;
+                za[2] += aR[cc] * zc * zc;
+              } else if (cc == n - 1) {
+                za[3] = zc;
+              }
+            }
+          warp_sum<4>(za);
+          const T rho0 = sqrt(za[0]);
+          Profile<T> P;
+          const T tz = rev_cp_t<T>(rho0, za[3], rv_al, rv_k, P);
+          // on the axis cp takes the direction e_1 (w = e_1)
+          const T vw = rho0 > T(0) ? za[1] / rho0 : vR[0];
+          const T aw = rho0 > T(0) ? za[2] / (rho0 * rho0) : aR[0];
+          F += rev_quad_value<T>(P, tz, vw, aw, rv_mA, c0_t, c1_t, c2_t, sig_t, n, pb.f.apply_op != 0);
+          continue;
+        }
         T inv = T(1);
         if constexpr (MK == kSphere) {
           if constexpr (kF64) {
@@ -441,6 +492,38 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
       const T tj = lane < D ? sj + sc * qgj : T(0);
       const T tn = sqrt(warp_sum1(tj * tj));
       sj = tj / tn;
+    } else if constexpr (MK == kRevolution) {
+      // Theta = Y + r g/|g|; Y = cp(Theta): scale Theta_h to R(t)/|Theta_h|, Y_{n-1} = t
+      T gg = T(0);
+#pragma unroll
+      for (int q = 0; q < L; ++q) gg += g[q] * g[q];
+      gg = fmax(warp_sum1(gg), T(1e-30));
+      const T sc = r / sqrt(gg);
+      T ta[2] = {T(0), T(0)};
+#pragma unroll
+      for (int m = 0; m < MB; ++m)
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          const int cc = G * (lane + 32 * m) + q;
+          const T th = Y[G * m + q] + sc * g[G * m + q];
+          Y[G * m + q] = th;
+          if (cc < n - 1) ta[0] += th * th;
+          else if (cc == n - 1) ta[1] = th;
+        }
+      warp_sum<2>(ta);
+      const T rho0 = sqrt(ta[0]);
+      Profile<T> P;
+      ty = rev_cp_t<T>(rho0, ta[1], rv_al, rv_k, P);
+      const T sR = rho0 > T(0) ? P.R / rho0 : T(0);
+#pragma unroll
+      for (int m = 0; m < MB; ++m)
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          const int cc = G * (lane + 32 * m) + q;
+          T& yc = Y[G * m + q];
+          if (cc < n - 1) yc = rho0 > T(0) ? yc * sR : (cc == 0 ? P.R : T(0));
+          else if (cc == n - 1) yc = ty;
+        }
     } else if constexpr (kF64) {
       T gg = T(0);
 #pragma unroll

@@ -35,7 +35,7 @@ import numpy as np
 FUNC_POLY = 0
 FUNC_TORUS_FOURIER = 1
 FUNC_SPHERE_QUAD = 2
-FUNC_REVOLUTION_QUAD = 3   # c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on a hypersurface of revolution
+FUNC_REVOLUTION_QUAD = 3   # c0 + c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on a hypersurface of revolution
 
 MANIFOLD_EUCLID = 0
 MANIFOLD_SPHERE = 1
@@ -88,8 +88,9 @@ class Func:
                     modes=[(int(t[1]), int(t[2]), int(t[3]), int(t[4])) for t in terms])
 
     @staticmethod
-    def revolution_quad(c1: float, c2: float, v: np.ndarray, a_diag: np.ndarray, apply_op: bool) -> "Func":
-        return Func(kind=FUNC_REVOLUTION_QUAD, apply_op=int(apply_op), coef=[float(c1), float(c2)],
+    def revolution_quad(c1: float, c2: float, v: np.ndarray, a_diag: np.ndarray, apply_op: bool,
+                        c0: float = 0.0) -> "Func":
+        return Func(kind=FUNC_REVOLUTION_QUAD, apply_op=int(apply_op), coef=[float(c1), float(c2)], c0=float(c0),
                     v=np.ascontiguousarray(v, dtype=np.float64), A=np.ascontiguousarray(a_diag, dtype=np.float64))
 
     @staticmethod

@@ -115,3 +115,13 @@ def test_small_dumbbell_walk_mean():
     m, se, ms, nf = O.solve(w.problem, w.params, w.points, 1500)
     assert nf == 0 and np.all(ms > 5)
     assert np.all(np.abs(m - w.exact) < 4 * se + 0.03), (m, w.exact, se)
+
+
+def test_constant_solution_telescopes():
+    """u = 1 (c0 = 1, f = sigma): S = 1 - W_K exactly, W_K < tau_W."""
+    w, _ = _op(1001, seed=5)
+    f = w.problem.f
+    w.problem.f = W.Func.revolution_quad(0.0, 0.0, np.zeros_like(f.v), np.zeros_like(f.A), apply_op=True, c0=1.0)
+    S, K, F = O.walk_scores(w.problem, w.params, w.points[:2], 6)
+    assert not F.any()
+    assert np.all((S > 1 - w.params.tau_w - 1e-12 * K) & (S <= 1 + 1e-12 * K))
