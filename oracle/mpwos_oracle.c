@@ -302,6 +302,45 @@ static double rev_cp_t(const orc_manifold* m, double rho0, double t0) {
   return t;
 }
 
+/* ---- Fourier curve x sphere (Example 3) ----------------------------------- */
+/* C(phi) = R (cos phi, sin phi, cos 2phi / 2, sin 2phi / 2, cos 3phi / 3, sin 3phi / 3)
+ * and its first two phi-derivatives. */
+static void fourier_curve(double R, double ph, double* C, double* C1, double* C2) {
+  for (int k = 1; k <= 3; ++k) {
+    double c = cos(k * ph), s = sin(k * ph);
+    C[2 * k - 2] = R * c / k;
+    C[2 * k - 1] = R * s / k;
+    C1[2 * k - 2] = -R * s;
+    C1[2 * k - 1] = R * c;
+    C2[2 * k - 2] = -R * k * c;
+    C2[2 * k - 1] = -R * k * s;
+  }
+}
+
+/* Minimise |C(phi) - xh|^2 by Newton's method on C'.(C - xh) = 0 from the angle
+ * of (x_1, x_2); where |C'|^2 + C''.(C - xh) falls below 0.1 |C'|^2 the
+ * Gauss-Newton derivative |C'|^2 is used; stops at a step below 1e-15 (1 + |phi|)
+ * or after 60 steps. */
+double orc_curve_cp_phi(const orc_manifold* m, const double* x) {
+  double ph = atan2(x[1], x[0]);
+  for (int it = 0; it < 60; ++it) {
+    double C[6], C1[6], C2[6];
+    fourier_curve(m->R, ph, C, C1, C2);
+    double F = 0.0, g2 = 0.0, h = 0.0;
+    for (int i = 0; i < 6; ++i) {
+      F += C1[i] * (C[i] - x[i]);
+      g2 += C1[i] * C1[i];
+      h += C2[i] * (C[i] - x[i]);
+    }
+    double J = g2 + h;
+    if (!(J > 0.1 * g2)) J = g2;
+    double pn = ph - F / J;
+    if (fabs(pn - ph) <= 1e-15 * (1.0 + fabs(ph))) { ph = pn; break; }
+    ph = pn;
+  }
+  return ph;
+}
+
 void orc_cp(const orc_manifold* m, const double* x, double* out) {
   int n = m->n;
   if (m->kind == ORC_EUCLID) {
@@ -319,6 +358,13 @@ void orc_cp(const orc_manifold* m, const double* x, double* out) {
     for (int i = 0; i < 3; ++i) out[i] = c[i] + s * w[i];
   } else if (m->kind == ORC_POINT_CLOUD) {
     cloud_cp(m, x, out);
+  } else if (m->kind == ORC_CURVE_SPHERE) {
+    double ph = orc_curve_cp_phi(m, x);
+    double C[6], C1[6], C2[6];
+    fourier_curve(m->R, ph, C, C1, C2);
+    for (int i = 0; i < 6; ++i) out[i] = C[i];
+    double ns = sqrt(x[6] * x[6] + x[7] * x[7] + x[8] * x[8]);
+    for (int i = 6; i < 9; ++i) out[i] = x[i] * (m->a / ns);
   } else if (m->kind == ORC_REVOLUTION) {
     double rho0 = 0.0;
     for (int i = 0; i < n - 1; ++i) rho0 += x[i] * x[i];
@@ -504,6 +550,12 @@ static double kappa_of(const orc_manifold* m) {
   /* largest absolute principal curvature (constant on these manifolds) */
   if (m->kind == ORC_EUCLID) return 0.0;
   if (m->kind == ORC_TORUS) return 1.0 / m->a;
+  if (m->kind == ORC_CURVE_SPHERE) {
+    /* the curve has constant speed |C'| = sqrt(3) R and |C''| = sqrt(14) R, so its
+     * curvature is sqrt(14) / (3 R); the sphere's is 1/a */
+    double kc = sqrt(14.0) / (3.0 * m->R), ks = 1.0 / m->a;
+    return kc > ks ? kc : ks;
+  }
   return 1.0; /* unit sphere, embedded unit sphere */
 }
 
@@ -702,6 +754,35 @@ double orc_func_eval(const orc_manifold* m, const orc_func* f, double sigma, con
     double h2p = 2.0 * R * R1, h2pp = 2.0 * R1 * R1 + 2.0 * R * R2;
     double L2 = (h2pp + md * R1 * h2p / R - h2p * R1 * R2 / G2) / G2 - 2.0 * (md + 1.0);
     return -L0 - L1 * vw - L2 * (aw - mA) + sigma * u;
+  }
+  if (f->kind == ORC_CURVE_SPHERE_FUNC) {
+    /* at x = (C(phi), a w): u = sum_t T_t(q_t phi) S_t(w), S_t = c_t + v_t.w + w^T A_t w.
+     * Delta_M = Delta_curve + Delta_{S^2(a)}; the curve has constant speed sqrt(3) R, so
+     * -Delta_curve T(q phi) = q^2 T / (3 R^2); on S^2(a) v.w has -Delta eigenvalue 2/a^2,
+     * the trace-free part of w^T A w 6/a^2, constants 0. */
+    double ph = atan2(x[1], x[0]);
+    double ns = sqrt(x[6] * x[6] + x[7] * x[7] + x[8] * x[8]);
+    double w[3] = {x[6] / ns, x[7] / ns, x[8] / ns};
+    double total = 0.0;
+    for (int t = 0; t < f->n_terms; ++t) {
+      int q = f->modes[4 * t], tk = f->modes[4 * t + 1];
+      const double* v = f->v + 3 * t;
+      const double* A = f->A + 9 * t;
+      double lin = v[0] * w[0] + v[1] * w[1] + v[2] * w[2];
+      double quad = 0.0, tr = A[0] + A[4] + A[8];
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) quad += A[3 * i + j] * w[i] * w[j];
+      double St = f->coef[t] + lin + quad;
+      double T = trig(tk, q * ph);
+      if (!f->apply_op) {
+        total += T * St;
+      } else {
+        double a2 = m->a * m->a;
+        double lap = (double)(q * q) / (3.0 * m->R * m->R) * St + 2.0 / a2 * lin + 6.0 / a2 * (quad - tr / 3.0);
+        total += T * (lap + sigma * St);
+      }
+    }
+    return total;
   }
   /* sphere quad: intrinsic unit vector s of the round sphere S^d */
   int D = m->d + 1;
@@ -1099,6 +1180,8 @@ static int run_walk_reduced(const orc_manifold* m, const orc_problem* pb, const 
  * sphere of R^3 (SPHERE_QUAD predictor).  Returns -1 for anything else. */
 static int check_problem(const orc_manifold* m, const orc_problem* pb) {
   if (m->kind == ORC_REVOLUTION && (!pb->closed || m->n < 4 || pb->f.kind != ORC_REVOLUTION_QUAD || pb->comp))
+    return -1;
+  if (m->kind == ORC_CURVE_SPHERE && (!pb->closed || m->n != 9 || pb->f.kind != ORC_CURVE_SPHERE_FUNC || pb->comp))
     return -1;
   if (m->kind == ORC_TORUS && !pb->closed && (pb->bnd_normal[2] != 0.0 || pb->bnd_offset != 0.0)) return -1;
   if (pb->comp == ORC_COMP_NONE) return 0;

@@ -26,13 +26,14 @@ extern "C" {
 #endif
 
 enum { ORC_EUCLID = 0, ORC_SPHERE = 1, ORC_TORUS = 2, ORC_EMBEDDED_SPHERE = 3, ORC_POINT_CLOUD = 4,
-       ORC_REVOLUTION = 5 };
+       ORC_REVOLUTION = 5, ORC_CURVE_SPHERE = 6 };
 enum { ORC_CP_FIT = 0, ORC_CP_NEAREST = 1 };
-enum { ORC_POLY = 0, ORC_TORUS_FOURIER = 1, ORC_SPHERE_QUAD = 2, ORC_REVOLUTION_QUAD = 3 };
+enum { ORC_POLY = 0, ORC_TORUS_FOURIER = 1, ORC_SPHERE_QUAD = 2, ORC_REVOLUTION_QUAD = 3, ORC_CURVE_SPHERE_FUNC = 4 };
 
 typedef struct {
   int kind, n, d;
-  double R, a;            /* torus: centre-circle radius, tube radius          */
+  double R, a;            /* torus: centre-circle radius, tube radius; curve x
+                             sphere (Example 3, n = 9): curve scale, sphere radius */
   const double* Q;        /* embedded sphere: n x (d+1) row-major, orthonormal */
   const double* b;        /* embedded sphere: shift, length n                  */
   const double* cloud;    /* point cloud: n_cloud x 3                          */
@@ -56,6 +57,8 @@ typedef struct {
   const double* v;        /* d+1 (revolution quad: n-1)                        */
   const double* A;        /* (d+1)^2 row-major (revolution quad: the n-1 diagonal entries) */
   /* revolution quad: u = c0 + coef[0] t + coef[1] t^2 + v.xh + sum_j A_j xh_j^2, t = x_{n-1} */
+  /* curve x sphere: u = sum_t T_t(q_t phi) (coef[t] + v_t.w + w^T A_t w), modes[4t] = q_t,
+   * modes[4t+1] = trig (0 cos, 1 sin), v_t = v[3t..], A_t = A[9t..] row-major */
 } orc_func;
 
 enum { ORC_COMP_NONE = 0, ORC_COMP_NORMAL2 = 1, ORC_COMP_EXACT = 2 };
@@ -127,6 +130,9 @@ double orc_comp_m(const orc_manifold* m, const orc_problem* pb, const double* x)
  * indicator (largest absolute principal curvature) at a point of M */
 void   orc_profile(const orc_manifold* m, double t, double* R, double* R1, double* R2);
 double orc_kappa_at(const orc_manifold* m, const double* y);
+/* curve x sphere: phi of the nearest point of the Fourier curve to the first six
+ * coordinates of x (Newton's method from the angle of (x_1, x_2)) */
+double orc_curve_cp_phi(const orc_manifold* m, const double* x);
 /* point cloud: k nearest (by distance^2, then index), mean distance h(x) */
 double orc_cloud_knn(const orc_manifold* m, const double* x, int64_t* idx, double* d2);
 

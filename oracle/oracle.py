@@ -10,7 +10,7 @@ import numpy as np
 from .build import build
 
 __all__ = ["lib", "philox", "u53", "gaussians", "chi2", "tracked_set", "em1", "c_sigma_r", "green_cdf", "green_cdf_inv",
-           "kt_minus_one", "cp", "delta_gamma", "func_eval", "profile", "kappa_at", "normal_coord", "comp_R", "comp_m", "walk_scores", "solve", "trace",
+           "kt_minus_one", "cp", "delta_gamma", "func_eval", "profile", "kappa_at", "curve_cp_phi", "normal_coord", "comp_R", "comp_m", "walk_scores", "solve", "trace",
            "OracleProblem", "cloud_knn"]
 
 _lib: Optional[C.CDLL] = None
@@ -74,6 +74,7 @@ def lib() -> C.CDLL:
         L.orc_cloud_knn.restype = C.c_double
         L.orc_normal_coord.restype = C.c_double
         L.orc_kappa_at.restype = C.c_double
+        L.orc_curve_cp_phi.restype = C.c_double
         L.orc_comp_R.restype = C.c_double
         L.orc_comp_R.argtypes = [C.c_void_p, C.c_void_p, _dp, C.c_double]
         L.orc_comp_m.restype = C.c_double
@@ -144,10 +145,13 @@ class OracleProblem:
             cf.term_off = _iptr(self._arr(off, np.int32))
             cf.var = _iptr(self._arr(var, np.int32))
             cf.pw = _iptr(self._arr(pw, np.int32))
-        elif f.kind == W.FUNC_TORUS_FOURIER:
+        elif f.kind in (W.FUNC_TORUS_FOURIER, W.FUNC_CURVE_SPHERE):
             coef, modes = f.flat_modes()
             cf.coef = _dptr(self._arr(coef))
             cf.modes = _iptr(self._arr(modes, np.int32))
+            if f.kind == W.FUNC_CURVE_SPHERE:
+                cf.v = _dptr(self._arr(f.v))
+                cf.A = _dptr(self._arr(f.A))
         else:
             if f.kind == W.FUNC_REVOLUTION_QUAD:
                 cf.coef = _dptr(self._arr(np.asarray(f.coef, dtype=np.float64)))
@@ -244,6 +248,12 @@ def profile(op: OracleProblem, t):
     R, R1, R2 = C.c_double(), C.c_double(), C.c_double()
     lib().orc_profile(C.byref(op.man), C.c_double(t), C.byref(R), C.byref(R1), C.byref(R2))
     return R.value, R1.value, R2.value
+
+
+def curve_cp_phi(op: OracleProblem, x):
+    """phi of the nearest point of the Fourier curve to x's first six coordinates."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_curve_cp_phi(C.byref(op.man), _dptr(x))
 
 
 def kappa_at(op: OracleProblem, y):

@@ -36,6 +36,7 @@ FUNC_POLY = 0
 FUNC_TORUS_FOURIER = 1
 FUNC_SPHERE_QUAD = 2
 FUNC_REVOLUTION_QUAD = 3   # c0 + c1 t + c2 t^2 + v.xh + sum_j A_j xh_j^2 on a hypersurface of revolution
+FUNC_CURVE_SPHERE = 4      # sum_t T_t(q_t phi) (c_t + v_t.w + w^T A_t w) on the Fourier curve x sphere
 
 MANIFOLD_EUCLID = 0
 MANIFOLD_SPHERE = 1
@@ -43,6 +44,7 @@ MANIFOLD_TORUS = 2
 MANIFOLD_EMBEDDED_SPHERE = 3
 MANIFOLD_POINT_CLOUD = 4
 MANIFOLD_REVOLUTION = 5    # {(xh, t): |xh| = R(t)} about the last axis, dumbbell profile (Example 2)
+MANIFOLD_CURVE_SPHERE = 6  # Fourier-embedded circle x S^2(a) in R^9 (Example 3)
 
 SAMPLER_FULL = 0      # n Gaussians per direction
 SAMPLER_REDUCED = 1   # dimension-reduced exact sampler (tracked coordinates + chi^2 remainder)
@@ -92,6 +94,14 @@ class Func:
                         c0: float = 0.0) -> "Func":
         return Func(kind=FUNC_REVOLUTION_QUAD, apply_op=int(apply_op), coef=[float(c1), float(c2)], c0=float(c0),
                     v=np.ascontiguousarray(v, dtype=np.float64), A=np.ascontiguousarray(a_diag, dtype=np.float64))
+
+    @staticmethod
+    def curve_sphere(terms, apply_op: bool) -> "Func":
+        """terms: (q, trig, c, v (3), A (3 x 3)) for T(q phi) (c + v.w + w^T A w)."""
+        return Func(kind=FUNC_CURVE_SPHERE, apply_op=int(apply_op), coef=[float(t[2]) for t in terms],
+                    modes=[(int(t[0]), int(t[1]), 0, 0) for t in terms],
+                    v=np.ascontiguousarray(np.concatenate([np.asarray(t[3], float).reshape(3) for t in terms])),
+                    A=np.ascontiguousarray(np.concatenate([np.asarray(t[4], float).reshape(9) for t in terms])))
 
     @staticmethod
     def sphere_quad(c0: float, v: np.ndarray, A: np.ndarray, apply_op: bool) -> "Func":
@@ -487,3 +497,38 @@ def dumbbell(P: int = 100, walks: int = 1000, n: int = 1001, seed: int = 0, alph
     pts = np.ascontiguousarray(np.concatenate([xh, t[:, None]], axis=1))
     exact = 0.15 * t + 0.05 * t * t + xh @ v + (xh * xh) @ A
     return Workload("dumbbell_e2", prob, pts, walks, Params(theta=0.95, c_kappa=1.2), exact, "f32")
+
+
+# ----------------------------------------------------------------------------
+# Example 3: the Fourier-embedded circle times S^2(a) in R^9
+# ----------------------------------------------------------------------------
+
+def fourier_curve(phi: np.ndarray, R: float = 1.0) -> np.ndarray:
+    """C(phi) = R (cos phi, sin phi, cos 2phi / 2, sin 2phi / 2, cos 3phi / 3, sin 3phi / 3)."""
+    phi = np.asarray(phi)
+    return R * np.stack([np.cos(phi), np.sin(phi), np.cos(2 * phi) / 2, np.sin(2 * phi) / 2,
+                         np.cos(3 * phi) / 3, np.sin(3 * phi) / 3], axis=-1)
+
+
+def curve_sphere(P: int = 100, walks: int = 1000, R: float = 1.0, a: float = 0.65, sigma: float = 2.0,
+                 seed: int = 0) -> Workload:
+    """Example 3: M = C(S^1) x S^2(a) in R^9, closed, d = 3,
+    u = cos(phi) w_1 + 0.3 sin(2 phi) w_2 + 0.2 cos(3 phi) (w_1^2 - w_2^2).
+
+    sigma is not given for this example; 2 keeps a walk near 800 steps at tau_W = 1e-8.
+    Query points: phi uniform in [0, 2 pi), w uniform on S^2 (seed)."""
+    man = Manifold(MANIFOLD_CURVE_SPHERE, n=9, d=3, R=R, a=a)
+    z3 = np.zeros(3)
+    z33 = np.zeros((3, 3))
+    terms = [(1, TRIG_COS, 0.0, np.array([1.0, 0.0, 0.0]), z33),
+             (2, TRIG_SIN, 0.0, np.array([0.0, 0.3, 0.0]), z33),
+             (3, TRIG_COS, 0.0, z3, np.diag([0.2, -0.2, 0.0]))]
+    prob = Problem(man, sigma=sigma, closed=True, f=Func.curve_sphere(terms, apply_op=True), g=Func.const(0.0))
+    g = _rng(seed)
+    phi = g.uniform(0.0, 2 * math.pi, P)
+    w = g.standard_normal((P, 3))
+    w /= np.linalg.norm(w, axis=1, keepdims=True)
+    pts = np.ascontiguousarray(np.concatenate([fourier_curve(phi, R), a * w], axis=1))
+    exact = (np.cos(phi) * w[:, 0] + 0.3 * np.sin(2 * phi) * w[:, 1]
+             + 0.2 * np.cos(3 * phi) * (w[:, 0] ** 2 - w[:, 1] ** 2))
+    return Workload("curve_sphere_e3", prob, pts, walks, Params(), exact, "f32")
