@@ -214,6 +214,8 @@ def secondary_leg(M, ctx):
          "Example 4 S^2 as 8000 points, k_nn = 6, nearest-point cp, 100 pts x 8000 walks, FP32"),
         ("dumbbell_e2_fp32", lambda: W.dumbbell(P=100, walks=1), 1000, M.FP32, W.SAMPLER_FULL,
          "Example 2 dumbbell in R^1001 (sigma = 2000, Newton cp), 100 pts x 1000 walks, full sampler, FP32"),
+        ("curve_sphere_e3_fp32", lambda: W.curve_sphere(P=100, walks=1), 10000, M.FP32, W.SAMPLER_FULL,
+         "Example 3 Fourier curve x S^2(0.65) in R^9 (Newton cp on the curve), 100 pts x 1e4 walks, FP32"),
     ]
     out = {}
     for name, make, N, prec, sampler, desc in cases:

@@ -51,6 +51,9 @@ extern "C" {
                                      {(xh, t) : |xh| = R(t)}, Example 2's dumbbell profile
                                      R(t) = sqrt(1 - (t/k)^2) (1 - al + 2 al (t/k)^2);
                                      cp by Newton's method in the profile parameter         */
+#define MPWOS_CURVE_SPHERE 6      /* Example 3: C(S^1) x S^2(a) in R^9 (n = 9, d = 3),
+                                     C(phi) = R (cos phi, sin phi, cos 2phi/2, sin 2phi/2,
+                                     cos 3phi/3, sin 3phi/3); R, a from the desc's R, a   */
 
 /* ---- closest point on a point cloud ------------------------------------ */
 #define MPWOS_CLOUD_CP_FIT 0      /* k nearest, PCA plane, quadratic height fit, projection */
@@ -62,6 +65,10 @@ extern "C" {
 #define MPWOS_FUNC_SPHERE_QUAD 2   /* c0 + v.s + s^T A s, s = intrinsic unit vector   */
 #define MPWOS_FUNC_REVOLUTION_QUAD 3 /* c0 + coef[0] t + coef[1] t^2 + v.xh + sum_j A_j xh_j^2 on
                                         MPWOS_REVOLUTION (v, A: n - 1 entries, A diagonal) */
+#define MPWOS_FUNC_CURVE_SPHERE 4  /* sum_t T_t(q_t phi) (coef[t] + v_t.w + w^T A_t w) on
+                                      MPWOS_CURVE_SPHERE, w the sphere factor's unit vector;
+                                      modes: 4 ints per term (q, trig 0 cos / 1 sin, 0, 0);
+                                      v: 3, A: 9 (row-major) entries per term           */
 
 /* ---- compensation term m_* (Sec. 2.3.3; m of eq. mismatch_definition) ---- */
 #define MPWOS_COMP_NONE 0      /* m_* = 0: the baseline method                              */

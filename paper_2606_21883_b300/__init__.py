@@ -128,10 +128,13 @@ class _Marshal:
             cf.term_off = self.arr(off, np.int32).ctypes.data_as(_ip)
             cf.var = self.arr(var, np.int32).ctypes.data_as(_ip)
             cf.pw = self.arr(pw, np.int32).ctypes.data_as(_ip)
-        elif f.kind == W.FUNC_TORUS_FOURIER:
+        elif f.kind in (W.FUNC_TORUS_FOURIER, W.FUNC_CURVE_SPHERE):
             coef, modes = f.flat_modes()
             cf.coef = self.arr(coef).ctypes.data_as(_dp)
             cf.modes = self.arr(modes, np.int32).ctypes.data_as(_ip)
+            if f.kind == W.FUNC_CURVE_SPHERE:
+                cf.v = self.arr(f.v).ctypes.data_as(_dp)
+                cf.A = self.arr(f.A).ctypes.data_as(_dp)
         else:
             if f.kind == W.FUNC_REVOLUTION_QUAD:
                 cf.coef = self.arr(np.asarray(f.coef, dtype=np.float64)).ctypes.data_as(_dp)

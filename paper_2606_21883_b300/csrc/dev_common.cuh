@@ -10,8 +10,9 @@ constexpr int kMaxTerms = 32;       // terms of a POLY / TORUS function
 constexpr int kMaxPolyFactors = 64; // total (var, pow) factors of a POLY
 constexpr int kMaxQuadDim = 32;     // d + 1 of a SPHERE_QUAD / embedded sphere
 
-enum ManifoldKind : int { kEuclid = 0, kSphere = 1, kTorus = 2, kEmbeddedSphere = 3, kPointCloud = 4, kRevolution = 5 };
-enum FuncKind : int { kPoly = 0, kTorusFourier = 1, kSphereQuad = 2, kRevolutionQuad = 3 };
+enum ManifoldKind : int { kEuclid = 0, kSphere = 1, kTorus = 2, kEmbeddedSphere = 3, kPointCloud = 4, kRevolution = 5,
+                          kCurveSphere = 6 };
+enum FuncKind : int { kPoly = 0, kTorusFourier = 1, kSphereQuad = 2, kRevolutionQuad = 3, kCurveSphereFunc = 4 };
 
 // A function on M (f or g), copied by value into the kernel parameters.
 struct DevFunc {

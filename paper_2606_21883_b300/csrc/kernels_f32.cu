@@ -50,6 +50,7 @@ static const void* walkn_f32_fn(const DevProblem& pb) {
   if (pb.mkind == kEuclid) return reinterpret_cast<const void*>(walkn_f32_kernel<kEuclid, 8>);
   if (pb.mkind == kSphere) return reinterpret_cast<const void*>(walkn_f32_kernel<kSphere, 8>);
   if (pb.mkind == kRevolution) return reinterpret_cast<const void*>(walkn_f32_kernel<kRevolution, 8>);
+  if (pb.mkind == kCurveSphere) return reinterpret_cast<const void*>(walkn_f32_kernel<kCurveSphere, 8>);
   switch (walkn_dq(pb.d + 1)) {
     case 8: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 8>);
     case 16: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 16>);
@@ -59,7 +60,8 @@ static const void* walkn_f32_fn(const DevProblem& pb) {
 }
 
 cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
-  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere && pb.mkind != kRevolution)
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere && pb.mkind != kRevolution &&
+      pb.mkind != kCurveSphere)
     return cudaErrorInvalidValue;
   DevProblem arg = pb;
   void* args[] = {&arg};

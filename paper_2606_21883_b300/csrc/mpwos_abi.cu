@@ -97,6 +97,7 @@ bool is_device_ptr(const void* p) {
 double kappa_of(const mpwos_manifold_desc* m) {
   if (m->kind == MPWOS_EUCLID) return 0.0;
   if (m->kind == MPWOS_TORUS) return 1.0 / m->a;
+  if (m->kind == MPWOS_CURVE_SPHERE) return std::max(std::sqrt(14.0) / (3.0 * m->R), 1.0 / m->a);
   return 1.0;
 }
 
@@ -195,6 +196,13 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       if (pr->f.kind != MPWOS_FUNC_REVOLUTION_QUAD) return fail(ctx, MPWOS_EINVAL, "REVOLUTION source must be REVOLUTION_QUAD");
       if (pa->sampler != MPWOS_SAMPLER_FULL) return fail(ctx, MPWOS_EINVAL, "REVOLUTION needs the full sampler");
       break;
+    case MPWOS_CURVE_SPHERE:
+      if (m->n != 9 || m->d != 3) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE lives in R^9 (n = 9, d = 3)");
+      if (!(m->R > 0.0 && m->a > 0.0)) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE needs R > 0 and a > 0");
+      if (!pr->closed) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE supports the closed problem only");
+      if (pr->f.kind != MPWOS_FUNC_CURVE_SPHERE) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE source must be CURVE_SPHERE data");
+      if (pa->sampler != MPWOS_SAMPLER_FULL) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE needs the full sampler");
+      break;
     case MPWOS_POINT_CLOUD:
       if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD lives in R^3 (n = 3, d = 2)");
       if (!m->cloud) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD needs cloud");
@@ -240,6 +248,12 @@ int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* 
       for (int t = 0; t < f->n_terms; ++t)
         if (f->modes[4 * t] < 0 || f->modes[4 * t] > 64 || f->modes[4 * t + 1] < 0 || f->modes[4 * t + 1] > 64)
           return fail(ctx, MPWOS_EINVAL, "torus mode numbers must lie in [0, 64]");
+    } else if (f->kind == MPWOS_FUNC_CURVE_SPHERE) {
+      if (m->kind != MPWOS_CURVE_SPHERE) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE data needs the CURVE_SPHERE manifold");
+      if (f->n_terms && (!f->coef || !f->modes || !f->v || !f->A)) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE data needs coef, modes, v, A");
+      for (int t = 0; t < f->n_terms; ++t)
+        if (f->modes[4 * t] < 0 || f->modes[4 * t] > 64 || (f->modes[4 * t + 1] != 0 && f->modes[4 * t + 1] != 1))
+          return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE modes: q in [0, 64], trig 0 or 1");
     } else if (f->kind == MPWOS_FUNC_REVOLUTION_QUAD) {
       if (m->kind != MPWOS_REVOLUTION) return fail(ctx, MPWOS_EINVAL, "REVOLUTION_QUAD needs the REVOLUTION manifold");
       if (f->n_terms != 2 || !f->coef || !f->v || !f->A) return fail(ctx, MPWOS_EINVAL, "REVOLUTION_QUAD needs 2 coef, v and A");
@@ -362,6 +376,9 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
       d.mode_f[t][3] = qq * qq;
     }
     if (f.n_terms == 1 && f.modes[0] <= 3 && f.modes[1] <= 3) d.single_mq = 4 * f.modes[0] + f.modes[1];
+  } else if (f.kind == MPWOS_FUNC_CURVE_SPHERE) {
+    for (int t = 0; t < f.n_terms; ++t)
+      for (int q = 0; q < 4; ++q) d.modes[t][q] = static_cast<int8_t>(f.modes[4 * t + q]);
   }
 }
 
@@ -602,6 +619,21 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
       df->Af = sc.upload(Af.data(), Af.size());
       if (!df->v || !df->A || !df->vf || !df->Af) return fail(ctx, MPWOS_ENOMEM, "SPHERE_QUAD data");
     }
+  }
+  // Fourier curve x sphere: f's v (3 per term) and A (9 per term)
+  if (m->kind == MPWOS_CURVE_SPHERE) {
+    const int nt = pr->f.n_terms > 0 ? pr->f.n_terms : 1;
+    std::vector<double> v(3 * nt, 0.0), A(9 * nt, 0.0);
+    if (pr->f.n_terms) {
+      std::copy(pr->f.v, pr->f.v + 3 * pr->f.n_terms, v.begin());
+      std::copy(pr->f.A, pr->f.A + 9 * pr->f.n_terms, A.begin());
+    }
+    std::vector<float> vf(v.begin(), v.end()), Af(A.begin(), A.end());
+    pb.f.v = sc.upload(v.data(), v.size());
+    pb.f.A = sc.upload(A.data(), A.size());
+    pb.f.vf = sc.upload(vf.data(), vf.size());
+    pb.f.Af = sc.upload(Af.data(), Af.size());
+    if (!pb.f.v || !pb.f.A || !pb.f.vf || !pb.f.Af) return fail(ctx, MPWOS_ENOMEM, "CURVE_SPHERE data");
   }
   // hypersurface of revolution: f's v and diag(A) (n - 1 entries), profile, tr(A)/(n-1)
   if (m->kind == MPWOS_REVOLUTION) {
@@ -1096,8 +1128,9 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   CK(cudaSetDevice(ctx->device));
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
-  if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD || m->kind == MPWOS_REVOLUTION)
-    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE, POINT_CLOUD and REVOLUTION are not supported (use mpwos_solve)");
+  if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD || m->kind == MPWOS_REVOLUTION ||
+      m->kind == MPWOS_CURVE_SPHERE)
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: EMBEDDED_SPHERE, POINT_CLOUD, REVOLUTION and CURVE_SPHERE are not supported (use mpwos_solve)");
   if (prm->sampler != MPWOS_SAMPLER_FULL)
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: the reduced sampler is not supported (use mpwos_solve)");
   if (prob->comp != MPWOS_COMP_NONE)
@@ -1245,6 +1278,11 @@ struct OwnedFunc {
       v.assign(src.v, src.v + D);
       A.assign(src.A, src.A + static_cast<size_t>(D) * D);
       f.v = v.data(); f.A = A.data();
+    } else if (src.kind == MPWOS_FUNC_CURVE_SPHERE) {      // per term: modes, v (3), A (9)
+      modes.assign(src.modes, src.modes + (src.modes ? 4 * src.n_terms : 0));
+      v.assign(src.v, src.v + (src.v ? 3 * src.n_terms : 0));
+      A.assign(src.A, src.A + (src.A ? 9 * src.n_terms : 0));
+      f.modes = modes.data(); f.v = v.data(); f.A = A.data();
     } else if (src.kind == MPWOS_FUNC_REVOLUTION_QUAD) {   // D = n - 1: v and diag(A)
       v.assign(src.v, src.v + D);
       A.assign(src.A, src.A + D);

@@ -22,6 +22,7 @@
 #include "dev_common.cuh"
 #include "green.cuh"
 #include "revolution.cuh"
+#include "curve_sphere.cuh"
 
 namespace mpwos {
 
@@ -289,6 +290,14 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
     c2_t = pick<T>(pb.f.coef[1], pb.f.coef_f[1]);
   }
   T ty = T(0);   // revolution: the axis coordinate Y_{n-1}
+  // Fourier curve x sphere (n = 9): v, A of f (3 and 9 per term), R, a
+  const T* vC = nullptr;
+  const T* aC = nullptr;
+  const T cs_R = pick<T>(pb.R, pb.sf.R), cs_a = pick<T>(pb.a_tube, pb.sf.a);
+  if constexpr (MK == kCurveSphere) {
+    vC = kF64 ? reinterpret_cast<const T*>(pb.f.v) : reinterpret_cast<const T*>(pb.f.vf);
+    aC = kF64 ? reinterpret_cast<const T*>(pb.f.A) : reinterpret_cast<const T*>(pb.f.Af);
+  }
 
   T Y[L];          // ambient state (sphere, R^n)
   T sj = T(0);     // intrinsic state (embedded sphere), lane j < D
@@ -441,6 +450,15 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
         for (int q = 0; q < L; ++q) { acc[0] += g[q] * g[q]; acc[1] += Y[q] * g[q]; }
         warp_sum<2>(acc);
         const T zs = (r * t) / sqrt(fmax(acc[0], T(1e-30)));
+        if constexpr (MK == kCurveSphere) {
+          // n = 9: every lane takes the whole Z and its closest point
+          T X[9], y9[9];
+#pragma unroll
+          for (int c = 0; c < 9; ++c) X[c] = gather<T, L, G>(Y, c) + zs * gather<T, L, G>(g, c);
+          curve_sphere_cp<T>(cs_R, cs_a, X, y9);
+          F += curve_sphere_value<T>(pb.f, vC, aC, cs_R, cs_a, sig_t, y9);
+          continue;
+        }
         if constexpr (MK == kRevolution) {
           // Z = Y + zs g; |Zh|^2, v.Zh, Zh^T diag(A) Zh and Z_{n-1} in one reduction
           T za[4] = {T(0), T(0), T(0), T(0)};
@@ -492,6 +510,25 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
       const T tj = lane < D ? sj + sc * qgj : T(0);
       const T tn = sqrt(warp_sum1(tj * tj));
       sj = tj / tn;
+    } else if constexpr (MK == kCurveSphere) {
+      T gg = T(0);
+#pragma unroll
+      for (int q = 0; q < L; ++q) gg += g[q] * g[q];
+      gg = fmax(warp_sum1(gg), T(1e-30));
+      const T sc = r / sqrt(gg);
+      T X[9], y9[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) X[c] = gather<T, L, G>(Y, c) + sc * gather<T, L, G>(g, c);
+      curve_sphere_cp<T>(cs_R, cs_a, X, y9);
+#pragma unroll
+      for (int m = 0; m < MB; ++m)
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+          const int cc = G * (lane + 32 * m) + q;
+#pragma unroll
+          for (int c = 0; c < 9; ++c)
+            if (c == cc) Y[G * m + q] = y9[c];
+        }
     } else if constexpr (MK == kRevolution) {
       // Theta = Y + r g/|g|; Y = cp(Theta): scale Theta_h to R(t)/|Theta_h|, Y_{n-1} = t
       T gg = T(0);
