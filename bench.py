@@ -39,17 +39,19 @@ METRIC = "walk-steps/s at fixed RMSE (torus, FP32 walk + FP64 accumulation)"
 UNIT = "walk-steps/s"
 # Algorithmic lane-operations per walk-step of the FP32 torus walk (N_V = 1):
 # the minimal operation count of one step, one wide multiply, three-input XOR
-# or MUFU op counting as one: 2 Philox4x32-10 blocks whose rounds 0..2 share
-# the per-walk and per-step work 64, 7 uniforms 14, 3 Box-Muller pairs 27,
-# sphere sample 9, radius table (side, sqrt, index, one 16-byte load, 3 FMA,
-# clamp) 17, interior sample 10, torus angles of cp(Z) 11, torus source
-# (-Delta_M + sigma) u for one mode 16, closest point of Theta 13, weight and
-# score in float pairs (S += V F by TwoSum, V *= c) 15, loop 3.
-OPS_PER_STEP = 199
+# or MUFU op counting as one: 1 Philox4x32-10 block whose rounds 0..2 have
+# their per-walk and per-step work hoisted 34, 5 uniforms (4 from low bits, 1
+# from high bits) 14, 2 uniform directions on S^2 (Archimedes: height,
+# sqrt(1 - z^2), sincos of the azimuth, 2 products) 18, radius table (side,
+# sqrt, index, one 16-byte load, 3 FMA, clamp) 17, Theta and Z 7, torus angles
+# of cp(Z) 11, torus source (-Delta_M + sigma) u for one mode 16, closest point
+# of Theta 13, weight and score in float pairs (S += V F by TwoSum, V *= c) 15,
+# loop 3.
+OPS_PER_STEP = 148
 # DRAM bytes (read + write) of one bench launch of the walk kernel, measured
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the
 # kernel as built now; the profile summary gives the command.
-TRAFFIC_BYTES = 20.37e6 + 602.73e6
+TRAFFIC_BYTES = 17.40e6 + 601.06e6
 
 
 def _peaks():

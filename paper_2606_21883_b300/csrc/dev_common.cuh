@@ -229,6 +229,24 @@ __host__ __device__ __forceinline__ void philox_step_pair(const PhiloxWalk& w, u
   out1 = U4{b0, b1, b2, b3};
 }
 
+// Block j = 0 of step k alone, with the same hoisting as philox_step_pair.
+__host__ __device__ __forceinline__ U4 philox_step_one(const PhiloxWalk& w, uint32_t k, const PhiloxKeys& K) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint64_t P = static_cast<uint64_t>(M0) * (w.x0 ^ k);
+  const uint32_t c2 = static_cast<uint32_t>(P >> 32) ^ K.b[1];
+  const uint64_t q = static_cast<uint64_t>(M1) * c2;
+  uint32_t a0 = static_cast<uint32_t>(q >> 32) ^ w.L ^ K.a[2], a1 = static_cast<uint32_t>(q);
+  uint32_t a2 = w.HA ^ static_cast<uint32_t>(P), a3 = w.LA;
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    const uint64_t pa0 = static_cast<uint64_t>(M0) * a0, pa1 = static_cast<uint64_t>(M1) * a2;
+    const uint32_t na0 = static_cast<uint32_t>(pa1 >> 32) ^ a1 ^ K.a[r];
+    const uint32_t na2 = static_cast<uint32_t>(pa0 >> 32) ^ a3 ^ K.b[r];
+    a0 = na0; a1 = static_cast<uint32_t>(pa1); a2 = na2; a3 = static_cast<uint32_t>(pa0);
+  }
+  return U4{a0, a1, a2, a3};
+}
+
 __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                              uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -275,6 +293,26 @@ __device__ __forceinline__ void box_muller64(double ua, double ub, double& g0, d
 }
 
 // FP32 Box-Muller pair (hardware approximations: MUFU lg2 / sin / cos).
+// The fifth 23-bit uniform of a block whose four words' low 23 bits are already
+// used: the high 9 bits of x and y and bits 23..27 of z (disjoint from those).
+__device__ __forceinline__ float u23_high(const U4& b) {
+  return u23((b.x >> 23) | ((b.y >> 23) << 9) | ((b.z >> 23) << 18));
+}
+
+// A uniform direction on S^2 from two uniforms in (0, 1] (Archimedes: the height
+// of a uniform point of the unit sphere is uniform on [-1, 1] and independent of
+// its azimuth): z = 2 uz - 1, sqrt(1 - z^2) = 2 sqrt(uz (1 - uz)), azimuth 2 pi uphi.
+// The same law as a normalised Gaussian 3-vector, from two uniforms instead of
+// three Gaussians and a norm.
+__device__ __forceinline__ void sphere_dir3(float uz, float uphi, float (&d)[3]) {
+  const float s = 2.0f * sqrtf(fmaf(-uz, uz, uz));
+  float sn, cs;
+  __sincosf(kTwoPiF * uphi, &sn, &cs);
+  d[0] = s * cs;
+  d[1] = s * sn;
+  d[2] = fmaf(2.0f, uz, -1.0f);
+}
+
 __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, float& g1) {
   const float rad = sqrtf(-1.38629436111989061f * __log2f(ua));   // -2 ln(ua) = -2 ln2 log2(ua)
   float s, c;

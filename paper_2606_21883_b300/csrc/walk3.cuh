@@ -158,10 +158,11 @@ __device__ __forceinline__ void walk3_f64_body(const DevProblem& pb) {
 // omega from the FP64 series (once per radius value); each walk's weight W and
 // score S in float pairs (~2^-48 relative), so the step loop issues no FP64
 // instruction; per-point sums over walks are FP64 (reduce kernel).
-// Draws of a step are packed: the step's 3(1+N_V) Gaussians come from
-// consecutive uniform pairs (Box-Muller) of the step's uniform stream (four
-// 24-bit uniforms per block), U_l follows at uniform index 2 ceil(3(1+N_V)/2)
-// + l.  N_V = 1 uses two blocks per step.
+// Draws of a step: N_V = 1 takes one block, block 0 of the step, whose five
+// 23-bit uniforms give the directions of Theta and Z (two each, sphere_dir3)
+// and U (the fifth, u23_high).  N_V > 1: the step's 3(1+N_V) Gaussians come
+// from consecutive uniform pairs (Box-Muller) of the step's uniform stream (four
+// 23-bit uniforms per block), U_l follows at uniform index 2 ceil(3(1+N_V)/2) + l.
 __device__ __forceinline__ float uniform_at32(uint32_t u, uint32_t kk, uint32_t i, uint32_t p,
                                               const PhiloxKeys& K) {
   const U4 b = philox4x32_10(u >> 2, kk, i, p, K);
@@ -407,20 +408,17 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
     const uint32_t kk = static_cast<uint32_t>(k);
     float Th[3], F = 0.0f;
     if (nv == 1) {
-      U4 b0, b1;
-      philox_step_pair(pw, kk, K, b0, b1);
-      float g[3], z[3];
-      box_muller32(u23(b0.x), u23(b0.y), g[0], g[1]);
-      box_muller32(u23(b0.z), u23(b0.w), g[2], z[0]);
-      box_muller32(u23(b1.x), u23(b1.y), z[1], z[2]);
-      const float U = u23(b1.z);
-      const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
-      for (int q = 0; q < 3; ++q) Th[q] = Y[q] + sc * g[q];
+      const U4 b = philox_step_one(pw, kk, K);
+      float dt[3], dz[3];
+      sphere_dir3(u23(b.x), u23(b.y), dt);
+      sphere_dir3(u23(b.z), u23(b.w), dz);
+      const float U = u23_high(b);
+      for (int q = 0; q < 3; ++q) Th[q] = Y[q] + r * dt[q];
       float t = table_lookup32(pb, a, U);
       t = fminf(fmaxf(t, 0.0f), 1.0f);
-      const float zs = (r * t) * rsqrtf(fmaxf(dot3(z, z), 1e-30f));
+      const float zs = r * t;
       float Z[3];
-      for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * z[q];
+      for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * dz[q];
       F = source_at32<MK, KM>(pb, Z);
       if constexpr (COMP) F += comp_m32<MK>(pb, Z, F);
     } else {
@@ -473,21 +471,17 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
 template <int MK, int MQ>
 __device__ __forceinline__ float fixed_step32(const DevProblem& pb, const PhiloxKeys& K, const PhiloxWalk& pw,
                                               uint32_t kk, float r, float a, float (&Y)[3]) {
-  U4 b0, b1;
-  philox_step_pair(pw, kk, K, b0, b1);
-  float g[3], z[3];
-  box_muller32(u23(b0.x), u23(b0.y), g[0], g[1]);
-  box_muller32(u23(b0.z), u23(b0.w), g[2], z[0]);
-  box_muller32(u23(b1.x), u23(b1.y), z[1], z[2]);
-  const float U = u23(b1.z);
-  const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
-  float t = table_lookup32(pb, a, U);
+  const U4 b = philox_step_one(pw, kk, K);
+  float dt[3], dz[3];
+  sphere_dir3(u23(b.x), u23(b.y), dt);
+  sphere_dir3(u23(b.z), u23(b.w), dz);
+  float t = table_lookup32(pb, a, u23_high(b));
   t = fminf(fmaxf(t, 0.0f), 1.0f);
-  const float zs = (r * t) * rsqrtf(fmaxf(dot3(z, z), 1e-30f));
+  const float zs = r * t;
   float Z[3], Th[3];
   for (int q = 0; q < 3; ++q) {
-    Z[q] = Y[q] + zs * z[q];
-    Th[q] = Y[q] + sc * g[q];
+    Z[q] = Y[q] + zs * dz[q];
+    Th[q] = Y[q] + r * dt[q];
   }
   float F;
   if constexpr (MK == kTorus && MQ >= 0) {

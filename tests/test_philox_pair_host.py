@@ -1,6 +1,6 @@
-"""The walk's two-block Philox evaluation (per-walk and per-step parts hoisted
-out of rounds 0..2) equals Philox4x32-10 on counters (0, k, i, p) and
-(1, k, i, p): the device header's functions compiled as host code by nvcc and
+"""The walk's two-block and one-block Philox evaluations (per-walk and per-step
+parts hoisted out of rounds 0..2) equal Philox4x32-10 on counters (0, k, i, p)
+and (1, k, i, p): the device header's functions compiled as host code by nvcc and
 run over random and structured (seed, i, p, k)."""
 import os
 import subprocess
@@ -27,8 +27,10 @@ int main() {
     U4 a, b;
     philox_step_pair(w, k, K, a, b);
     const U4 ra = philox4x32_10(0u, k, i, p, K), rb = philox4x32_10(1u, k, i, p, K);
+    const U4 o = philox_step_one(w, k, K);
     bad += a.x != ra.x || a.y != ra.y || a.z != ra.z || a.w != ra.w ||
-           b.x != rb.x || b.y != rb.y || b.z != rb.z || b.w != rb.w;
+           b.x != rb.x || b.y != rb.y || b.z != rb.z || b.w != rb.w ||
+           o.x != ra.x || o.y != ra.y || o.z != ra.z || o.w != ra.w;
   }
   std::printf("%ld\n", bad);
   return bad != 0;
