@@ -156,6 +156,7 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7):
 
     def run(reqs, rate):
         ids, lat, steps = [], [], 0.0
+        by_kind = {}
         t0 = _t.perf_counter()
         arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
         pending = {}
@@ -165,29 +166,39 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7):
             while q < len(reqs) and arrivals[q] <= now:
                 kind, w, budget, target = reqs[q]
                 rid = ctx.submit(w.problem, w.params, w.points, budget, target, precision=M.FP32)
-                pending[rid] = len(w.points)
+                pending[rid] = (len(w.points), kind)
                 q += 1
             for rid in list(pending):
                 if ctx.poll(rid) >= 2:
-                    mean, se, ms, walks, lt, rc = ctx.fetch(rid, pending.pop(rid))
+                    npts, kind = pending.pop(rid)
+                    mean, se, ms, walks, lt, rc = ctx.fetch(rid, npts)
                     lat.append(lt)
+                    by_kind.setdefault(kind, []).append(lt)
                     steps += float(np.sum(ms * walks))
             _t.sleep(0.0005)
-        return np.array(lat), steps, _t.perf_counter() - t0
+        return np.array(lat), steps, _t.perf_counter() - t0, by_kind
 
     calib = _serving_mix(rng, n_calib, cloud_w)
-    _, st_c, T_c = run(calib, 0.0)                       # all at once: capacity
+    _, st_c, T_c, _ = run(calib, 0.0)                    # all at once: capacity
     cap_rate = n_calib / T_c
     rate = 0.7 * cap_rate
     reqs = _serving_mix(rng, n_req, cloud_w)
-    lat, steps, T = run(reqs, rate)
+    lat, steps, T, by_kind = run(reqs, rate)
     kinds = {k: sum(1 for r in reqs if r[0] == k) for k in ["torus", "cap", "cloud", "s999", "s20"]}
     return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "mean_ms": 1e3 * float(lat.mean()), "requests": int(len(lat)), "arrival_rate_hz": rate,
             "capacity_hz": cap_rate, "walk_steps_per_s": steps / T, "mix": kinds,
+            "by_kind_ms": {k: {"p50": 1e3 * float(np.percentile(v, 50)), "max": 1e3 * float(np.max(v))}
+                           for k, v in sorted(by_kind.items())},
             "recipe": "Poisson arrivals at 0.7 x capacity (capacity from a burst of 24); points log-uniform "
                       "(torus <=4096, cap/cloud/S^999 <=64, S^20 <=4), budget log-uniform 256-65536 (S^999 <=4096, "
                       "S^20 <=1024), target stderr log-uniform 1e-3-1e-2, FP32 walks, reduced sampler on S^999/S^20"}
+
+
+def _serving_cloud(P):
+    w = W.point_cloud(P=P, walks=1)
+    w.params.tau_w = 1e-4
+    return w
 
 
 def secondary_leg(M, ctx):
@@ -212,6 +223,8 @@ def secondary_leg(M, ctx):
          W.SAMPLER_FULL, "Example 1 cut torus, 100 pts x 1e5 walks, second-order m_* (predictor u), FP32"),
         ("torus_cut_e1_exact_fp32", lambda: W.torus_cut(P=100, walks=1, comp=W.COMP_EXACT), 100000, M.FP32,
          W.SAMPLER_FULL, "Example 1 cut torus, 100 pts x 1e5 walks, exact mismatch m (predictor u), FP32"),
+        ("point_cloud_200k_fp32", lambda: _serving_cloud(64), 4096, M.FP32, W.SAMPLER_FULL,
+         "the serving mix's 200k-point cloud (k_nn = 16, quadratic-fit cp, tau_W = 1e-4), 64 pts x 4096 walks, FP32"),
         ("sphere_cloud_e4_fp32", lambda: W.sphere_cloud_legendre(P=100, walks=1), 8000, M.FP32, W.SAMPLER_FULL,
          "Example 4 S^2 as 8000 points, k_nn = 6, nearest-point cp, 100 pts x 8000 walks, FP32"),
         ("dumbbell_e2_fp32", lambda: W.dumbbell(P=100, walks=1), 1000, M.FP32, W.SAMPLER_FULL,
