@@ -146,6 +146,8 @@ struct DevProblem {
   // hypersurface of revolution: profile parameters, c_kappa, tr(A)/(n-1) of f
   double rv_alpha, rv_kappa, rv_mA;
   float rv_alpha_f, rv_kappa_f, rv_mA_f, rv_ck_f;
+  // dynamic walk queue (zeroed before each launch; null: static stride)
+  unsigned long long* wk_next;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
@@ -332,6 +334,17 @@ __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, floa
 template <typename T> __device__ __forceinline__ T pick(double d, float f);
 template <> __device__ __forceinline__ double pick<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float pick<float>(double, float f) { return f; }
+
+// The walk a thread (or warp) takes after walk w.  With a queue counter the
+// first walk of each of the `stride` threads is static and every later one is
+// taken from the counter, so threads whose walks end early take more walks and
+// walks of uneven length keep the lanes busy; without one, the static stride.
+// Either way each enumeration index is walked once, and a walk's draws depend
+// on (seed, point, walk index) only.
+__device__ __forceinline__ int64_t next_walk(const DevProblem& pb, int64_t w, int64_t stride) {
+  if (pb.wk_next) return pb.wk_w0 + stride + static_cast<int64_t>(atomicAdd(pb.wk_next, 1ull));
+  return w + stride;
+}
 
 // Walk enumeration index -> (point, walk index, output slot).
 struct WalkId {

@@ -598,6 +598,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   copy_func(pr->f, pb.f);
   if (!pr->closed) copy_func(pr->g, pb.g);
   copy_pred(*pr, pb.pred);
+  pb.wk_next = sc.alloc<unsigned long long>(1);   // dynamic walk queue (static stride if null)
   const int n = m->n;
   if (!pr->closed) {
     std::vector<float> ef(pr->bnd_normal, pr->bnd_normal + n);
@@ -789,6 +790,7 @@ int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tabc)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
+  if (pb.wk_next) CK(cudaMemsetAsync(pb.wk_next, 0, sizeof(unsigned long long), st));
   if (pb.reduced) {
     const int blk = 128;
     int64_t grid = static_cast<int64_t>(ctx->sm_count) * occupancy_walkr(pb, fp64, blk);

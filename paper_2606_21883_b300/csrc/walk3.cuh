@@ -95,7 +95,7 @@ __device__ __forceinline__ void walk3_f64_body(const DevProblem& pb) {
       pb.S_out[o] = S;
       pb.K_out[o] = static_cast<int32_t>(k);
       pb.flag_out[o] = flag;
-      w += stride;
+      w = next_walk(pb, w, stride);
       if (w >= total) break;
       init(w);
       continue;
@@ -386,7 +386,7 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
       pb.S_out[o] = f2_to_double(S);
       pb.K_out[o] = k;
       pb.flag_out[o] = flag;
-      w += stride;
+      w = next_walk(pb, w, stride);
       if (w >= total) break;
       init(w);
       continue;

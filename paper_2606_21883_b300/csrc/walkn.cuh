@@ -395,7 +395,11 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
         pb.K_out[o] = static_cast<int32_t>(k);
         pb.flag_out[o] = flag;
       }
-      w += nwarps;
+      {
+        int64_t nxt = 0;
+        if (lane == 0) nxt = next_walk(pb, w, nwarps);
+        w = __shfl_sync(0xffffffffu, nxt, 0);
+      }
       if (w >= total) break;
       init(w);
       continue;

@@ -283,7 +283,7 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
       pb.S_out[o] = wa.score();
       pb.K_out[o] = static_cast<int32_t>(k);
       pb.flag_out[o] = flag;
-      w += stride;
+      w = next_walk(pb, w, stride);
       if (w >= total) break;
       init(w);
       continue;
