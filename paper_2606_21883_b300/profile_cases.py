@@ -35,10 +35,10 @@ def _case(name):
         w = W.hypersphere_half(P=148, walks=1)
         w.params.max_steps = 16
         return w, 128, {}
-    if name == "s999_red":   # S^999 half to completion (~4900 steps per walk), reduced sampler
-        w = W.hypersphere_half(P=2048, walks=1)
+    if name == "s999_red":   # S^999 half to completion (~4900 steps per walk), reduced sampler, ~7 walks per thread
+        w = W.hypersphere_half(P=4096, walks=1)
         w.params.sampler = W.SAMPLER_REDUCED
-        return w, 32, {}
+        return w, 256, {}
     if name == "s20_red":   # S^20 in R^1000, reduced sampler, walks capped at 20000 steps
         w = W.embedded_s20(P=1184, walks=1)
         w.params.sampler = W.SAMPLER_REDUCED
