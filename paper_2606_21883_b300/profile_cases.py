@@ -6,6 +6,7 @@
     python -m paper_2606_21883_b300.profile_cases s999      # walkn_f32_kernel<sphere>
     python -m paper_2606_21883_b300.profile_cases s999_red  # walkr_kernel<float, sphere> (reduced sampler)
     python -m paper_2606_21883_b300.profile_cases s20_red   # walkr_kernel<float, embedded> (reduced sampler)
+    python -m paper_2606_21883_b300.profile_cases dumbbell  # walkn_f32_kernel<revolution> (Example 2, n = 1001)
 
 Each case runs `--reps` walk launches into device buffers (the first one
 warms tables and caches) and prints one line with the walk-steps and the
@@ -44,12 +45,15 @@ def _case(name):
         w.params.sampler = W.SAMPLER_REDUCED
         w.params.max_steps = 20000
         return w, 16, {}
+    if name == "dumbbell":   # Example 2 in R^1001, walks to completion (~85 steps), 4 walks per warp slot
+        w = W.dumbbell(P=2368, walks=1)
+        return w, 64, {}
     raise SystemExit(f"unknown case {name}")
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999", "s999_red", "s20_red"])
+    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999", "s999_red", "s20_red", "dumbbell"])
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     import torch
