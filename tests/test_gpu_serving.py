@@ -47,9 +47,12 @@ def _mix():
     emb = W.embedded_s20(P=2, walks=1, n=64, d=5, sigma=6.0)
     emb.params.tau_w = 1e-4
     cut = W.torus_cut(P=10, walks=1, comp=W.COMP_NORMAL2)   # Example 1, compensated
+    dmb = W.dumbbell(P=3, walks=1)                           # Example 2, R^1001
+    crv = W.curve_sphere(P=4, walks=1)                       # Example 3, R^9
     return [(cap, 4096, 5e-3, M.FP32), (tor, 8192, 2e-2, M.FP32), (hyp, 256, 0.0, M.FP32),
             (cld, 1024, 2e-2, M.FP32), (emb, 512, 0.0, M.FP64), (cap, 2048, 0.0, M.FP64),
-            (cut, 2048, 0.0, M.FP32), (cut, 256, 0.0, M.FP64)]
+            (cut, 2048, 0.0, M.FP32), (cut, 256, 0.0, M.FP64), (dmb, 512, 0.0, M.FP32),
+            (crv, 1024, 1e-2, M.FP32)]
 
 
 def test_same_alone_and_in_mix(ctx):
