@@ -106,6 +106,113 @@ __device__ __forceinline__ T cloud_knn(const DevProblem& pb, const T* x, Knn<T, 
   return h / T(k);
 }
 
+// cloud_knn for the FP32 walk, made by a whole warp (all 32 lanes call it
+// together, each with its own query x and a flag saying whether it has one).
+// The warp takes the queries one at a time: for each it visits the same cells
+// as cloud_knn, scans each cell's points one per lane, and keeps the sorted list
+// of the nearest so far spread one entry per lane (entry j in lane j), a
+// candidate being inserted by shifting the entries after it one lane up.
+// Candidates are inserted in the order cloud_knn inserts them (cells, then
+// points ascending), so the k nearest -- and everything computed from them --
+// are identical to cloud_knn's; the query's lane then receives them.  A
+// candidate that passed the filter but no longer beats the k-th entry lands
+// beyond entry k - 1 and never moves back (entries only move up).
+template <int KM>
+__device__ __forceinline__ float cloud_knn_coop(const DevProblem& pb, const float* x, bool valid, Knn<float, KM>& R) {
+  constexpr unsigned kAll = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int k = pb.cl_k;
+  const float* P = pb.cl_pts32;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) { R.d2[j] = INFINITY; R.idx[j] = -1; R.gid[j] = 0x7fffffff; }
+  const float cs = pb.cl_cell_f;
+  const int gx = pb.cl_dims[0], gy = pb.cl_dims[1], gz = pb.cl_dims[2];
+  const int rmax = max(gx, max(gy, gz));
+  unsigned qm = __ballot_sync(kAll, valid);
+  while (qm) {
+    const int src = __ffs(qm) - 1;
+    qm &= qm - 1;
+    const float q[3] = {__shfl_sync(kAll, x[0], src), __shfl_sync(kAll, x[1], src), __shfl_sync(kAll, x[2], src)};
+    int c[3];
+    float lo[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = pb.cl_origin_f[a];
+      int ci = static_cast<int>(floorf((q[a] - lo[a]) / cs));
+      c[a] = ci < 0 ? 0 : (ci >= pb.cl_dims[a] ? pb.cl_dims[a] - 1 : ci);
+    }
+    float ld = INFINITY;
+    int lg = 0x7fffffff, lp = -1;
+    for (int Rr = 0; Rr <= rmax; ++Rr) {
+      for (int dz = -Rr; dz <= Rr; ++dz) {
+        const int zz = c[2] + dz;
+        if (zz < 0 || zz >= gz) continue;
+        for (int dy = -Rr; dy <= Rr; ++dy) {
+          const int yy = c[1] + dy;
+          if (yy < 0 || yy >= gy) continue;
+          const bool face = (dz == -Rr || dz == Rr || dy == -Rr || dy == Rr);
+          const int step = face ? 1 : 2 * Rr;
+          for (int dx = -Rr; dx <= Rr; dx += step) {
+            const int xx = c[0] + dx;
+            if (xx < 0 || xx >= gx) continue;
+            const int cell = (zz * gy + yy) * gx + xx;
+            const int b = pb.cl_start[cell], e = pb.cl_start[cell + 1];
+            for (int base = b; base < e; base += 32) {
+              const int qq = base + lane;
+              const bool ok = qq < e;
+              float cd = INFINITY;
+              int cg = 0x7fffffff;
+              if (ok) {
+                const float ddx = P[3 * qq] - q[0], ddy = P[3 * qq + 1] - q[1], ddz = P[3 * qq + 2] - q[2];
+                cd = ddx * ddx + ddy * ddy + ddz * ddz;
+                cg = pb.cl_orig[qq];
+              }
+              const float kd = __shfl_sync(kAll, ld, k - 1);
+              const int kg = __shfl_sync(kAll, lg, k - 1);
+              unsigned bm = __ballot_sync(kAll, ok && (cd < kd || (cd == kd && cg < kg)));
+              while (bm) {
+                const int s = __ffs(bm) - 1;
+                bm &= bm - 1;
+                const float nd = __shfl_sync(kAll, cd, s);
+                const int ng = __shfl_sync(kAll, cg, s);
+                const int np = base + s;
+                const float pd = __shfl_up_sync(kAll, ld, 1);
+                const int pg = __shfl_up_sync(kAll, lg, 1), pp = __shfl_up_sync(kAll, lp, 1);
+                const bool lt_here = nd < ld || (nd == ld && ng < lg);
+                const bool lt_prev = lane > 0 && (nd < pd || (nd == pd && ng < pg));
+                if (lt_here) {
+                  if (lt_prev) { ld = pd; lg = pg; lp = pp; } else { ld = nd; lg = ng; lp = np; }
+                }
+              }
+            }
+          }
+        }
+      }
+      float guard = INFINITY;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        if (c[a] - Rr > 0) guard = fminf(guard, q[a] - (lo[a] + static_cast<float>(c[a] - Rr) * cs));
+        if (c[a] + Rr < pb.cl_dims[a] - 1) guard = fminf(guard, (lo[a] + static_cast<float>(c[a] + Rr + 1) * cs) - q[a]);
+      }
+      const float kd = __shfl_sync(kAll, ld, k - 1);
+      if (kd <= guard * guard || guard == INFINITY) break;
+    }
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+      if (j < k) {
+        const float dj = __shfl_sync(kAll, ld, j);
+        const int pj = __shfl_sync(kAll, lp, j), gj = __shfl_sync(kAll, lg, j);
+        if (lane == src) { R.d2[j] = dj; R.idx[j] = pj; R.gid[j] = gj; }
+      }
+    }
+  }
+  float h = 0.0f;
+#pragma unroll
+  for (int j = 0; j < KM; ++j)
+    if (j < k) h += sqrtf(R.d2[j]);
+  return h / static_cast<float>(k);
+}
+
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi (columns of V).
 template <typename T>
 __device__ __forceinline__ void jacobi3_dev(T A[3][3], T lam[3], T V[3][3]) {

@@ -30,10 +30,12 @@ static const void* walk3_f32_fn(const DevProblem& pb) {
         default: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true>);
       }
     }
-    case kPointCloud:
+    case kPointCloud:   // k >= 12: the warp-cooperative neighbour search (same results, faster there)
+      if (pb.cl_k >= 12)
+        return pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_cloud_coop_kernel<16>)
+                             : reinterpret_cast<const void*>(walk3_f32_cloud_coop_kernel<32>);
       return pb.cl_k <= 8 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 8>)
-           : pb.cl_k <= 16 ? reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 16>)
-                           : reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 32>);
+                          : reinterpret_cast<const void*>(walk3_f32_cloud_kernel<kPointCloud, 16>);
     default: return nullptr;
   }
 }

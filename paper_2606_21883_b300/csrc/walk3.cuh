@@ -465,6 +465,143 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
   }
 }
 
+// The FP32 point-cloud walk: walk3_f32_body's step for a closed cloud problem,
+// with every k-nearest search made by the whole warp (cloud_knn_coop; the
+// neighbours, and so every result, are those of the per-lane search).  A lane
+// whose walks are exhausted stays in the loop inactive -- it offers no query and
+// skips its projections -- until every lane of its warp is done, so the warp's
+// searches always have all 32 lanes.
+template <int KM>
+__device__ __forceinline__ void walk3_f32_cloud_body(const DevProblem& pb) {
+  const int64_t total = pb.wk_w1;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  bool active = w < total;
+  const PhiloxKeys& K = pb.keys;
+  const int nv = pb.n_v;
+  const int max_steps = static_cast<int>(pb.max_steps);
+  const float theta = pb.sf.theta;
+  const float sqs = pb.sf.sqrt_sigma;
+  const F2 tau = f2_from_double(pb.tau_w);
+  const float inv_sigma = pb.sf.inv_sigma;
+  const bool f_const = source_is_constant(pb.f);
+
+  float Y[3] = {0.0f, 0.0f, 0.0f};
+  F2 W{1.0f, 0.0f}, S{0.0f, 0.0f};
+  int k = 0;
+  int64_t o = 0;
+  uint32_t p = 0, i = 0;
+  PhiloxWalk pw{};
+  float r_prev = -1.0f;
+  F2 c2{1.0f, 0.0f}, om2{0.0f, 0.0f};
+  auto set_weights = [&](float a) {
+    if (!pb.em1_fp64) {
+      weights_from_em1(em1_poly32(pb, 0.25f * a * a), inv_sigma, c2, om2);
+    } else {
+      const double ad = static_cast<double>(a);
+      const double em1 = em1_series(0.5, 0.25 * (ad * ad));
+      const double c = 1.0 / (1.0 + em1);
+      c2 = f2_from_double(c);
+      om2 = f2_from_double(one_minus_c(em1, c) / pb.sigma);
+    }
+  };
+  auto init = [&](int64_t ww) {
+    const WalkId id = walk_id(pb, ww);
+    p = id.p; i = id.i; o = id.o;
+    const double* y0 = pb.pts + static_cast<size_t>(p) * 3;
+    Y[0] = static_cast<float>(y0[0]); Y[1] = static_cast<float>(y0[1]); Y[2] = static_cast<float>(y0[2]);
+    W = F2{1.0f, 0.0f};
+    S = F2{0.0f, 0.0f};
+    k = 0;
+    pw = philox_walk(i, p, K);
+  };
+  if (active) init(w);
+  // F at Z: f itself when constant, else f at the fitted closest point
+  auto source = [&](const float* Z) -> float {
+    if (f_const) return func3<kPointCloud, float>(pb, pb.f, Z);
+    Knn<float, KM> R;
+    const float h = cloud_knn_coop<KM>(pb, Z, active, R);
+    float cZ[3] = {Z[0], Z[1], Z[2]};
+    if (active) cloud_project<float, KM>(pb, Z, R, h, cZ);
+    return func3<kPointCloud, float>(pb, pb.f, cZ);
+  };
+
+  for (;;) {
+    if (active) {
+      bool done = false;
+      int flag = 0;
+      if (W.hi < tau.hi || (W.hi == tau.hi && W.lo < tau.lo)) done = true;
+      if (!done && k >= max_steps) { done = true; flag = 1; }
+      if (done) {
+        pb.S_out[o] = f2_to_double(S);
+        pb.K_out[o] = k;
+        pb.flag_out[o] = flag;
+        w = next_walk(pb, w, stride);
+        active = w < total;
+        if (active) init(w);
+      }
+    }
+    if (__all_sync(0xffffffffu, !active)) break;
+    float r, a;
+    {
+      Knn<float, KM> R;
+      const float hY = cloud_knn_coop<KM>(pb, Y, active, R);
+      r = theta * (pb.sf.c_h * (active ? hY : 0.0f));   // rho_geo = c_h h(Y); closed: no delta_Gamma
+      a = sqs * r;
+    }
+    if (r != r_prev) {
+      set_weights(a);
+      r_prev = r;
+    }
+    const uint32_t kk = static_cast<uint32_t>(k);
+    float Th[3], F = 0.0f;
+    if (nv == 1) {
+      const U4 b = philox_step_one(pw, kk, K);
+      float dt[3], dz[3];
+      sphere_dir3(u23(b.x), u23(b.y), dt);
+      sphere_dir3(u23(b.z), u23(b.w), dz);
+      const float U = u23_high(b);
+      for (int q = 0; q < 3; ++q) Th[q] = Y[q] + r * dt[q];
+      float t = table_lookup32(pb, a, U);
+      t = fminf(fmaxf(t, 0.0f), 1.0f);
+      const float zs = r * t;
+      float Z[3];
+      for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * dz[q];
+      F = source(Z);
+    } else {
+      float g[3];
+      for (int q = 0; q < 3; ++q) g[q] = gaussian_at32(static_cast<uint32_t>(q), kk, i, p, K);
+      const float sc = r * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
+      for (int q = 0; q < 3; ++q) Th[q] = Y[q] + sc * g[q];
+      const uint32_t nu = 2u * ((3u * static_cast<uint32_t>(1 + nv) + 1u) / 2u);
+      for (int l = 0; l < nv; ++l) {
+        const float U = uniform_at32(nu + static_cast<uint32_t>(l), kk, i, p, K);
+        float t = table_lookup32(pb, a, U);
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        for (int q = 0; q < 3; ++q)
+          g[q] = gaussian_at32(3u * static_cast<uint32_t>(1 + l) + static_cast<uint32_t>(q), kk, i, p, K);
+        const float zs = (r * t) * rsqrtf(fmaxf(dot3(g, g), 1e-30f));
+        float Z[3];
+        for (int q = 0; q < 3; ++q) Z[q] = Y[q] + zs * g[q];
+        F += source(Z);
+      }
+      F /= static_cast<float>(nv);
+    }
+    float Yn[3] = {Y[0], Y[1], Y[2]};
+    {
+      Knn<float, KM> R;
+      const float h = cloud_knn_coop<KM>(pb, Th, active, R);
+      if (active) cloud_project<float, KM>(pb, Th, R, h, Yn);
+    }
+    if (active) {
+      S = f2_add(S, f2_mul_f(f2_mul(W, om2), F));
+      W = f2_mul(W, c2);
+      Y[0] = Yn[0]; Y[1] = Yn[1]; Y[2] = Yn[2];
+      ++k;
+    }
+  }
+}
+
 // One FP32 step of a constant-radius walk with N_V = 1: the draws of step kk,
 // Theta and Z from Y, F = f(cp(Z)) (returned), then Y = cp(Theta).  MQ >= 0:
 // the torus source is one Fourier term with modes (MQ / 4, MQ % 4).
@@ -605,6 +742,13 @@ __global__ void __launch_bounds__(256, FIXED ? 6 : 4) walk3_f32_kernel(const Dev
 template <int MK, int KM>
 __global__ void __launch_bounds__(128) walk3_f32_cloud_kernel(const DevProblem pb) {
   walk3_f32_body<MK, KM, false>(pb);
+}
+// The same walk with the warp-cooperative neighbour search: faster where a
+// cell holds enough points to fill a warp's scan (k >= 12: +50 % at k = 16),
+// slower for small k (-58 % at k = 6), so the host picks by k.
+template <int KM>
+__global__ void __launch_bounds__(128) walk3_f32_cloud_coop_kernel(const DevProblem pb) {
+  walk3_f32_cloud_body<KM>(pb);
 }
 template <int MK, int KM, bool COMP = false>
 __global__ void __launch_bounds__(128) walk3_f64_kernel(const DevProblem pb) { walk3_f64_body<MK, KM, COMP>(pb); }
