@@ -7,7 +7,8 @@
     python -m paper_2606_21883_b300.profile_cases s999_red  # walkr_kernel<float, sphere> (reduced sampler)
     python -m paper_2606_21883_b300.profile_cases s20_red   # walkr_kernel<float, embedded> (reduced sampler)
     python -m paper_2606_21883_b300.profile_cases dumbbell  # walkn_f32_kernel<revolution> (Example 2, n = 1001)
-    python -m paper_2606_21883_b300.profile_cases cloud     # walk3_f32_cloud_kernel (the 200k-point cloud, k = 16)
+    python -m paper_2606_21883_b300.profile_cases cloud     # walk3_f32_cloud_coop_kernel (the 200k-point cloud, k = 16)
+    python -m paper_2606_21883_b300.profile_cases e1_comp   # walk3_f32_kernel<torus, general, m_*> (Example 1)
 
 Each case runs `--reps` walk launches into device buffers (the first one
 warms tables and caches) and prints one line with the walk-steps and the
@@ -50,6 +51,9 @@ def _case(name):
         w = W.point_cloud(P=64, walks=1)
         w.params.tau_w = 1e-4
         return w, 1024, {}
+    if name == "e1_comp":   # Example 1's cut torus with the second-order m_*, 100 points x 16384 walks (~73 steps)
+        w = W.torus_cut(P=100, walks=1, comp=W.COMP_NORMAL2)
+        return w, 16384, {}
     if name == "dumbbell":   # Example 2 in R^1001, walks to completion (~85 steps), 4 walks per warp slot
         w = W.dumbbell(P=2368, walks=1)
         return w, 64, {}
@@ -58,7 +62,8 @@ def _case(name):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999", "s999_red", "s20_red", "dumbbell", "cloud"])
+    ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999", "s999_red", "s20_red", "dumbbell", "cloud",
+                                         "e1_comp"])
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     import torch
