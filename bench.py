@@ -342,6 +342,7 @@ def main():
     ctx = M.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
+    ctx.set_autotune(True)                  # the first warm-up solve picks the walk kernel's block size
     P, N = args.points, args.walks
     pts_dev = torch.tensor(w.points, dtype=torch.float64, device="cuda")
     outs = tuple(torch.zeros(P, dtype=torch.float64, device="cuda") for _ in range(3))
@@ -398,6 +399,8 @@ def main():
         ctx.solve(w.problem, w.params, pts_host, N, precision=M.FP32, out=host_out)
         e2e_t.append(time.perf_counter() - t0)
     clocks = sampler.stop()
+    tuned = ctx.autotune_entries()
+    ctx.set_autotune(False)                 # the serving and secondary legs launch the default shapes
 
     steps_per_solve = float(msteps.sum() * N)
     tmax, e2e_mean = max_over_ranks(dist, "cuda", t_dev, float(np.mean(e2e_t)))
@@ -430,6 +433,7 @@ def main():
                          "ops_per_walk_step": OPS_PER_STEP,
                          "peak_source": f"148 SM x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz ({src} max clock)"},
             "clocks": clocks,
+            "autotune": tuned,
         }
         if not args.no_serving and world == 1:
             line["serving"] = serving_leg(M, ctx)

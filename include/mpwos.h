@@ -316,6 +316,40 @@ int mpwos_tc_project(mpwos_ctx* ctx, const double* Q, int n, int D, const float*
 /* Number of the library's own kernel launches so far on this context. */
 int64_t mpwos_launch_count(const mpwos_ctx* ctx);
 
+/* Launch-shape autotuner (runtime only; the method does not depend on it).
+ * enable != 0 turns it on for this context, 0 off (the default).  While on,
+ * the first mpwos_solve or mpwos_walk_scores for a walk kernel instance and
+ * ambient dimension n with enough walks (at least 2 (candidates + 1) full
+ * waves) splits its walks into candidates + 1 equal parts, runs each of the
+ * first parts with one candidate block size (32, 64, 128, 256 threads, up to
+ * the kernel's limit; each launch fills every SM), times each part with CUDA
+ * events, divides by the part's walk-steps, keeps the fastest and runs the last
+ * part with it; one host synchronisation.  Later calls for that instance, request serving included,
+ * launch the pick.  Smaller calls launch the default shape and record nothing.
+ * Results never depend on the shape: each walk's random numbers are a function
+ * of (point, walk, step) alone and per-point sums run in a fixed order.  The
+ * tensor-core walk keeps its fixed shape; mpwos_solve_noalloc always launches
+ * the default shape.  Picks persist until the context is destroyed.
+ * MPWOS_EINVAL for a null context. */
+int mpwos_set_autotune(mpwos_ctx* ctx, int enable);
+
+/* One autotuned kernel: `kernel` its (mangled) name, owned by the CUDA runtime
+ * (NULL if unavailable); n the ambient dimension; block the pick; per
+ * candidate block size, the measured GPU time per walk-step in ns. */
+typedef struct {
+  const char* kernel;
+  int n;
+  int block;
+  int n_candidates;
+  int candidates[4];
+  double ns_per_walk_step[4];
+} mpwos_tune_entry;
+
+/* Copies up to `capacity` picks into `entries` (caller-owned) and their total
+ * number into *count.  MPWOS_EINVAL for a null context or count, a negative
+ * capacity, or capacity > 0 with null entries. */
+int mpwos_autotune_entries(mpwos_ctx* ctx, mpwos_tune_entry* entries, int capacity, int* count);
+
 #ifdef __cplusplus
 }
 #endif

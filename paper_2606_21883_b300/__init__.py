@@ -60,6 +60,11 @@ class Params(C.Structure):
                 ("projection", C.c_int), ("sampler", C.c_int)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("kernel", C.c_char_p), ("n", C.c_int), ("block", C.c_int), ("n_candidates", C.c_int),
+                ("candidates", C.c_int * 4), ("ns_per_walk_step", C.c_double * 4)]
+
+
 _lib: Optional[C.CDLL] = None
 
 
@@ -95,6 +100,8 @@ def lib() -> C.CDLL:
         L.mpwos_cancel.argtypes = [C.c_void_p, C.c_uint64]
         L.mpwos_fetch.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(C.c_double)]
+        L.mpwos_set_autotune.argtypes = [C.c_void_p, C.c_int]
+        L.mpwos_autotune_entries.argtypes = [C.c_void_p, C.POINTER(TuneEntry), C.c_int, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -211,6 +218,25 @@ class Context:
 
     def set_stream(self, stream_handle: int):
         return self._check(self.L.mpwos_set_stream(self.h, C.c_void_p(stream_handle)))
+
+    def set_autotune(self, enable: bool = True):
+        """Turn the launch-shape autotuner on or off (mpwos_set_autotune)."""
+        return self._check(self.L.mpwos_set_autotune(self.h, 1 if enable else 0))
+
+    def autotune_entries(self) -> list:
+        """The autotuner's picks: one dict per (kernel, n) with the pick and the
+        measured GPU ns per walk-step of each candidate block size."""
+        count = C.c_int(0)
+        self._check(self.L.mpwos_autotune_entries(self.h, None, 0, C.byref(count)))
+        arr = (TuneEntry * max(count.value, 1))()
+        self._check(self.L.mpwos_autotune_entries(self.h, arr, count.value, C.byref(count)))
+        out = []
+        for e in arr[:count.value]:
+            nc = e.n_candidates
+            out.append({"kernel": e.kernel.decode() if e.kernel else None, "n": e.n, "block": e.block,
+                        "ns_per_walk_step": {int(e.candidates[c]): float(e.ns_per_walk_step[c])
+                                             for c in range(nc)}})
+        return out
 
     # -- the walk ---------------------------------------------------------------
     def solve(self, problem, params, pts, N, precision=FP64, out=None, projection=PROJ_AUTO):

@@ -127,6 +127,16 @@ cudaError_t launch_walkr_f32(const DevProblem& pb, int grid, int block, cudaStre
 
 int occupancy_walkr_f64(const DevProblem& pb, int block);
 
+const void* walk_fn_f32(const DevProblem& pb) {
+  if (pb.reduced)
+    return (pb.mkind == kEuclid || pb.mkind == kSphere || pb.mkind == kEmbeddedSphere) ? walkr32_fn(pb) : nullptr;
+  if (pb.n == 3 && pb.mkind != kEmbeddedSphere) return walk3_f32_fn(pb);
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere && pb.mkind != kRevolution &&
+      pb.mkind != kCurveSphere)
+    return nullptr;
+  return walkn_f32_fn(pb);
+}
+
 int occupancy_walkr(const DevProblem& pb, bool fp64, int block) {
   if (fp64) return occupancy_walkr_f64(pb, block);
   int nb = 0;

@@ -247,6 +247,17 @@ cudaError_t launch_reduced_start(const double* pts, int n, const int* T, int nT,
   return cudaGetLastError();
 }
 
+const void* walk_fn_f64(const DevProblem& pb) {
+  if (pb.reduced)
+    return (pb.mkind == kEuclid || pb.mkind == kSphere || pb.mkind == kEmbeddedSphere) ? walkr_fn<double>(pb)
+                                                                                       : nullptr;
+  if (pb.n == 3 && pb.mkind != kEmbeddedSphere) return walk3_f64_fn(pb);
+  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere && pb.mkind != kRevolution &&
+      pb.mkind != kCurveSphere)
+    return nullptr;
+  return walkn_f64_fn(pb);
+}
+
 int occupancy_walkr_f64(const DevProblem& pb, int block) {
   int nb = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walkr_fn<double>(pb), block, 0);

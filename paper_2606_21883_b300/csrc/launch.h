@@ -29,6 +29,11 @@ cudaError_t launch_reduced_start(const double* pts, int n, const int* T, int nT,
 // Resident blocks per SM of the walk kernel chosen for pb.
 int occupancy_walk_f64(const DevProblem& pb, bool n3, int block);
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block);
+// The kernel that launch_walkr_*, launch_walk3_* or launch_walkn_* runs for pb
+// (reduced sampler, n = 3 thread walk or warp walk, in that order); nullptr if
+// none applies.  The launch-shape autotuner keys its picks by it.
+const void* walk_fn_f64(const DevProblem& pb);
+const void* walk_fn_f32(const DevProblem& pb);
 
 // Intrinsic start points s0 = normalize(Q^T (y0 - b)) of an embedded sphere
 // (QT: D x n device array), one warp per point.

@@ -53,6 +53,14 @@ struct CloudGrid {
 struct ServeEngine;
 void serve_shutdown(mpwos_ctx* ctx);
 
+// One autotuned walk kernel instance: the candidate block sizes, the GPU time
+// per walk-step each measured, and the pick.
+struct TuneEntry {
+  int block = 0;
+  std::vector<int> cand;
+  std::vector<double> ns_per_step;
+};
+
 struct mpwos_ctx {
   std::recursive_mutex mu;           // public calls and the request scheduler
   ServeEngine* serve = nullptr;
@@ -64,6 +72,8 @@ struct mpwos_ctx {
   long long launches = 0;
   std::map<std::tuple<int, int, double>, Table> tables;  // (n, NA, z_max or a) -> table
   std::map<std::tuple<const void*, int64_t, int, double>, CloudGrid> clouds;  // (ptr, N, k, checksum) -> grid
+  bool autotune = false;
+  std::map<std::pair<const void*, int>, TuneEntry> tune;  // (walk kernel, n) -> measured launch shapes
 };
 
 namespace {
@@ -779,20 +789,27 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   return MPWOS_OK;
 }
 
-int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid);
+int launch_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid, int block);
+
+int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid) {
+  return launch_walks(ctx, pb, fp64, st, max_grid, 0);
+}
 
 int run_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64) { return run_walks_on(ctx, pb, fp64, ctx->stream, 0); }
 
 // Launch the walk kernel for pb's work range on st; max_grid > 0 caps the grid,
 // max_grid < 0 takes a 1/|max_grid| share of the full grid (served requests
-// leave SMs to the other requests in flight).
-int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid) {
+// leave SMs to the other requests in flight).  block > 0 replaces the default
+// block size (a multiple of 32 within the kernel's limit; the tensor-core walk
+// keeps its own); the grid is then the SM count times the resident blocks of
+// that size.
+int launch_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid, int block_req) {
   if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tabc)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
   if (pb.wk_next) CK(cudaMemsetAsync(pb.wk_next, 0, sizeof(unsigned long long), st));
   if (pb.reduced) {
-    const int blk = 128;
+    const int blk = block_req > 0 ? block_req : 128;
     int64_t grid = static_cast<int64_t>(ctx->sm_count) * occupancy_walkr(pb, fp64, blk);
     const int64_t need = (pb.wk_w1 - pb.wk_w0 + blk - 1) / blk;
     if (max_grid < 0) grid = std::max<int64_t>(ctx->sm_count, grid / (-max_grid));
@@ -817,7 +834,7 @@ int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
     return MPWOS_OK;
   }
   const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
-  const int block = n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256) : 128;
+  const int block = block_req > 0 ? block_req : (n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256) : 128);
   const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
   const int64_t per_block = n3 ? block : block / 32;
   int64_t grid = static_cast<int64_t>(ctx->sm_count) * occ;
@@ -833,9 +850,136 @@ int run_walks_on(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   return MPWOS_OK;
 }
 
+// The autotuned block size for pb's walk kernel, or 0 (the default shape)
+// when tuning is off or nothing was measured for it yet.
+int tuned_block(mpwos_ctx* ctx, const DevProblem& pb, bool fp64) {
+  if (!ctx->autotune || (pb.tc_bimg && !fp64)) return 0;
+  const void* fn = fp64 ? walk_fn_f64(pb) : walk_fn_f32(pb);
+  const auto it = ctx->tune.find({fn, pb.n});
+  return it == ctx->tune.end() ? 0 : it->second.block;
+}
+
+// Walks of pb's range on the context's stream, with the launch-shape
+// autotuner when it is on.  The first call for a (kernel, n) with at least two
+// waves of walks per part splits its walks into (candidates + 1) equal parts;
+// each of the first parts runs with one candidate block size (32 to 256
+// threads within the kernel's limit, each launch filling every SM) and is timed
+// with CUDA events, divided by its walk-steps (read back from K_out, whose row
+// for walk w is w in these calls); the fastest is kept and runs the last part.  Each walk's draws depend only on
+// (point, walk, step), so the shape changes no result.
+int run_walks_tuned(mpwos_ctx* ctx, DevProblem& pb, bool fp64) {
+  cudaStream_t st = ctx->stream;
+  if (!ctx->autotune || (pb.tc_bimg && !fp64)) return launch_walks(ctx, pb, fp64, st, 0, 0);
+  const void* fn = fp64 ? walk_fn_f64(pb) : walk_fn_f32(pb);
+  if (!fn || pb.wk_points || pb.wk_i0 != 0 || pb.out_stride != pb.wk_i1) return launch_walks(ctx, pb, fp64, st, 0, 0);
+  const auto key = std::make_pair(fn, pb.n);
+  const auto it = ctx->tune.find(key);
+  if (it != ctx->tune.end()) return launch_walks(ctx, pb, fp64, st, 0, it->second.block);
+  cudaFuncAttributes fa{};
+  CK(cudaFuncGetAttributes(&fa, fn));
+  const bool n3 = !pb.reduced && pb.n == 3 && pb.mkind != kEmbeddedSphere;
+  const bool warp = !pb.reduced && !n3;
+  std::vector<int> cand;
+  for (int b : {32, 64, 128, 256})
+    if (b <= fa.maxThreadsPerBlock) cand.push_back(b);
+  // a chunk is two waves of the largest resident walker set among the candidates
+  int64_t wave = 0;
+  for (int b : cand) {
+    const int occ = pb.reduced ? occupancy_walkr(pb, fp64, b)
+                               : (fp64 ? occupancy_walk_f64(pb, n3, b) : occupancy_walk_f32(pb, n3, b));
+    wave = std::max<int64_t>(wave, static_cast<int64_t>(ctx->sm_count) * occ * (warp ? b / 32 : b));
+  }
+  const int64_t nc = static_cast<int64_t>(cand.size());
+  if (cand.empty() || pb.wk_w1 - pb.wk_w0 < 2 * wave * (nc + 1)) return launch_walks(ctx, pb, fp64, st, 0, 0);
+  // every chunk is useful work, so the chunks take most of the call: the more
+  // waves a chunk holds, the less its time depends on its longest walk
+  const int64_t chunk = (pb.wk_w1 - pb.wk_w0) / (nc + 1);
+  std::vector<cudaEvent_t> ev(cand.size() + 1, nullptr);
+  int rc = MPWOS_OK;
+  for (auto& e : ev)
+    if (!rc && cudaEventCreate(&e) != cudaSuccess) rc = fail(ctx, MPWOS_ECUDA, "autotune: event create");
+  const int64_t w0 = pb.wk_w0, w1 = pb.wk_w1;
+  if (!rc && cudaEventRecord(ev[0], st) != cudaSuccess) rc = fail(ctx, MPWOS_ECUDA, "autotune: event record");
+  for (int64_t c = 0; c < nc && !rc; ++c) {
+    pb.wk_w0 = w0 + c * chunk;
+    pb.wk_w1 = pb.wk_w0 + chunk;
+    rc = launch_walks(ctx, pb, fp64, st, 0, cand[c]);
+    if (!rc && cudaEventRecord(ev[c + 1], st) != cudaSuccess) rc = fail(ctx, MPWOS_ECUDA, "autotune: event record");
+  }
+  std::vector<int32_t> ks;
+  if (!rc) {
+    ks.resize(static_cast<size_t>(nc * chunk));
+    if (cudaMemcpyAsync(ks.data(), pb.K_out + w0, ks.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      rc = fail(ctx, MPWOS_ECUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+  }
+  TuneEntry te;
+  te.cand = cand;
+  double best = 0.0;
+  for (int64_t c = 0; c < nc && !rc; ++c) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ev[c], ev[c + 1]) != cudaSuccess) {
+      rc = fail(ctx, MPWOS_ECUDA, "autotune: event timing");
+      break;
+    }
+    int64_t steps = 0;
+    for (int64_t q = c * chunk; q < (c + 1) * chunk; ++q) steps += ks[static_cast<size_t>(q)];
+    const double ns = 1e6 * ms / static_cast<double>(std::max<int64_t>(steps, chunk));
+    te.ns_per_step.push_back(ns);
+    if (te.block == 0 || ns < best) {
+      best = ns;
+      te.block = cand[c];
+    }
+  }
+  for (auto& e : ev)
+    if (e) cudaEventDestroy(e);
+  pb.wk_w0 = w0 + nc * chunk;
+  pb.wk_w1 = w1;
+  if (!rc) {
+    ctx->tune[key] = te;
+    rc = launch_walks(ctx, pb, fp64, st, 0, te.block);
+  }
+  pb.wk_w0 = w0;
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+int mpwos_set_autotune(mpwos_ctx* ctx, int enable) {
+  if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  ctx->autotune = enable != 0;
+  return MPWOS_OK;
+}
+
+int mpwos_autotune_entries(mpwos_ctx* ctx, mpwos_tune_entry* entries, int capacity, int* count) {
+  if (!ctx || !count || capacity < 0 || (capacity > 0 && !entries)) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  *count = static_cast<int>(ctx->tune.size());
+  int q = 0;
+  for (const auto& kv : ctx->tune) {
+    if (q >= capacity) break;
+    mpwos_tune_entry& e = entries[q++];
+    e = mpwos_tune_entry{};
+    const char* name = nullptr;
+    if (cudaFuncGetName(&name, kv.first.first) != cudaSuccess) {
+      cudaGetLastError();
+      name = nullptr;
+    }
+    e.kernel = name;
+    e.n = kv.first.second;
+    e.block = kv.second.block;
+    e.n_candidates = static_cast<int>(std::min<size_t>(kv.second.cand.size(), 4));
+    for (int c = 0; c < e.n_candidates; ++c) {
+      e.candidates[c] = kv.second.cand[c];
+      e.ns_per_walk_step[c] = kv.second.ns_per_step[c];
+    }
+  }
+  return MPWOS_OK;
+}
 
 void mpwos_params_default(mpwos_params* p) {
   if (!p) return;
@@ -921,7 +1065,7 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
   pb.K_out = dK ? K : sc.alloc<int32_t>(W);
   pb.flag_out = dF ? flags : sc.alloc<int32_t>(W);
   if (!pb.S_out || !pb.K_out || !pb.flag_out) return fail(ctx, MPWOS_ENOMEM, "per-walk outputs (%zu walks)", W);
-  rc = run_walks(ctx, pb, prm->precision == MPWOS_FP64);
+  rc = run_walks_tuned(ctx, pb, prm->precision == MPWOS_FP64);
   if (rc) return rc;
   if (!dS) CK(cudaMemcpyAsync(S, pb.S_out, W * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   if (!dK) CK(cudaMemcpyAsync(K, pb.K_out, W * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
@@ -957,7 +1101,7 @@ int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_proble
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !nflag || !om || !os || !ot)
     return fail(ctx, MPWOS_ENOMEM, "scratch for %zu walks", W);
   CK(cudaMemsetAsync(nflag, 0, sizeof(unsigned long long), ctx->stream));
-  rc = run_walks(ctx, pb, prm->precision == MPWOS_FP64);
+  rc = run_walks_tuned(ctx, pb, prm->precision == MPWOS_FP64);
   if (rc) return rc;
   if (P) {
     CK(launch_reduce(pb.S_out, pb.K_out, pb.flag_out, P, N, om, os, ot, nflag, ctx->stream));
@@ -1387,7 +1531,8 @@ int req_round(mpwos_ctx* ctx, Request& r, int64_t i1) {
   for (int64_t w0 = 0; w0 < total; w0 += E.chunk_walks) {
     r.pb.wk_w0 = w0;
     r.pb.wk_w1 = std::min(total, w0 + E.chunk_walks);
-    int rc = run_walks_on(ctx, r.pb, r.prm.precision == MPWOS_FP64, st, max_grid);
+    const bool fp64 = r.prm.precision == MPWOS_FP64;
+    int rc = launch_walks(ctx, r.pb, fp64, st, max_grid, tuned_block(ctx, r.pb, fp64));
     if (rc) return rc;
   }
   CK(cudaMemsetAsync(r.nflag, 0, sizeof(unsigned long long), st));

@@ -29,3 +29,15 @@ def test_library_exports_every_declared_symbol():
 
 def test_library_targets_sm103a():
     assert any("compute_103a,code=sm_103a" in a for a in B.ARCH)
+
+
+def test_autotune_calls_reject_null_context():
+    """Host-side argument checks of the autotuner's entry points (no GPU needed)."""
+    lib = ctypes.CDLL(B.build())
+    lib.mpwos_set_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.mpwos_autotune_entries.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int)]
+    einval = 1
+    assert lib.mpwos_set_autotune(None, 1) == einval
+    n = ctypes.c_int(-1)
+    assert lib.mpwos_autotune_entries(None, None, 0, ctypes.byref(n)) == einval
