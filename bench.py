@@ -250,7 +250,38 @@ def secondary_leg(M, ctx):
                      "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))), "seconds": dt,
                      "mean_steps_per_walk": float(ms.mean())}
     out["torus_fp32_over_fp64"] = out["torus_fp32"]["walk_steps_per_s"] / out["torus_fp64"]["walk_steps_per_s"]
+    out["cloud_knn_200k"] = knn_leg(M, ctx)
     return out
+
+
+def knn_leg(M, ctx, nq=262144):
+    """The 200k cloud's k = 16 nearest search on its own: the walk's grid search (per
+    thread and warp-cooperative) against the all-pairs scan, queries/s by CUDA events
+    on device-resident queries near the surface."""
+    import torch
+    w = W.point_cloud(P=1, walks=1)
+    cloud = w.problem.manifold.cloud
+    rng = np.random.default_rng(3)
+    x = cloud[rng.choice(cloud.shape[0], nq)] + rng.uniform(-0.02, 0.02, (nq, 3))
+    xd = torch.tensor(x, device="cuda")
+    k = w.problem.manifold.k_nn
+    out = (torch.empty((nq, k), dtype=torch.int32, device="cuda"),
+           torch.empty((nq, k), dtype=torch.float64, device="cuda"),
+           torch.empty(nq, dtype=torch.float64, device="cuda"))
+    res = {"queries": nq, "k": k, "cloud_points": int(cloud.shape[0])}
+    for name, prec, meth in (("grid_fp32", M.FP32, M.KNN_GRID), ("grid_warp_fp32", M.FP32, M.KNN_GRID_WARP),
+                             ("scan_fp32", M.FP32, M.KNN_SCAN), ("grid_fp64", M.FP64, M.KNN_GRID)):
+        ctx.cloud_knn(w.problem, xd, precision=prec, method=meth, out=out)     # warm (grid built once)
+        ts = []
+        for _ in range(3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.cloud_knn(w.problem, xd, precision=prec, method=meth, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) / 1e3)
+        res[name + "_queries_per_s"] = nq / float(np.median(ts))
+    return res
 
 
 def cpu_baseline(target_s: float = 25.0):

@@ -313,6 +313,26 @@ int mpwos_c_sigma_r(mpwos_ctx* ctx, int n, const double* a, double* c, int64_t c
 int mpwos_tc_project(mpwos_ctx* ctx, const double* Q, int n, int D, const float* G, int64_t rows,
                      float* out, float* gg);
 
+/* ---- k nearest cloud points --------------------------------------------- */
+#define MPWOS_KNN_GRID 0       /* the walk's search: expanding cubes of grid cells, a thread per query */
+#define MPWOS_KNN_GRID_WARP 1  /* its warp-cooperative form (FP32 only; the FP32 walk's at k >= 12)   */
+#define MPWOS_KNN_SCAN 2       /* every cloud point, staged through shared memory (comparison)         */
+
+/* The k = m->k_nn nearest points of the point cloud m (MPWOS_POINT_CLOUD;
+ * Sec. 2.1 representation (iii)) to each of nq query points x (nq x 3,
+ * row-major), as the walk's closest-point step finds them (the first step of
+ * its cp; h(x), eq. rho_geo_spacing, is their mean distance).  Order: by
+ * distance^2, ties by cloud index.  Distances in `precision` (MPWOS_FP32: x
+ * and the cloud rounded to FP32 as the FP32 walk holds them; MPWOS_FP64).  All
+ * three methods give identical results at one precision.  Outputs
+ * (caller-owned): idx (nq x k cloud indices), d2 (nq x k, widened to FP64), h
+ * (nq).  x, idx, d2 and h may each be host or device memory.  MPWOS_EINVAL:
+ * m not a point cloud, k_nn outside [1, 32], n_cloud outside [k_nn, 2^31),
+ * nq < 0, a null array with nq > 0, an unknown method or precision, or
+ * MPWOS_KNN_GRID_WARP with MPWOS_FP64. */
+int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const double* x, int64_t nq,
+                    int precision, int method, int32_t* idx, double* d2, double* h);
+
 /* Number of the library's own kernel launches so far on this context. */
 int64_t mpwos_launch_count(const mpwos_ctx* ctx);
 

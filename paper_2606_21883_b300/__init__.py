@@ -24,6 +24,7 @@ MPWOS_ETIMEDOUT, MPWOS_ECANCELED, MPWOS_EMAXSTEPS, MPWOS_ENOTFOUND, MPWOS_EBUSY 
 FP64, FP32 = 0, 1
 PROJ_AUTO, PROJ_TENSOR, PROJ_CUDA = 0, 1, 2
 SAMPLER_FULL, SAMPLER_REDUCED = 0, 1
+KNN_GRID, KNN_GRID_WARP, KNN_SCAN = 0, 1, 2
 COMP_NONE, COMP_NORMAL2, COMP_EXACT = 0, 1, 2
 
 _dp = C.POINTER(C.c_double)
@@ -101,6 +102,8 @@ def lib() -> C.CDLL:
         L.mpwos_fetch.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(C.c_double)]
         L.mpwos_set_autotune.argtypes = [C.c_void_p, C.c_int]
+        L.mpwos_cloud_knn.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_void_p]
         L.mpwos_autotune_entries.argtypes = [C.c_void_p, C.POINTER(TuneEntry), C.c_int, C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -218,6 +221,27 @@ class Context:
 
     def set_stream(self, stream_handle: int):
         return self._check(self.L.mpwos_set_stream(self.h, C.c_void_p(stream_handle)))
+
+    def cloud_knn(self, problem, x, precision=FP32, method=KNN_GRID, out=None):
+        """mpwos_cloud_knn: the k nearest cloud points of the queries x (nq x 3) as the
+        walk finds them: (idx nq x k, d2 nq x k, h nq).  x host or device; out, if given,
+        is a tuple of device tensors (idx int32, d2, h) written in place."""
+        mar = _Marshal()
+        md, _ = mar.problem(problem)
+        nq = int(x.shape[0])
+        if not hasattr(x, "data_ptr"):
+            x = mar.arr(x)
+        k = int(problem.manifold.k_nn)
+        if out is None:
+            idx = np.zeros((nq, k), dtype=np.int32)
+            d2 = np.zeros((nq, k))
+            h = np.zeros(nq)
+        else:
+            idx, d2, h = out
+        rc = self.L.mpwos_cloud_knn(self.h, C.byref(md), _ptr(x), nq, int(precision), int(method), _ptr(idx),
+                                    _ptr(d2), _ptr(h))
+        self._check(rc)
+        return idx, d2, h
 
     def set_autotune(self, enable: bool = True):
         """Turn the launch-shape autotuner on or off (mpwos_set_autotune)."""

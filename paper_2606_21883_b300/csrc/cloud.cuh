@@ -376,4 +376,127 @@ __device__ __forceinline__ void cloud_project(const DevProblem& pb, const T* x, 
   for (int i = 0; i < 3; ++i) out[i] = c[i] + s * (xi1 * u[i] + et1 * v[i] + z1 * nr[i]);
 }
 
+// ---------------------------------------------------------------------------
+// k-nearest queries outside the walk (verification and the search comparison)
+// ---------------------------------------------------------------------------
+template <typename T, int KM>
+__device__ __forceinline__ void knn_store(const Knn<T, KM>& R, int k, T hq, int64_t q, int32_t* idx, double* d2,
+                                          double* h) {
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    if (j < k) {
+      idx[q * k + j] = R.gid[j];
+      d2[q * k + j] = static_cast<double>(R.d2[j]);
+    }
+  }
+  h[q] = static_cast<double>(hq);
+}
+
+// The walk's own grid search for nq query points (x: nq x 3, FP64, converted
+// to T as the walk holds them).  COOP (FP32 only): the warp-cooperative search,
+// all 32 lanes of a warp passing through it together.
+template <typename T, int KM, bool COOP>
+__global__ void __launch_bounds__(128) cloud_knn_query_kernel(const DevProblem pb, const double* xq, int64_t nq,
+                                                              int32_t* idx, double* d2, double* h) {
+  const int64_t nthreads = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = static_cast<int64_t>(blockIdx.x) * blockDim.x + (threadIdx.x - lane); base < nq;
+       base += nthreads) {   // warp-uniform trip count
+    const int64_t q = base + lane;
+    const bool has = q < nq;
+    T x[3] = {T(0), T(0), T(0)};
+    if (has)
+      for (int a = 0; a < 3; ++a) x[a] = static_cast<T>(xq[3 * q + a]);
+    Knn<T, KM> R;
+    T hq;
+    if constexpr (COOP) {
+      hq = cloud_knn_coop<KM>(pb, x, has, R);
+    } else {
+      if (!has) continue;
+      hq = cloud_knn<T, KM>(pb, x, R);
+    }
+    if (has) knn_store<T, KM>(R, pb.cl_k, hq, q, idx, d2, h);
+  }
+}
+
+// The all-pairs search: every cloud point against each query, the cloud
+// staged through shared memory kScanTile points at a time as (x, y, z,
+// original index) quadruples (one 16-byte load per point in FP32).  Tile t
+// holds the sorted positions t, t + T, t + 2T, ... (T tiles): a sample of the
+// whole cloud, so the first tile already bounds the k-th distance closely and
+// later insertions are rare (in cell order a query's bound would shrink only
+// as the sweep approached it, inserting thousands of times).  Each thread
+// serves kScanQ queries (q0 + m blockDim.x), so that one pass of the cloud
+// through L2 serves kScanQ x 128 queries, and keeps each query's current k-th
+// distance in a register so that most pairs end after one comparison.  Same
+// distances and the same (distance^2, original index) order as the grid
+// search, so the same k nearest; kept as the measured comparison for it.
+constexpr int kScanTile = 512;
+constexpr int kScanQ = 4;
+
+// knn_insert out of line: the scan's rare insertions stay off the per-pair path.
+template <typename T, int KM>
+__device__ __noinline__ void knn_insert_outlined(Knn<T, KM>& R, int k, T dd, int pos, int g) {
+  knn_insert<T, KM>(R, k, dd, pos, g);
+}
+
+template <typename T>
+struct ScanPt { T x, y, z; int g; };
+template <>
+struct __align__(16) ScanPt<float> { float x, y, z; int g; };
+
+template <typename T, int KM>
+__global__ void __launch_bounds__(128) cloud_knn_scan_kernel(const DevProblem pb, const double* xq, int64_t nq,
+                                                             int64_t ncl, int32_t* idx, double* d2, double* h) {
+  __shared__ ScanPt<T> sp[kScanTile];
+  const int64_t q0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * kScanQ + threadIdx.x;
+  const int k = pb.cl_k;
+  T x[kScanQ][3];
+  bool has[kScanQ];
+  T kth[kScanQ];
+  Knn<T, KM> R[kScanQ];
+#pragma unroll
+  for (int m = 0; m < kScanQ; ++m) {
+    const int64_t q = q0 + static_cast<int64_t>(m) * blockDim.x;
+    has[m] = q < nq;
+    for (int a = 0; a < 3; ++a) x[m][a] = has[m] ? static_cast<T>(xq[3 * q + a]) : T(0);
+    kth[m] = T(INFINITY);
+#pragma unroll
+    for (int j = 0; j < KM; ++j) { R[m].d2[j] = T(INFINITY); R[m].idx[j] = -1; R[m].gid[j] = 0x7fffffff; }
+  }
+  const T* P = cloud_pts<T>(pb);
+  const int64_t ntiles = (ncl + kScanTile - 1) / kScanTile;
+  for (int64_t t = 0; t < ntiles; ++t) {
+    const int nt = static_cast<int>((ncl - t + ntiles - 1) / ntiles);   // positions t + i ntiles < ncl
+    __syncthreads();
+    for (int i = threadIdx.x; i < nt; i += blockDim.x) {
+      const int64_t pi = t + static_cast<int64_t>(i) * ntiles;
+      sp[i] = ScanPt<T>{P[3 * pi], P[3 * pi + 1], P[3 * pi + 2], pb.cl_orig[pi]};
+    }
+    __syncthreads();
+    for (int i = 0; i < nt; ++i) {
+      const ScanPt<T> c = sp[i];
+      const int pos = static_cast<int>(t + static_cast<int64_t>(i) * ntiles);
+#pragma unroll
+      for (int m = 0; m < kScanQ; ++m) {
+        const T ddx = c.x - x[m][0], ddy = c.y - x[m][1], ddz = c.z - x[m][2];
+        const T dd = ddx * ddx + ddy * ddy + ddz * ddz;
+        if (has[m] && dd <= kth[m]) {   // otherwise knn_insert would reject it too
+          knn_insert_outlined<T, KM>(R[m], k, dd, pos, c.g);
+          kth[m] = R[m].d2[k - 1];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < kScanQ; ++m) {
+    if (!has[m]) continue;
+    T hq = T(0);
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) hq += sqrt(R[m].d2[j]);
+    knn_store<T, KM>(R[m], k, hq / T(k), q0 + static_cast<int64_t>(m) * blockDim.x, idx, d2, h);
+  }
+}
+
 }  // namespace mpwos

@@ -156,6 +156,30 @@ int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
   return nb < 1 ? 1 : nb;
 }
 
+cudaError_t launch_cloud_knn_f32(const DevProblem& pb, const double* x, int64_t nq, int method, int64_t ncl,
+                                 int32_t* idx, double* d2, double* h, int max_blocks, cudaStream_t st) {
+  if (nq <= 0) return cudaSuccess;
+  const int64_t need = (nq + 127) / 128;
+  const unsigned grid = static_cast<unsigned>(need < max_blocks ? need : max_blocks);
+  const bool small = pb.cl_k <= 8, mid = pb.cl_k <= 16;
+  if (method == 0) {
+    if (small) cloud_knn_query_kernel<float, 8, false><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+    else if (mid) cloud_knn_query_kernel<float, 16, false><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+    else cloud_knn_query_kernel<float, 32, false><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+  } else if (method == 1) {
+    if (mid) cloud_knn_query_kernel<float, 16, true><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+    else cloud_knn_query_kernel<float, 32, true><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+  } else if (method == 2) {
+    const unsigned g = static_cast<unsigned>((nq + 128 * kScanQ - 1) / (128 * kScanQ));
+    if (small) cloud_knn_scan_kernel<float, 8><<<g, 128, 0, st>>>(pb, x, nq, ncl, idx, d2, h);
+    else if (mid) cloud_knn_scan_kernel<float, 16><<<g, 128, 0, st>>>(pb, x, nq, ncl, idx, d2, h);
+    else cloud_knn_scan_kernel<float, 32><<<g, 128, 0, st>>>(pb, x, nq, ncl, idx, d2, h);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 __global__ void green_radius32_kernel(const double* a, const double* U, double* t, int64_t count,
                                       const float4* tabc, int NA, int NS, float tab_scale, float z_scale) {
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;

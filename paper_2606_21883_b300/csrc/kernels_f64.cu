@@ -247,6 +247,27 @@ cudaError_t launch_reduced_start(const double* pts, int n, const int* T, int nT,
   return cudaGetLastError();
 }
 
+cudaError_t launch_cloud_knn_f64(const DevProblem& pb, const double* x, int64_t nq, int method, int64_t ncl,
+                                 int32_t* idx, double* d2, double* h, int max_blocks, cudaStream_t st) {
+  if (nq <= 0) return cudaSuccess;
+  const int64_t need = (nq + 127) / 128;
+  const unsigned grid = static_cast<unsigned>(need < max_blocks ? need : max_blocks);
+  const bool small = pb.cl_k <= 8, mid = pb.cl_k <= 16;
+  if (method == 0) {
+    if (small) cloud_knn_query_kernel<double, 8, false><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+    else if (mid) cloud_knn_query_kernel<double, 16, false><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+    else cloud_knn_query_kernel<double, 32, false><<<grid, 128, 0, st>>>(pb, x, nq, idx, d2, h);
+  } else if (method == 2) {
+    const unsigned g = static_cast<unsigned>((nq + 128 * kScanQ - 1) / (128 * kScanQ));
+    if (small) cloud_knn_scan_kernel<double, 8><<<g, 128, 0, st>>>(pb, x, nq, ncl, idx, d2, h);
+    else if (mid) cloud_knn_scan_kernel<double, 16><<<g, 128, 0, st>>>(pb, x, nq, ncl, idx, d2, h);
+    else cloud_knn_scan_kernel<double, 32><<<g, 128, 0, st>>>(pb, x, nq, ncl, idx, d2, h);
+  } else {
+    return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 const void* walk_fn_f64(const DevProblem& pb) {
   if (pb.reduced)
     return (pb.mkind == kEuclid || pb.mkind == kSphere || pb.mkind == kEmbeddedSphere) ? walkr_fn<double>(pb)

@@ -63,6 +63,14 @@ cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[
                               int* orig, cudaStream_t st);
 cudaError_t launch_cloud_hmax(const DevProblem& pb, int64_t N, unsigned long long* hmax_bits, cudaStream_t st);
 
+// k nearest cloud points of nq queries (x: nq x 3 FP64, device) by method
+// (0: the walk's grid search, 1: its warp-cooperative form, FP32 only, 2: the
+// all-pairs scan); idx and d2 nq x k, h nq, all device arrays.
+cudaError_t launch_cloud_knn_f32(const DevProblem& pb, const double* x, int64_t nq, int method, int64_t ncl,
+                                 int32_t* idx, double* d2, double* h, int max_blocks, cudaStream_t st);
+cudaError_t launch_cloud_knn_f64(const DevProblem& pb, const double* x, int64_t nq, int method, int64_t ncl,
+                                 int32_t* idx, double* d2, double* h, int max_blocks, cudaStream_t st);
+
 // Verification primitives.
 cudaError_t launch_philox(const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, int64_t count,
                           cudaStream_t st);

@@ -948,6 +948,66 @@ int run_walks_tuned(mpwos_ctx* ctx, DevProblem& pb, bool fp64) {
 
 extern "C" {
 
+int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const double* x, int64_t nq, int precision,
+                    int method, int32_t* idx, double* d2, double* h) {
+  if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  if (!m || m->kind != MPWOS_POINT_CLOUD || !m->cloud) return fail(ctx, MPWOS_EINVAL, "not a point cloud");
+  if (m->k_nn < 1 || m->k_nn > 32) return fail(ctx, MPWOS_EINVAL, "k_nn must lie in [1, 32]");
+  if (m->n_cloud < m->k_nn || m->n_cloud > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "need k_nn <= n_cloud < 2^31");
+  if (nq < 0 || (nq > 0 && (!x || !idx || !d2 || !h))) return fail(ctx, MPWOS_EINVAL, "queries or outputs");
+  if (precision != MPWOS_FP32 && precision != MPWOS_FP64) return fail(ctx, MPWOS_EINVAL, "precision");
+  if (method != MPWOS_KNN_GRID && method != MPWOS_KNN_GRID_WARP && method != MPWOS_KNN_SCAN)
+    return fail(ctx, MPWOS_EINVAL, "unknown method %d", method);
+  if (method == MPWOS_KNN_GRID_WARP && precision == MPWOS_FP64)
+    return fail(ctx, MPWOS_EINVAL, "the warp-cooperative search is FP32 only");
+  if (nq == 0) return MPWOS_OK;
+  CloudGrid* G = nullptr;
+  int rc = get_cloud(ctx, m, &G);
+  if (rc) return rc;
+  DevProblem pb;
+  std::memset(&pb, 0, sizeof pb);
+  pb.cl_pts64 = G->pts64;
+  pb.cl_pts32 = G->pts32;
+  pb.cl_orig = G->orig;
+  pb.cl_start = G->start;
+  for (int a = 0; a < 3; ++a) {
+    pb.cl_origin[a] = G->origin[a];
+    pb.cl_dims[a] = G->dims[a];
+    pb.cl_origin_f[a] = static_cast<float>(G->origin[a]);
+  }
+  pb.cl_cell = G->cell;
+  pb.cl_cell_f = static_cast<float>(G->cell);
+  pb.cl_k = m->k_nn;
+  const int k = m->k_nn;
+  Scratch sc(ctx);
+  const bool dx = is_device_ptr(x), di = is_device_ptr(idx), dd = is_device_ptr(d2), dh = is_device_ptr(h);
+  const double* xd = x;
+  if (!dx) {
+    double* t = sc.alloc<double>(static_cast<size_t>(nq) * 3);
+    if (!t) return fail(ctx, MPWOS_ENOMEM, "queries");
+    CK(cudaMemcpyAsync(t, x, sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, ctx->stream));
+    xd = t;
+  }
+  int32_t* io = di ? idx : sc.alloc<int32_t>(static_cast<size_t>(nq) * k);
+  double* d2o = dd ? d2 : sc.alloc<double>(static_cast<size_t>(nq) * k);
+  double* ho = dh ? h : sc.alloc<double>(static_cast<size_t>(nq));
+  if (!io || !d2o || !ho) return fail(ctx, MPWOS_ENOMEM, "kNN outputs");
+  const int max_blocks = ctx->sm_count * 16;
+  const cudaError_t e =
+      precision == MPWOS_FP32
+          ? launch_cloud_knn_f32(pb, xd, nq, method, m->n_cloud, io, d2o, ho, max_blocks, ctx->stream)
+          : launch_cloud_knn_f64(pb, xd, nq, method, m->n_cloud, io, d2o, ho, max_blocks, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "kNN launch: %s", cudaGetErrorString(e));
+  ctx->launches++;
+  if (!di) CK(cudaMemcpyAsync(idx, io, sizeof(int32_t) * nq * k, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dd) CK(cudaMemcpyAsync(d2, d2o, sizeof(double) * nq * k, cudaMemcpyDeviceToHost, ctx->stream));
+  if (!dh) CK(cudaMemcpyAsync(h, ho, sizeof(double) * nq, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MPWOS_OK;
+}
+
 int mpwos_set_autotune(mpwos_ctx* ctx, int enable) {
   if (!ctx) return MPWOS_EINVAL;
   std::lock_guard<std::recursive_mutex> lock_(ctx->mu);

@@ -9,6 +9,7 @@
     python -m paper_2606_21883_b300.profile_cases dumbbell  # walkn_f32_kernel<revolution> (Example 2, n = 1001)
     python -m paper_2606_21883_b300.profile_cases cloud     # walk3_f32_cloud_coop_kernel (the 200k-point cloud, k = 16)
     python -m paper_2606_21883_b300.profile_cases e1_comp   # walk3_f32_kernel<torus, general, m_*> (Example 1)
+    python -m paper_2606_21883_b300.profile_cases knn       # cloud_knn_query_kernel and cloud_knn_scan_kernel (200k cloud, k = 16)
 
 Each case runs `--reps` walk launches into device buffers (the first one
 warms tables and caches) and prints one line with the walk-steps and the
@@ -60,13 +61,41 @@ def _case(name):
     raise SystemExit(f"unknown case {name}")
 
 
+def _knn(reps, nq=262144):
+    """The 200k cloud's k = 16 nearest of nq queries near the surface: per rep, the
+    FP32 grid search (cloud_knn_query_kernel) and then the all-pairs scan
+    (cloud_knn_scan_kernel), each timed by wall clock around synchronisation."""
+    import torch
+    from . import KNN_GRID, KNN_SCAN
+    w = W.point_cloud(P=1, walks=1)
+    cloud = w.problem.manifold.cloud
+    rng = np.random.default_rng(3)
+    x = cloud[rng.choice(cloud.shape[0], nq)] + rng.uniform(-0.02, 0.02, (nq, 3))   # the benchmark's queries
+    xd = torch.tensor(x, device="cuda")
+    k = w.problem.manifold.k_nn
+    out = (torch.empty((nq, k), dtype=torch.int32, device="cuda"), torch.empty((nq, k), dtype=torch.float64, device="cuda"),
+           torch.empty(nq, dtype=torch.float64, device="cuda"))
+    ctx = Context(0)
+    for _ in range(max(1, reps)):
+        for name, meth in (("grid", KNN_GRID), ("scan", KNN_SCAN)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.cloud_knn(w.problem, xd, precision=FP32, method=meth, out=out)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            print(f"knn {name}: {nq} queries x {cloud.shape[0]} points, {dt * 1e3:.2f} ms wall, {nq / dt:.3e} queries/s")
+    ctx.close()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("case", choices=["torus", "s20_tc", "s20_cuda", "s999", "s999_red", "s20_red", "dumbbell", "cloud",
-                                         "e1_comp"])
+                                         "e1_comp", "knn"])
     ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args(argv)
     import torch
+    if args.case == "knn":
+        return _knn(args.reps)
 
     w, N, kw = _case(args.case)
     ctx = Context(0)
