@@ -81,10 +81,19 @@ __device__ __forceinline__ T cloud_knn(const DevProblem& pb, const T* x, Knn<T, 
             const int cell = (zz * gy + yy) * gx + xx;
             const int b = pb.cl_start[cell], e = pb.cl_start[cell + 1];
             for (int q = b; q < e; ++q) {
-              const T px = P[3 * q], py = P[3 * q + 1], pz = P[3 * q + 2];
+              T px, py, pz;
+              int g;
+              if constexpr (sizeof(T) == 4) {   // one 16-byte load: x, y, z, original index
+                const float4 c4 = pb.cl_pts4[q];
+                px = c4.x; py = c4.y; pz = c4.z;
+                g = __float_as_int(c4.w);
+              } else {
+                px = P[3 * q]; py = P[3 * q + 1]; pz = P[3 * q + 2];
+                g = pb.cl_orig[q];
+              }
               const T ddx = px - x[0], ddy = py - x[1], ddz = pz - x[2];
               const T dd = ddx * ddx + ddy * ddy + ddz * ddz;
-              knn_insert<T, KM>(R, k, dd, q, pb.cl_orig[q]);
+              knn_insert<T, KM>(R, k, dd, q, g);
             }
           }
         }
@@ -122,7 +131,6 @@ __device__ __forceinline__ float cloud_knn_coop(const DevProblem& pb, const floa
   constexpr unsigned kAll = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int k = pb.cl_k;
-  const float* P = pb.cl_pts32;
 #pragma unroll
   for (int j = 0; j < KM; ++j) { R.d2[j] = INFINITY; R.idx[j] = -1; R.gid[j] = 0x7fffffff; }
   const float cs = pb.cl_cell_f;
@@ -163,9 +171,10 @@ __device__ __forceinline__ float cloud_knn_coop(const DevProblem& pb, const floa
               float cd = INFINITY;
               int cg = 0x7fffffff;
               if (ok) {
-                const float ddx = P[3 * qq] - q[0], ddy = P[3 * qq + 1] - q[1], ddz = P[3 * qq + 2] - q[2];
+                const float4 c4 = pb.cl_pts4[qq];   // x, y, z, original index
+                const float ddx = c4.x - q[0], ddy = c4.y - q[1], ddz = c4.z - q[2];
                 cd = ddx * ddx + ddy * ddy + ddz * ddz;
-                cg = pb.cl_orig[qq];
+                cg = __float_as_int(c4.w);
               }
               const float kd = __shfl_sync(kAll, ld, k - 1);
               const int kg = __shfl_sync(kAll, lg, k - 1);
@@ -471,7 +480,12 @@ __global__ void __launch_bounds__(128) cloud_knn_scan_kernel(const DevProblem pb
     __syncthreads();
     for (int i = threadIdx.x; i < nt; i += blockDim.x) {
       const int64_t pi = t + static_cast<int64_t>(i) * ntiles;
-      sp[i] = ScanPt<T>{P[3 * pi], P[3 * pi + 1], P[3 * pi + 2], pb.cl_orig[pi]};
+      if constexpr (sizeof(T) == 4) {
+        const float4 c4 = pb.cl_pts4[pi];
+        sp[i] = ScanPt<T>{c4.x, c4.y, c4.z, __float_as_int(c4.w)};
+      } else {
+        sp[i] = ScanPt<T>{P[3 * pi], P[3 * pi + 1], P[3 * pi + 2], pb.cl_orig[pi]};
+      }
     }
     __syncthreads();
     for (int i = 0; i < nt; ++i) {

@@ -148,6 +148,9 @@ struct DevProblem {
   float rv_alpha_f, rv_kappa_f, rv_mA_f, rv_ck_f;
   // dynamic walk queue (zeroed before each launch; null: static stride)
   unsigned long long* wk_next;
+  // point cloud in cell order as FP32 (x, y, z, original index as int bits):
+  // one 16-byte load per candidate in the FP32 searches
+  const float4* cl_pts4;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {

@@ -415,7 +415,7 @@ __global__ void cloud_scan_kernel(const int* counts, int ncells, int* start) {
 }
 
 __global__ void cloud_scatter_kernel(const double* pts, int64_t N, const int* cell, const int* start, int* cursor,
-                                     double* spts64, float* spts32, int* orig) {
+                                     double* spts64, float* spts32, float4* spts4, int* orig) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= N) return;
   const int id = cell[i];
@@ -424,6 +424,8 @@ __global__ void cloud_scatter_kernel(const double* pts, int64_t N, const int* ce
     spts64[3 * pos + a] = pts[3 * i + a];
     spts32[3 * pos + a] = static_cast<float>(pts[3 * i + a]);
   }
+  spts4[pos] = make_float4(static_cast<float>(pts[3 * i]), static_cast<float>(pts[3 * i + 1]),
+                           static_cast<float>(pts[3 * i + 2]), __int_as_float(static_cast<int>(i)));
   orig[pos] = static_cast<int>(i);
 }
 
@@ -439,7 +441,7 @@ __global__ void cloud_hmax_kernel(const DevProblem pb, int64_t N, unsigned long 
 
 cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[3], double cs, const int dims[3],
                               int* cell, int* counts, int* start, int* cursor, double* spts64, float* spts32,
-                              int* orig, cudaStream_t st) {
+                              float4* spts4, int* orig, cudaStream_t st) {
   const int ncells = dims[0] * dims[1] * dims[2];
   cudaMemsetAsync(counts, 0, sizeof(int) * ncells, st);
   cudaMemsetAsync(cursor, 0, sizeof(int) * ncells, st);
@@ -447,7 +449,7 @@ cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[
   cloud_cell_kernel<<<grid, 256, 0, st>>>(pts, N, origin[0], origin[1], origin[2], cs, dims[0], dims[1], dims[2], cell,
                                           counts);
   cloud_scan_kernel<<<1, 1024, 0, st>>>(counts, ncells, start);
-  cloud_scatter_kernel<<<grid, 256, 0, st>>>(pts, N, cell, start, cursor, spts64, spts32, orig);
+  cloud_scatter_kernel<<<grid, 256, 0, st>>>(pts, N, cell, start, cursor, spts64, spts32, spts4, orig);
   return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fix
 // Point-cloud grid (counting sort by cell) and the largest h(p) over the cloud.
 cudaError_t launch_cloud_grid(const double* pts, int64_t N, const double origin[3], double cs, const int dims[3],
                               int* cell, int* counts, int* start, int* cursor, double* spts64, float* spts32,
-                              int* orig, cudaStream_t st);
+                              float4* spts4, int* orig, cudaStream_t st);
 cudaError_t launch_cloud_hmax(const DevProblem& pb, int64_t N, unsigned long long* hmax_bits, cudaStream_t st);
 
 // k nearest cloud points of nq queries (x: nq x 3 FP64, device) by method

@@ -40,6 +40,7 @@ struct Table {
 struct CloudGrid {
   double* pts64 = nullptr;
   float* pts32 = nullptr;
+  float4* pts4 = nullptr;
   int* orig = nullptr;
   int* start = nullptr;
   double origin[3] = {0, 0, 0};
@@ -499,6 +500,7 @@ int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
   int *cell = nullptr, *counts = nullptr, *cursor = nullptr;
   CK(cudaMalloc(&G.pts64, sizeof(double) * 3 * N));
   CK(cudaMalloc(&G.pts32, sizeof(float) * 3 * N));
+  CK(cudaMalloc(&G.pts4, sizeof(float4) * N));
   CK(cudaMalloc(&G.orig, sizeof(int) * N));
   CK(cudaMalloc(&G.start, sizeof(int) * (ncells + 1)));
   CK(cudaMalloc(&dpts, sizeof(double) * 3 * N));
@@ -506,14 +508,15 @@ int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
   CK(cudaMalloc(&counts, sizeof(int) * ncells));
   CK(cudaMalloc(&cursor, sizeof(int) * ncells));
   CK(cudaMemcpyAsync(dpts, P, sizeof(double) * 3 * N, cudaMemcpyHostToDevice, ctx->stream));
-  CK(launch_cloud_grid(dpts, N, G.origin, cs, G.dims, cell, counts, G.start, cursor, G.pts64, G.pts32, G.orig,
-                       ctx->stream));
+  CK(launch_cloud_grid(dpts, N, G.origin, cs, G.dims, cell, counts, G.start, cursor, G.pts64, G.pts32, G.pts4,
+                       G.orig, ctx->stream));
   ctx->launches += 3;
   // largest h(p) over the cloud
   DevProblem tmp;
   std::memset(&tmp, 0, sizeof tmp);
   tmp.cl_pts64 = G.pts64;
   tmp.cl_pts32 = G.pts32;
+  tmp.cl_pts4 = G.pts4;
   tmp.cl_orig = G.orig;
   tmp.cl_start = G.start;
   for (int a = 0; a < 3; ++a) { tmp.cl_origin[a] = G.origin[a]; tmp.cl_dims[a] = G.dims[a]; }
@@ -748,6 +751,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     }
     pb.cl_pts64 = G->pts64;
     pb.cl_pts32 = G->pts32;
+    pb.cl_pts4 = G->pts4;
     pb.cl_orig = G->orig;
     pb.cl_start = G->start;
     for (int a = 0; a < 3; ++a) { pb.cl_origin[a] = G->origin[a]; pb.cl_dims[a] = G->dims[a]; }
@@ -970,6 +974,7 @@ int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const double* 
   std::memset(&pb, 0, sizeof pb);
   pb.cl_pts64 = G->pts64;
   pb.cl_pts32 = G->pts32;
+  pb.cl_pts4 = G->pts4;
   pb.cl_orig = G->orig;
   pb.cl_start = G->start;
   for (int a = 0; a < 3; ++a) {
@@ -1089,6 +1094,7 @@ void mpwos_destroy(mpwos_ctx* ctx) {
   for (auto& kv : ctx->clouds) {
     cudaFree(kv.second.pts64);
     cudaFree(kv.second.pts32);
+    cudaFree(kv.second.pts4);
     cudaFree(kv.second.orig);
     cudaFree(kv.second.start);
   }
