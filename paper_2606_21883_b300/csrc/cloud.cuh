@@ -342,7 +342,9 @@ __device__ __forceinline__ void cloud_project(const DevProblem& pb, const T* x, 
     T dsum = L[j][j];
 #pragma unroll
     for (int p = 0; p < j; ++p) dsum -= L[j][p] * L[j][p];
-    const T djj = sqrt(fmax(dsum, T(1e-300)));
+    // floor against a singular fit (collinear or repeated neighbours): a tiny
+    // positive pivot representable in T (1e-300 underflows to 0 in FP32)
+    const T djj = sqrt(fmax(dsum, sizeof(T) == 4 ? T(1e-30f) : T(1e-300)));
     L[j][j] = djj;
 #pragma unroll
     for (int i = j + 1; i < 6; ++i) {
