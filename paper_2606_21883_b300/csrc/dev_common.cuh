@@ -30,7 +30,8 @@ struct DevFunc {
   float coef_f[kMaxTerms];             // FP32 copies of coef, c0 (the FP32 walks read no double)
   float c0_f;
   float mode_f[kMaxTerms][4];          // TORUS_FOURIER: m, q, m^2, q^2 as floats
-  int single_mq;                       // TORUS_FOURIER with one term, m, q <= 3: 4 m + q; else -1
+  int single_mq;                       // TORUS_FOURIER with one term, m, q <= 3: 4 m + q + 16 [sin in theta]
+                                       // + 32 [sin in phi]; else -1
 };
 
 // Compensation term m_* (Sec. 2.3.3): the predictor u_* and the difference

@@ -24,8 +24,11 @@ static const void* walk3_f32_fn(const DevProblem& pb) {
       const int mq = (pb.n_v == 1 && pb.f.kind == kTorusFourier) ? pb.f.single_mq : -1;
       switch (mq) {
 #define MPWOS_MQ(c) case c: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true, c>);
-        MPWOS_MQ(0) MPWOS_MQ(1) MPWOS_MQ(2) MPWOS_MQ(3) MPWOS_MQ(4) MPWOS_MQ(5) MPWOS_MQ(6) MPWOS_MQ(7)
-        MPWOS_MQ(8) MPWOS_MQ(9) MPWOS_MQ(10) MPWOS_MQ(11) MPWOS_MQ(12) MPWOS_MQ(13) MPWOS_MQ(14) MPWOS_MQ(15)
+#define MPWOS_MQ16(b) MPWOS_MQ(b + 0) MPWOS_MQ(b + 1) MPWOS_MQ(b + 2) MPWOS_MQ(b + 3) MPWOS_MQ(b + 4) \
+  MPWOS_MQ(b + 5) MPWOS_MQ(b + 6) MPWOS_MQ(b + 7) MPWOS_MQ(b + 8) MPWOS_MQ(b + 9) MPWOS_MQ(b + 10)           \
+  MPWOS_MQ(b + 11) MPWOS_MQ(b + 12) MPWOS_MQ(b + 13) MPWOS_MQ(b + 14) MPWOS_MQ(b + 15)
+        MPWOS_MQ16(0) MPWOS_MQ16(16) MPWOS_MQ16(32) MPWOS_MQ16(48)
+#undef MPWOS_MQ16
 #undef MPWOS_MQ
         default: return reinterpret_cast<const void*>(walk3_f32_kernel<kTorus, 1, true>);
       }

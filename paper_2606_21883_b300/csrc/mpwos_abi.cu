@@ -386,7 +386,8 @@ void copy_func(const mpwos_func& f, DevFunc& d) {
       d.mode_f[t][2] = m * m;
       d.mode_f[t][3] = qq * qq;
     }
-    if (f.n_terms == 1 && f.modes[0] <= 3 && f.modes[1] <= 3) d.single_mq = 4 * f.modes[0] + f.modes[1];
+    if (f.n_terms == 1 && f.modes[0] <= 3 && f.modes[1] <= 3)
+      d.single_mq = 4 * f.modes[0] + f.modes[1] + (f.modes[2] != 0 ? 16 : 0) + (f.modes[3] != 0 ? 32 : 0);
   } else if (f.kind == MPWOS_FUNC_CURVE_SPHERE) {
     for (int t = 0; t < f.n_terms; ++t)
       for (int q = 0; q < 4; ++q) d.modes[t][q] = static_cast<int8_t>(f.modes[4 * t + q]);

@@ -222,22 +222,23 @@ __device__ __forceinline__ float torus_series32(const DevProblem& pb, const DevF
   return total;
 }
 
-// The single torus Fourier term with compile-time mode numbers M, Q (the
-// launch picks the instance once; the angle multiples become straight-line
-// code): the same value as torus_series32 for that term.
-template <int M, int Q>
+// The single torus Fourier term with compile-time mode numbers M, Q and
+// trig choices (TSIN: sin(M theta), else cos; PSIN: sin(Q phi), else cos) --
+// the launch picks the instance once, so the angle multiples become
+// straight-line code with no per-step selects: the same value as
+// torus_series32 for that term.
+template <int M, int Q, bool TSIN, bool PSIN>
 __device__ __forceinline__ float torus_term32(const DevProblem& pb, const DevFunc& fn, float ct, float st, float cph,
                                               float sph) {
   float cm, sm, cq, sq;
   angle_multiple(M, ct, st, cm, sm);
   angle_multiple(Q, cph, sph, cq, sq);
-  const bool tcos = fn.modes[0][2] == 0;
-  const float Tv = tcos ? cm : sm;
-  const float Pv = fn.modes[0][3] == 0 ? cq : sq;
+  const float Tv = TSIN ? sm : cm;
+  const float Pv = PSIN ? sq : cq;
   if (!fn.apply_op) return fn.coef_f[0] * (Tv * Pv);
   const float ia = pb.sf.inv_a;
   const float irr = __fdividef(1.0f, pb.sf.R + pb.sf.a * ct);
-  const float Tp = tcos ? -static_cast<float>(M) * sm : static_cast<float>(M) * cm;
+  const float Tp = TSIN ? static_cast<float>(M) * cm : -static_cast<float>(M) * sm;
   const float lap = static_cast<float>(M * M) * Tv * (ia * ia) + st * Tp * (ia * irr) +
                     static_cast<float>(Q * Q) * Tv * (irr * irr);
   return fn.coef_f[0] * (Pv * (lap + pb.sf.sigma * Tv));
@@ -604,7 +605,8 @@ __device__ __forceinline__ void walk3_f32_cloud_body(const DevProblem& pb) {
 
 // One FP32 step of a constant-radius walk with N_V = 1: the draws of step kk,
 // Theta and Z from Y, F = f(cp(Z)) (returned), then Y = cp(Theta).  MQ >= 0:
-// the torus source is one Fourier term with modes (MQ / 4, MQ % 4).
+// the torus source is one Fourier term with modes ((MQ / 4) % 4, MQ % 4),
+// sin in theta if bit 4 of MQ is set and sin in phi if bit 5 is (else cos).
 template <int MK, int MQ>
 __device__ __forceinline__ float fixed_step32(const DevProblem& pb, const PhiloxKeys& K, const PhiloxWalk& pw,
                                               uint32_t kk, float r, float a, float (&Y)[3]) {
@@ -624,7 +626,7 @@ __device__ __forceinline__ float fixed_step32(const DevProblem& pb, const Philox
   if constexpr (MK == kTorus && MQ >= 0) {
     float ct, st, cph, sph;
     torus_angles32(pb.sf.R, Z, ct, st, cph, sph);
-    F = torus_term32<MQ / 4, MQ % 4>(pb, pb.f, ct, st, cph, sph);
+    F = torus_term32<(MQ / 4) % 4, MQ % 4, ((MQ >> 4) & 1) != 0, ((MQ >> 5) & 1) != 0>(pb, pb.f, ct, st, cph, sph);
   } else {
     F = source_at32<MK, 1>(pb, Z);
   }
@@ -726,8 +728,8 @@ __device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
 // fixed-radius loop fits 40 registers (6 blocks, 48 warps per SM: measured
 // fastest on B300; 7 blocks spill), the general loop 64 (4 blocks); the point-cloud walk uses
 // 128-thread blocks with a larger register budget.  MQ >= 0 (torus, one
-// Fourier term with modes m = MQ / 4, q = MQ % 4, N_V = 1): the host launches
-// the instance with those modes built in.  COMP: with the compensation term
+// Fourier term with modes m = (MQ / 4) % 4, q = MQ % 4 and its trig choices in
+// bits 4 and 5, N_V = 1): the host launches the instance with those built in.  COMP: with the compensation term
 // (general loop only).
 template <int MK, int KM, bool FIXED, int MQ = -1, bool COMP = false>
 __global__ void __launch_bounds__(256, FIXED ? 6 : 4) walk3_f32_kernel(const DevProblem pb) {
