@@ -1196,11 +1196,13 @@ int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_para
                     const double* pts, int64_t P, int64_t N, double* S, int64_t* K,
                     int32_t* flags, int n_threads) {
   if (check_problem(m, pb) != 0) return -1;
+  int nt = 1;
 #ifdef _OPENMP
-  if (n_threads > 0) omp_set_num_threads(n_threads);
+  nt = n_threads > 0 ? n_threads : omp_get_max_threads();   /* this call only: no process-wide setting */
 #endif
+  (void)nt;
   int64_t total = P * N;
-#pragma omp parallel
+#pragma omp parallel num_threads(nt)
   {
     work_t w;
     work_alloc(&w, m->n);
@@ -1219,7 +1221,10 @@ int orc_walk_scores(const orc_manifold* m, const orc_problem* pb, const orc_para
   return 0;
 }
 
-/* Per-point estimator (eq. mc_estimator): Kahan sums of S and S^2 in walk order. */
+/* Per-point estimator (eq. mc_estimator): the mean of the path scores by a
+ * Kahan sum in walk order, and its standard error sqrt(s^2 / N) with the sample
+ * variance by its definition, s^2 = sum (S - mean)^2 / (N - 1) (a second Kahan
+ * pass in walk order). */
 int orc_solve(const orc_manifold* m, const orc_problem* pb, const orc_params* pr,
               const double* pts, int64_t P, int64_t N, double* mean, double* stderr_,
               double* mean_steps, int64_t* n_flagged, int n_threads) {
@@ -1232,17 +1237,20 @@ int orc_solve(const orc_manifold* m, const orc_problem* pb, const orc_params* pr
   }
   int64_t nf = 0;
   for (int64_t p = 0; p < P; ++p) {
-    double s1 = 0.0, c1 = 0.0, s2 = 0.0, c2 = 0.0, ks = 0.0;
+    double s1 = 0.0, c1 = 0.0, ks = 0.0;
     for (int64_t i = 0; i < N; ++i) {
       double v = S[p * N + i];
       double y = v - c1, t = s1 + y; c1 = (t - s1) - y; s1 = t;
-      double y2 = v * v - c2, t2 = s2 + y2; c2 = (t2 - s2) - y2; s2 = t2;
       ks += (double)K[p * N + i];
       nf += fl[p * N + i];
     }
     double mu = s1 / (double)N;
-    double var = (N > 1) ? (s2 - (double)N * mu * mu) / (double)(N - 1) : 0.0;
-    if (var < 0.0) var = 0.0;
+    double q = 0.0, cq = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+      double dv = S[p * N + i] - mu;
+      double y = dv * dv - cq, t = q + y; cq = (t - q) - y; q = t;
+    }
+    double var = (N > 1) ? q / (double)(N - 1) : 0.0;
     mean[p] = mu;
     stderr_[p] = sqrt(var / (double)N);
     mean_steps[p] = ks / (double)N;
