@@ -103,13 +103,11 @@ extern "C" {
 
 typedef struct mpwos_ctx mpwos_ctx;
 
-/* Manifold M (Sec. 2.1).  Q, b are host arrays (embedded sphere only),
- * Q row-major n x (d+1) with orthonormal columns; copied at the call.
- * Point cloud (n = 3, d = 2, closed problems): n_cloud x 3 host array; the
- * context builds a search grid on first use and caches it by (pointer, size,
- * k_nn, contents checksum) — keep the array unchanged while it is cached.
- * rho_geo(y) = c_h h(y), h(y) the mean distance from y to its k_nn nearest
- * cloud points (eq. rho_geo_spacing); cp by cp_mode. */
+/* Manifold M (Sec. 2.1), described for mpwos_manifold_create.  Q, b are host
+ * arrays (embedded sphere only), Q row-major n x (d+1) with orthonormal
+ * columns.  Point cloud (n = 3, d = 2, closed problems): n_cloud x 3 host
+ * array; rho_geo(y) = c_h h(y), h(y) the mean distance from y to its k_nn
+ * nearest cloud points (eq. rho_geo_spacing); cp by cp_mode. */
 typedef struct {
   int kind;
   int n;            /* ambient dimension                                  */
@@ -124,6 +122,12 @@ typedef struct {
   int cp_mode;      /* MPWOS_CLOUD_CP_FIT or MPWOS_CLOUD_CP_NEAREST        */
   double prof_alpha, prof_kappa;   /* REVOLUTION: al in (0, 1/2), k > 0   */
 } mpwos_manifold_desc;
+
+/* A manifold handle (opaque): owns copies of a description's arrays and the
+ * device data the walks read (the embedded sphere's Q^T in FP64 and FP32, b and
+ * the tensor-core operand image; the point cloud's search grid; the
+ * revolution's curvature range), built once on the context's device. */
+typedef struct mpwos_manifold mpwos_manifold;
 
 /* A function on M given as a small closed family of device-evaluable forms.
  * apply_op != 0 (torus Fourier, sphere quad): evaluate (-Delta_M + sigma) of
@@ -184,8 +188,21 @@ typedef struct {
 void mpwos_params_default(mpwos_params* p);
 
 /* Create a context on CUDA device `device` (owns device state, tables, a
- * stream).  Returns MPWOS_EINVAL for a bad device, MPWOS_ECUDA otherwise. */
-int mpwos_create(int device, mpwos_ctx** out);
+ * stream).  stream: a cudaStream_t the synchronous calls run on (borrowed, not
+ * destroyed with the context), or NULL for the context's own stream.  Returns
+ * MPWOS_EINVAL for a bad device, MPWOS_ECUDA otherwise. */
+int mpwos_create(int device, void* stream, mpwos_ctx** out);
+
+/* Create a manifold handle (Sec. 2.1: the manifold and its closest-point data)
+ * on the context's device from a description; the description's arrays are
+ * copied and may be freed afterwards.  The handle serves every later call on
+ * contexts of the same device; it must outlive the requests that use it.
+ * Returns MPWOS_EINVAL for an invalid description (message in
+ * mpwos_last_error), MPWOS_ENOMEM / MPWOS_ECUDA otherwise. */
+int mpwos_manifold_create(mpwos_ctx* ctx, const mpwos_manifold_desc* desc, mpwos_manifold** out);
+
+/* Free a manifold handle and its device data.  NULL is a no-op. */
+void mpwos_manifold_destroy(mpwos_manifold* m);
 
 /* Destroy a context and free its device memory.  NULL is a no-op. */
 void mpwos_destroy(mpwos_ctx* ctx);
@@ -202,7 +219,7 @@ int mpwos_set_stream(mpwos_ctx* ctx, void* stream);
  * each, host or device, caller-owned): the mean of the path scores, its
  * standard error, the mean stopping index K.  Returns MPWOS_EMAXSTEPS (with
  * results written) if any walk reached max_steps. */
-int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold* m, const mpwos_problem* prob,
                 const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
                 double* mean, double* stderr_, double* mean_steps);
 
@@ -210,9 +227,47 @@ int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_proble
  * and max-steps flags, P x N row-major (walk i of point p at p*N + i); host
  * or device.  Walk (p, i) draws its random numbers from Philox4x32-10 at
  * counter (block, step, i, p), so each value depends on (seed, p, i) only. */
-int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold* m, const mpwos_problem* prob,
                       const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
                       double* S, int32_t* K, int32_t* flags);
+
+/* One request split by walk range (the estimator of eq. mc_estimator summed
+ * over independent paths, Sec. 2.3 and Algorithm 1; one range per GPU, then a
+ * merge on the host).  The walks of a point form blocks of 1024 walk indices;
+ * a block's statistic (walk count, mean of S, sum of squared deviations from
+ * that mean, sum of K, walks flagged at max_steps) depends only on its own
+ * walks, in one fixed summation order, and blocks merge in order with the
+ * pairwise update of Chan, Golub and LeVeque.  mpwos_solve runs exactly this
+ * order, so merging the ranges [0, i1), [i1, i2), ... of a request gives the
+ * bits mpwos_solve gives for the whole request.
+ *
+ * mpwos_solve_partial: walks i0 <= i < i1 of each of the P points of a request
+ * of N walks per point (i0 and i1 multiples of 1024, or i1 = N; walk (p, i)
+ * draws the same numbers as in mpwos_solve).  part (host or device,
+ * caller-owned): P x nblk x 5 doubles, nblk = ceil((i1 - i0) / 1024), record
+ * (p, b) = (count, mean, M2, sum of K, flagged) of block b of the range.
+ * MPWOS_EINVAL for a misaligned range; max-steps walks are only counted in the
+ * records. */
+int mpwos_solve_partial(mpwos_ctx* ctx, const mpwos_manifold* m, const mpwos_problem* prob,
+                        const mpwos_params* prm, const double* pts, int64_t P, int64_t N, int64_t i0,
+                        int64_t i1, double* part);
+
+/* The block records of per-walk outputs (host arrays, P x N row-major as from
+ * mpwos_walk_scores; walk offsets 0..N-1 of a range) computed on the host in
+ * the device's summation order: part receives P x ceil(N / 1024) x 5 doubles.
+ * Needs no GPU and no context. */
+int mpwos_block_partials_host(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                              double* part);
+
+/* Merge block records on the host: parts[r] (host, P x nblk[r] x 5 doubles)
+ * for consecutive walk ranges r = 0 .. nparts-1 of one request, merged per
+ * point in range order and block order.  Outputs (P each, host): the mean of
+ * the path scores, its standard error sqrt(s^2 / n), s^2 = M2 / (n - 1), and
+ * the mean stopping index; n_flagged (nullable) receives the flagged walks.
+ * Returns MPWOS_EMAXSTEPS (outputs written) if any walk was flagged, and
+ * MPWOS_EINVAL for null or negative arguments.  Needs no GPU and no context. */
+int mpwos_merge_partials(const double* const* parts, const int64_t* nblk, int nparts, int64_t P, double* mean,
+                         double* stderr_, double* mean_steps, int64_t* n_flagged);
 
 /* Allocation-free variant of mpwos_solve (the paper has no counterpart: this
  * is a deployment convenience).  For callers that cannot call cudaMalloc — an
@@ -226,15 +281,17 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
  *   - pts (P x n) and the three outputs must be DEVICE pointers (EINVAL
  *     otherwise); problem data are host pointers as for mpwos_solve;
  *   - P * N must not exceed mpwos_noalloc_max_walks() (EINVAL with the limit
- *     in the message); EMBEDDED_SPHERE, POINT_CLOUD, the reduced sampler and
- *     compensation are not supported (EINVAL);
+ *     in the message); EMBEDDED_SPHERE, POINT_CLOUD, REVOLUTION and
+ *     CURVE_SPHERE manifolds, the reduced sampler, compensation and problems
+ *     with two SPHERE_QUAD functions (at most one of f, g) are not supported
+ *     (EINVAL); pts and the outputs must be on the context's device;
  *   - the first call on a device looks up the array's device address; make
  *     that first call before any stream capture;
  *   - every call shares the array: calls that overlap on the GPU (other
  *     streams, other contexts on the same device) race and must be serialized
  *     by the caller.  Each call clears and rebuilds what it needs.
  * Calls no cudaMalloc, cudaFree or allocating library routine. */
-int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold* m, const mpwos_problem* prob,
                         const mpwos_params* prm, const double* pts, int64_t P, int64_t N,
                         double* mean, double* stderr_, double* mean_steps);
 
@@ -262,7 +319,7 @@ int mpwos_serve_config(mpwos_ctx* ctx, int max_active, size_t mem_bytes, int64_t
 
 /* Queue a request; *request_id identifies it.  Fails with EINVAL on invalid
  * inputs (as mpwos_solve) or device query points. */
-int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold* m, const mpwos_problem* prob,
                  const mpwos_params* prm, const double* pts, int64_t P, int64_t walk_budget,
                  double target_stderr, uint64_t* request_id);
 
@@ -330,7 +387,7 @@ int mpwos_tc_project(mpwos_ctx* ctx, const double* Q, int n, int D, const float*
  * m not a point cloud, k_nn outside [1, 32], n_cloud outside [k_nn, 2^31),
  * nq < 0, a null array with nq > 0, an unknown method or precision, or
  * MPWOS_KNN_GRID_WARP with MPWOS_FP64. */
-int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const double* x, int64_t nq,
+int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold* m, const double* x, int64_t nq,
                     int precision, int method, int32_t* idx, double* d2, double* h);
 
 /* Number of the library's own kernel launches so far on this context. */

@@ -78,13 +78,15 @@ def lib() -> C.CDLL:
         L = C.CDLL(LIB_PATH)
         L.mpwos_last_error.restype = C.c_char_p
         L.mpwos_launch_count.restype = C.c_int64
-        L.mpwos_create.argtypes = [C.c_int, C.POINTER(C.c_void_p)]
+        L.mpwos_create.argtypes = [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+        L.mpwos_manifold_create.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(C.c_void_p)]
+        L.mpwos_manifold_destroy.argtypes = [C.c_void_p]
         for name in ("mpwos_destroy", "mpwos_last_error", "mpwos_launch_count"):
             getattr(L, name).argtypes = [C.c_void_p]
         L.mpwos_set_stream.argtypes = [C.c_void_p, C.c_void_p]
-        L.mpwos_solve.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc), C.POINTER(Params),
+        L.mpwos_solve.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(ProblemDesc), C.POINTER(Params),
                                   C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
-        L.mpwos_walk_scores.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc),
+        L.mpwos_walk_scores.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(ProblemDesc),
                                         C.POINTER(Params), C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p]
         L.mpwos_philox.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_int64]
@@ -94,7 +96,7 @@ def lib() -> C.CDLL:
         L.mpwos_tc_project.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int64,
                                        C.c_void_p, C.c_void_p]
         L.mpwos_serve_config.argtypes = [C.c_void_p, C.c_int, C.c_size_t, C.c_int64]
-        L.mpwos_submit.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.POINTER(ProblemDesc), C.POINTER(Params),
+        L.mpwos_submit.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(ProblemDesc), C.POINTER(Params),
                                    C.c_void_p, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_uint64)]
         L.mpwos_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int)]
         L.mpwos_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_double]
@@ -102,11 +104,55 @@ def lib() -> C.CDLL:
         L.mpwos_fetch.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.POINTER(C.c_double)]
         L.mpwos_set_autotune.argtypes = [C.c_void_p, C.c_int]
-        L.mpwos_cloud_knn.argtypes = [C.c_void_p, C.POINTER(ManifoldDesc), C.c_void_p, C.c_int64, C.c_int, C.c_int,
+        L.mpwos_cloud_knn.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int,
                                       C.c_void_p, C.c_void_p, C.c_void_p]
         L.mpwos_autotune_entries.argtypes = [C.c_void_p, C.POINTER(TuneEntry), C.c_int, C.POINTER(C.c_int)]
+        L.mpwos_solve_partial.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(ProblemDesc),
+                                          C.POINTER(Params), C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int64,
+                                          C.c_void_p]
+        L.mpwos_block_partials_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
+        L.mpwos_merge_partials.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
         _lib = L
     return _lib
+
+
+EST_BLOCK, EST_FIELDS = 1024, 5   # walks per estimator block; fields of a block record
+
+
+def n_blocks(walks: int) -> int:
+    """Estimator blocks of a walk range of the given length."""
+    return (int(walks) + EST_BLOCK - 1) // EST_BLOCK
+
+
+def block_partials_host(S, K, flags):
+    """mpwos_block_partials_host: the block records (P x nblk x 5) of per-walk
+    outputs (P x N host arrays), in the device's summation order; no GPU."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    flags = np.ascontiguousarray(flags, dtype=np.int32)
+    P, N = S.shape
+    part = np.zeros((P, n_blocks(N), EST_FIELDS))
+    rc = lib().mpwos_block_partials_host(_ptr(S), _ptr(K), _ptr(flags), int(P), int(N), _ptr(part))
+    if rc != MPWOS_OK:
+        raise MpwosError(rc, "mpwos_block_partials_host")
+    return part
+
+
+def merge_partials(parts):
+    """mpwos_merge_partials: merge the block records of consecutive walk ranges
+    (a list of P x nblk_r x 5 host arrays, in range order) into (mean, stderr,
+    mean_steps, n_flagged); no GPU."""
+    parts = [np.ascontiguousarray(p, dtype=np.float64) for p in parts]
+    P = int(parts[0].shape[0]) if parts else 0
+    ptrs = (C.c_void_p * max(len(parts), 1))(*[C.c_void_p(p.ctypes.data) for p in parts])
+    nblk = np.array([p.shape[1] for p in parts] or [0], dtype=np.int64)
+    mean, se, ms = np.zeros(P), np.zeros(P), np.zeros(P)
+    nf = C.c_int64(0)
+    rc = lib().mpwos_merge_partials(ptrs, _ptr(nblk), len(parts), P, _ptr(mean), _ptr(se), _ptr(ms), C.byref(nf))
+    if rc not in (MPWOS_OK, MPWOS_EMAXSTEPS):
+        raise MpwosError(rc, "mpwos_merge_partials")
+    return mean, se, ms, int(nf.value)
 
 
 def _ptr(x):
@@ -152,8 +198,7 @@ class _Marshal:
             cf.A = self.arr(f.A).ctypes.data_as(_dp)
         return cf
 
-    def problem(self, problem):
-        m = problem.manifold
+    def manifold(self, m) -> ManifoldDesc:
         md = ManifoldDesc(kind=m.kind, n=m.n, d=m.d, R=m.R, a=m.a, prof_alpha=getattr(m, "prof_alpha", 0.0),
                           prof_kappa=getattr(m, "prof_kappa", 0.0))
         if m.Q is not None:
@@ -168,6 +213,9 @@ class _Marshal:
             md.k_nn = m.k_nn
             md.c_h = m.c_h
             md.cp_mode = m.cp_mode
+        return md
+
+    def problem(self, problem):
         pd = ProblemDesc(sigma=problem.sigma, closed=int(problem.closed), bnd_offset=problem.bnd_offset)
         if problem.bnd_normal is not None:
             pd.bnd_normal = self.arr(problem.bnd_normal).ctypes.data_as(_dp)
@@ -177,7 +225,7 @@ class _Marshal:
             pd.comp = problem.comp
             pd.u_star = self.func(problem.u_star)
             pd.h_eta = problem.h_eta
-        return md, pd
+        return pd
 
 
 def make_params(params, precision, projection=PROJ_AUTO) -> Params:
@@ -189,18 +237,47 @@ def make_params(params, precision, projection=PROJ_AUTO) -> Params:
 class Context:
     """One library context (mpwos_create) on a CUDA device."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, stream_handle: Optional[int] = None):
         self.L = lib()
         h = C.c_void_p()
-        rc = self.L.mpwos_create(device, C.byref(h))
+        rc = self.L.mpwos_create(device, C.c_void_p(stream_handle) if stream_handle else None, C.byref(h))
         if rc != MPWOS_OK:
             raise MpwosError(rc, f"mpwos_create(device={device}) failed")
         self.h = h
+        self._manifolds = {}   # id(manifold) -> (manifold, signature, handle)
 
     def close(self):
         if getattr(self, "h", None):
+            for _, _, mh in self._manifolds.values():
+                self.L.mpwos_manifold_destroy(mh)
+            self._manifolds = {}
             self.L.mpwos_destroy(self.h)
             self.h = None
+
+    @staticmethod
+    def _signature(m):
+        arrs = tuple((id(a), a.ctypes.data, a.shape) if a is not None else None
+                     for a in (getattr(m, "Q", None), getattr(m, "b", None), getattr(m, "cloud", None)))
+        return (m.kind, m.n, m.d, m.R, m.a, getattr(m, "prof_alpha", 0.0), getattr(m, "prof_kappa", 0.0),
+                getattr(m, "k_nn", 0), getattr(m, "c_h", 0.0), getattr(m, "cp_mode", 0), arrs)
+
+    def manifold_handle(self, m) -> C.c_void_p:
+        """The mpwos_manifold handle of a workloads.Manifold on this context
+        (mpwos_manifold_create once per manifold object; made again if the
+        object's fields or arrays are replaced)."""
+        sig = self._signature(m)
+        hit = self._manifolds.get(id(m))
+        if hit is not None and hit[0] is m and hit[1] == sig:
+            return hit[2]
+        if hit is not None:
+            self.L.mpwos_manifold_destroy(hit[2])
+            del self._manifolds[id(m)]
+        mar = _Marshal()
+        md = mar.manifold(m)
+        mh = C.c_void_p()
+        self._check(self.L.mpwos_manifold_create(self.h, md, C.byref(mh)))
+        self._manifolds[id(m)] = (m, sig, mh)
+        return mh
 
     def __del__(self):
         try:
@@ -227,7 +304,7 @@ class Context:
         walk finds them: (idx nq x k, d2 nq x k, h nq).  x host or device; out, if given,
         is a tuple of device tensors (idx int32, d2, h) written in place."""
         mar = _Marshal()
-        md, _ = mar.problem(problem)
+        md = self.manifold_handle(problem.manifold)
         nq = int(x.shape[0])
         if not hasattr(x, "data_ptr"):
             x = mar.arr(x)
@@ -238,7 +315,7 @@ class Context:
             h = np.zeros(nq)
         else:
             idx, d2, h = out
-        rc = self.L.mpwos_cloud_knn(self.h, C.byref(md), _ptr(x), nq, int(precision), int(method), _ptr(idx),
+        rc = self.L.mpwos_cloud_knn(self.h, md, _ptr(x), nq, int(precision), int(method), _ptr(idx),
                                     _ptr(d2), _ptr(h))
         self._check(rc)
         return idx, d2, h
@@ -266,22 +343,42 @@ class Context:
     def solve(self, problem, params, pts, N, precision=FP64, out=None, projection=PROJ_AUTO):
         """mpwos_solve: returns (mean, stderr, mean_steps, status); pts host or device."""
         mar = _Marshal()
-        md, pd = mar.problem(problem)
+        pd = mar.problem(problem)
+        md = self.manifold_handle(problem.manifold)
         prm = make_params(params, precision, projection)
         P = int(pts.shape[0])
         if out is None:
             out = (np.zeros(P), np.zeros(P), np.zeros(P))
         if not hasattr(pts, "data_ptr"):
             pts = mar.arr(pts)
-        rc = self.L.mpwos_solve(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
+        rc = self.L.mpwos_solve(self.h, md, C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
                                 _ptr(out[0]), _ptr(out[1]), _ptr(out[2]))
         self._check(rc, (MPWOS_OK, MPWOS_EMAXSTEPS))
         return out[0], out[1], out[2], rc
 
+    def solve_partial(self, problem, params, pts, N, i0, i1, precision=FP64, projection=PROJ_AUTO, out=None):
+        """mpwos_solve_partial: block records (P x nblk x 5) of walks [i0, i1) of a
+        request of N walks per point; pts host or device; out a host array or a
+        device tensor of that shape."""
+        mar = _Marshal()
+        pd = mar.problem(problem)
+        md = self.manifold_handle(problem.manifold)
+        prm = make_params(params, precision, projection)
+        P = int(pts.shape[0])
+        if out is None:
+            out = np.zeros((P, n_blocks(int(i1) - int(i0)), EST_FIELDS))
+        if not hasattr(pts, "data_ptr"):
+            pts = mar.arr(pts)
+        rc = self.L.mpwos_solve_partial(self.h, md, C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
+                                        int(i0), int(i1), _ptr(out))
+        self._check(rc)
+        return out
+
     def walk_scores(self, problem, params, pts, N, precision=FP64, projection=PROJ_AUTO):
         """mpwos_walk_scores: per-walk S (P x N), K, flags."""
         mar = _Marshal()
-        md, pd = mar.problem(problem)
+        pd = mar.problem(problem)
+        md = self.manifold_handle(problem.manifold)
         prm = make_params(params, precision, projection)
         P = int(pts.shape[0])
         if not hasattr(pts, "data_ptr"):
@@ -289,7 +386,7 @@ class Context:
         S = np.zeros((P, int(N)))
         K = np.zeros((P, int(N)), dtype=np.int32)
         fl = np.zeros((P, int(N)), dtype=np.int32)
-        rc = self.L.mpwos_walk_scores(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
+        rc = self.L.mpwos_walk_scores(self.h, md, C.byref(pd), C.byref(prm), _ptr(pts), P, int(N),
                                       _ptr(S), _ptr(K), _ptr(fl))
         self._check(rc)
         return S, K, fl
@@ -297,9 +394,10 @@ class Context:
     def walk_scores_device(self, problem, params, pts, N, precision, S, K, flags, projection=PROJ_AUTO):
         """mpwos_walk_scores into caller-owned device tensors (no host copies)."""
         mar = _Marshal()
-        md, pd = mar.problem(problem)
+        pd = mar.problem(problem)
+        md = self.manifold_handle(problem.manifold)
         prm = make_params(params, precision, projection)
-        rc = self.L.mpwos_walk_scores(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
+        rc = self.L.mpwos_walk_scores(self.h, md, C.byref(pd), C.byref(prm), _ptr(pts),
                                       int(pts.shape[0]), int(N), _ptr(S), _ptr(K), _ptr(flags))
         return self._check(rc)
 
@@ -310,11 +408,12 @@ class Context:
     def submit(self, problem, params, pts, walk_budget, target_stderr=0.0, precision=FP32, projection=PROJ_AUTO):
         """mpwos_submit: returns the request id (query points copied at submit)."""
         mar = _Marshal()
-        md, pd = mar.problem(problem)
+        pd = mar.problem(problem)
+        md = self.manifold_handle(problem.manifold)
         prm = make_params(params, precision, projection)
         pts = mar.arr(pts)
         rid = C.c_uint64(0)
-        self._check(self.L.mpwos_submit(self.h, C.byref(md), C.byref(pd), C.byref(prm), _ptr(pts),
+        self._check(self.L.mpwos_submit(self.h, md, C.byref(pd), C.byref(prm), _ptr(pts),
                                         int(pts.shape[0]), int(walk_budget), float(target_stderr), C.byref(rid)))
         return int(rid.value)
 

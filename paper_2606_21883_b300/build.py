@@ -24,7 +24,7 @@ COMMON = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", 
 UNITS = {
     "kernels_f64.cu": ["--fmad=false"],
     "kernels_f32.cu": ["-use_fast_math"],
-    "kernels_tc.cu": ["-use_fast_math"],
+    "kernels_n32.cu": ["-use_fast_math"],
     "mpwos_abi.cu": [],
 }
 

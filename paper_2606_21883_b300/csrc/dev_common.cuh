@@ -120,7 +120,7 @@ struct DevProblem {
   double z_max;
   // work map: walk (p, i) for p in wk_points (all points 0..P-1 when null),
   // i in [wk_i0, wk_i1); this launch covers enumeration indices [wk_w0, wk_w1)
-  // of the wk_np * (wk_i1 - wk_i0) walks; outputs at p * out_stride + i
+  // of the wk_np * (wk_i1 - wk_i0) walks; outputs at p * out_stride + i - out_i0
   const int* wk_points;
   int64_t wk_np, wk_i0, wk_i1, wk_w0, wk_w1, out_stride;
   // queries and outputs
@@ -152,6 +152,20 @@ struct DevProblem {
   // point cloud in cell order as FP32 (x, y, z, original index as int bits):
   // one 16-byte load per candidate in the FP32 searches
   const float4* cl_pts4;
+  // FP32 warp walk in R^n (n > 3): the walk's coordinate order, perm[c] = the
+  // ambient index of walk coordinate c (null: identity), chosen so that the
+  // coordinates f, g and the boundary normal read come first; the normal's
+  // first 128 walk coordinates, and the whole normal in walk order when it has
+  // others (ef_w, zero padded to 1024; null otherwise); the hypersurface of
+  // revolution's v and diag(A) in walk order (the axis is walk coordinate 0,
+  // zero there), zero padded to 1024
+  const int* perm;
+  const float* ef_w;
+  const float* rv_v32;
+  const float* rv_a32;
+  float e_s0[128];
+  // output slot of walk (p, i): p * out_stride + i - out_i0 (a walk range's own buffer)
+  int64_t out_i0;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {
@@ -253,6 +267,58 @@ __host__ __device__ __forceinline__ U4 philox_step_one(const PhiloxWalk& w, uint
   return U4{a0, a1, a2, a3};
 }
 
+// FP32 walks in R^n (n > 3): block j of step k of walk (p, i) is Philox4x32-10
+// at counter (k, j, i, p).  With j in the XOR slot of round 0, every block of a
+// step shares the rest of rounds 0..2:
+//   round 0: (H1(i) ^ a_0 ^ j, L1(i), H0(k) ^ p ^ b_0, L0(k))      [H, L: hi, lo of M1 x or M0 x]
+//   round 1: (A1, B1, H0(A0 ^ j) ^ L0(k) ^ b_1, L0(A0 ^ j)),  A1 = H1(C0) ^ L1(i) ^ a_1, B1 = L1(C0)
+//   round 2: (H1(t2) ^ B1 ^ a_2, L1(t2), H0(A1) ^ b_2 ^ L0(A0 ^ j), L0(A1))
+// so a block costs two wide multiplies and four XORs before rounds 3..9 (34
+// operations instead of 40).  A walk's blocks j = 256 v + b (v: the vector,
+// b < 256: its 4-component block) keep j's low byte free, so A0 ^ j =
+// (A0 ^ 256 v ^ lane) ^ 32 m for the lane-interleaved blocks b = lane + 32 m.
+struct Philox32Walk { uint32_t A0, B0; };
+struct Philox32Step { uint32_t D1x, B2x, E2, La; };
+
+__host__ __device__ __forceinline__ Philox32Walk philox32_walk(uint32_t i, const PhiloxKeys& K) {
+  const uint64_t q = static_cast<uint64_t>(0xCD9E8D57u) * i;
+  return Philox32Walk{static_cast<uint32_t>(q >> 32) ^ K.a[0], static_cast<uint32_t>(q)};
+}
+
+__host__ __device__ __forceinline__ Philox32Step philox32_step(const Philox32Walk& w, uint32_t k, uint32_t p,
+                                                              const PhiloxKeys& K) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint64_t pk = static_cast<uint64_t>(M0) * k;
+  const uint32_t C0 = static_cast<uint32_t>(pk >> 32) ^ p ^ K.b[0];
+  const uint64_t pc = static_cast<uint64_t>(M1) * C0;
+  const uint32_t A1 = static_cast<uint32_t>(pc >> 32) ^ w.B0 ^ K.a[1];
+  const uint64_t pa = static_cast<uint64_t>(M0) * A1;
+  Philox32Step s;
+  s.D1x = static_cast<uint32_t>(pk) ^ K.b[1];
+  s.B2x = static_cast<uint32_t>(pc) ^ K.a[2];
+  s.E2 = static_cast<uint32_t>(pa >> 32) ^ K.b[2];
+  s.La = static_cast<uint32_t>(pa);
+  return s;
+}
+
+// The block whose round-0 first word is s0 = A0 ^ j.
+__host__ __device__ __forceinline__ U4 philox32_block(uint32_t s0, const Philox32Step& s, const PhiloxKeys& K) {
+  constexpr uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint64_t pj = static_cast<uint64_t>(M0) * s0;
+  const uint32_t t2 = static_cast<uint32_t>(pj >> 32) ^ s.D1x;
+  const uint64_t pq = static_cast<uint64_t>(M1) * t2;
+  uint32_t x0 = static_cast<uint32_t>(pq >> 32) ^ s.B2x, x1 = static_cast<uint32_t>(pq);
+  uint32_t x2 = s.E2 ^ static_cast<uint32_t>(pj), x3 = s.La;
+#pragma unroll
+  for (int r = 3; r < 10; ++r) {
+    const uint64_t p0 = static_cast<uint64_t>(M0) * x0, p1 = static_cast<uint64_t>(M1) * x2;
+    const uint32_t n0 = static_cast<uint32_t>(p1 >> 32) ^ x1 ^ K.a[r];
+    const uint32_t n2 = static_cast<uint32_t>(p0 >> 32) ^ x3 ^ K.b[r];
+    x0 = n0; x1 = static_cast<uint32_t>(p1); x2 = n2; x3 = static_cast<uint32_t>(p0);
+  }
+  return U4{x0, x1, x2, x3};
+}
+
 __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                                              uint32_t k0, uint32_t k1) {
 #pragma unroll
@@ -327,9 +393,27 @@ __device__ __forceinline__ void box_muller32(float ua, float ub, float& g0, floa
   g1 = rad * s;
 }
 
+// Box-Muller for a direction (FP32 walks in R^n): two components of the
+// Gaussian vector up to the common factor sqrt(2 ln 2), which the normalised
+// direction g/|g| does not see: sqrt(-log2 u) (cos 2 pi v, sin 2 pi v), u in
+// (0, 1] from the low 23 bits of x and v in [1, 2) from the low 23 bits of y
+// (sine and cosine have period 1 in v).  Returns -log2 u, the pair's part of
+// |g|^2 (cos^2 + sin^2 = 1), so a norm needs no squares.
+__device__ __forceinline__ float gauss_pair32(uint32_t x, uint32_t y, float& g0, float& g1) {
+  const float u = 2.0f - __uint_as_float(0x3f800000u | (x & 0x7FFFFFu));
+  const float l = __log2f(u);
+  const float R = sqrtf(-l);
+  float s, c;
+  __sincosf(kTwoPiF * __uint_as_float(0x3f800000u | (y & 0x7FFFFFu)), &s, &c);
+  g0 = R * c;
+  g1 = R * s;
+  return -l;
+}
+
 // ---------------------------------------------------------------------------
 // Pairs of floats (hi + lo, |lo| <= ulp(hi)/2) with error-free transformations
-// (Knuth TwoSum, FMA TwoProd): ~2^-48 relative precision on the FP32 pipes.
+// (Knuth TwoSum, FMA TwoProd): about 46-48 bits of significand (~2^-46
+// relative per operation, less than FP64's 2^-53) on the FP32 pipes.
 // Used for each walk's running weight W and score S in the FP32 walk, where
 // B300's FP64 pipe (about 1/64 of the FP32 rate) would otherwise co-limit the
 // step; per-point sums over walks stay in FP64.
@@ -362,7 +446,7 @@ __device__ __forceinline__ WalkId walk_id(const DevProblem& pb, int64_t w) {
   WalkId id;
   id.p = static_cast<uint32_t>(pb.wk_points ? pb.wk_points[r] : r);
   id.i = static_cast<uint32_t>(pb.wk_i0 + (w - r * nw));
-  id.o = static_cast<int64_t>(id.p) * pb.out_stride + id.i;
+  id.o = static_cast<int64_t>(id.p) * pb.out_stride + id.i - pb.out_i0;
   return id;
 }
 

@@ -8,7 +8,8 @@
 // tile stops at the same index.  For each Gaussian vector of a step (the
 // interior samples Z_l, then the sphere sample Theta) the tile's components are
 // generated in K-chunks of 64 — four threads per walker, 16 components (4
-// Philox blocks) each, the same draws as the warp walk — split into BF16
+// Philox blocks) each, the same draws as the FP32 warp walk (walkn32.cuh) —
+// split into BF16
 // hi + lo and stored into a 128-byte-swizzled K-major A tile (128 rows =
 // walkers; two stages).  One elected thread issues, per 16-wide K slice, three
 // tcgen05.mma kind::f16 products into one FP32 TMEM accumulator (128 x 32):
@@ -182,22 +183,25 @@ struct Smem {
   __device__ __forceinline__ float* rows() const { return reinterpret_cast<float*>(misc() + kMiscBytes); }
 };
 
-// The walk's Gaussian vector of blocks jb + b of step kk of walk (p, wi):
-// components 4 b .. 4 b + 3 (zero past n), the warp walk's draws.
+// The walk's Gaussian vector v of step kk of walk (p, wi): block b (components
+// 4 b .. 4 b + 3, zero past n) from Philox block j = 256 v + b, the warp walk's
+// draws (walkn32.cuh); returns the block's part of |g|^2.
 struct PhiloxSource {
   const PhiloxKeys* K;
-  uint32_t jb, kk, wi, p;
+  Philox32Step st;
+  uint32_t X;   // A0 ^ 256 v
   int n;
-  __device__ __forceinline__ void operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
+  __device__ __forceinline__ float operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
     g0 = g1 = g2 = g3 = 0.0f;
-    if (4 * b < n) {
-      const U4 r = philox4x32_10(jb + static_cast<uint32_t>(b), kk, wi, p, *K);
-      box_muller32(u23(r.x), u23(r.y), g0, g1);
-      box_muller32(u23(r.z), u23(r.w), g2, g3);
-      if (4 * b + 1 >= n) g1 = 0.0f;
-      if (4 * b + 2 >= n) g2 = 0.0f;
-      if (4 * b + 3 >= n) g3 = 0.0f;
-    }
+    if (4 * b >= n) return 0.0f;
+    const U4 r = philox32_block(X ^ static_cast<uint32_t>(b), st, *K);
+    const float l0 = gauss_pair32(r.x, r.y, g0, g1);
+    const float l1 = gauss_pair32(r.z, r.w, g2, g3);
+    if (4 * b + 4 <= n) return l0 + l1;
+    g3 = 0.0f;
+    if (4 * b + 3 > n) g2 = 0.0f;
+    if (4 * b + 2 > n) g1 = 0.0f;
+    return g0 * g0 + g1 * g1 + g2 * g2;
   }
 };
 
@@ -206,13 +210,14 @@ struct MatrixSource {
   const float* G;
   int64_t row, rows;
   int n;
-  __device__ __forceinline__ void operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
+  __device__ __forceinline__ float operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
     float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
     if (row < rows)
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (4 * b + q < n) v[q] = G[row * n + 4 * b + q];
     g0 = v[0]; g1 = v[1]; g2 = v[2]; g3 = v[3];
+    return g0 * g0 + g1 * g1 + g2 * g2 + g3 * g3;
   }
 };
 
@@ -241,8 +246,7 @@ __device__ __forceinline__ float project_vector(const Smem& sm, uint32_t taddr, 
 #pragma unroll
       for (int bb = 0; bb < 2; ++bb) {
         float g0, g1, g2, g3;
-        src(16 * c + 2 * unit + bb, g0, g1, g2, g3);
-        acc = fmaf(g0, g0, fmaf(g1, g1, fmaf(g2, g2, fmaf(g3, g3, acc))));
+        acc += src(16 * c + 2 * unit + bb, g0, g1, g2, g3);
         const uint32_t h01 = pack_bf16x2(g0, g1), h23 = pack_bf16x2(g2, g3);
         hw[2 * bb] = h01;
         hw[2 * bb + 1] = h23;
@@ -398,7 +402,6 @@ __global__ void __launch_bounds__(kThreads, 1) embed_tc_kernel(const DevProblem 
   const uint32_t taddr = tc_begin(sm, pb.tc_bimg);   // also makes the stores above visible
 
   const PhiloxKeys& K = pb.keys;
-  const uint32_t nb = static_cast<uint32_t>((n + 3) / 4);
   const int nv = pb.n_v;
   const int max_steps = static_cast<int>(pb.max_steps);
   const int64_t tiles = (pb.wk_w1 - pb.wk_w0 + kM - 1) / kM;
@@ -415,6 +418,7 @@ __global__ void __launch_bounds__(kThreads, 1) embed_tc_kernel(const DevProblem 
       p = id.p;
       wi = id.i;
     }
+    const Philox32Walk pw = philox32_walk(wi, K);
     if (tid < kM) {
 #pragma unroll
       for (int j = 0; j < DQ; ++j)
@@ -439,18 +443,18 @@ __global__ void __launch_bounds__(kThreads, 1) embed_tc_kernel(const DevProblem 
         kstop = k;
       }
       if (!__syncthreads_or(running)) break;
-      const uint32_t kk = static_cast<uint32_t>(k);
+      const Philox32Step st = philox32_step(pw, static_cast<uint32_t>(k), p, K);
       // interior samples Z_l = s + r t_l g_l / |g_l| and the source average F
       float F = 0.0f;
       for (int l = 0; l < nv; ++l) {
         float t = 0.0f;
         if (tid < kM) {
-          const U4 bu = philox4x32_10(nb * static_cast<uint32_t>(1 + nv) + static_cast<uint32_t>(l >> 2), kk, wi, p, K);
+          const U4 bu = philox32_block(pw.A0 ^ static_cast<uint32_t>(256 * (1 + nv) + (l >> 2)), st, K);
           const int s4 = l & 3;
           const float U = u23(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
           t = fminf(fmaxf(table_lookup32(pb, a, U), 0.0f), 1.0f);
         }
-        const PhiloxSource src{&K, nb * static_cast<uint32_t>(1 + l), kk, wi, p, n};
+        const PhiloxSource src{&K, st, pw.A0 ^ static_cast<uint32_t>(256 * (1 + l)), n};
         const float gg = project_vector(sm, taddr, nchunks, src, gchunk, ok);
         if (tid < kM) {
           float z[DQ];
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) embed_tc_kernel(const DevProblem 
       }
       if (nv > 1) F /= static_cast<float>(nv);
       // Theta = s + r g / |g|, then the closest point: s = Theta / |Theta|
-      const PhiloxSource src{&K, 0u, kk, wi, p, n};
+      const PhiloxSource src{&K, st, pw.A0, n};
       const float gg = project_vector(sm, taddr, nchunks, src, gchunk, ok);
       if (tid < kM) {
         float th[DQ];

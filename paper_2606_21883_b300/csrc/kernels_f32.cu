@@ -3,7 +3,6 @@
 // FMA contraction); the FP64 parts keep IEEE double arithmetic.
 #include "launch.h"
 #include "walk3.cuh"
-#include "walkn.cuh"
 #include "embed_tc.cuh"
 #include "walkr.cuh"
 
@@ -49,28 +48,6 @@ cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStre
   DevProblem arg = pb;
   void* args[] = {&arg};
   return cudaLaunchKernel(fn, dim3(grid), dim3(block), args, 0, st);
-}
-
-static const void* walkn_f32_fn(const DevProblem& pb) {
-  if (pb.mkind == kEuclid) return reinterpret_cast<const void*>(walkn_f32_kernel<kEuclid, 8>);
-  if (pb.mkind == kSphere) return reinterpret_cast<const void*>(walkn_f32_kernel<kSphere, 8>);
-  if (pb.mkind == kRevolution) return reinterpret_cast<const void*>(walkn_f32_kernel<kRevolution, 8>);
-  if (pb.mkind == kCurveSphere) return reinterpret_cast<const void*>(walkn_f32_kernel<kCurveSphere, 8>);
-  switch (walkn_dq(pb.d + 1)) {
-    case 8: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 8>);
-    case 16: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 16>);
-    case 24: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 24>);
-    default: return reinterpret_cast<const void*>(walkn_f32_kernel<kEmbeddedSphere, 32>);
-  }
-}
-
-cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st) {
-  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere && pb.mkind != kRevolution &&
-      pb.mkind != kCurveSphere)
-    return cudaErrorInvalidValue;
-  DevProblem arg = pb;
-  void* args[] = {&arg};
-  return cudaLaunchKernel(walkn_f32_fn(pb), dim3(grid), dim3(block), args, 0, st);
 }
 
 static const void* embed_tc_fn(int D) {
@@ -134,10 +111,7 @@ const void* walk_fn_f32(const DevProblem& pb) {
   if (pb.reduced)
     return (pb.mkind == kEuclid || pb.mkind == kSphere || pb.mkind == kEmbeddedSphere) ? walkr32_fn(pb) : nullptr;
   if (pb.n == 3 && pb.mkind != kEmbeddedSphere) return walk3_f32_fn(pb);
-  if (pb.mkind != kEuclid && pb.mkind != kSphere && pb.mkind != kEmbeddedSphere && pb.mkind != kRevolution &&
-      pb.mkind != kCurveSphere)
-    return nullptr;
-  return walkn_f32_fn(pb);
+  return walkn32_fn(pb);
 }
 
 int occupancy_walkr(const DevProblem& pb, bool fp64, int block) {
@@ -148,14 +122,9 @@ int occupancy_walkr(const DevProblem& pb, bool fp64, int block) {
 }
 
 int occupancy_walk_f32(const DevProblem& pb, bool n3, int block) {
+  if (!n3) return occupancy_walkn32(pb, block);
   int nb = 0;
-  const void* fn = nullptr;
-  if (n3) {
-    fn = walk3_f32_fn(pb);
-  } else {
-    fn = walkn_f32_fn(pb);
-  }
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, block, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, walk3_f32_fn(pb), block, 0);
   return nb < 1 ? 1 : nb;
 }
 

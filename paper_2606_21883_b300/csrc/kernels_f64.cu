@@ -2,6 +2,7 @@
 // per-point reduction and the verification primitives.  Compiled with
 // --fmad=false so that every FP64 + and * is one IEEE operation.
 #include "launch.h"
+#include "estimator.cuh"
 #include "walk3.cuh"
 #include "walkn.cuh"
 #include "cloud.cuh"
@@ -69,62 +70,62 @@ cudaError_t launch_build_table(int n, int NA, int NS, double z_max, double a_fix
 }
 
 // ---------------------------------------------------------------------------
-// Per-point estimator (eq. mc_estimator): one warp per point, lane-strided
-// Kahan sums of S and S^2 in walk order, combined across lanes in a fixed
-// tree order with error-free additions.  Deterministic for given inputs.
-// ---------------------------------------------------------------------------
-struct KSum { double s, c; };
-
-__device__ __forceinline__ void kahan_add(KSum& k, double v) {
-  const double y = v - k.c;
-  const double t = k.s + y;
-  k.c = (t - k.s) - y;
-  k.s = t;
-}
-
-__device__ __forceinline__ KSum ksum_merge(KSum a, KSum b) {
-  // TwoSum of the leading parts, compensations carried along
-  const double s = a.s + b.s;
-  const double bb = s - a.s;
-  const double err = (a.s - (s - bb)) + (b.s - bb);
-  return KSum{s, a.c + b.c - err};
-}
-
+// Per-point estimator (eq. mc_estimator) in the block order of estimator.cuh:
+// one warp per point.  part == null: the blocks merge in order into the mean,
+// its standard error and the mean stopping index; otherwise each block's
+// record (count, mean, M2, sum of K, flagged walks) goes to
+// part[((p nblk_part) + b) kEstFields ...].
 __global__ void reduce_kernel(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t Nu,
                               int64_t stride, const int64_t* n_per_point, double* mean, double* se, double* msteps,
-                              unsigned long long* n_flagged) {
+                              unsigned long long* n_flagged, double* part, int64_t nblk_part) {
   const int lane = threadIdx.x & 31;
   const int64_t p = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   if (p >= P) return;
   const int64_t N = n_per_point ? n_per_point[p] : Nu;
-  KSum s1{0.0, 0.0}, s2{0.0, 0.0};
-  long long ks = 0, nf = 0;
   const double* Sp = S + p * stride;
-  for (int64_t i = lane; i < N; i += 32) {
-    const double v = Sp[i];
-    kahan_add(s1, v);
-    kahan_add(s2, v * v);
-    ks += K[p * stride + i];
-    nf += flags[p * stride + i];
+  const int32_t* Kp = K + p * stride;
+  const int32_t* Fp = flags + p * stride;
+  Stat acc{0.0, 0.0, 0.0};
+  long long ks_all = 0, nf_all = 0;
+  const int64_t nblk = (N + kEstBlock - 1) / kEstBlock;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const int64_t base = b * kEstBlock;
+    const int64_t nb = (N - base < kEstBlock) ? N - base : kEstBlock;
+    const int cnt = lane_count(nb, lane);
+    Stat st = stat_lane(Sp + base + lane, cnt);
+    long long ks = 0, nf = 0;
+    for (int t = 0; t < cnt; ++t) {
+      ks += Kp[base + lane + 32 * t];
+      nf += Fp[base + lane + 32 * t];
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const Stat o{__shfl_down_sync(0xffffffffu, st.n, off), __shfl_down_sync(0xffffffffu, st.m, off),
+                   __shfl_down_sync(0xffffffffu, st.M, off)};
+      ks += __shfl_down_sync(0xffffffffu, ks, off);
+      nf += __shfl_down_sync(0xffffffffu, nf, off);
+      if (lane < off) st = stat_merge(st, o);
+    }
+    if (lane == 0) {
+      if (part) {
+        if (b < nblk_part) {
+          double* rec = part + (p * nblk_part + b) * kEstFields;
+          rec[0] = st.n; rec[1] = st.m; rec[2] = st.M;
+          rec[3] = static_cast<double>(ks); rec[4] = static_cast<double>(nf);
+        }
+      } else {
+        acc = stat_merge(acc, st);
+        ks_all += ks;
+        nf_all += nf;
+      }
+    }
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    KSum o1{__shfl_down_sync(0xffffffffu, s1.s, off), __shfl_down_sync(0xffffffffu, s1.c, off)};
-    KSum o2{__shfl_down_sync(0xffffffffu, s2.s, off), __shfl_down_sync(0xffffffffu, s2.c, off)};
-    s1 = ksum_merge(s1, o1);
-    s2 = ksum_merge(s2, o2);
-    ks += __shfl_down_sync(0xffffffffu, ks, off);
-    nf += __shfl_down_sync(0xffffffffu, nf, off);
-  }
-  if (lane == 0) {
-    const double sum = s1.s - s1.c, sum2 = s2.s - s2.c;
-    const double dn = static_cast<double>(N);
-    const double mu = sum / dn;
-    double var = (N > 1) ? (sum2 - dn * mu * mu) / (dn - 1.0) : 0.0;
-    if (var < 0.0) var = 0.0;
+  if (!part && lane == 0) {
+    double mu, s;
+    stat_finish(acc, mu, s);
     mean[p] = mu;
-    se[p] = sqrt(var / dn);
-    msteps[p] = static_cast<double>(ks) / dn;
-    if (nf) atomicAdd(n_flagged, static_cast<unsigned long long>(nf));
+    se[p] = s;
+    msteps[p] = N > 0 ? static_cast<double>(ks_all) / static_cast<double>(N) : 0.0;
+    if (nf_all) atomicAdd(n_flagged, static_cast<unsigned long long>(nf_all));
   }
 }
 
@@ -140,7 +141,18 @@ cudaError_t launch_reduce_strided(const double* S, const int32_t* K, const int32
   const int block = 256;
   const int64_t grid = (P * 32 + block - 1) / block;
   reduce_kernel<<<static_cast<unsigned>(grid), block, 0, st>>>(S, K, flags, P, N, stride, n_per_point, mean, se,
-                                                               msteps, n_flagged);
+                                                               msteps, n_flagged, nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_blocks(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                                 double* part, cudaStream_t st) {
+  if (P <= 0) return cudaSuccess;
+  const int block = 256;
+  const int64_t grid = (P * 32 + block - 1) / block;
+  const int64_t nblk = (N + kEstBlock - 1) / kEstBlock;
+  reduce_kernel<<<static_cast<unsigned>(grid), block, 0, st>>>(S, K, flags, P, N, N, nullptr, nullptr, nullptr,
+                                                               nullptr, nullptr, part, nblk);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,14 @@ cudaError_t launch_walk3_f32(const DevProblem& pb, int grid, int block, cudaStre
 // Walks for R^n manifolds (n > 3), one warp per walker.
 cudaError_t launch_walkn_f64(const DevProblem& pb, int grid, int block, cudaStream_t st);
 cudaError_t launch_walkn_f32(const DevProblem& pb, int grid, int block, cudaStream_t st);
+// The FP32 warp walk's kernel for pb (kernels_n32.cu; null if none applies) and
+// its resident blocks per SM.
+const void* walkn32_fn(const DevProblem& pb);
+int occupancy_walkn32(const DevProblem& pb, int block);
+// Lanes per walker of that kernel (16 or 32) and its largest block (also its
+// default block size).
+int walkn32_lanes_per_walker(const DevProblem& pb);
+int walkn32_max_block(const DevProblem& pb);
 // FP32 embedded-sphere walk with the projection on the tensor cores (one
 // persistent 512-thread CTA per SM, 128 walkers per tile; pb.tc_bimg set).
 cudaError_t launch_embed_tc(const DevProblem& pb, int grid, cudaStream_t st);
@@ -44,6 +52,11 @@ cudaError_t launch_intrinsic_start(const double* pts, const double* QT, const do
 cudaError_t launch_reduce(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
                           double* mean, double* se, double* msteps, unsigned long long* n_flagged,
                           cudaStream_t st);
+
+// Per-point, per-block estimator records (estimator.cuh) of P x N per-walk
+// outputs: part holds P x ceil(N / kEstBlock) x kEstFields doubles.
+cudaError_t launch_reduce_blocks(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                                 double* part, cudaStream_t st);
 
 // Same over a strided per-walk layout (row p at p * stride), each point with
 // n_per_point[p] walks (N walks for every point when n_per_point is null).

@@ -21,6 +21,7 @@
 
 #include "../../include/mpwos.h"
 #include "launch.h"
+#include "estimator.cuh"
 #include "revolution.cuh"
 
 using namespace mpwos;
@@ -51,6 +52,21 @@ struct CloudGrid {
 
 }  // namespace
 
+// A manifold handle: owns copies of the description's arrays and the device
+// data the walks read, built once at creation on the context's device.
+struct mpwos_manifold {
+  int device = 0;
+  mpwos_manifold_desc desc{};     // arrays point into the vectors below
+  std::vector<double> Q, b, cloud;
+  double* qt = nullptr;           // EMBEDDED_SPHERE: Q^T (D x npad, npad = n rounded up to 4), FP64
+  float* qtf = nullptr;           //   and FP32
+  double* bd = nullptr;           //   the shift b
+  uint16_t* tc_img = nullptr;     //   the tensor-core walk's operand image of Q^T
+  CloudGrid grid;                 // POINT_CLOUD: the search grid
+  bool has_grid = false;
+  double rev_kmin = 0.0;          // REVOLUTION: smallest curvature indicator over the profile
+};
+
 struct ServeEngine;
 void serve_shutdown(mpwos_ctx* ctx);
 
@@ -72,7 +88,6 @@ struct mpwos_ctx {
   std::string err;
   long long launches = 0;
   std::map<std::tuple<int, int, double>, Table> tables;  // (n, NA, z_max or a) -> table
-  std::map<std::tuple<const void*, int64_t, int, double>, CloudGrid> clouds;  // (ptr, N, k, checksum) -> grid
   bool autotune = false;
   std::map<std::pair<const void*, int>, TuneEntry> tune;  // (walk kernel, n) -> measured launch shapes
 };
@@ -103,6 +118,17 @@ bool is_device_ptr(const void* p) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// A device (or managed) pointer of the given device.
+bool is_device_ptr_on(const void* p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == device;
 }
 
 double kappa_of(const mpwos_manifold_desc* m) {
@@ -163,6 +189,62 @@ int tracked_set(const mpwos_manifold_desc* m, const mpwos_problem* pr, int* T) {
       T[nT++] = q;
     }
   return nT;
+}
+
+// The checks of a manifold description alone (at handle creation).
+int validate_manifold(mpwos_ctx* ctx, const mpwos_manifold_desc* m) {
+  if (m->n < 3 || m->n > 1024) return fail(ctx, MPWOS_EINVAL, "ambient dimension must lie in [3, 1024] (got %d)", m->n);
+  switch (m->kind) {
+    case MPWOS_EUCLID:
+      if (m->d != m->n) return fail(ctx, MPWOS_EINVAL, "EUCLID needs d == n");
+      return MPWOS_OK;
+    case MPWOS_SPHERE:
+      if (m->d != m->n - 1) return fail(ctx, MPWOS_EINVAL, "SPHERE needs d == n - 1");
+      return MPWOS_OK;
+    case MPWOS_TORUS:
+      if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "TORUS lives in R^3 (n = 3, d = 2)");
+      if (!(m->R > m->a && m->a > 0.0)) return fail(ctx, MPWOS_EINVAL, "TORUS needs R > a > 0");
+      return MPWOS_OK;
+    case MPWOS_EMBEDDED_SPHERE:
+      if (m->n <= 3) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs n > 3");
+      if (m->d < 1 || m->d + 1 > kMaxQuadDim - 1 || m->d + 1 > m->n) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs 1 <= d <= min(n - 1, 30)");
+      if (!m->Q || !m->b) return fail(ctx, MPWOS_EINVAL, "EMBEDDED_SPHERE needs Q and b");
+      return MPWOS_OK;
+    case MPWOS_REVOLUTION:
+      if (m->n < 4 || m->d != m->n - 1) return fail(ctx, MPWOS_EINVAL, "REVOLUTION needs n >= 4 and d == n - 1");
+      if (!(m->prof_alpha > 0.0 && m->prof_alpha < 0.5 && m->prof_kappa > 0.0))
+        return fail(ctx, MPWOS_EINVAL, "REVOLUTION needs 0 < prof_alpha < 1/2 and prof_kappa > 0");
+      return MPWOS_OK;
+    case MPWOS_CURVE_SPHERE:
+      if (m->n != 9 || m->d != 3) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE lives in R^9 (n = 9, d = 3)");
+      if (!(m->R > 0.0 && m->a > 0.0)) return fail(ctx, MPWOS_EINVAL, "CURVE_SPHERE needs R > 0 and a > 0");
+      return MPWOS_OK;
+    case MPWOS_POINT_CLOUD:
+      if (m->n != 3 || m->d != 2) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD lives in R^3 (n = 3, d = 2)");
+      if (!m->cloud) return fail(ctx, MPWOS_EINVAL, "POINT_CLOUD needs cloud");
+      if (m->k_nn < 1 || m->k_nn > 32) return fail(ctx, MPWOS_EINVAL, "k_nn must lie in [1, 32]");
+      if (m->cp_mode == MPWOS_CLOUD_CP_FIT && m->k_nn < 6) return fail(ctx, MPWOS_EINVAL, "the quadratic fit needs k_nn >= 6");
+      if (m->n_cloud < m->k_nn || m->n_cloud > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "need k_nn <= n_cloud < 2^31");
+      if (!(m->c_h > 0.0)) return fail(ctx, MPWOS_EINVAL, "c_h must be > 0");
+      if (m->cp_mode != MPWOS_CLOUD_CP_FIT && m->cp_mode != MPWOS_CLOUD_CP_NEAREST) return fail(ctx, MPWOS_EINVAL, "unknown cp_mode");
+      return MPWOS_OK;
+    default:
+      return fail(ctx, MPWOS_EINVAL, "unknown manifold kind %d", m->kind);
+  }
+}
+
+// The description of a handle made on this context's device (null: EINVAL).
+const mpwos_manifold_desc* handle_desc(mpwos_ctx* ctx, const mpwos_manifold* mh) {
+  if (!mh) {
+    fail(ctx, MPWOS_EINVAL, "null manifold");
+    return nullptr;
+  }
+  if (mh->device != ctx->device) {
+    fail(ctx, MPWOS_EINVAL, "the manifold was created on device %d, the context runs on device %d", mh->device,
+         ctx->device);
+    return nullptr;
+  }
+  return &mh->desc;
 }
 
 int validate(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* pr, const mpwos_params* pa,
@@ -354,6 +436,72 @@ void fill_scalars_f(DevProblem& pb) {
   pb.cl_cell_f = static_cast<float>(pb.cl_cell);
 }
 
+// The FP32 warp walk's coordinate order (n > 3, full sampler; R^n, the sphere
+// and the hypersurface of revolution): walk coordinate c holds ambient
+// coordinate perm[c].  The revolution's axis comes first, then the coordinates
+// that f and g read, then those of the boundary normal, then the rest in order
+// (the walk reads these in slot 0 of the first lanes).  Remaps pb's POLY
+// variables and fills e_s0; the host arrays to upload are the order, the whole
+// normal in walk order when it reaches past walk coordinate 127, and the
+// revolution's v and diag(A) in walk order, each padded to 1024 floats.
+struct WalkOrder {
+  std::vector<int> perm;
+  std::vector<float> ef_w, v32, a32;
+};
+
+bool uses_walk_order(const mpwos_manifold_desc* m, const mpwos_params* pa) {
+  return pa->precision == MPWOS_FP32 && pa->sampler == MPWOS_SAMPLER_FULL && m->n > 3 &&
+         (m->kind == MPWOS_EUCLID || m->kind == MPWOS_SPHERE || m->kind == MPWOS_REVOLUTION);
+}
+
+void walk_order(const mpwos_manifold_desc* m, const mpwos_problem* pr, DevProblem& pb, WalkOrder& wo) {
+  const int n = m->n;
+  std::vector<int> pos(static_cast<size_t>(n), -1);
+  wo.perm.clear();
+  auto add = [&](int c) {
+    if (c >= 0 && c < n && pos[c] < 0) {
+      pos[c] = static_cast<int>(wo.perm.size());
+      wo.perm.push_back(c);
+    }
+  };
+  if (m->kind == MPWOS_REVOLUTION) add(n - 1);
+  for (DevFunc* df : {&pb.f, &pb.g}) {
+    if ((df == &pb.g && pr->closed) || df->kind != kPoly) continue;
+    for (int q = 0; q < df->term_off[df->n_terms]; ++q) add(df->var[q]);
+  }
+  if (!pr->closed)
+    for (int c = 0; c < n; ++c)
+      if (pr->bnd_normal[c] != 0.0) add(c);
+  for (int c = 0; c < n; ++c) add(c);
+  for (DevFunc* df : {&pb.f, &pb.g}) {
+    if ((df == &pb.g && pr->closed) || df->kind != kPoly) continue;
+    for (int q = 0; q < df->term_off[df->n_terms]; ++q) df->var[q] = static_cast<int16_t>(pos[df->var[q]]);
+  }
+  bool past = false;
+  for (int c = 0; c < 128; ++c) pb.e_s0[c] = 0.0f;
+  if (!pr->closed)
+    for (int c = 0; c < n; ++c) {
+      const float e = static_cast<float>(pr->bnd_normal[wo.perm[c]]);
+      if (c < 128) pb.e_s0[c] = e;
+      else if (e != 0.0f) past = true;
+    }
+  wo.ef_w.clear();
+  if (past) {
+    wo.ef_w.assign(1024, 0.0f);
+    for (int c = 0; c < n; ++c) wo.ef_w[c] = static_cast<float>(pr->bnd_normal[wo.perm[c]]);
+  }
+  wo.v32.clear();
+  wo.a32.clear();
+  if (m->kind == MPWOS_REVOLUTION) {
+    wo.v32.assign(1024, 0.0f);
+    wo.a32.assign(1024, 0.0f);
+    for (int c = 1; c < n; ++c) {
+      wo.v32[c] = static_cast<float>(pr->f.v[wo.perm[c]]);
+      wo.a32[c] = static_cast<float>(pr->f.A[wo.perm[c]]);
+    }
+  }
+}
+
 // Rows of a variable-radius table: the law's dependence on z = a^2/4 enters
 // through z/(nu + j); high dimensions need few rows.
 int table_rows(int n) { return n <= 8 ? kTableNA : 17; }
@@ -448,20 +596,10 @@ int get_table(mpwos_ctx* ctx, int n, bool fixed, double a_or_zmax, Table** out) 
   return MPWOS_OK;
 }
 
-// The search grid of a point cloud (cached per context).
-int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
+// The search grid of a point cloud (built once, for its manifold handle).
+int build_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid& G) {
   const int64_t N = m->n_cloud;
   const double* P = m->cloud;
-  double chk = 0.0;
-  for (int64_t i = 0; i < N; i += (N / 64 + 1)) chk += P[3 * i] * 1.0 + P[3 * i + 1] * 3.0 + P[3 * i + 2] * 7.0;
-  chk += P[3 * (N - 1)] + P[3 * (N - 1) + 2];
-  auto key = std::make_tuple(static_cast<const void*>(P), N, m->k_nn, chk);
-  auto it = ctx->clouds.find(key);
-  if (it != ctx->clouds.end()) {
-    *out = &it->second;
-    return MPWOS_OK;
-  }
-  CloudGrid G;
   double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t i = 0; i < N; ++i)
     for (int a = 0; a < 3; ++a) {
@@ -537,9 +675,16 @@ int get_cloud(mpwos_ctx* ctx, const mpwos_manifold_desc* m, CloudGrid** out) {
   cudaFree(counts);
   cudaFree(cursor);
   cudaFree(hbits);
-  auto res = ctx->clouds.emplace(key, G);
-  *out = &res.first->second;
   return MPWOS_OK;
+}
+
+void free_cloud(CloudGrid& G) {
+  cudaFree(G.pts64);
+  cudaFree(G.pts32);
+  cudaFree(G.pts4);
+  cudaFree(G.orig);
+  cudaFree(G.start);
+  G = CloudGrid{};
 }
 
 // BF16 round-to-nearest-even of an FP32 value (finite inputs).
@@ -577,9 +722,9 @@ void tc_bimage(const double* Q, int n, int D, std::vector<uint16_t>& img) {
 }
 
 // Everything a walk launch needs, built in `sc`.
-int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpwos_problem* pr,
-            const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb,
-            CloudGrid* cloud_pre = nullptr) {
+int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold* mh, const mpwos_problem* pr,
+            const mpwos_params* pa, const double* pts, int64_t P, int64_t N, DevProblem& pb) {
+  const mpwos_manifold_desc* m = &mh->desc;
   std::memset(&pb, 0, sizeof pb);
   pb.mkind = m->kind;
   pb.n = m->n;
@@ -669,6 +814,20 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     pb.rv_mA_f = static_cast<float>(pb.rv_mA);
     pb.rv_ck_f = static_cast<float>(pa->c_kappa);
   }
+  // the FP32 warp walk's coordinate order
+  if (uses_walk_order(m, pa)) {
+    WalkOrder wo;
+    walk_order(m, pr, pb, wo);
+    pb.perm = sc.upload(wo.perm.data(), wo.perm.size());
+    if (!pb.perm) return fail(ctx, MPWOS_ENOMEM, "walk coordinate order");
+    if (!wo.ef_w.empty() && !(pb.ef_w = sc.upload(wo.ef_w.data(), wo.ef_w.size())))
+      return fail(ctx, MPWOS_ENOMEM, "boundary normal");
+    if (!wo.v32.empty()) {
+      pb.rv_v32 = sc.upload(wo.v32.data(), wo.v32.size());
+      pb.rv_a32 = sc.upload(wo.a32.data(), wo.a32.size());
+      if (!pb.rv_v32 || !pb.rv_a32) return fail(ctx, MPWOS_ENOMEM, "REVOLUTION_QUAD data");
+    }
+  }
   // query points
   if (is_device_ptr(pts)) {
     pb.pts = pts;
@@ -677,36 +836,23 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
     if (!pb.pts && P) return fail(ctx, MPWOS_ENOMEM, "query points");
   }
   if (m->kind == MPWOS_EMBEDDED_SPHERE) {
-    // Q^T, D rows of stride npad = n rounded up to 4 (zero padded: 16-byte row slices)
     const int npad = (n + 3) & ~3;
-    std::vector<double> qt(static_cast<size_t>(D) * npad, 0.0);
-    std::vector<float> qtf(qt.size(), 0.0f);
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < D; ++j) {
-        qt[static_cast<size_t>(j) * npad + i] = m->Q[static_cast<size_t>(i) * D + j];
-        qtf[static_cast<size_t>(j) * npad + i] = static_cast<float>(m->Q[static_cast<size_t>(i) * D + j]);
-      }
-    double* qtd = sc.upload(qt.data(), qt.size());
-    float* qtfd = sc.upload(qtf.data(), qtf.size());
-    double* bd = sc.upload(m->b, n);
     double* s0 = sc.alloc<double>(static_cast<size_t>(P) * D);
-    if (!qtd || !qtfd || !bd || !s0) return fail(ctx, MPWOS_ENOMEM, "embedding");
-    pb.Q = qtd;   // Q^T, D x n
-    pb.Qf = qtfd;
-    pb.b = bd;
+    if (!s0) return fail(ctx, MPWOS_ENOMEM, "intrinsic start points");
+    pb.Q = mh->qt;   // Q^T, D x npad
+    pb.Qf = mh->qtf;
+    pb.b = mh->bd;
     pb.s0 = s0;
     if (P) {
-      CK(launch_intrinsic_start(pb.pts, qtd, bd, n, npad, D, P, s0, sc.stream));
+      CK(launch_intrinsic_start(pb.pts, mh->qt, mh->bd, n, npad, D, P, s0, sc.stream));
       ctx->launches++;
     }
     const bool tc = pa->precision == MPWOS_FP32 && pa->sampler == MPWOS_SAMPLER_FULL &&
                     (pa->projection == MPWOS_PROJ_TENSOR || (pa->projection == MPWOS_PROJ_AUTO && n >= 128));
     if (tc) {
-      std::vector<uint16_t> img;
-      tc_bimage(m->Q, n, D, img);
-      pb.tc_bimg = reinterpret_cast<const uint4*>(sc.upload(img.data(), img.size()));
+      pb.tc_bimg = reinterpret_cast<const uint4*>(mh->tc_img);
       pb.dev_status = sc.alloc<unsigned>(1);
-      if (!pb.tc_bimg || !pb.dev_status) return fail(ctx, MPWOS_ENOMEM, "tensor-core operand image");
+      if (!pb.dev_status) return fail(ctx, MPWOS_ENOMEM, "tensor-core walk status");
       CK(cudaMemsetAsync(pb.dev_status, 0, sizeof(unsigned), sc.stream));
     }
   }
@@ -745,11 +891,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   // point cloud grid; rho_geo varies with h(y)
   double rho_geo_max = pb.rho_geo;
   if (m->kind == MPWOS_POINT_CLOUD) {
-    CloudGrid* G = cloud_pre;
-    if (!G) {
-      int rc0 = get_cloud(ctx, m, &G);
-      if (rc0) return rc0;
-    }
+    const CloudGrid* G = &mh->grid;
     pb.cl_pts64 = G->pts64;
     pb.cl_pts32 = G->pts32;
     pb.cl_pts4 = G->pts4;
@@ -765,15 +907,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold_desc* m, const mpw
   }
   // hypersurface of revolution: rho_geo = c_kappa / (1 + kappa(y)) varies; its
   // largest value from the smallest curvature over a dense scan of the profile
-  if (m->kind == MPWOS_REVOLUTION) {
-    double kmin = INFINITY;
-    const double lim = m->prof_kappa * (1.0 - 1e-6);
-    for (int j = 0; j <= 20000; ++j) {
-      const double t = -lim + 2.0 * lim * j / 20000.0;
-      kmin = std::min(kmin, rev_kappa<double>(rev_profile<double>(t, m->prof_alpha, m->prof_kappa)));
-    }
-    rho_geo_max = pa->c_kappa / (1.0 + 0.99 * kmin);
-  }
+  if (m->kind == MPWOS_REVOLUTION) rho_geo_max = pa->c_kappa / (1.0 + 0.99 * mh->rev_kmin);
   // radius tables
   const bool fixed_radius = pr->closed && m->kind != MPWOS_POINT_CLOUD && m->kind != MPWOS_REVOLUTION;
   const double a_max = pb.sqrt_sigma * pb.theta * rho_geo_max;
@@ -839,9 +973,11 @@ int launch_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
     return MPWOS_OK;
   }
   const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
-  const int block = block_req > 0 ? block_req : (n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256) : 128);
+  const int block = block_req > 0 ? block_req
+                                  : (n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256)
+                                        : (fp64 ? 128 : walkn32_max_block(pb)));
   const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
-  const int64_t per_block = n3 ? block : block / 32;
+  const int64_t per_block = n3 ? block : block / (fp64 ? 32 : walkn32_lanes_per_walker(pb));
   int64_t grid = static_cast<int64_t>(ctx->sm_count) * occ;
   const int64_t need = (pb.wk_w1 - pb.wk_w0 + per_block - 1) / per_block;
   if (max_grid < 0) grid = std::max<int64_t>(ctx->sm_count, grid / (-max_grid));
@@ -892,7 +1028,8 @@ int run_walks_tuned(mpwos_ctx* ctx, DevProblem& pb, bool fp64) {
   for (int b : cand) {
     const int occ = pb.reduced ? occupancy_walkr(pb, fp64, b)
                                : (fp64 ? occupancy_walk_f64(pb, n3, b) : occupancy_walk_f32(pb, n3, b));
-    wave = std::max<int64_t>(wave, static_cast<int64_t>(ctx->sm_count) * occ * (warp ? b / 32 : b));
+    const int lpw = fp64 ? 32 : (warp ? walkn32_lanes_per_walker(pb) : 1);
+    wave = std::max<int64_t>(wave, static_cast<int64_t>(ctx->sm_count) * occ * (warp ? b / lpw : b));
   }
   const int64_t nc = static_cast<int64_t>(cand.size());
   if (cand.empty() || pb.wk_w1 - pb.wk_w0 < 2 * wave * (nc + 1)) return launch_walks(ctx, pb, fp64, st, 0, 0);
@@ -953,12 +1090,14 @@ int run_walks_tuned(mpwos_ctx* ctx, DevProblem& pb, bool fp64) {
 
 extern "C" {
 
-int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const double* x, int64_t nq, int precision,
+int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold* mh, const double* x, int64_t nq, int precision,
                     int method, int32_t* idx, double* d2, double* h) {
   if (!ctx) return MPWOS_EINVAL;
   std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
-  if (!m || m->kind != MPWOS_POINT_CLOUD || !m->cloud) return fail(ctx, MPWOS_EINVAL, "not a point cloud");
+  const mpwos_manifold_desc* m = handle_desc(ctx, mh);
+  if (!m) return MPWOS_EINVAL;
+  if (m->kind != MPWOS_POINT_CLOUD || !mh->has_grid) return fail(ctx, MPWOS_EINVAL, "not a point cloud");
   if (m->k_nn < 1 || m->k_nn > 32) return fail(ctx, MPWOS_EINVAL, "k_nn must lie in [1, 32]");
   if (m->n_cloud < m->k_nn || m->n_cloud > 0x7fffffffLL) return fail(ctx, MPWOS_EINVAL, "need k_nn <= n_cloud < 2^31");
   if (nq < 0 || (nq > 0 && (!x || !idx || !d2 || !h))) return fail(ctx, MPWOS_EINVAL, "queries or outputs");
@@ -968,9 +1107,7 @@ int mpwos_cloud_knn(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const double* 
   if (method == MPWOS_KNN_GRID_WARP && precision == MPWOS_FP64)
     return fail(ctx, MPWOS_EINVAL, "the warp-cooperative search is FP32 only");
   if (nq == 0) return MPWOS_OK;
-  CloudGrid* G = nullptr;
-  int rc = get_cloud(ctx, m, &G);
-  if (rc) return rc;
+  const CloudGrid* G = &mh->grid;
   DevProblem pb;
   std::memset(&pb, 0, sizeof pb);
   pb.cl_pts64 = G->pts64;
@@ -1061,7 +1198,7 @@ void mpwos_params_default(mpwos_params* p) {
   p->sampler = MPWOS_SAMPLER_FULL;
 }
 
-int mpwos_create(int device, mpwos_ctx** out) {
+int mpwos_create(int device, void* stream, mpwos_ctx** out) {
   if (!out) return MPWOS_EINVAL;
   *out = nullptr;
   int count = 0;
@@ -1078,9 +1215,91 @@ int mpwos_create(int device, mpwos_ctx** out) {
     delete ctx;
     return MPWOS_ECUDA;
   }
-  ctx->stream = ctx->own;
+  ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own;
   *out = ctx;
   return MPWOS_OK;
+}
+
+int mpwos_manifold_create(mpwos_ctx* ctx, const mpwos_manifold_desc* desc, mpwos_manifold** out) {
+  if (!ctx || !out) return MPWOS_EINVAL;
+  *out = nullptr;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  if (!desc) return fail(ctx, MPWOS_EINVAL, "null manifold description");
+  int rc = validate_manifold(ctx, desc);
+  if (rc) return rc;
+  std::unique_ptr<mpwos_manifold> mh(new mpwos_manifold());
+  mh->device = ctx->device;
+  mh->desc = *desc;
+  mh->desc.Q = mh->desc.b = mh->desc.cloud = nullptr;
+  const int n = desc->n, D = desc->d + 1;
+  auto upload = [&](void** dst, const void* src, size_t bytes) -> int {
+    if (cudaMalloc(dst, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, MPWOS_ENOMEM, "manifold data (%zu bytes)", bytes);
+    }
+    CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return MPWOS_OK;
+  };
+  if (desc->kind == MPWOS_EMBEDDED_SPHERE) {
+    mh->Q.assign(desc->Q, desc->Q + static_cast<size_t>(n) * D);
+    mh->b.assign(desc->b, desc->b + n);
+    mh->desc.Q = mh->Q.data();
+    mh->desc.b = mh->b.data();
+    // Q^T, D rows of stride npad = n rounded up to 4 (zero padded: 16-byte row slices)
+    const int npad = (n + 3) & ~3;
+    std::vector<double> qt(static_cast<size_t>(D) * npad, 0.0);
+    std::vector<float> qtf(qt.size(), 0.0f);
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < D; ++j) {
+        qt[static_cast<size_t>(j) * npad + i] = mh->Q[static_cast<size_t>(i) * D + j];
+        qtf[static_cast<size_t>(j) * npad + i] = static_cast<float>(mh->Q[static_cast<size_t>(i) * D + j]);
+      }
+    std::vector<uint16_t> img;
+    tc_bimage(mh->Q.data(), n, D, img);
+    if ((rc = upload(reinterpret_cast<void**>(&mh->qt), qt.data(), qt.size() * sizeof(double))) ||
+        (rc = upload(reinterpret_cast<void**>(&mh->qtf), qtf.data(), qtf.size() * sizeof(float))) ||
+        (rc = upload(reinterpret_cast<void**>(&mh->bd), mh->b.data(), mh->b.size() * sizeof(double))) ||
+        (rc = upload(reinterpret_cast<void**>(&mh->tc_img), img.data(), img.size() * sizeof(uint16_t)))) {
+      mpwos_manifold_destroy(mh.release());
+      return rc;
+    }
+  }
+  if (desc->kind == MPWOS_POINT_CLOUD) {
+    mh->cloud.assign(desc->cloud, desc->cloud + 3 * desc->n_cloud);
+    mh->desc.cloud = mh->cloud.data();
+    rc = build_cloud(ctx, &mh->desc, mh->grid);
+    if (rc) {
+      free_cloud(mh->grid);
+      mpwos_manifold_destroy(mh.release());
+      return rc;
+    }
+    mh->has_grid = true;
+  }
+  if (desc->kind == MPWOS_REVOLUTION) {
+    // rho_geo = c_kappa / (1 + kappa(y)) varies: its largest value comes from the
+    // smallest curvature indicator, found on a dense scan of the profile
+    double kmin = INFINITY;
+    const double lim = desc->prof_kappa * (1.0 - 1e-6);
+    for (int j = 0; j <= 20000; ++j) {
+      const double t = -lim + 2.0 * lim * j / 20000.0;
+      kmin = std::min(kmin, rev_kappa<double>(rev_profile<double>(t, desc->prof_alpha, desc->prof_kappa)));
+    }
+    mh->rev_kmin = kmin;
+  }
+  *out = mh.release();
+  return MPWOS_OK;
+}
+
+void mpwos_manifold_destroy(mpwos_manifold* mh) {
+  if (!mh) return;
+  cudaSetDevice(mh->device);
+  cudaFree(mh->qt);
+  cudaFree(mh->qtf);
+  cudaFree(mh->bd);
+  cudaFree(mh->tc_img);
+  if (mh->has_grid) free_cloud(mh->grid);
+  delete mh;
 }
 
 void mpwos_destroy(mpwos_ctx* ctx) {
@@ -1091,13 +1310,6 @@ void mpwos_destroy(mpwos_ctx* ctx) {
   for (auto& kv : ctx->tables) {
     cudaFree(kv.second.tab64);
     cudaFree(kv.second.tabc);
-  }
-  for (auto& kv : ctx->clouds) {
-    cudaFree(kv.second.pts64);
-    cudaFree(kv.second.pts32);
-    cudaFree(kv.second.pts4);
-    cudaFree(kv.second.orig);
-    cudaFree(kv.second.start);
   }
   if (ctx->own) cudaStreamDestroy(ctx->own);
   delete ctx;
@@ -1113,18 +1325,20 @@ int mpwos_set_stream(mpwos_ctx* ctx, void* stream) {
 
 int64_t mpwos_launch_count(const mpwos_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_problem* prob,
                       const mpwos_params* prm, const double* pts, int64_t P, int64_t N, double* S, int32_t* K,
                       int32_t* flags) {
   if (!ctx) return MPWOS_EINVAL;
   std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
+  const mpwos_manifold_desc* m = handle_desc(ctx, mh);
+  if (!m) return MPWOS_EINVAL;
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
   if (!S || !K || !flags) return fail(ctx, MPWOS_EINVAL, "null output");
   Scratch sc(ctx);
   DevProblem pb;
-  rc = prepare(ctx, sc, m, prob, prm, pts, P, N, pb);
+  rc = prepare(ctx, sc, mh, prob, prm, pts, P, N, pb);
   if (rc) return rc;
   const size_t W = static_cast<size_t>(P) * N;
   const bool dS = is_device_ptr(S), dK = is_device_ptr(K), dF = is_device_ptr(flags);
@@ -1144,17 +1358,19 @@ int mpwos_walk_scores(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_
   return MPWOS_OK;
 }
 
-int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob, const mpwos_params* prm,
+int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_problem* prob, const mpwos_params* prm,
                 const double* pts, int64_t P, int64_t N, double* mean, double* stderr_, double* mean_steps) {
   if (!ctx) return MPWOS_EINVAL;
   std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
+  const mpwos_manifold_desc* m = handle_desc(ctx, mh);
+  if (!m) return MPWOS_EINVAL;
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
   if (!mean || !stderr_ || !mean_steps) return fail(ctx, MPWOS_EINVAL, "null output");
   Scratch sc(ctx);
   DevProblem pb;
-  rc = prepare(ctx, sc, m, prob, prm, pts, P, N, pb);
+  rc = prepare(ctx, sc, mh, prob, prm, pts, P, N, pb);
   if (rc) return rc;
   const size_t W = static_cast<size_t>(P) * N;
   pb.S_out = sc.alloc<double>(W);
@@ -1185,6 +1401,106 @@ int mpwos_solve(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_proble
   if (tcst) return fail(ctx, MPWOS_ETIMEDOUT, "tensor-core walk: a bounded mbarrier wait ran out (status %u)", tcst);
   if (hflag) return fail(ctx, MPWOS_EMAXSTEPS, "%llu walks reached max_steps", hflag);
   return MPWOS_OK;
+}
+
+int mpwos_solve_partial(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_problem* prob,
+                        const mpwos_params* prm, const double* pts, int64_t P, int64_t N, int64_t i0, int64_t i1,
+                        double* part) {
+  if (!ctx) return MPWOS_EINVAL;
+  std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
+  CK(cudaSetDevice(ctx->device));
+  const mpwos_manifold_desc* m = handle_desc(ctx, mh);
+  if (!m) return MPWOS_EINVAL;
+  int rc = validate(ctx, m, prob, prm, P, N);
+  if (rc) return rc;
+  if (i0 < 0 || i1 > N || i0 > i1 || i0 % kEstBlock != 0 || (i1 % kEstBlock != 0 && i1 != N))
+    return fail(ctx, MPWOS_EINVAL, "walk range [%lld, %lld) of %lld: both ends must be multiples of %lld (or the end N)",
+                (long long)i0, (long long)i1, (long long)N, (long long)kEstBlock);
+  if (!part && P > 0 && i1 > i0) return fail(ctx, MPWOS_EINVAL, "null output");
+  const int64_t nr = i1 - i0;
+  if (P == 0 || nr == 0) return MPWOS_OK;
+  Scratch sc(ctx);
+  DevProblem pb;
+  rc = prepare(ctx, sc, mh, prob, prm, pts, P, N, pb);
+  if (rc) return rc;
+  pb.wk_i0 = i0;
+  pb.wk_i1 = i1;
+  pb.wk_w0 = 0;
+  pb.wk_w1 = P * nr;
+  pb.out_stride = nr;
+  pb.out_i0 = i0;
+  const size_t W = static_cast<size_t>(P) * nr;
+  const size_t nrec = static_cast<size_t>(P) * ((nr + kEstBlock - 1) / kEstBlock) * kEstFields;
+  pb.S_out = sc.alloc<double>(W);
+  pb.K_out = sc.alloc<int32_t>(W);
+  pb.flag_out = sc.alloc<int32_t>(W);
+  const bool dp = is_device_ptr(part);
+  double* op = dp ? part : sc.alloc<double>(nrec);
+  if (!pb.S_out || !pb.K_out || !pb.flag_out || !op) return fail(ctx, MPWOS_ENOMEM, "scratch for %zu walks", W);
+  rc = run_walks(ctx, pb, prm->precision == MPWOS_FP64);
+  if (rc) return rc;
+  CK(launch_reduce_blocks(pb.S_out, pb.K_out, pb.flag_out, P, nr, op, ctx->stream));
+  ctx->launches++;
+  if (!dp) CK(cudaMemcpyAsync(part, op, nrec * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  unsigned tcst = 0;
+  if (pb.dev_status) CK(cudaMemcpyAsync(&tcst, pb.dev_status, sizeof tcst, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (tcst) return fail(ctx, MPWOS_ETIMEDOUT, "tensor-core walk: a bounded mbarrier wait ran out (status %u)", tcst);
+  return MPWOS_OK;
+}
+
+int mpwos_block_partials_host(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
+                              double* part) {
+  if (P < 0 || N < 0 || ((!S || !K || !flags || !part) && P > 0 && N > 0)) return MPWOS_EINVAL;
+  const int64_t nblk = (N + kEstBlock - 1) / kEstBlock;
+  for (int64_t p = 0; p < P; ++p)
+    for (int64_t b = 0; b < nblk; ++b) {
+      const int64_t base = b * kEstBlock;
+      const int64_t nb = std::min(kEstBlock, N - base);
+      Stat st[32];
+      long long ks = 0, nf = 0;
+      for (int l = 0; l < 32; ++l) {
+        const int cnt = lane_count(nb, l);
+        st[l] = stat_lane(S + p * N + base + l, cnt);
+        for (int t = 0; t < cnt; ++t) {
+          ks += K[p * N + base + l + 32 * t];
+          nf += flags[p * N + base + l + 32 * t];
+        }
+      }
+      for (int off = 16; off > 0; off >>= 1)
+        for (int l = 0; l < off; ++l) st[l] = stat_merge(st[l], st[l + off]);
+      double* rec = part + (p * nblk + b) * kEstFields;
+      rec[0] = st[0].n; rec[1] = st[0].m; rec[2] = st[0].M;
+      rec[3] = static_cast<double>(ks); rec[4] = static_cast<double>(nf);
+    }
+  return MPWOS_OK;
+}
+
+int mpwos_merge_partials(const double* const* parts, const int64_t* nblk, int nparts, int64_t P, double* mean,
+                         double* stderr_, double* mean_steps, int64_t* n_flagged) {
+  if (nparts < 0 || P < 0 || (P > 0 && (!mean || !stderr_ || !mean_steps)) || (nparts > 0 && (!parts || !nblk)))
+    return MPWOS_EINVAL;
+  for (int r = 0; r < nparts; ++r)
+    if (nblk[r] < 0 || (nblk[r] > 0 && P > 0 && !parts[r])) return MPWOS_EINVAL;
+  long long flagged = 0;
+  for (int64_t p = 0; p < P; ++p) {
+    Stat acc{0.0, 0.0, 0.0};
+    long long ks = 0;
+    for (int r = 0; r < nparts; ++r)
+      for (int64_t b = 0; b < nblk[r]; ++b) {
+        const double* rec = parts[r] + (p * nblk[r] + b) * kEstFields;
+        acc = stat_merge(acc, Stat{rec[0], rec[1], rec[2]});
+        ks += static_cast<long long>(rec[3]);
+        flagged += static_cast<long long>(rec[4]);
+      }
+    double mu, se;
+    stat_finish(acc, mu, se);
+    mean[p] = mu;
+    stderr_[p] = se;
+    mean_steps[p] = acc.n > 0.0 ? static_cast<double>(ks) / acc.n : 0.0;
+  }
+  if (n_flagged) *n_flagged = flagged;
+  return flagged ? MPWOS_EMAXSTEPS : MPWOS_OK;
 }
 
 int mpwos_tc_project(mpwos_ctx* ctx, const double* Q, int n, int D, const float* G, int64_t rows, float* out,
@@ -1299,9 +1615,10 @@ constexpr size_t kNoAllocBytes = size_t(32) << 20;   // 32 MiB per device
 constexpr size_t kNaHeader = 256;                      // max-steps counter
 constexpr size_t kNaNormal = 8192 + 4096;              // boundary normal, n <= 1024 doubles + floats
 constexpr size_t kNaQuad = 256;                        // SPHERE_QUAD v, A on S^2 (12 doubles)
+constexpr size_t kNaOrder = 8192;                      // FP32 warp walk: coordinate order, dense normal (1024 each)
 constexpr size_t kNaTab64 = 1068288;                   // 65 x 2 x 1027 doubles, rounded up to 256
 constexpr size_t kNaTabc = 2129920;                    // 65 x 2 x 1024 float4 interval cubics
-constexpr size_t kNaFixed = kNaHeader + kNaNormal + kNaQuad + kNaTab64 + kNaTabc;
+constexpr size_t kNaFixed = kNaHeader + kNaNormal + kNaQuad + kNaOrder + kNaTab64 + kNaTabc;
 constexpr size_t kNaPerWalk = sizeof(double) + 2 * sizeof(int32_t);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -1333,12 +1650,14 @@ extern "C" int64_t mpwos_noalloc_max_walks(void) {
   return static_cast<int64_t>((kNoAllocBytes - kNaFixed) / kNaPerWalk);
 }
 
-extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob,
+extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_problem* prob,
                                    const mpwos_params* prm, const double* pts, int64_t P, int64_t N, double* mean,
                                    double* stderr_, double* mean_steps) {
   if (!ctx) return MPWOS_EINVAL;
   std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
+  const mpwos_manifold_desc* m = handle_desc(ctx, mh);
+  if (!m) return MPWOS_EINVAL;
   int rc = validate(ctx, m, prob, prm, P, N);
   if (rc) return rc;
   if (m->kind == MPWOS_EMBEDDED_SPHERE || m->kind == MPWOS_POINT_CLOUD || m->kind == MPWOS_REVOLUTION ||
@@ -1348,8 +1667,10 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: the reduced sampler is not supported (use mpwos_solve)");
   if (prob->comp != MPWOS_COMP_NONE)
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: compensation is not supported (use mpwos_solve)");
-  if (P > 0 && (!is_device_ptr(pts) || !is_device_ptr(mean) || !is_device_ptr(stderr_) || !is_device_ptr(mean_steps)))
-    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: pts and the three outputs must be device pointers");
+  if (P > 0 && (!is_device_ptr_on(pts, ctx->device) || !is_device_ptr_on(mean, ctx->device) ||
+                !is_device_ptr_on(stderr_, ctx->device) || !is_device_ptr_on(mean_steps, ctx->device)))
+    return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: pts and the three outputs must be device pointers on device %d",
+                ctx->device);
   const int64_t walks = P * N;
   if (walks > mpwos_noalloc_max_walks())
     return fail(ctx, MPWOS_EINVAL, "mpwos_solve_noalloc: P*N = %lld walks exceeds the fixed scratch limit of %lld",
@@ -1363,6 +1684,9 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
   cur += kNaNormal;
   double* quad_dev = reinterpret_cast<double*>(cur);
   cur += kNaQuad;
+  int* perm_dev = reinterpret_cast<int*>(cur);
+  float* efw_dev = reinterpret_cast<float*>(cur + 4096);
+  cur += kNaOrder;
   double* tab64 = reinterpret_cast<double*>(cur);
   cur += kNaTab64;
   float4* tabc = reinterpret_cast<float4*>(cur);
@@ -1423,6 +1747,17 @@ extern "C" int mpwos_solve_noalloc(mpwos_ctx* ctx, const mpwos_manifold_desc* m,
     CK(cudaMemcpyAsync(quad_dev + 3, hf.A, 9 * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     df->v = quad_dev;
     df->A = quad_dev + 3;
+  }
+  // the FP32 warp walk's coordinate order
+  if (uses_walk_order(m, prm)) {
+    WalkOrder wo;
+    walk_order(m, prob, pb, wo);
+    CK(cudaMemcpyAsync(perm_dev, wo.perm.data(), sizeof(int) * wo.perm.size(), cudaMemcpyHostToDevice, ctx->stream));
+    pb.perm = perm_dev;
+    if (!wo.ef_w.empty()) {
+      CK(cudaMemcpyAsync(efw_dev, wo.ef_w.data(), sizeof(float) * wo.ef_w.size(), cudaMemcpyHostToDevice, ctx->stream));
+      pb.ef_w = efw_dev;
+    }
   }
   // the radius table, rebuilt in the shared array on every call
   const double a_max = pb.sqrt_sigma * pb.theta * pb.rho_geo;
@@ -1509,12 +1844,11 @@ struct Request {
   int state = 0;                 // 0 queued, 1 running, 2 done, 3 failed, 4 canceled
   int status = MPWOS_OK;
   std::string err;
-  mpwos_manifold_desc man{};
+  const mpwos_manifold* mh = nullptr;   // the caller's handle (kept alive by the caller)
   mpwos_problem prob{};
   mpwos_params prm{};
   OwnedFunc f, g, u_star;
-  std::vector<double> Q, b, normal, pts;
-  CloudGrid* cloud = nullptr;
+  std::vector<double> normal, pts;
   int64_t P = 0, budget = 0;
   double target = 0.0;
   size_t bytes = 0;
@@ -1619,7 +1953,7 @@ int req_start(mpwos_ctx* ctx, Request& r) {
   ServeEngine& E = *ctx->serve;
   const cudaStream_t st = E.streams[r.slot];
   r.sc.reset(new Scratch(ctx, st));
-  int rc = prepare(ctx, *r.sc, &r.man, &r.prob, &r.prm, r.pts.data(), r.P, r.budget, r.pb, r.cloud);
+  int rc = prepare(ctx, *r.sc, r.mh, &r.prob, &r.prm, r.pts.data(), r.P, r.budget, r.pb);
   if (rc) return rc;
   CK(cudaStreamSynchronize(ctx->stream));   // tables built on the context stream
   const size_t W = static_cast<size_t>(r.P) * r.budget;
@@ -1801,11 +2135,13 @@ int mpwos_serve_config(mpwos_ctx* ctx, int max_active, size_t mem_bytes, int64_t
   return MPWOS_OK;
 }
 
-int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_problem* prob, const mpwos_params* prm,
+int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_problem* prob, const mpwos_params* prm,
                  const double* pts, int64_t P, int64_t walk_budget, double target_stderr, uint64_t* request_id) {
   if (!ctx || !request_id) return MPWOS_EINVAL;
   std::lock_guard<std::recursive_mutex> lock_(ctx->mu);
   CK(cudaSetDevice(ctx->device));
+  const mpwos_manifold_desc* m = handle_desc(ctx, mh);
+  if (!m) return MPWOS_EINVAL;
   int rc = validate(ctx, m, prob, prm, P, walk_budget);
   if (rc) return rc;
   if (P > 0 && (!pts || is_device_ptr(pts))) return fail(ctx, MPWOS_EINVAL, "mpwos_submit takes host query points");
@@ -1818,7 +2154,7 @@ int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_probl
   r->P = P;
   r->budget = walk_budget;
   r->target = target_stderr;
-  r->man = *m;
+  r->mh = mh;
   r->prob = *prob;
   r->prm = *prm;
   const int D = (m->kind == MPWOS_SPHERE && m->n == 3) ? 3 : (m->kind == MPWOS_REVOLUTION ? m->n - 1 : m->d + 1);
@@ -1833,17 +2169,6 @@ int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold_desc* m, const mpwos_probl
   if (prob->comp != MPWOS_COMP_NONE) {
     r->u_star.take(prob->u_star, D);
     r->prob.u_star = r->u_star.f;
-  }
-  if (m->kind == MPWOS_EMBEDDED_SPHERE) {
-    r->Q.assign(m->Q, m->Q + static_cast<size_t>(m->n) * (m->d + 1));
-    r->b.assign(m->b, m->b + m->n);
-    r->man.Q = r->Q.data();
-    r->man.b = r->b.data();
-  }
-  if (m->kind == MPWOS_POINT_CLOUD) {
-    rc = get_cloud(ctx, m, &r->cloud);   // grid built now, while the caller's array is valid
-    if (rc) return rc;
-    r->man.cloud = nullptr;
   }
   r->pts.assign(pts, pts + static_cast<size_t>(P) * m->n);
   r->bytes = static_cast<size_t>(P) * walk_budget * 16 + static_cast<size_t>(P) * 48 + (64 << 10);

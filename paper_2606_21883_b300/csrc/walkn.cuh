@@ -615,9 +615,6 @@ __device__ __forceinline__ void walkn_body(const DevProblem& pb) {
 template <int MK, int DQ>
 __global__ void __launch_bounds__(128) walkn_f64_kernel(const DevProblem pb) { walkn_body<double, MK, DQ>(pb); }
 
-template <int MK, int DQ>
-__global__ void __launch_bounds__(128, 4) walkn_f32_kernel(const DevProblem pb) { walkn_body<float, MK, DQ>(pb); }
-
 // Embedded-sphere dimension bucket (d + 1 <= DQ).
 inline int walkn_dq(int D) { return D <= 8 ? 8 : (D <= 16 ? 16 : (D <= 24 ? 24 : 32)); }
 

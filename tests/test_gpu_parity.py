@@ -2,10 +2,9 @@
 
 FP64 mode draws the same Philox numbers as the oracle, so every walk is
 compared element by element: |S_gpu - S_oracle| <= 1e-12 max(1, |S|) and
-identical stopping index K.  A walk may differ only where a threshold decision
-(delta_Gamma < eps, W < tau_W) sits within rounding of the threshold; such walks
-are counted and must be rare (<= 1e-3 of walks here, and each must be one of
-the walks whose compared quantities are flagged).  FP32 mode is compared
+identical stopping index K and flags, on every walk: the seeded cases here
+contain no walk whose threshold decision (delta_Gamma < eps, W < tau_W) sits
+within rounding of the threshold, so no mismatch is allowed.  FP32 mode is compared
 statistically: |mean32 - mean64| < 4 sqrt(se32^2 + se64^2) per point.
 """
 import math
@@ -36,12 +35,12 @@ def _rows(name):
         return [ln.split() for ln in fh if ln.strip() and not ln.startswith("#")]
 
 
-def _walk_parity(ctx, work, N, max_mismatch_frac=1e-3):
+def _walk_parity(ctx, work, N):
     Sg, Kg, Fg = ctx.walk_scores(work.problem, work.params, work.points, N, precision=M.FP64)
     So, Ko, Fo = O.walk_scores(work.problem, work.params, work.points, N)
     ok = (np.abs(Sg - So) <= REL * np.maximum(1.0, np.abs(So))) & (Kg == Ko) & (Fg == Fo)
     bad = np.count_nonzero(~ok)
-    assert bad <= max(0, int(max_mismatch_frac * ok.size)), (
+    assert bad == 0, (
         f"{bad} of {ok.size} walks differ; first: {np.argwhere(~ok)[:3].tolist()} "
         f"S {Sg[~ok][:3]} vs {So[~ok][:3]}, K {Kg[~ok][:3]} vs {Ko[~ok][:3]}")
     return Sg, Kg, So, Ko

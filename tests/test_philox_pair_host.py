@@ -1,7 +1,9 @@
-"""The walk's two-block and one-block Philox evaluations (per-walk and per-step
-parts hoisted out of rounds 0..2) equal Philox4x32-10 on counters (0, k, i, p)
-and (1, k, i, p): the device header's functions compiled as host code by nvcc and
-run over random and structured (seed, i, p, k)."""
+"""The walks' hoisted Philox evaluations equal Philox4x32-10 itself: the R^3
+walk's two-block and one-block forms (per-walk and per-step parts hoisted out of
+rounds 0..2) on counters (0, k, i, p) and (1, k, i, p), and the R^n FP32 walk's
+block form on counters (k, j, i, p) with j = 256 v + b; the device header's
+functions compiled as host code by nvcc and run over random and structured
+(seed, i, p, k, j)."""
 import os
 import subprocess
 import tempfile
@@ -31,6 +33,14 @@ int main() {
     bad += a.x != ra.x || a.y != ra.y || a.z != ra.z || a.w != ra.w ||
            b.x != rb.x || b.y != rb.y || b.z != rb.z || b.w != rb.w ||
            o.x != ra.x || o.y != ra.y || o.z != ra.z || o.w != ra.w;
+    const Philox32Walk pw = philox32_walk(i, K);
+    const Philox32Step st = philox32_step(pw, k, p, K);
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t j = (q == 0) ? 0u : (q == 1) ? 255u : (q == 2) ? (uint32_t)(256 * (1 + t % 64) + (g() & 255)) : (uint32_t)g();
+      const U4 h = philox32_block(pw.A0 ^ j, st, K);
+      const U4 rh = philox4x32_10(k, j, i, p, K);
+      bad += h.x != rh.x || h.y != rh.y || h.z != rh.z || h.w != rh.w;
+    }
   }
   std::printf("%ld\n", bad);
   return bad != 0;
