@@ -54,6 +54,39 @@ OPS_PER_STEP = 148
 TRAFFIC_BYTES = 16.46e6 + 600.81e6
 
 
+# Algorithmic lane-operations per walk-step of the other walk kernels (N_V = 1),
+# counted the same way (warp-uniform scalar work once per walker).
+def ops_full_sampler(n, revolution=False):
+    """The R^n warp walk with the full sampler (n Gaussians per direction), per
+    16-component group of a direction: 3 Philox blocks with rounds 0..2 hoisted
+    (3 x 34 = 102), 8 radial halves (mask, 2 - m, log2, sqrt, sum: 40), 8 angle
+    halves (16-bit fraction: 2, 2 pi scale, sin, cos, 2 products: 56); then Z:
+    Yh.g with Yh from shared memory (16 FMA + 4 loads), Theta: radii to and
+    from shared memory (4), Yh += s g and |Yh|^2 (32 FMA + 8 loads/stores).
+    The hypersurface of revolution's Z adds (Yh + s g), v and A terms per
+    component (5.5, with v and A loads).  Scalar part of a step: 200."""
+    groups = n / 16.0
+    z = 102 + 40 + 56 + (16 * 5.5 + 10 if revolution else 20)
+    theta = 102 + 40 + 56 + 4 + 40
+    return groups * (z + theta) + 200
+
+
+def ops_tc_embedded(n):
+    """The tensor-core embedded-sphere walk: per component of each of the two
+    directions, its share of a hoisted Philox block (34 / 4), of two 23-bit
+    Box-Muller pairs (23 / 4), the BF16 hi/lo split (3), the shared-memory store
+    and |g|^2 (0.75); the Q^T g products run on the tensor pipe.  Scalar part: 300."""
+    return 2 * n * (34 / 4 + 23 / 4 + 3 + 0.75) + 300
+
+
+# The dimension-reduced sampler on S^999 (walkr_kernel): per direction one
+# Philox block of 4 normals (40 + 2 Box-Muller pairs 23.5) and one chi^2 by
+# Marsaglia-Tsang (its block 40 + a pair 11.75 + the acceptance test 17), and
+# per step the radius, weights, stop test and source (~80).
+OPS_REDUCED_S999 = 2 * (40 + 23.5 + 40 + 11.75 + 17) + 80
+MUFU_PER_PAIR = 4   # log2, sqrt, sin, cos of one Box-Muller pair
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -147,52 +180,105 @@ def _serving_mix(rng, n_req, cloud_w):
     return out
 
 
-def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7):
-    """p50/p99 latency of Poisson arrivals at ~70% of the measured capacity."""
+def _lat_summary(lat, by_kind):
+    lat = np.asarray(lat)
+    rest = np.concatenate([np.asarray(v) for k, v in by_kind.items() if k != "s20"] or [np.zeros(0)])
+    pct = lambda a, q: 1e3 * float(np.percentile(a, q)) if len(a) else None
+    return {"p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": 1e3 * float(lat.mean()),
+            "p99_ms_without_s20": pct(rest, 99),
+            "by_kind_ms": {k: {"p50": pct(v, 50), "max": 1e3 * float(np.max(v))} for k, v in sorted(by_kind.items())}}
+
+
+def _fifo(arrivals, service):
+    """Latencies of one FIFO server: request q starts at max(its arrival, the end of q - 1)."""
+    fin, out = 0.0, []
+    for a, d in zip(arrivals, service):
+        fin = max(fin, a) + d
+        out.append(fin - a)
+    return out
+
+
+def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
+    """p50/p99 latency of Poisson arrivals at ~70% of the measured capacity, and the
+    same arrivals served one request at a time (the latency baselines)."""
     import time as _t
     rng = np.random.default_rng(seed)
     cloud_w = W.point_cloud(P=1, walks=1)
     cloud_w.params.tau_w = 1e-4
 
-    def run(reqs, rate):
-        ids, lat, steps = [], [], 0.0
-        by_kind = {}
+    def run(c, reqs, arrivals, prec):
+        lat, steps, pending, q = [None] * len(reqs), [0.0] * len(reqs), {}, 0
         t0 = _t.perf_counter()
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs))) if rate else np.zeros(len(reqs))
-        pending = {}
-        q = 0
         while q < len(reqs) or pending:
             now = _t.perf_counter() - t0
             while q < len(reqs) and arrivals[q] <= now:
                 kind, w, budget, target = reqs[q]
-                rid = ctx.submit(w.problem, w.params, w.points, budget, target, precision=M.FP32)
-                pending[rid] = (len(w.points), kind)
+                rid = c.submit(w.problem, w.params, w.points, budget, target, precision=prec)
+                pending[rid] = q
                 q += 1
             for rid in list(pending):
-                if ctx.poll(rid) >= 2:
-                    npts, kind = pending.pop(rid)
-                    mean, se, ms, walks, lt, rc = ctx.fetch(rid, npts)
-                    lat.append(lt)
-                    by_kind.setdefault(kind, []).append(lt)
-                    steps += float(np.sum(ms * walks))
+                if c.poll(rid) >= 2:
+                    qq = pending.pop(rid)
+                    mean, se, ms, walks, lt, rc = c.fetch(rid, len(reqs[qq][1].points))
+                    lat[qq] = lt
+                    steps[qq] = float(np.sum(ms * walks))
             _t.sleep(0.0005)
-        return np.array(lat), steps, _t.perf_counter() - t0, by_kind
+        return np.array(lat), np.array(steps), _t.perf_counter() - t0
+
+    def by_kind(reqs, lat):
+        out = {}
+        for (kind, *_), lt in zip(reqs, lat):
+            out.setdefault(kind, []).append(lt)
+        return out
 
     calib = _serving_mix(rng, n_calib, cloud_w)
-    _, st_c, T_c, _ = run(calib, 0.0)                    # all at once: capacity
+    _, _, T_c = run(ctx, calib, np.zeros(n_calib), M.FP32)     # all at once: capacity
     cap_rate = n_calib / T_c
     rate = 0.7 * cap_rate
     reqs = _serving_mix(rng, n_req, cloud_w)
-    lat, steps, T, by_kind = run(reqs, rate)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    lat, steps, T = run(ctx, reqs, arrivals, M.FP32)
     kinds = {k: sum(1 for r in reqs if r[0] == k) for k in ["torus", "cap", "cloud", "s999", "s20"]}
-    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "mean_ms": 1e3 * float(lat.mean()), "requests": int(len(lat)), "arrival_rate_hz": rate,
-            "capacity_hz": cap_rate, "walk_steps_per_s": steps / T, "mix": kinds,
-            "by_kind_ms": {k: {"p50": 1e3 * float(np.percentile(v, 50)), "max": 1e3 * float(np.max(v))}
-                           for k, v in sorted(by_kind.items())},
-            "recipe": "Poisson arrivals at 0.7 x capacity (capacity from a burst of 24); points log-uniform "
-                      "(torus <=4096, cap/cloud/S^999 <=64, S^20 <=4), budget log-uniform 256-65536 (S^999 <=4096, "
-                      "S^20 <=1024), target stderr log-uniform 1e-3-1e-2, FP32 walks, reduced sampler on S^999/S^20"}
+    out = {**_lat_summary(lat, by_kind(reqs, lat)), "requests": int(len(lat)), "arrival_rate_hz": rate,
+           "capacity_hz": cap_rate, "walk_steps_per_s": float(steps.sum()) / T, "mix": kinds,
+           "recipe": "Poisson arrivals at 0.7 x capacity (capacity from a burst of 24); points log-uniform "
+                     "(torus <=4096, cap/cloud/S^999 <=64, S^20 <=4), budget log-uniform 256-65536 (S^999 <=4096, "
+                     "S^20 <=1024), target stderr log-uniform 1e-3-1e-2, FP32 walks, reduced sampler on S^999/S^20; "
+                     "chunks sized to ~10 ms of GPU time"}
+    if baseline:
+        # one request at a time: each request's service time alone on a context with
+        # one slot, then the FIFO queue the same arrivals form in front of it
+        base = M.Context(ctx.device)
+        base.serve_config(max_active=1)
+        svc32, svc64 = [], []
+        for (kind, w, budget, target), st in zip(reqs, steps):
+            rid = base.submit(w.problem, w.params, w.points, budget, target, precision=M.FP32)
+            base.wait(rid)
+            svc32.append(base.fetch(rid, len(w.points))[4])          # submit to done, measured by the library
+            # FP64: the request's points with min(budget, 64) walks each, scaled to the
+            # walk-steps the served request ran (the FP64 walk is ~10^3 x slower on B300:
+            # the whole stream in FP64 would hold the GPU for hours)
+            nb = min(budget, 64)
+            rid = base.submit(w.problem, w.params, w.points, nb, 0.0, precision=M.FP64)
+            base.wait(rid)
+            _, _, ms, walks, lt, _ = base.fetch(rid, len(w.points))
+            s64 = float(np.sum(ms * walks))
+            svc64.append(lt * max(1.0, st / max(s64, 1.0)))
+        base.close()
+        l32, l64 = _fifo(arrivals, svc32), _fifo(arrivals, svc64)
+        out["fp32_one_at_a_time"] = {**_lat_summary(l32, by_kind(reqs, l32)),
+                                     "service_s_total": float(np.sum(svc32)),
+                                     "recipe": "the same requests and arrival times, FP32 walks, one request in flight "
+                                               "(max_active = 1): each service time measured alone, latency = FIFO "
+                                               "finish - arrival"}
+        out["fp64_one_at_a_time"] = {**_lat_summary(l64, by_kind(reqs, l64)),
+                                     "service_s_total": float(np.sum(svc64)),
+                                     "recipe": "estimated: the same requests and arrival times, FP64 walks, one request "
+                                               "in flight; each service time measured on the request's points with "
+                                               "min(budget, 64) walks and scaled linearly to the walk-steps of the "
+                                               "served request (an upper estimate for requests that leave the GPU "
+                                               "idle); latency = FIFO finish - arrival"}
+    return out
 
 
 def _serving_cloud(P):
@@ -201,18 +287,204 @@ def _serving_cloud(P):
     return w
 
 
-def secondary_leg(M, ctx):
-    """Short runs of the other configurations (not the headline metric): each is
-    one mpwos_solve timed by wall clock around device synchronisation, after a
-    warm call that builds its tables."""
+def device_sm_count():
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def issue_peak(sm, mhz):
+    """Lane-operations per second: one warp instruction per SM sub-partition per clock."""
+    return sm * 4 * 32 * mhz * 1e6
+
+
+def mufu_peak(sm, mhz):
+    """MUFU results per second: 16 per SM per clock (log2, sqrt, sin, cos, ...)."""
+    return sm * 16 * mhz * 1e6
+
+
+def roofline_block(kernel, ops_per_step, walk_steps, seconds, sm, mhz, src, mufu_per_step=None):
+    peak = issue_peak(sm, mhz)
+    achieved = ops_per_step * walk_steps / seconds
+    out = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+           "frac": achieved / peak, "kernel": kernel, "kernel_ms": 1e3 * seconds,
+           "ops_per_walk_step": ops_per_step, "traffic": None,
+           "peak_source": f"{sm} SM x 4 SMSP x 32 lanes x {mhz:.0f} MHz ({src} max clock)"}
+    if mufu_per_step:
+        mp = mufu_peak(sm, mhz)
+        out["mufu"] = {"per_walk_step": mufu_per_step, "achieved": mufu_per_step * walk_steps / seconds / 1e12,
+                       "peak": mp / 1e12, "frac": mufu_per_step * walk_steps / seconds / mp,
+                       "peak_source": f"{sm} SM x 16 per clock x {mhz:.0f} MHz"}
+    return out
+
+
+def kernel_run(M, ctx, w, N, prec, projection=None, reps=1):
+    """The walk kernel alone on device buffers (mpwos_walk_scores), timed by CUDA
+    events on the library's stream after a small warm call (tables, handles);
+    returns (seconds, per-walk S and K as host arrays)."""
+    import torch
+    kw = {} if projection is None else {"projection": projection}
+    P = len(w.points)
+    pts = torch.tensor(w.points, dtype=torch.float64, device="cuda")
+    S = torch.empty((P, N), dtype=torch.float64, device="cuda")
+    K = torch.empty((P, N), dtype=torch.int32, device="cuda")
+    F = torch.empty((P, N), dtype=torch.int32, device="cuda")
+    pw = min(P, 8)
+    ctx.walk_scores_device(w.problem, w.params, pts[:pw], 4, prec, S[:pw, :4].contiguous(), K[:pw, :4].contiguous(),
+                           F[:pw, :4].contiguous(), **kw)
+    stream = torch.cuda.current_stream()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        ctx.walk_scores_device(w.problem, w.params, pts, N, prec, S, K, F, **kw)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b) / 1e3)
+    return float(min(ts)), S.cpu().numpy(), K.cpu().numpy()
+
+
+def solve_run(M, ctx, w, N, prec):
+    """One mpwos_solve into device buffers, timed by CUDA events after a small warm call."""
+    import torch
+    P = len(w.points)
+    pts = torch.tensor(w.points, dtype=torch.float64, device="cuda")
+    outs = tuple(torch.zeros(P, dtype=torch.float64, device="cuda") for _ in range(3))
+    ctx.solve(w.problem, w.params, pts[:min(P, 8)], 4, precision=prec)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    ctx.solve(w.problem, w.params, pts, N, precision=prec, out=outs)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / 1e3, tuple(o.cpu().numpy() for o in outs)
+
+
+def torus_generic(P, walks=1):
+    """The closed torus with a two-mode source u = sin(theta) cos(2 phi) + 0.5 cos(2 theta) sin(phi):
+    the walk evaluates the generic Fourier series instead of a one-mode kernel instance."""
+    w = W.torus_closed(P=P, walks=walks)
+    w.problem.f = W.Func.torus([(1.0, 1, 2, W.TRIG_SIN, W.TRIG_COS), (0.5, 2, 1, W.TRIG_COS, W.TRIG_SIN)],
+                               apply_op=True)
+    th, ph = W.torus_angles(P, 0)
+    w.exact = np.sin(th) * np.cos(2 * ph) + 0.5 * np.cos(2 * th) * np.sin(ph)
+    return w
+
+
+def config3_leg(M, ctx, sm, mhz, src):
+    """S^999 half at its stated size (16384 points x 4096 walks) with the
+    dimension-reduced sampler in FP32: walk-steps/s, RMSE, FP32-vs-FP64 agreement
+    on 8 sampled points, roofline of the reduced walk, and the oracle on a subset."""
+    import oracle as O
+    w = W.hypersphere_half(P=16384, walks=1)
+    w.params.sampler = W.SAMPLER_REDUCED
+    N = 4096
+    dt, (mean, se, ms) = solve_run(M, ctx, w, N, M.FP32)
+    steps = float(ms.sum() * N)
+    idx = np.random.default_rng(11).choice(len(w.points), 8, replace=False)
+    sub = W.Workload("s999_sub", w.problem, w.points[idx].copy(), 1, w.params, w.exact[idx], "f64")
+    m64, s64, _, _ = ctx.solve(sub.problem, sub.params, sub.points, N, precision=M.FP64)
+    agree = np.abs(mean[idx] - m64) < 4.0 * np.sqrt(se[idx] ** 2 + s64 ** 2)
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    mo, so, to, _ = O.solve(w.problem, w.params, w.points[:16], 64, n_threads=cores)
+    t_orc = time.perf_counter() - t0
+    return {"workload": "S^999 in R^1000, x_1 > 0, sigma = 1, eps = 1e-3, 16384 pts x 4096 walks to completion, "
+                        "dimension-reduced sampler, FP32 (BASELINE config 3 at full size)",
+            "walk_steps_per_s": steps / dt, "query_pts_per_s": len(w.points) / dt, "seconds": dt,
+            "walk_steps": steps, "mean_steps_per_walk": float(ms.mean()),
+            "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))), "mean_stderr": float(se.mean()),
+            "fp32_vs_fp64": {"points": 8, "walks": N, "within_4_combined_se": int(agree.sum()),
+                             "max_abs_diff": float(np.max(np.abs(mean[idx] - m64)))},
+            "roofline": roofline_block("walkr_kernel<float, sphere>", OPS_REDUCED_S999, steps, dt, sm, mhz, src),
+            "cpu_baseline": {"value": float(to.sum() * 64) / t_orc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"16 points x 64 walks, reduced sampler, FP64, {t_orc:.1f} s"}}
+
+
+def config4_leg(M, ctx, sm, mhz, src):
+    """S^20 in R^1000 (32768 points x 2048 walks of 226,786 steps): a fixed window
+    of steps for every walk (the full sampler with Q^T g on the tensor cores, and
+    the reduced sampler), and the RMSE of complete walks on a 256-point subset."""
+    w = W.embedded_s20(P=32768, walks=1)
+    N = 2048
+    out = {"workload": "S^20 randomly embedded in R^1000 (seeded orthonormal Q, shift b), sigma = 0.5, "
+                       "32768 pts x 2048 walks; every walk runs a fixed window of steps (flagged at the window; "
+                       "a complete walk is 226,786 steps), FP32 (BASELINE config 4)"}
+    w.params.max_steps = 16
+    dt, S, K = kernel_run(M, ctx, w, N, M.FP32, projection=M.PROJ_TENSOR)
+    steps = float(K.sum(dtype=np.int64))
+    out["tensor_core_window_16"] = {
+        "walk_steps_per_s": steps / dt, "seconds": dt, "walk_steps": steps,
+        "roofline": roofline_block("embed_tc_kernel<24>", ops_tc_embedded(1000), steps, dt, sm, mhz, src,
+                                   mufu_per_step=MUFU_PER_PAIR * 1000)}
+    del S, K
+    w.params.sampler = W.SAMPLER_REDUCED
+    w.params.max_steps = 256
+    dt, S, K = kernel_run(M, ctx, w, N, M.FP32)
+    steps = float(K.sum(dtype=np.int64))
+    out["reduced_window_256"] = {"walk_steps_per_s": steps / dt, "seconds": dt, "walk_steps": steps}
+    del S, K
+    sub = W.embedded_s20(P=256, walks=1)
+    sub.params.sampler = W.SAMPLER_REDUCED
+    dt, (mean, se, ms) = solve_run(M, ctx, sub, 16, M.FP32)
+    out["rmse_256_points_16_complete_walks_reduced"] = {
+        "rmse": float(np.sqrt(np.mean((mean - sub.exact) ** 2))), "mean_stderr": float(se.mean()),
+        "mean_steps_per_walk": float(ms.mean()), "seconds": dt}
+    return out
+
+
+def secondary_leg(M, ctx, sm, mhz, src):
+    """The other configurations (not the headline metric): short runs, each with
+    walk-steps/s and RMSE; the n = 1000 walks and the tensor-core walk also with
+    their roofline (kernel alone, CUDA events)."""
+    out = {}
+    # S^2 cap (config 1) at its stated size, FP64 (the per-walk parity mode)
+    w = W.sphere_cap(P=64, walks=1)
+    dt, (mean, se, ms) = solve_run(M, ctx, w, 1000, M.FP64)
+    out["s2_cap_fp64"] = {"workload": "S^2 cap z > 0, 64 pts x 1000 walks, FP64 (BASELINE config 1)",
+                          "walk_steps_per_s": float(ms.sum() * 1000) / dt, "query_pts_per_s": 64 / dt,
+                          "latency_ms": 1e3 * dt, "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))),
+                          "mean_steps_per_walk": float(ms.mean())}
+    # the torus with a two-mode source: the generic Fourier-series walk beside the headline's one-mode instance
+    w = torus_generic(4096)
+    dt, S, K = kernel_run(M, ctx, w, 10_000, M.FP32)
+    steps = float(K.sum(dtype=np.int64))
+    out["torus_generic_series_fp32"] = {
+        "workload": "closed torus, 4096 pts x 1e4 walks, two-mode source (generic series), FP32 walk kernel",
+        "walk_steps_per_s": steps / dt, "seconds": dt,
+        "rmse": float(np.sqrt(np.mean((S.mean(axis=1) - w.exact) ** 2)))}
+    del S, K
+    out["s999_half_reduced_config3"] = config3_leg(M, ctx, sm, mhz, src)
+    # S^999 with the full sampler (the paper's form of the step: n Gaussians per direction)
+    w = W.hypersphere_half(P=4096, walks=1)
+    dt, S, K = kernel_run(M, ctx, w, 16, M.FP32)
+    steps = float(K.sum(dtype=np.int64))
+    out["s999_half_full_sampler_fp32"] = {
+        "workload": "S^999 half, 4096 pts x 16 walks to completion, full sampler (2000 Gaussians per step), FP32",
+        "walk_steps_per_s": steps / dt, "seconds": dt, "mean_steps_per_walk": float(K.mean()),
+        "rmse": float(np.sqrt(np.mean((S.mean(axis=1) - w.exact) ** 2))),
+        "roofline": roofline_block("walkn32s_kernel<sphere, 16, 4>", ops_full_sampler(1000), steps, dt, sm, mhz, src,
+                                   mufu_per_step=MUFU_PER_PAIR * 1000)}
+    del S, K
+    out["s20_in_r1000_config4"] = config4_leg(M, ctx, sm, mhz, src)
+    # Example 2's dumbbell (full sampler, Newton closest point)
+    w = W.dumbbell(P=2368, walks=1)
+    dt, S, K = kernel_run(M, ctx, w, 64, M.FP32)
+    steps = float(K.sum(dtype=np.int64))
+    wr = W.dumbbell(P=100, walks=1)
+    _, (mean, se, ms) = solve_run(M, ctx, wr, 1000, M.FP32)
+    out["dumbbell_e2_fp32"] = {
+        "workload": "Example 2 dumbbell in R^1001 (sigma = 2000, Newton cp), full sampler, FP32; rate on "
+                    "2368 pts x 64 walks, RMSE on 100 pts x 1000 walks",
+        "walk_steps_per_s": steps / dt, "seconds": dt, "mean_steps_per_walk": float(K.mean()),
+        "rmse": float(np.sqrt(np.mean((mean - wr.exact) ** 2))),
+        "roofline": roofline_block("walkn32s_kernel<revolution, 16, 4>", ops_full_sampler(1001, True), steps, dt,
+                                   sm, mhz, src, mufu_per_step=MUFU_PER_PAIR * 1001)}
+    del S, K
+    # the rest (solve, wall clock around synchronisation)
     import torch
     cases = [
-        ("s999_half_reduced_fp32", lambda: W.hypersphere_half(P=16384, walks=1), 64, M.FP32, W.SAMPLER_REDUCED,
-         "S^999 in R^1000, x_1 > 0, 16384 pts x 64 walks to completion, dimension-reduced sampler, FP32"),
-        ("s20_in_r1000_reduced_fp32", lambda: W.embedded_s20(P=4096, walks=1), 16, M.FP32, W.SAMPLER_REDUCED,
-         "S^20 in R^1000, 4096 pts x 16 walks of 226,786 steps, dimension-reduced sampler, FP32"),
-        ("s2_cap_fp64", lambda: W.sphere_cap(P=64, walks=1), 1000, M.FP64, W.SAMPLER_FULL,
-         "S^2 cap, 64 pts x 1000 walks, FP64 (per-walk parity mode)"),
         ("torus_fp64", lambda: W.torus_closed(P=4096, walks=1), 50, M.FP64, W.SAMPLER_FULL,
          "torus, 4096 pts x 50 walks, FP64 walk (per-walk parity mode)"),
         ("torus_fp32", lambda: W.torus_closed(P=4096, walks=1), 50, M.FP32, W.SAMPLER_FULL,
@@ -227,12 +499,9 @@ def secondary_leg(M, ctx):
          "the serving mix's 200k-point cloud (k_nn = 16, quadratic-fit cp, tau_W = 1e-4), 64 pts x 4096 walks, FP32"),
         ("sphere_cloud_e4_fp32", lambda: W.sphere_cloud_legendre(P=100, walks=1), 8000, M.FP32, W.SAMPLER_FULL,
          "Example 4 S^2 as 8000 points, k_nn = 6, nearest-point cp, 100 pts x 8000 walks, FP32"),
-        ("dumbbell_e2_fp32", lambda: W.dumbbell(P=100, walks=1), 1000, M.FP32, W.SAMPLER_FULL,
-         "Example 2 dumbbell in R^1001 (sigma = 2000, Newton cp), 100 pts x 1000 walks, full sampler, FP32"),
         ("curve_sphere_e3_fp32", lambda: W.curve_sphere(P=100, walks=1), 10000, M.FP32, W.SAMPLER_FULL,
          "Example 3 Fourier curve x S^2(0.65) in R^9 (Newton cp on the curve), 100 pts x 1e4 walks, FP32"),
     ]
-    out = {}
     for name, make, N, prec, sampler, desc in cases:
         w = make()
         w.params.sampler = sampler
@@ -322,9 +591,30 @@ def run_reference(args):
     return 0
 
 
-def rank_workload(points, walks, rank):
-    """Weak scaling: every rank solves its own batch of the torus workload (seed = rank)."""
-    return W.torus_closed(P=points, walks=walks, seed=rank)
+def rank_walk_range(N, rank, world, block=1024):
+    """Walk range [i0, i1) of `rank` when a request of N walks per point is split
+    over `world` ranks at estimator-block boundaries (block walks each), so that
+    the ranks' block records merge to the bits of the whole request."""
+    nb = (N + block - 1) // block
+    b0, b1 = nb * rank // world, nb * (rank + 1) // world
+    return min(N, b0 * block), min(N, b1 * block)
+
+
+def gather_partials(dist, part, world):
+    """Every rank's block records (a P x nblk x 5 FP64 tensor, nblk per rank) in
+    rank order: one all_gather of the counts, one of the records padded to the
+    largest range; returned as host arrays."""
+    import torch
+    P, nb, F = part.shape
+    cnt = torch.tensor([nb], dtype=torch.int64, device=part.device)
+    counts = [torch.zeros_like(cnt) for _ in range(world)]
+    dist.all_gather(counts, cnt)
+    counts = [int(c.item()) for c in counts]
+    pad = torch.zeros((P, max(counts), F), dtype=torch.float64, device=part.device)
+    pad[:, :nb] = part
+    bufs = [torch.empty_like(pad) for _ in range(world)]
+    dist.all_gather(bufs, pad)
+    return [b[:, :c].cpu().numpy() for b, c in zip(bufs, counts)]
 
 
 def max_over_ranks(dist, device, *values):
@@ -342,6 +632,98 @@ def aggregate_rate(steps_per_rank_step, steps, world, tmax):
     return steps_per_rank_step * steps * world / tmax
 
 
+# One kernel on a small seeded case, for profiler captures (--leg NAME).
+def _leg_case(M, name, P, N, max_steps):
+    kw = {}
+    if name == "torus":
+        w = W.torus_closed(P=P or 64, walks=1)
+    elif name in ("s20_tc", "s20_cuda"):
+        w = W.embedded_s20(P=P or 148, walks=1)
+        kw["projection"] = M.PROJ_TENSOR if name == "s20_tc" else M.PROJ_CUDA
+    elif name == "s20_red":
+        w = W.embedded_s20(P=P or 1184, walks=1)
+        w.params.sampler = W.SAMPLER_REDUCED
+    elif name == "s999_full":
+        w = W.hypersphere_half(P=P or 148, walks=1)
+    elif name == "s999_red":
+        w = W.hypersphere_half(P=P or 4096, walks=1)
+        w.params.sampler = W.SAMPLER_REDUCED
+    elif name == "dumbbell":
+        w = W.dumbbell(P=P or 2368, walks=1)
+    elif name == "cloud":
+        w = _serving_cloud(P or 64)
+    elif name == "e1_comp":
+        w = W.torus_cut(P=P or 100, walks=1, comp=W.COMP_NORMAL2)
+    else:
+        raise SystemExit(f"unknown leg {name}")
+    if max_steps:
+        w.params.max_steps = max_steps
+    return w, kw
+
+
+def run_knn_leg(args, nq=262144):
+    """The 200k cloud's k = 16 nearest of nq queries near the surface: per rep the
+    FP32 grid search (cloud_knn_query_kernel), then the all-pairs scan
+    (cloud_knn_scan_kernel), each timed by wall clock around synchronisation."""
+    import torch
+    import paper_2606_21883_b300 as M
+    w = W.point_cloud(P=1, walks=1)
+    cloud = w.problem.manifold.cloud
+    rng = np.random.default_rng(3)
+    x = cloud[rng.choice(cloud.shape[0], nq)] + rng.uniform(-0.02, 0.02, (nq, 3))
+    xd = torch.tensor(x, device="cuda")
+    k = w.problem.manifold.k_nn
+    out = (torch.empty((nq, k), dtype=torch.int32, device="cuda"), torch.empty((nq, k), dtype=torch.float64, device="cuda"),
+           torch.empty(nq, dtype=torch.float64, device="cuda"))
+    ctx = M.Context(0)
+    for _ in range(max(1, args.reps)):
+        for name, meth in (("grid", M.KNN_GRID), ("scan", M.KNN_SCAN)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.cloud_knn(w.problem, xd, precision=M.FP32, method=meth, out=out)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            print(json.dumps({"leg": f"knn_{name}", "queries": nq, "cloud": int(cloud.shape[0]),
+                              "wall_ms": 1e3 * dt, "queries_per_s": nq / dt}), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_leg(args):
+    """One walk kernel on a small case (device buffers), --reps launches; prints
+    the walk-steps and the last launch's time.  For profiler captures."""
+    import torch
+    import paper_2606_21883_b300 as M
+    if args.leg == "knn":
+        return run_knn_leg(args)
+    if args.leg == "serving":
+        ctx = M.Context(0)
+        for r in range(max(1, args.reps)):
+            out = serving_leg(M, ctx, seed=7 + r, baseline=not args.no_baseline)
+            print(json.dumps({"leg": "serving", "seed": 7 + r, **out}), flush=True)
+        ctx.close()
+        return 0
+    ctx = M.Context(0)
+    w, kw = _leg_case(M, args.leg, args.points, args.walks, args.max_steps)
+    P, N = len(w.points), args.walks
+    pts = torch.tensor(w.points, dtype=torch.float64, device="cuda")
+    S = torch.empty((P, N), dtype=torch.float64, device="cuda")
+    K = torch.empty((P, N), dtype=torch.int32, device="cuda")
+    F = torch.empty((P, N), dtype=torch.int32, device="cuda")
+    dt = 0.0
+    for _ in range(max(1, args.reps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.walk_scores_device(w.problem, w.params, pts, N, M.FP32, S, K, F, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    steps = int(K.sum().item())
+    print(json.dumps({"leg": args.leg, "points": P, "walks": N, "max_steps": args.max_steps, "walk_steps": steps,
+                      "last_launch_ms": 1e3 * dt, "walk_steps_per_s": steps / dt}), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -352,9 +734,18 @@ def main():
     ap.add_argument("--walks", type=int, default=10_000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true", help="serving leg without the FP64 one-at-a-time baseline")
+    ap.add_argument("--leg", default=None, help="run one kernel case (torus, s999_full, s999_red, s20_tc, s20_cuda, "
+                                                 "s20_red, dumbbell, cloud, e1_comp, knn) and exit")
+    ap.add_argument("--max-steps", type=int, default=0)
+    ap.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg:
+        if args.points == 4096:
+            args.points = 0
+        return run_leg(args)
 
     import torch
     import paper_2606_21883_b300 as M
@@ -368,19 +759,30 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    # weak scaling: every rank solves its own 4096-point batch (seed = rank)
-    w = rank_workload(args.points, args.walks, rank)
+    # one request (the torus batch, seed 0) on every rank; N = 1: its 10^4 walks per
+    # point on one GPU (mpwos_solve); N > 1: 10,240 walks per point and rank, the
+    # request's walk range split at estimator blocks, merged on the host
+    w = W.torus_closed(P=args.points, walks=1)
     ctx = M.Context(local)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
     ctx.set_autotune(True)                  # the first warm-up solve picks the walk kernel's block size
-    P, N = args.points, args.walks
+    P = args.points
+    N_total = args.walks if world == 1 else M.EST_BLOCK * ((args.walks + M.EST_BLOCK - 1) // M.EST_BLOCK) * world
+    i0, i1 = rank_walk_range(N_total, rank, world)
+    N = i1 - i0
     pts_dev = torch.tensor(w.points, dtype=torch.float64, device="cuda")
     outs = tuple(torch.zeros(P, dtype=torch.float64, device="cuda") for _ in range(3))
+    part = torch.zeros((P, M.n_blocks(N), M.EST_FIELDS), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    merged = {}
 
     def step():
-        return ctx.solve(w.problem, w.params, pts_dev, N, precision=M.FP32, out=outs)
+        if world == 1:
+            return ctx.solve(w.problem, w.params, pts_dev, N, precision=M.FP32, out=outs)
+        ctx.solve_partial(w.problem, w.params, pts_dev, N_total, i0, i1, precision=M.FP32, out=part)
+        parts = gather_partials(dist, part, world)           # the one exchange: every rank's block records
+        merged["r"] = M.merge_partials(parts)                  # same bits as one GPU running all N_total walks
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -402,8 +804,11 @@ def main():
     torch.cuda.synchronize()
     launches = ctx.launch_count() - launches0
     t_dev = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / 1e3
-    mean = outs[0].cpu().numpy()
-    msteps = outs[2].cpu().numpy()
+    if world == 1:
+        mean = outs[0].cpu().numpy()
+        msteps = outs[2].cpu().numpy()
+    else:
+        mean, _, msteps, _ = merged["r"]
 
     # the walk kernel alone (device-resident per-walk outputs): its launch duration
     S_dev = torch.empty(P * N, dtype=torch.float64, device="cuda")
@@ -423,52 +828,65 @@ def main():
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     pts_host = torch.tensor(w.points, dtype=torch.float64).pin_memory()
     host_out = tuple(torch.zeros(P, dtype=torch.float64).pin_memory() for _ in range(3))
+    host_part = torch.zeros((P, M.n_blocks(N), M.EST_FIELDS), dtype=torch.float64).pin_memory()
     e2e_t = []
     for s in range(max(2, min(args.steps, 3))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx.solve(w.problem, w.params, pts_host, N, precision=M.FP32, out=host_out)
+        if world == 1:
+            ctx.solve(w.problem, w.params, pts_host, N, precision=M.FP32, out=host_out)
+        else:
+            ctx.solve_partial(w.problem, w.params, pts_host, N_total, i0, i1, precision=M.FP32, out=host_part)
+            M.merge_partials(gather_partials(dist, host_part.cuda(), world))
         e2e_t.append(time.perf_counter() - t0)
     clocks = sampler.stop()
     tuned = ctx.autotune_entries()
     ctx.set_autotune(False)                 # the serving and secondary legs launch the default shapes
 
-    steps_per_solve = float(msteps.sum() * N)
+    steps_rank = float(np.sum(msteps) * N) if world == 1 else float(np.sum(msteps) * N_total) / world
     tmax, e2e_mean = max_over_ranks(dist, "cuda", t_dev, float(np.mean(e2e_t)))
-    value = aggregate_rate(steps_per_solve, args.steps, world, tmax)
+    value = aggregate_rate(steps_rank, args.steps, world, tmax)
     rmse = float(np.sqrt(np.mean((mean - w.exact) ** 2)))
 
     if rank == 0:
         peaks, src = _peaks()
         sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-        peak_ops = 148 * 4 * 32 * sm_mhz * 1e6          # lane-ops/s: one warp instruction per SMSP per clock
-        achieved = OPS_PER_STEP * steps_per_solve / t_kernel
+        sm = device_sm_count()
+        peak_ops = issue_peak(sm, sm_mhz)
+        achieved = OPS_PER_STEP * P * N * 525 / t_kernel
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "torus_closed R=1 a=0.4 sigma=2 u=sin(th)cos(2ph)", "points": P,
-                       "walks_per_point": N, "steps_per_walk": 525, "walk_steps_per_step": steps_per_solve,
-                       "precision": "FP32 walk; per-walk weight and score in float pairs (~2^-46); per-point FP64 Kahan sums", "parallelism": f"dp{world} (points)",
+                       "walks_per_point": N_total, "walks_per_point_per_gpu": N, "steps_per_walk": 525,
+                       "walk_steps_per_step": steps_rank * world,
+                       "precision": "FP32 walk; per-walk weight and score in float pairs (~2^-46 relative per "
+                                    "operation, below FP64's 2^-53); per-point FP64 estimator sums",
+                       "parallelism": "dp1" if world == 1 else
+                                      f"dp{world} (one request split by walk range; block records all-gathered, "
+                                      "merged on the host)",
                        "l2": "flushed between timed steps (256 MB write)", "rmse": rmse,
-                       "query_pts_per_s": P * args.steps * world / tmax},
+                       "query_pts_per_s": P * args.steps / tmax},
             "rmse": rmse,
-            "query_pts_per_s": P * args.steps * world / tmax,
-            "e2e": {"value": steps_per_solve * world / e2e_mean, "unit": UNIT,
-                    "h2d_bytes_per_step": int(P * 3 * 8), "d2h_bytes_per_step": int(3 * P * 8)},
+            "query_pts_per_s": P * args.steps / tmax,
+            "e2e": {"value": steps_rank * world / e2e_mean, "unit": UNIT,
+                    "h2d_bytes_per_step": int(P * 3 * 8),
+                    "d2h_bytes_per_step": int(3 * P * 8) if world == 1 else int(host_part.numel() * 8)},
             "gpu_launches": int(launches),
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                          "frac": achieved / peak_ops, "traffic": TRAFFIC_BYTES, "traffic_unit": "bytes per launch",
                          "traffic_source": "profiles/walk3_f32_torus_bench_traffic.md",
                          "kernel": "walk3_f32_kernel<torus>", "kernel_ms": 1e3 * t_kernel,
                          "ops_per_walk_step": OPS_PER_STEP,
-                         "peak_source": f"148 SM x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz ({src} max clock)"},
+                         "peak_source": f"{sm} SM (device attribute) x 4 SMSP x 32 lanes x {sm_mhz:.0f} MHz "
+                                        f"({src} max SM clock): one warp instruction per SM sub-partition per clock"},
             "clocks": clocks,
             "autotune": tuned,
         }
         if not args.no_serving and world == 1:
             line["serving"] = serving_leg(M, ctx)
-            line["secondary"] = secondary_leg(M, ctx)
+            line["secondary"] = secondary_leg(M, ctx, sm, sm_mhz, src)
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline()
         print(json.dumps(line), flush=True)

@@ -259,6 +259,20 @@ int mpwos_solve_partial(mpwos_ctx* ctx, const mpwos_manifold* m, const mpwos_pro
 int mpwos_block_partials_host(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
                               double* part);
 
+/* The least-squares step of the coarse predictor u_* of the compensation term
+ * (Sec. 2.3.3): given estimates u at P points of a torus of centre-circle radius
+ * R (pts: P x 3 host), the torus Fourier series sum_t c_t T_t(m theta) P_t(q phi)
+ * with T, P in {cos, sin} (no sin of a zero multiple), m <= max_m, q <= max_q,
+ * nearest to u in least squares (Householder QR, FP64); theta = atan2(x_3,
+ * |(x_1, x_2)| - R), phi = atan2(x_2, x_1).  The estimates come from a
+ * baseline solve (comp = NONE) at points of Omega.  Outputs (host): coef and
+ * modes (4 per term: m, q, theta trig, phi trig; trig 0 = cos, 1 = sin), in the
+ * TORUS_FOURIER layout of u_star, and their number n_terms (at most 64).
+ * Returns MPWOS_EINVAL for a basis of more than 64 terms, P smaller than the
+ * basis, or a rank-deficient fit.  Needs no GPU and no context. */
+int mpwos_fit_torus_series(const double* pts, const double* u, int64_t P, double R, int max_m, int max_q,
+                           double* coef, int* modes, int* n_terms);
+
 /* Merge block records on the host: parts[r] (host, P x nblk[r] x 5 doubles)
  * for consecutive walk ranges r = 0 .. nparts-1 of one request, merged per
  * point in range order and block order.  Outputs (P each, host): the mean of
@@ -306,8 +320,11 @@ int64_t mpwos_noalloc_max_walks(void);
  * (target 0: exactly `walk_budget` walks, as mpwos_solve).  Requests are
  * admitted while a stream slot and serving memory are free (16 slots and a
  * quarter of the free device memory by default), run concurrently on their
- * own streams in bounded chunks, and are advanced by a scheduler thread of the
- * context.  A walk's draws depend only on (seed, point, walk index), so a
+ * own streams, and are advanced by a scheduler thread of the context.  A
+ * round's walks go out in chunks of about 10 ms of GPU time each (the walk
+ * cost measured on the request's previous chunks, at its share of the grid;
+ * at most chunk_walks walks), two in flight per request, so that a newly
+ * admitted request waits at most about one chunk for the SMs.  A walk's draws depend only on (seed, point, walk index), so a
  * request's results do not depend on the other requests in flight; with
  * target 0 they equal mpwos_solve's bit for bit.  Point clouds: the search
  * grid is built at submit. */

@@ -113,6 +113,8 @@ def lib() -> C.CDLL:
         L.mpwos_block_partials_host.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p]
         L.mpwos_merge_partials.argtypes = [C.POINTER(C.c_void_p), C.c_void_p, C.c_int, C.c_int64, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
+        L.mpwos_fit_torus_series.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_double, C.c_int, C.c_int,
+                                             C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -153,6 +155,24 @@ def merge_partials(parts):
     if rc not in (MPWOS_OK, MPWOS_EMAXSTEPS):
         raise MpwosError(rc, "mpwos_merge_partials")
     return mean, se, ms, int(nf.value)
+
+
+def fit_torus_series(pts, u, R: float, max_m: int = 3, max_q: int = 3):
+    """mpwos_fit_torus_series: the least-squares torus Fourier series (modes m <=
+    max_m, q <= max_q) through estimates u at points pts (P x 3) of a torus of
+    centre-circle radius R, as a u_star closed form; no GPU."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    coef = np.zeros(64)
+    modes = np.zeros((64, 4), dtype=np.int32)
+    nt = C.c_int(0)
+    rc = lib().mpwos_fit_torus_series(_ptr(pts), _ptr(u), int(len(u)), float(R), int(max_m), int(max_q),
+                                      _ptr(coef), _ptr(modes), C.byref(nt))
+    if rc != MPWOS_OK:
+        raise MpwosError(rc, "mpwos_fit_torus_series")
+    from . import workloads as W
+    n = nt.value
+    return W.Func.torus([(float(coef[t]), *map(int, modes[t])) for t in range(n)], apply_op=False)
 
 
 def _ptr(x):
@@ -244,6 +264,7 @@ class Context:
         if rc != MPWOS_OK:
             raise MpwosError(rc, f"mpwos_create(device={device}) failed")
         self.h = h
+        self.device = device
         self._manifolds = {}   # id(manifold) -> (manifold, signature, handle)
 
     def close(self):
@@ -373,6 +394,19 @@ class Context:
                                         int(i0), int(i1), _ptr(out))
         self._check(rc)
         return out
+
+    def fit_torus_predictor(self, problem, params, P=400, walks=2000, max_m=3, max_q=3, seed=12345,
+                            precision=FP32):
+        """u_* of Sec. 2.3.3 for a torus problem: the baseline solve (m_* = 0) at P
+        points of Omega, then mpwos_fit_torus_series through its estimates."""
+        from . import workloads as W
+        if problem.manifold.kind != W.MANIFOLD_TORUS:
+            raise ValueError("fit_torus_predictor needs a torus problem")
+        base = W.Problem(problem.manifold, problem.sigma, problem.closed, problem.f, problem.g,
+                         problem.bnd_normal, problem.bnd_offset)
+        pts = W.torus_domain_points(problem, P, seed)
+        u = self.solve(base, params, pts, walks, precision=precision)[0]
+        return fit_torus_series(pts, u, problem.manifold.R, max_m, max_q)
 
     def walk_scores(self, problem, params, pts, N, precision=FP64, projection=PROJ_AUTO):
         """mpwos_walk_scores: per-walk S (P x N), K, flags."""

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -942,50 +943,58 @@ int run_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64) { return run_walks_on(c
 // block size (a multiple of 32 within the kernel's limit; the tensor-core walk
 // keeps its own); the grid is then the SM count times the resident blocks of
 // that size.
+// The launch shape launch_walks uses for pb: block size, walkers per block and
+// grid (before the grid is capped to the walks at hand).
+struct LaunchShape {
+  int block = 0;
+  int64_t per_block = 0, grid = 0;
+};
+
+LaunchShape launch_shape(mpwos_ctx* ctx, const DevProblem& pb, bool fp64, int64_t max_grid, int block_req) {
+  LaunchShape sh;
+  if (pb.reduced) {
+    sh.block = block_req > 0 ? block_req : 128;
+    sh.per_block = sh.block;
+    sh.grid = static_cast<int64_t>(ctx->sm_count) * occupancy_walkr(pb, fp64, sh.block);
+    if (max_grid < 0) sh.grid = std::max<int64_t>(ctx->sm_count, sh.grid / (-max_grid));
+  } else if (pb.tc_bimg && !fp64) {
+    // one persistent CTA per SM (or a share of them), 128 walkers per tile
+    sh.block = 512;
+    sh.per_block = 128;
+    sh.grid = ctx->sm_count;
+    if (max_grid < 0) sh.grid = std::max<int64_t>(1, sh.grid / (-max_grid));
+  } else {
+    const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
+    sh.block = block_req > 0 ? block_req
+                             : (n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256)
+                                   : (fp64 ? 128 : walkn32_max_block(pb)));
+    const int occ = fp64 ? occupancy_walk_f64(pb, n3, sh.block) : occupancy_walk_f32(pb, n3, sh.block);
+    sh.per_block = n3 ? sh.block : sh.block / (fp64 ? 32 : walkn32_lanes_per_walker(pb));
+    sh.grid = static_cast<int64_t>(ctx->sm_count) * occ;
+    if (max_grid < 0) sh.grid = std::max<int64_t>(ctx->sm_count, sh.grid / (-max_grid));
+  }
+  if (max_grid > 0 && sh.grid > max_grid) sh.grid = max_grid;
+  return sh;
+}
+
 int launch_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int64_t max_grid, int block_req) {
   if (pb.wk_w1 <= pb.wk_w0) return MPWOS_OK;
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tabc)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
   if (pb.wk_next) CK(cudaMemsetAsync(pb.wk_next, 0, sizeof(unsigned long long), st));
-  if (pb.reduced) {
-    const int blk = block_req > 0 ? block_req : 128;
-    int64_t grid = static_cast<int64_t>(ctx->sm_count) * occupancy_walkr(pb, fp64, blk);
-    const int64_t need = (pb.wk_w1 - pb.wk_w0 + blk - 1) / blk;
-    if (max_grid < 0) grid = std::max<int64_t>(ctx->sm_count, grid / (-max_grid));
-    if (max_grid > 0 && grid > max_grid) grid = max_grid;
-    if (grid > need) grid = need;
-    const cudaError_t e = fp64 ? launch_walkr_f64(pb, static_cast<int>(grid), blk, st)
-                               : launch_walkr_f32(pb, static_cast<int>(grid), blk, st);
-    if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "reduced walk launch: %s", cudaGetErrorString(e));
-    ctx->launches++;
-    return MPWOS_OK;
-  }
-  if (pb.tc_bimg && !fp64) {
-    // one persistent CTA per SM (or a share of them), 128 walkers per tile
-    const int64_t tiles = (pb.wk_w1 - pb.wk_w0 + 127) / 128;
-    int64_t grid = ctx->sm_count;
-    if (max_grid < 0) grid = std::max<int64_t>(1, grid / (-max_grid));
-    if (max_grid > 0 && grid > max_grid) grid = max_grid;
-    if (grid > tiles) grid = tiles;
-    const cudaError_t e = launch_embed_tc(pb, static_cast<int>(grid), st);
-    if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "tensor-core walk launch: %s", cudaGetErrorString(e));
-    ctx->launches++;
-    return MPWOS_OK;
-  }
-  const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
-  const int block = block_req > 0 ? block_req
-                                  : (n3 ? ((fp64 || pb.mkind == kPointCloud) ? 128 : 256)
-                                        : (fp64 ? 128 : walkn32_max_block(pb)));
-  const int occ = fp64 ? occupancy_walk_f64(pb, n3, block) : occupancy_walk_f32(pb, n3, block);
-  const int64_t per_block = n3 ? block : block / (fp64 ? 32 : walkn32_lanes_per_walker(pb));
-  int64_t grid = static_cast<int64_t>(ctx->sm_count) * occ;
-  const int64_t need = (pb.wk_w1 - pb.wk_w0 + per_block - 1) / per_block;
-  if (max_grid < 0) grid = std::max<int64_t>(ctx->sm_count, grid / (-max_grid));
-  if (max_grid > 0 && grid > max_grid) grid = max_grid;
-  if (grid > need) grid = need;
+  const LaunchShape sh = launch_shape(ctx, pb, fp64, max_grid, block_req);
+  const int64_t need = (pb.wk_w1 - pb.wk_w0 + sh.per_block - 1) / sh.per_block;
+  const int grid = static_cast<int>(std::min(sh.grid, need));
   cudaError_t e;
-  if (n3) e = fp64 ? launch_walk3_f64(pb, (int)grid, block, st) : launch_walk3_f32(pb, (int)grid, block, st);
-  else e = fp64 ? launch_walkn_f64(pb, (int)grid, block, st) : launch_walkn_f32(pb, (int)grid, block, st);
+  if (pb.reduced) {
+    e = fp64 ? launch_walkr_f64(pb, grid, sh.block, st) : launch_walkr_f32(pb, grid, sh.block, st);
+  } else if (pb.tc_bimg && !fp64) {
+    e = launch_embed_tc(pb, grid, st);
+  } else {
+    const bool n3 = pb.n == 3 && pb.mkind != kEmbeddedSphere;
+    if (n3) e = fp64 ? launch_walk3_f64(pb, grid, sh.block, st) : launch_walk3_f32(pb, grid, sh.block, st);
+    else e = fp64 ? launch_walkn_f64(pb, grid, sh.block, st) : launch_walkn_f32(pb, grid, sh.block, st);
+  }
   if (e != cudaSuccess) return fail(ctx, MPWOS_ECUDA, "walk launch: %s", cudaGetErrorString(e));
   ctx->launches++;
   return MPWOS_OK;
@@ -1449,6 +1458,62 @@ int mpwos_solve_partial(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_pr
   return MPWOS_OK;
 }
 
+int mpwos_fit_torus_series(const double* pts, const double* u, int64_t P, double R, int max_m, int max_q,
+                           double* coef, int* modes, int* n_terms) {
+  if (!pts || !u || !coef || !modes || !n_terms || max_m < 0 || max_q < 0 || !(R > 0.0)) return MPWOS_EINVAL;
+  // the basis T(m theta) P(q phi), T, P in {cos, sin}, without sin(0 .), m outer, q inner
+  std::vector<std::array<int, 4>> basis;
+  for (int m = 0; m <= max_m; ++m)
+    for (int tk = 0; tk < (m == 0 ? 1 : 2); ++tk)
+      for (int q = 0; q <= max_q; ++q)
+        for (int pk = 0; pk < (q == 0 ? 1 : 2); ++pk) basis.push_back({m, q, tk, pk});
+  const int nb = static_cast<int>(basis.size());
+  if (nb > kMaxPredTerms || P < nb) return MPWOS_EINVAL;
+  // A (P x nb, column-major) at the points' angles: phi the azimuth, theta the
+  // angle in the tube's meridian plane (the parametrisation of Example 1)
+  std::vector<double> A(static_cast<size_t>(P) * nb), b(u, u + P);
+  for (int64_t i = 0; i < P; ++i) {
+    const double x = pts[3 * i], y = pts[3 * i + 1], z = pts[3 * i + 2];
+    const double ph = std::atan2(y, x), th = std::atan2(z, std::hypot(x, y) - R);
+    for (int c = 0; c < nb; ++c) {
+      const auto& bs = basis[c];
+      const double tv = bs[2] ? std::sin(bs[0] * th) : std::cos(bs[0] * th);
+      const double pv = bs[3] ? std::sin(bs[1] * ph) : std::cos(bs[1] * ph);
+      A[static_cast<size_t>(c) * P + i] = tv * pv;
+    }
+  }
+  // least squares by Householder QR: A = QR, then R c = (Q^T b)[0 .. nb)
+  for (int k = 0; k < nb; ++k) {
+    double* ak = A.data() + static_cast<size_t>(k) * P;
+    double nrm = 0.0;
+    for (int64_t i = k; i < P; ++i) nrm += ak[i] * ak[i];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0)) return MPWOS_EINVAL;   // rank deficient: too few distinct points
+    const double alpha = ak[k] > 0.0 ? -nrm : nrm;
+    std::vector<double> v(ak + k, ak + P);
+    v[0] -= alpha;
+    double vv = 0.0;
+    for (double t : v) vv += t * t;
+    auto reflect = [&](double* col) {
+      double d = 0.0;
+      for (int64_t i = k; i < P; ++i) d += v[i - k] * col[i];
+      const double f = 2.0 * d / vv;
+      for (int64_t i = k; i < P; ++i) col[i] -= f * v[i - k];
+    };
+    for (int c = k; c < nb; ++c) reflect(A.data() + static_cast<size_t>(c) * P);
+    reflect(b.data());
+  }
+  for (int k = nb - 1; k >= 0; --k) {
+    double t = b[k];
+    for (int c = k + 1; c < nb; ++c) t -= A[static_cast<size_t>(c) * P + k] * coef[c];
+    coef[k] = t / A[static_cast<size_t>(k) * P + k];
+  }
+  for (int c = 0; c < nb; ++c)
+    for (int j = 0; j < 4; ++j) modes[4 * c + j] = basis[c][j];
+  *n_terms = nb;
+  return MPWOS_OK;
+}
+
 int mpwos_block_partials_host(const double* S, const int32_t* K, const int32_t* flags, int64_t P, int64_t N,
                               double* part) {
   if (P < 0 || N < 0 || ((!S || !K || !flags || !part) && P > 0 && N > 0)) return MPWOS_EINVAL;
@@ -1869,6 +1934,15 @@ struct Request {
   int64_t cur = 0;
   bool cancel = false;
   std::chrono::steady_clock::time_point t_submit, t_done;
+  // the round in flight: its walks go out in time-sized chunks, at most two
+  // outstanding; the chunk events time them (walk cost per grid block)
+  int64_t round_total = 0, round_issued = 0, round_i1 = 0;
+  int inflight = 0;
+  bool reducing = false;
+  cudaEvent_t cev[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  int64_t cwalks[2] = {0, 0}, cgrid[2] = {0, 0};
+  int chead = 0;
+  double block_ns_per_walk = 0.0;   // measured GPU ns per walk times the launch's blocks (0: unknown)
 };
 
 }  // namespace
@@ -1880,7 +1954,8 @@ struct ServeEngine {
   std::vector<bool> slot_busy;
   int max_active = 16;
   size_t mem_budget = 0, mem_used = 0;
-  int64_t chunk_walks = int64_t(1) << 20;
+  int64_t chunk_walks = int64_t(1) << 20;   // cap of a chunk
+  double chunk_target_ms = 10.0;              // a chunk's aimed GPU time
   uint64_t next_id = 1;
   bool stop = false;
   std::condition_variable_any cv;
@@ -1909,6 +1984,58 @@ void req_finish(mpwos_ctx* ctx, Request& r, int state, int status, const std::st
   E.mem_used -= std::min(E.mem_used, r.bytes);
 }
 
+// Launch the next chunk of the round in flight (at most two outstanding).  A
+// chunk aims at chunk_target_ms of GPU time at its launch's share of the grid
+// (all requests in flight split the SMs); the first chunk of a request, with
+// no measurement yet, is one resident wave of walkers.
+int req_issue(mpwos_ctx* ctx, Request& r) {
+  ServeEngine& E = *ctx->serve;
+  const cudaStream_t st = E.streams[r.slot];
+  const bool fp64 = r.prm.precision == MPWOS_FP64;
+  int running = 0;
+  for (auto& kv : E.reqs) running += kv.second->state == 1;
+  const int64_t max_grid = running > 1 ? -static_cast<int64_t>(running) : 0;
+  const int block = tuned_block(ctx, r.pb, fp64);
+  const LaunchShape sh = launch_shape(ctx, r.pb, fp64, max_grid, block);
+  const int64_t grid = sh.grid;
+  int64_t n = std::max<int64_t>(1, grid * sh.per_block);
+  if (r.block_ns_per_walk > 0.0)
+    n = static_cast<int64_t>(E.chunk_target_ms * 1e6 * static_cast<double>(grid) / r.block_ns_per_walk);
+  n = std::max<int64_t>(n, 1);
+  n = std::min<int64_t>(n, E.chunk_walks);
+  n = std::min<int64_t>(n, r.round_total - r.round_issued);
+  const int c = (r.chead + r.inflight) & 1;
+  r.pb.wk_w0 = r.round_issued;
+  r.pb.wk_w1 = r.round_issued + n;
+  CK(cudaEventRecord(r.cev[c][0], st));
+  int rc = launch_walks(ctx, r.pb, fp64, st, max_grid, block);
+  if (rc) return rc;
+  CK(cudaEventRecord(r.cev[c][1], st));
+  r.cwalks[c] = n;
+  r.cgrid[c] = grid;
+  r.round_issued += n;
+  r.inflight++;
+  return MPWOS_OK;
+}
+
+// After the round's last chunk: the per-point reduction and its copies to the host.
+int req_reduce(mpwos_ctx* ctx, Request& r) {
+  ServeEngine& E = *ctx->serve;
+  const cudaStream_t st = E.streams[r.slot];
+  CK(cudaMemsetAsync(r.nflag, 0, sizeof(unsigned long long), st));
+  CK(launch_reduce_strided(r.S, r.K, r.F, r.P, 0, r.budget, r.nper, r.mean, r.se, r.ms, r.nflag, st));
+  ctx->launches++;
+  CK(cudaMemcpyAsync(r.h_mean, r.mean, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(r.h_se, r.se, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(r.h_ms, r.ms, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(r.h_flag, r.nflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  if (r.pb.dev_status) CK(cudaMemcpyAsync(r.h_flag + 1, r.pb.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaEventRecord(r.ev, st));
+  r.reducing = true;
+  r.cur = r.round_i1;
+  return MPWOS_OK;
+}
+
 int req_round(mpwos_ctx* ctx, Request& r, int64_t i1) {
   ServeEngine& E = *ctx->serve;
   const cudaStream_t st = E.streams[r.slot];
@@ -1924,28 +2051,29 @@ int req_round(mpwos_ctx* ctx, Request& r, int64_t i1) {
   r.pb.wk_i0 = i0;
   r.pb.wk_i1 = i1;
   r.pb.out_stride = r.budget;
-  const int64_t total = r.pb.wk_np * (i1 - i0);
-  // requests in flight share the SMs: each launch takes a 1/running share of a full grid
-  int running = 0;
-  for (auto& kv : E.reqs) running += kv.second->state == 1;
-  const int64_t max_grid = running > 1 ? -static_cast<int64_t>(running) : 0;
-  for (int64_t w0 = 0; w0 < total; w0 += E.chunk_walks) {
-    r.pb.wk_w0 = w0;
-    r.pb.wk_w1 = std::min(total, w0 + E.chunk_walks);
-    const bool fp64 = r.prm.precision == MPWOS_FP64;
-    int rc = launch_walks(ctx, r.pb, fp64, st, max_grid, tuned_block(ctx, r.pb, fp64));
-    if (rc) return rc;
+  r.round_total = r.pb.wk_np * (i1 - i0);
+  r.round_issued = 0;
+  r.round_i1 = i1;
+  r.reducing = false;
+  int rc = req_issue(ctx, r);
+  if (!rc && r.round_issued < r.round_total) rc = req_issue(ctx, r);
+  return rc;
+}
+
+// A chunk of the round in flight has finished: update the walk cost, keep two
+// chunks outstanding, and reduce after the last.
+int req_chunk_done(mpwos_ctx* ctx, Request& r) {
+  const int c = r.chead;
+  float ms = 0.0f;
+  if (cudaEventElapsedTime(&ms, r.cev[c][0], r.cev[c][1]) == cudaSuccess && r.cwalks[c] > 0) {
+    const double cost = 1e6 * static_cast<double>(ms) * static_cast<double>(r.cgrid[c]) / static_cast<double>(r.cwalks[c]);
+    r.block_ns_per_walk = r.block_ns_per_walk > 0.0 ? 0.5 * (r.block_ns_per_walk + cost) : cost;
   }
-  CK(cudaMemsetAsync(r.nflag, 0, sizeof(unsigned long long), st));
-  CK(launch_reduce_strided(r.S, r.K, r.F, r.P, 0, r.budget, r.nper, r.mean, r.se, r.ms, r.nflag, st));
-  ctx->launches++;
-  CK(cudaMemcpyAsync(r.h_mean, r.mean, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(r.h_se, r.se, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(r.h_ms, r.ms, sizeof(double) * r.P, cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(r.h_flag, r.nflag, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
-  if (r.pb.dev_status) CK(cudaMemcpyAsync(r.h_flag + 1, r.pb.dev_status, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-  CK(cudaEventRecord(r.ev, st));
-  r.cur = i1;
+  cudaGetLastError();
+  r.chead ^= 1;
+  r.inflight--;
+  if (!r.cancel && r.round_issued < r.round_total) return req_issue(ctx, r);
+  if (r.inflight == 0) return req_reduce(ctx, r);   // a canceled request stops here
   return MPWOS_OK;
 }
 
@@ -1974,6 +2102,9 @@ int req_start(mpwos_ctx* ctx, Request& r) {
   r.active.resize(r.P);
   for (int64_t p = 0; p < r.P; ++p) { r.active[p] = static_cast<int>(p); r.h_n[p] = 0; }
   r.cur = 0;
+  for (auto& pair : r.cev)
+    for (auto& e : pair)
+      if (!e) CK(cudaEventCreate(&e));
   const int64_t n0 = r.target > 0.0 ? std::min(r.budget, kFirstRoundWalks) : r.budget;
   return req_round(ctx, r, n0);
 }
@@ -2035,6 +2166,20 @@ void serve_loop(mpwos_ctx* ctx) {
     for (auto& kv : E.reqs) {
       Request& r = *kv.second;
       if (r.state != 1) continue;
+      if (!r.reducing) {
+        // chunks finish in order on the request's stream
+        while (r.state == 1 && !r.reducing && r.inflight > 0) {
+          const cudaError_t q = cudaEventQuery(r.cev[r.chead][1]);
+          if (q == cudaErrorNotReady) break;
+          if (q != cudaSuccess) {
+            req_finish(ctx, r, 3, MPWOS_ECUDA, cudaGetErrorString(q));
+            break;
+          }
+          const int rc = req_chunk_done(ctx, r);
+          if (rc) req_finish(ctx, r, 3, rc, ctx->err);
+        }
+        continue;
+      }
       const cudaError_t q = cudaEventQuery(r.ev);
       if (q == cudaSuccess) req_advance(ctx, r);
       else if (q != cudaErrorNotReady) req_finish(ctx, r, 3, MPWOS_ECUDA, cudaGetErrorString(q));
@@ -2082,6 +2227,9 @@ void req_release(mpwos_ctx* ctx, uint64_t id) {
   cudaFreeHost(r->h_act);
   cudaFreeHost(r->h_flag);
   if (r->ev) cudaEventDestroy(r->ev);
+  for (auto& pair : r->cev)
+    for (auto& e : pair)
+      if (e) cudaEventDestroy(e);
   ctx->serve->reqs.erase(id);
 }
 

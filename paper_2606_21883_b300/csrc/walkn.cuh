@@ -1,20 +1,20 @@
-// walkn.cuh — the MPWoS walk in R^n (n up to 1024), one warp per walker.
+// walkn.cuh — the FP64 MPWoS walk in R^n (n up to 1024), one warp per walker,
+// and the precision-generic pieces (WalkAcc, the source evaluators) that the
+// FP32 walks in walkn32s.cuh and walkn32.cuh reuse.
 //
 // Layout: the walker's n-vectors live in registers, distributed over the 32
-// lanes in Philox-block order: block b (G consecutive components G b .. G b +
-// G - 1; G = 4 in FP32, 2 in FP64) belongs to lane b mod 32, register slot
-// b / 32.  A lane therefore generates exactly the Gaussians of the components
-// it owns, and every norm or dot product is a per-lane partial sum followed by
-// a butterfly shuffle reduction.  The embedded sphere Q S^d + b is walked in
-// its intrinsic coordinate s (lane j holds s_j, j <= d): cp(Y + v) = Q
-// normalize(s + Q^T v) + b, so only Q^T g of each Gaussian vector is needed;
-// Q^T is stored transposed (D x n) so that a lane's 16-byte slice of a row is
-// one coalesced load.
+// lanes in Philox-block order: block b (components 2b, 2b + 1) belongs to lane
+// b mod 32, register slot b / 32.  A lane therefore generates exactly the
+// Gaussians of the components it owns, and every norm or dot product is a
+// per-lane partial sum followed by a butterfly shuffle reduction.  The
+// embedded sphere Q S^d + b is walked in its intrinsic coordinate s (lane j
+// holds s_j, j <= d): cp(Y + v) = Q normalize(s + Q^T v) + b, so only Q^T g of
+// each Gaussian vector is needed; Q^T is stored transposed (D x n) so that a
+// lane's 16-byte slice of a row is one coalesced load.
 //
-// Draws of step k of walk (p, i), Philox counter (j, k, i, p), nb = ceil(n/G):
+// Draws of step k of walk (p, i), Philox counter (j, k, i, p), nb = ceil(n/2):
 //   Theta direction: blocks [0, nb);  Z_l direction: blocks [nb(1+l), nb(2+l));
-//   FP64: U_l = u53(x, y) of block nb(1+N_V) + l  (identical to the CPU oracle);
-//   FP32: U_l = u23(word l mod 4) of block nb(1+N_V) + l/4.
+//   U_l = u53(x, y) of block nb(1+N_V) + l  (identical to the CPU oracle).
 // The hypersurface of revolution (revolution.cuh) keeps Y in the ambient layout;
 // its closest point needs |Yh|^2 and Y_{n-1} (one reduction), then the same
 // Newton iteration in every lane.

@@ -207,6 +207,21 @@ def torus_points(theta: np.ndarray, phi: np.ndarray, R: float, a: float) -> np.n
     return np.stack([rr * np.cos(phi), rr * np.sin(phi), a * np.sin(theta)], axis=1)
 
 
+def torus_domain_points(problem: "Problem", P: int, seed: int = 12345) -> np.ndarray:
+    """P points of a torus problem's Omega, (theta, phi) uniform, rejecting e.x <= h
+    on a boundary problem (P x 3)."""
+    man = problem.manifold
+    g = _rng(seed)
+    out, have = [], 0
+    while have < P:
+        x = torus_points(g.uniform(0.0, 2 * math.pi, 4 * P), g.uniform(0.0, 2 * math.pi, 4 * P), man.R, man.a)
+        if not problem.closed:
+            x = x[x @ problem.bnd_normal > problem.bnd_offset]
+        out.append(x)
+        have += len(x)
+    return np.concatenate(out)[:P]
+
+
 def embedding(n: int, d: int, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Seeded orthonormal Q (n x (d+1), from a Gaussian QR, sign-fixed) and shift b ~ N(0, I)."""
     g = _rng(seed)

@@ -125,10 +125,8 @@ def test_e1_coarse_fitted_predictor(ctx):
     (measured: RMSE 0.017 against the baseline's 0.049 at 10^5 walks; 0.0136 with the exact u):
     the expansion uses differences of R_* in s only, where the predictor's own residual on M
     cancels."""
-    from paper_2606_21883_b300 import predictor as PR
     base = W.torus_cut(P=100, walks=1)
-    solve = lambda pr, pa, pts, N: ctx.solve(pr, pa, pts, N, precision=M.FP32)[0]
-    u_star = PR.fit_torus_predictor(solve, base.problem, base.params, P=400, walks=2000)
+    u_star = ctx.fit_torus_predictor(base.problem, base.params, P=400, walks=2000)
     w = W.torus_cut(P=100, walks=1, comp=W.COMP_NORMAL2, u_star=u_star)
     m0 = ctx.solve(base.problem, base.params, base.points, 100000, precision=M.FP32)[0]
     m2 = ctx.solve(w.problem, w.params, w.points, 100000, precision=M.FP32)[0]

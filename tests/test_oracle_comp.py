@@ -211,22 +211,3 @@ def test_compensation_reduces_e1_bias():
     assert np.sqrt(np.mean(e0 ** 2)) > 3 * np.sqrt(np.mean(e2 ** 2)) + 0.01
     assert np.sqrt(np.mean(e1 ** 2)) < 0.7 * np.sqrt(np.mean(e0 ** 2))
 
-
-def test_predictor_fit_recovers_a_series_in_its_span():
-    """The least-squares step of the coarse predictor: fed exact values of Example 1's u (a
-    series in the basis), it returns u's coefficients."""
-    from paper_2606_21883_b300 import predictor as PR
-    w = W.torus_cut(P=2, walks=1)
-    terms = W.torus_cut_terms()
-
-    def exact_solve(problem, params, pts, N):
-        th = np.arctan2(pts[:, 2], np.hypot(pts[:, 0], pts[:, 1]) - 1.0)
-        ph = np.arctan2(pts[:, 1], pts[:, 0])
-        return W.torus_series_value(terms, th, ph)
-
-    u_star = PR.fit_torus_predictor(exact_solve, w.problem, w.params, P=300)
-    assert len(u_star.coef) == 49
-    rng = np.random.default_rng(0)
-    th, ph = rng.uniform(0, 2 * math.pi, 50), rng.uniform(0, 2 * math.pi, 50)
-    got = W.torus_series_value([(c, *md) for c, md in zip(u_star.coef, u_star.modes)], th, ph)
-    assert np.allclose(got, W.torus_series_value(terms, th, ph), atol=1e-9)
