@@ -19,6 +19,7 @@ oracle on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import math
 import os
@@ -85,6 +86,18 @@ def ops_tc_embedded(n):
 # per step the radius, weights, stop test and source (~80).
 OPS_REDUCED_S999 = 2 * (40 + 23.5 + 40 + 11.75 + 17) + 80
 MUFU_PER_PAIR = 4   # log2, sqrt, sin, cos of one Box-Muller pair
+
+
+def ops_reduced_embedded(d):
+    """The dimension-reduced sampler on S^d embedded in R^1000 (walkr_kernel), per
+    direction: d + 1 intrinsic normals (ceil((d + 1) / 4) Philox blocks at 40,
+    ceil((d + 1) / 2) Box-Muller pairs at 11.75) and one chi^2 by Marsaglia-Tsang
+    (68.75); per step: the Theta and Z updates with their normalisations
+    (2 x (3 (d + 1) + 2)), the source v.z + z^T A z ((d + 1)^2 + 2 (d + 1)) and the
+    radius, weights and stop test (80)."""
+    D = d + 1
+    direction = 40 * math.ceil(D / 4) + 11.75 * math.ceil(D / 2) + 68.75
+    return 2 * direction + 2 * (3 * D + 2) + D * D + 2 * D + 80
 
 
 def _peaks():
@@ -206,10 +219,20 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
     cloud_w = W.point_cloud(P=1, walks=1)
     cloud_w.params.tau_w = 1e-4
 
+    def log(msg):
+        print(f"[serving {_t.perf_counter() - T0:8.2f} s] {msg}", file=sys.stderr, flush=True)
+
+    T0 = _t.perf_counter()
+
     def run(c, reqs, arrivals, prec):
         lat, steps, pending, q = [None] * len(reqs), [0.0] * len(reqs), {}, 0
         t0 = _t.perf_counter()
+        t_log = t0
         while q < len(reqs) or pending:
+            if _t.perf_counter() - t_log > 10.0:
+                t_log = _t.perf_counter()
+                log(f"{q} of {len(reqs)} submitted, {len(pending)} pending: "
+                    + ", ".join(f"{reqs[qq][0]}/{len(reqs[qq][1].points)}/{c.poll(rid)}" for rid, qq in pending.items()))
             now = _t.perf_counter() - t0
             while q < len(reqs) and arrivals[q] <= now:
                 kind, w, budget, target = reqs[q]
@@ -237,7 +260,9 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
     rate = 0.7 * cap_rate
     reqs = _serving_mix(rng, n_req, cloud_w)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    log(f"capacity {cap_rate:.2f} requests/s")
     lat, steps, T = run(ctx, reqs, arrivals, M.FP32)
+    log(f"stream served in {T:.1f} s")
     kinds = {k: sum(1 for r in reqs if r[0] == k) for k in ["torus", "cap", "cloud", "s999", "s20"]}
     out = {**_lat_summary(lat, by_kind(reqs, lat)), "requests": int(len(lat)), "arrival_rate_hz": rate,
            "capacity_hz": cap_rate, "walk_steps_per_s": float(steps.sum()) / T, "mix": kinds,
@@ -255,15 +280,20 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
             rid = base.submit(w.problem, w.params, w.points, budget, target, precision=M.FP32)
             base.wait(rid)
             svc32.append(base.fetch(rid, len(w.points))[4])          # submit to done, measured by the library
-            # FP64: the request's points with min(budget, 64) walks each, scaled to the
-            # walk-steps the served request ran (the FP64 walk is ~10^3 x slower on B300:
-            # the whole stream in FP64 would hold the GPU for hours)
-            nb = min(budget, 64)
-            rid = base.submit(w.problem, w.params, w.points, nb, 0.0, precision=M.FP64)
-            base.wait(rid)
-            _, _, ms, walks, lt, _ = base.fetch(rid, len(w.points))
-            s64 = float(np.sum(ms * walks))
-            svc64.append(lt * max(1.0, st / max(s64, 1.0)))
+            # FP64: the FP64 walk is ~10^3 x slower on B300 (the whole stream in FP64
+            # would hold the GPU for hours), so the request's FP64 service time is its
+            # FP32 one times the FP64 / FP32 time ratio of one sample of it: its points,
+            # min(budget, 64) walks each, at most 2048 steps per walk, in both precisions
+            smp = copy.deepcopy(w.params)
+            smp.max_steps = min(int(smp.max_steps), 2048)
+            t_smp = []
+            for prec in (M.FP32, M.FP64):
+                rid = base.submit(w.problem, smp, w.points, min(budget, 64), 0.0, precision=prec)
+                base.wait(rid)
+                t_smp.append(base.fetch(rid, len(w.points))[4])
+            svc64.append(svc32[-1] * t_smp[1] / max(t_smp[0], 1e-9))
+            log(f"one at a time: {kind} {len(w.points)} pts: FP32 {svc32[-1]:.3f} s, sample FP32 {t_smp[0]:.3f} s "
+                f"FP64 {t_smp[1]:.3f} s -> FP64 {svc64[-1]:.3f} s")
         base.close()
         l32, l64 = _fifo(arrivals, svc32), _fifo(arrivals, svc64)
         out["fp32_one_at_a_time"] = {**_lat_summary(l32, by_kind(reqs, l32)),
@@ -274,10 +304,10 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
         out["fp64_one_at_a_time"] = {**_lat_summary(l64, by_kind(reqs, l64)),
                                      "service_s_total": float(np.sum(svc64)),
                                      "recipe": "estimated: the same requests and arrival times, FP64 walks, one request "
-                                               "in flight; each service time measured on the request's points with "
-                                               "min(budget, 64) walks and scaled linearly to the walk-steps of the "
-                                               "served request (an upper estimate for requests that leave the GPU "
-                                               "idle); latency = FIFO finish - arrival"}
+                                               "in flight; each service time = its measured FP32 one-at-a-time time x "
+                                               "the FP64 / FP32 time ratio of a sample of the request (its points, "
+                                               "min(budget, 64) walks, <= 2048 steps per walk) run in both "
+                                               "precisions; latency = FIFO finish - arrival"}
     return out
 
 
@@ -423,8 +453,22 @@ def config4_leg(M, ctx, sm, mhz, src):
     w.params.max_steps = 256
     dt, S, K = kernel_run(M, ctx, w, N, M.FP32)
     steps = float(K.sum(dtype=np.int64))
-    out["reduced_window_256"] = {"walk_steps_per_s": steps / dt, "seconds": dt, "walk_steps": steps}
+    out["reduced_window_256"] = {
+        "walk_steps_per_s": steps / dt, "seconds": dt, "walk_steps": steps,
+        "roofline": roofline_block("walkr_kernel<float, embedded>", ops_reduced_embedded(20), steps, dt, sm, mhz,
+                                   src)}
     del S, K
+    import oracle as O
+    cores = os.cpu_count() or 1
+    cs = W.embedded_s20(P=2, walks=1)
+    cs.params.sampler = W.SAMPLER_REDUCED
+    cs.params.max_steps = 20000
+    t0 = time.perf_counter()
+    _, _, to, _ = O.solve(cs.problem, cs.params, cs.points, 8, n_threads=cores)
+    t_orc = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": float(to.sum() * 8) / t_orc, "unit": UNIT, "cores": cores, "kind": "oracle",
+                           "sample": f"2 points x 8 walks, a window of 20,000 steps each, reduced sampler, FP64, "
+                                     f"{t_orc:.1f} s"}
     sub = W.embedded_s20(P=256, walks=1)
     sub.params.sampler = W.SAMPLER_REDUCED
     dt, (mean, se, ms) = solve_run(M, ctx, sub, 16, M.FP32)

@@ -323,8 +323,9 @@ int64_t mpwos_noalloc_max_walks(void);
  * own streams, and are advanced by a scheduler thread of the context.  A
  * round's walks go out in chunks of about 10 ms of GPU time each (the walk
  * cost measured on the request's previous chunks, at its share of the grid;
- * at most chunk_walks walks), two in flight per request, so that a newly
- * admitted request waits at most about one chunk for the SMs.  A walk's draws depend only on (seed, point, walk index), so a
+ * at least one resident wave of walkers, at most chunk_walks walks), two in
+ * flight per request, so that a newly admitted request waits at most about one
+ * chunk for the SMs.  A walk's draws depend only on (seed, point, walk index), so a
  * request's results do not depend on the other requests in flight; with
  * target 0 they equal mpwos_solve's bit for bit.  Point clouds: the search
  * grid is built at submit. */

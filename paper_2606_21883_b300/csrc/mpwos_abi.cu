@@ -1930,6 +1930,8 @@ struct Request {
   int64_t* h_n = nullptr;
   int* h_act = nullptr;
   unsigned long long* h_flag = nullptr;
+  void* hbuf = nullptr;   // the pinned host block the h_ arrays live in
+  size_t hcls = 0;        // its size class in the engine's pool
   std::vector<int> active;
   int64_t cur = 0;
   bool cancel = false;
@@ -1947,7 +1949,41 @@ struct Request {
 
 }  // namespace
 
+// Pinned host blocks for the requests' results, kept by power-of-two size
+// class and reused: cudaFreeHost (and often cudaMallocHost) synchronizes the
+// whole device, which would make every finished request wait for the longest
+// kernel in flight.
+struct PinnedPool {
+  std::map<size_t, std::vector<void*>> free_;
+  void* get(size_t bytes, size_t* cls) {
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    *cls = c;
+    auto& v = free_[c];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      return p;
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, c) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, size_t cls) {
+    if (p) free_[cls].push_back(p);
+  }
+  void release() {
+    for (auto& kv : free_)
+      for (void* p : kv.second) cudaFreeHost(p);
+    free_.clear();
+  }
+};
+
 struct ServeEngine {
+  PinnedPool pinned;
   std::map<uint64_t, std::unique_ptr<Request>> reqs;
   std::deque<uint64_t> queue;
   std::vector<cudaStream_t> streams;
@@ -1972,6 +2008,9 @@ void req_free_device(Request& r) {
 
 void req_finish(mpwos_ctx* ctx, Request& r, int state, int status, const std::string& err) {
   ServeEngine& E = *ctx->serve;
+  // a failed request may still have copies into its pinned block in flight:
+  // drain its own stream before the block can go back to the pool
+  if (state == 3 && r.slot >= 0) cudaStreamSynchronize(E.streams[r.slot]);
   r.state = state;
   r.status = status;
   r.err = err;
@@ -1986,8 +2025,9 @@ void req_finish(mpwos_ctx* ctx, Request& r, int state, int status, const std::st
 
 // Launch the next chunk of the round in flight (at most two outstanding).  A
 // chunk aims at chunk_target_ms of GPU time at its launch's share of the grid
-// (all requests in flight split the SMs); the first chunk of a request, with
-// no measurement yet, is one resident wave of walkers.
+// (all requests in flight split the SMs), and holds at least one resident wave
+// of walkers; the first chunk of a request, with no measurement yet, is one
+// wave.
 int req_issue(mpwos_ctx* ctx, Request& r) {
   ServeEngine& E = *ctx->serve;
   const cudaStream_t st = E.streams[r.slot];
@@ -1998,10 +2038,14 @@ int req_issue(mpwos_ctx* ctx, Request& r) {
   const int block = tuned_block(ctx, r.pb, fp64);
   const LaunchShape sh = launch_shape(ctx, r.pb, fp64, max_grid, block);
   const int64_t grid = sh.grid;
-  int64_t n = std::max<int64_t>(1, grid * sh.per_block);
-  if (r.block_ns_per_walk > 0.0)
-    n = static_cast<int64_t>(E.chunk_target_ms * 1e6 * static_cast<double>(grid) / r.block_ns_per_walk);
-  n = std::max<int64_t>(n, 1);
+  // never less than one resident wave: a chunk lasts at least its longest walk,
+  // so fewer walks than the grid holds would not end sooner
+  const int64_t wave = std::max<int64_t>(1, grid * sh.per_block);
+  int64_t n = wave;
+  if (r.block_ns_per_walk > 0.0) {
+    const double want = E.chunk_target_ms * 1e6 * static_cast<double>(grid) / r.block_ns_per_walk;
+    n = want >= static_cast<double>(E.chunk_walks) ? E.chunk_walks : std::max<int64_t>(wave, static_cast<int64_t>(want));
+  }
   n = std::min<int64_t>(n, E.chunk_walks);
   n = std::min<int64_t>(n, r.round_total - r.round_issued);
   const int c = (r.chead + r.inflight) & 1;
@@ -2220,12 +2264,7 @@ Request* find_req(mpwos_ctx* ctx, uint64_t id) {
 void req_release(mpwos_ctx* ctx, uint64_t id) {
   Request* r = find_req(ctx, id);
   if (!r) return;
-  cudaFreeHost(r->h_mean);
-  cudaFreeHost(r->h_se);
-  cudaFreeHost(r->h_ms);
-  cudaFreeHost(r->h_n);
-  cudaFreeHost(r->h_act);
-  cudaFreeHost(r->h_flag);
+  ctx->serve->pinned.put(r->hbuf, r->hcls);
   if (r->ev) cudaEventDestroy(r->ev);
   for (auto& pair : r->cev)
     for (auto& e : pair)
@@ -2254,6 +2293,7 @@ void serve_shutdown(mpwos_ctx* ctx) {
     req_release(ctx, id);
   }
   for (auto& st : E->streams) cudaStreamDestroy(st);
+  E->pinned.release();
   delete E;
   ctx->serve = nullptr;
 }
@@ -2320,15 +2360,25 @@ int mpwos_submit(mpwos_ctx* ctx, const mpwos_manifold* mh, const mpwos_problem* 
   }
   r->pts.assign(pts, pts + static_cast<size_t>(P) * m->n);
   r->bytes = static_cast<size_t>(P) * walk_budget * 16 + static_cast<size_t>(P) * 48 + (64 << 10);
-  CK(cudaMallocHost(&r->h_mean, sizeof(double) * std::max<int64_t>(P, 1)));
-  CK(cudaMallocHost(&r->h_se, sizeof(double) * std::max<int64_t>(P, 1)));
-  CK(cudaMallocHost(&r->h_ms, sizeof(double) * std::max<int64_t>(P, 1)));
-  CK(cudaMallocHost(&r->h_n, sizeof(int64_t) * std::max<int64_t>(P, 1)));
-  CK(cudaMallocHost(&r->h_act, sizeof(int) * std::max<int64_t>(P, 1)));
-  CK(cudaMallocHost(&r->h_flag, 2 * sizeof(unsigned long long)));   // [0] flagged walks, [1] kernel status
+  CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
+  {   // one pinned block: mean, se, mean K, walk counts (8 B each per point), two
+      // flag words ([0] flagged walks, [1] kernel status), active points (4 B)
+    const size_t Pn = static_cast<size_t>(std::max<int64_t>(P, 1));
+    r->hbuf = E.pinned.get(Pn * 32 + 16 + Pn * 4, &r->hcls);
+    if (!r->hbuf) {
+      cudaEventDestroy(r->ev);
+      return fail(ctx, MPWOS_ENOMEM, "pinned host memory for the request's results");
+    }
+    double* h = static_cast<double*>(r->hbuf);
+    r->h_mean = h;
+    r->h_se = h + Pn;
+    r->h_ms = h + 2 * Pn;
+    r->h_n = reinterpret_cast<int64_t*>(h + 3 * Pn);
+    r->h_flag = reinterpret_cast<unsigned long long*>(h + 4 * Pn);
+    r->h_act = reinterpret_cast<int*>(h + 4 * Pn + 2);
+  }
   r->h_flag[0] = 0;
   r->h_flag[1] = 0;
-  CK(cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming));
   r->t_submit = std::chrono::steady_clock::now();
   const uint64_t id = r->id;
   if (P == 0) {
