@@ -210,23 +210,27 @@ __device__ __forceinline__ void walk_body(const DevProblem& pb, float* ys, float
   // pass 1 of a vector: the radii of the lane's pairs into shared memory; returns
   // the lane's part of |g|^2 (of the partial last group: the squares of its
   // valid components)
+  // (the partial group runs in the same iteration as the other lanes' last full
+  // group; with an even number of valid components its pairs are whole and need
+  // no angles)
   auto radial_pass = [&](uint32_t x) -> float {
     float sl = 0.0f;
-#pragma unroll 2
-    for (int m = 0; m < nfull; ++m) {
+    for (int m = 0; m < mend; ++m) {
       float R[8];
-      sl += radii(x, m, R);
+      const float s_all = radii(x, m, R);
       *reinterpret_cast<float4*>(rs + RM * m + 4 * hl) = make_float4(R[0], R[1], R[2], R[3]);
       *reinterpret_cast<float4*>(rs + RM * m + YQ + 4 * hl) = make_float4(R[4], R[5], R[6], R[7]);
-    }
-    if (mpart >= 0) {
-      float R[8], gq[16];
-      radii(x, mpart, R);
-      *reinterpret_cast<float4*>(rs + RM * mpart + 4 * hl) = make_float4(R[0], R[1], R[2], R[3]);
-      *reinterpret_cast<float4*>(rs + RM * mpart + YQ + 4 * hl) = make_float4(R[4], R[5], R[6], R[7]);
-      angle8(blk(x, mpart, 2), R, gq);
+      if (m != mpart) {
+        sl += s_all;
+      } else if ((rem & 1) == 0) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) sl += q < rem ? gq[q] * gq[q] : 0.0f;
+        for (int q = 0; q < 8; ++q) sl += 2 * q < rem ? R[q] * R[q] : 0.0f;
+      } else {
+        float gq[16];
+        angle8(blk(x, m, 2), R, gq);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sl += q < rem ? gq[q] * gq[q] : 0.0f;
+      }
     }
     return sl;
   };
