@@ -74,10 +74,11 @@ def ops_full_sampler(n, revolution=False):
 
 def ops_tc_embedded(n):
     """The tensor-core embedded-sphere walk: per component of each of the two
-    directions, its share of a hoisted Philox block (34 / 4), of two 23-bit
-    Box-Muller pairs (23 / 4), the BF16 hi/lo split (3), the shared-memory store
-    and |g|^2 (0.75); the Q^T g products run on the tensor pipe.  Scalar part: 300."""
-    return 2 * n * (34 / 4 + 23 / 4 + 3 + 0.75) + 300
+    directions, its share of a 16-component group (3 hoisted Philox blocks
+    102 / 16, 8 radial halves 40 / 16, 8 angle halves 56 / 16), the BF16 hi/lo
+    split (3), the shared-memory store (0.25); the Q^T g products run on the
+    tensor pipe.  Scalar part: 300."""
+    return 2 * n * ((102 + 40 + 56) / 16 + 3 + 0.25) + 300
 
 
 # The dimension-reduced sampler on S^999 (walkr_kernel): per direction one

@@ -74,9 +74,9 @@ struct DevProblem {
   // manifold
   int mkind, n, d;
   double R, a_tube;
-  const double* Q;    // n x (d+1) row-major (embedded sphere), device
+  const double* Q;    // embedded sphere: Q^T, (d+1) rows of npad = n rounded up to 4, device
   const double* b;
-  const float* Qf;
+  const float* Qf;    // FP32 Q^T in the warp walk's group order: (d+1) rows of 1024
   const float* bf;
   // point cloud: points sorted by grid cell (xyz interleaved), original
   // indices, cell start offsets (cells + 1), grid origin / cell size / dims
@@ -408,6 +408,62 @@ __device__ __forceinline__ float gauss_pair32(uint32_t x, uint32_t y, float& g0,
   g0 = R * c;
   g1 = R * s;
   return -l;
+}
+
+// Radial half of one block: R = sqrt(-log2 u) of four pairs; returns the sum
+// of -log2 u.
+__device__ __forceinline__ float radial4(const U4& r, float* R) {
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+  float sl = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float u = 2.0f - __uint_as_float(0x3f800000u | (w[k] & 0x7FFFFFu));
+    const float l = __log2f(u);
+    R[k] = sqrtf(-l);
+    sl -= l;
+  }
+  return sl;
+}
+
+// Angle halves: the group's 16 components g[2q] = R_q cos, g[2q+1] = R_q sin,
+// angle of pair 2k from the low and of pair 2k + 1 from the high 16 bits of
+// word k (as the fraction bits of a float in [1, 2): sine and cosine have
+// period 1 there).
+__device__ __forceinline__ void angle8(const U4& a, const float (&R)[8], float (&g)[16]) {
+  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float s, c;
+    __sincosf(kTwoPiF * __uint_as_float(0x3f800000u | ((w[k] << 7) & 0x7FFF80u)), &s, &c);
+    g[4 * k] = R[2 * k] * c;
+    g[4 * k + 1] = R[2 * k] * s;
+    __sincosf(kTwoPiF * __uint_as_float(0x3f800000u | ((w[k] >> 9) & 0x7FFF80u)), &s, &c);
+    g[4 * k + 2] = R[2 * k + 1] * c;
+    g[4 * k + 3] = R[2 * k + 1] * s;
+  }
+}
+
+// One group of 16 direction components, 16 G .. 16 G + 15, of the FP32 walks in
+// R^n (n > 3): radial words from blocks j = 4 G and 4 G + 1 (pairs 8 G + 0..7),
+// angle halves from block 4 G + 2, each pair sqrt(-log2 u) (cos 2 pi a, sin
+// 2 pi a) with a 16-bit angle a; X = A0 ^ 256 v selects the vector (philox32_block
+// then runs at counter (k, 256 v + 4 G + c, i, p)).  Components past n are zero;
+// returns the sum of squares of the group's components.
+__device__ __forceinline__ float gauss_group16(uint32_t X, int G, const Philox32Step& st, const PhiloxKeys& K,
+                                               int n, float (&g)[16]) {
+  float R[8];
+  const uint32_t j = static_cast<uint32_t>(4 * G);
+  const float sl = radial4(philox32_block(X ^ j, st, K), R) + radial4(philox32_block(X ^ (j + 1u), st, K), R + 4);
+  angle8(philox32_block(X ^ (j + 2u), st, K), R, g);
+  const int valid = n - 16 * G;
+  if (valid >= 16) return sl;
+  float s = 0.0f;
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    g[q] = q < valid ? g[q] : 0.0f;
+    s += g[q] * g[q];
+  }
+  return s;
 }
 
 // ---------------------------------------------------------------------------

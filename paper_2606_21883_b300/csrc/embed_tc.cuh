@@ -48,6 +48,7 @@ constexpr int kABytes = 2 * 2 * kAHalf;              // 2 stages x (hi + lo): 64
 constexpr int kMiscBytes = 64 + 4 * kThreads + 4 * 32 * 32 + 4 * 32 + 64;
 constexpr int kSStride = 37;                 // walker row: s[0..31], W (hi, lo), S (hi, lo); odd: conflict-free
 constexpr int kSBytes = kM * kSStride * 4;   // 18.5 KB
+static_assert(kTPW * kUPT * 8 == kChunkK && kUPT * 8 == 16, "one 16-component group per thread per chunk");
 constexpr int kSmemBytes = kBBytes + kABytes + kMiscBytes + kSBytes + 1024;   // + 1 KB alignment slack
 constexpr uint32_t kStatusTimeout = 1u;
 
@@ -183,25 +184,22 @@ struct Smem {
   __device__ __forceinline__ float* rows() const { return reinterpret_cast<float*>(misc() + kMiscBytes); }
 };
 
-// The walk's Gaussian vector v of step kk of walk (p, wi): block b (components
-// 4 b .. 4 b + 3, zero past n) from Philox block j = 256 v + b, the warp walk's
-// draws (walkn32.cuh); returns the block's part of |g|^2.
+// The walk's Gaussian vector v of step kk of walk (p, wi) in 16-component
+// groups: group G (components 16 G .. 16 G + 15, zero past n) by
+// gauss_group16, the draws of the CUDA-core walk (walkn32.cuh, gen_groups);
+// returns the group's part of |g|^2.
 struct PhiloxSource {
   const PhiloxKeys* K;
   Philox32Step st;
   uint32_t X;   // A0 ^ 256 v
   int n;
-  __device__ __forceinline__ float operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
-    g0 = g1 = g2 = g3 = 0.0f;
-    if (4 * b >= n) return 0.0f;
-    const U4 r = philox32_block(X ^ static_cast<uint32_t>(b), st, *K);
-    const float l0 = gauss_pair32(r.x, r.y, g0, g1);
-    const float l1 = gauss_pair32(r.z, r.w, g2, g3);
-    if (4 * b + 4 <= n) return l0 + l1;
-    g3 = 0.0f;
-    if (4 * b + 3 > n) g2 = 0.0f;
-    if (4 * b + 2 > n) g1 = 0.0f;
-    return g0 * g0 + g1 * g1 + g2 * g2;
+  __device__ __forceinline__ float operator()(int G, float (&g)[16]) const {
+    if (16 * G >= n) {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) g[q] = 0.0f;
+      return 0.0f;
+    }
+    return gauss_group16(X, G, st, *K, n, g);
   }
 };
 
@@ -210,21 +208,22 @@ struct MatrixSource {
   const float* G;
   int64_t row, rows;
   int n;
-  __device__ __forceinline__ float operator()(int b, float& g0, float& g1, float& g2, float& g3) const {
-    float v[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (row < rows)
+  __device__ __forceinline__ float operator()(int grp, float (&g)[16]) const {
+    float s = 0.0f;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (4 * b + q < n) v[q] = G[row * n + 4 * b + q];
-    g0 = v[0]; g1 = v[1]; g2 = v[2]; g3 = v[3];
-    return g0 * g0 + g1 * g1 + g2 * g2 + g3 * g3;
+    for (int q = 0; q < 16; ++q) {
+      const int c = 16 * grp + q;
+      g[q] = (row < rows && c < n) ? G[row * n + c] : 0.0f;
+      s += g[q] * g[q];
+    }
+    return s;
   }
 };
 
 // Q^T g into the TMEM accumulator (row = walker) for the vector that `src`
-// generates; returns |g|^2 to threads < 128.  Thread (row, part) generates the
-// 16-byte units kUPT part + 0 .. kUPT - 1 of each chunk c (blocks 2 unit + 0, 1
-// of 16 c, components 8 unit + 0..7 of 64 c).  g is the CTA's running chunk
+// generates; returns |g|^2 to threads < 128.  Thread (row, part) generates
+// group 4 c + part of each chunk c (components 64 c + 16 part + 0..15), the
+// 16-byte units kUPT part + 0 .. kUPT - 1 of the chunk.  g is the CTA's running chunk
 // count (uniform): chunk g uses stage g & 1 for the (g >> 1)-th time.  The
 // caller reads TMEM (warps 0..3, warp-uniformly) and then calls tc_fence_before.
 template <class Src>
@@ -239,19 +238,18 @@ __device__ __forceinline__ float project_vector(const Smem& sm, uint32_t taddr, 
     if (u >= 1 && ok) ok = mbar_wait(smem_u32(&sm.empty()[s]), (u - 1) & 1u);   // chunk gc - 2 has left the stage
     unsigned char* Ahi = sm.A() + (2 * s) * kAHalf;
     unsigned char* Alo = Ahi + kAHalf;
+    float gq[16];   // the thread's group 4 c + part: components 64 c + 16 part + 0..15
+    acc += src(4 * c + part, gq);
 #pragma unroll
-    for (int uu = 0; uu < kUPT; ++uu) {   // a 16-byte unit = 8 components = 2 blocks of 4
+    for (int uu = 0; uu < kUPT; ++uu) {   // a 16-byte unit = 8 components
       const int unit = kUPT * part + uu;
       uint32_t hw[4], lw[4];
 #pragma unroll
-      for (int bb = 0; bb < 2; ++bb) {
-        float g0, g1, g2, g3;
-        acc += src(16 * c + 2 * unit + bb, g0, g1, g2, g3);
-        const uint32_t h01 = pack_bf16x2(g0, g1), h23 = pack_bf16x2(g2, g3);
-        hw[2 * bb] = h01;
-        hw[2 * bb + 1] = h23;
-        lw[2 * bb] = pack_bf16x2(g0 - bf16_low(h01), g1 - bf16_high(h01));
-        lw[2 * bb + 1] = pack_bf16x2(g2 - bf16_low(h23), g3 - bf16_high(h23));
+      for (int e = 0; e < 4; ++e) {
+        const float g0 = gq[8 * uu + 2 * e], g1 = gq[8 * uu + 2 * e + 1];
+        const uint32_t h01 = pack_bf16x2(g0, g1);
+        hw[e] = h01;
+        lw[e] = pack_bf16x2(g0 - bf16_low(h01), g1 - bf16_high(h01));
       }
       const uint32_t off = sw128(row, static_cast<uint32_t>(unit));
       *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);

@@ -841,7 +841,7 @@ int prepare(mpwos_ctx* ctx, Scratch& sc, const mpwos_manifold* mh, const mpwos_p
     double* s0 = sc.alloc<double>(static_cast<size_t>(P) * D);
     if (!s0) return fail(ctx, MPWOS_ENOMEM, "intrinsic start points");
     pb.Q = mh->qt;   // Q^T, D x npad
-    pb.Qf = mh->qtf;
+    pb.Qf = mh->qtf;   // group order, rows of 1024
     pb.b = mh->bd;
     pb.s0 = s0;
     if (P) {
@@ -1255,15 +1255,21 @@ int mpwos_manifold_create(mpwos_ctx* ctx, const mpwos_manifold_desc* desc, mpwos
     mh->b.assign(desc->b, desc->b + n);
     mh->desc.Q = mh->Q.data();
     mh->desc.b = mh->b.data();
-    // Q^T, D rows of stride npad = n rounded up to 4 (zero padded: 16-byte row slices)
+    // Q^T, D rows of stride npad = n rounded up to 4 (zero padded: 16-byte row
+    // slices); the FP32 copy in the warp walk's group order: rows of 1024, the
+    // 16-byte slice c of component group G = lane + 32 s at 512 s + 128 c + 4 lane,
+    // so that a warp's loads of one slice are contiguous
     const int npad = (n + 3) & ~3;
     std::vector<double> qt(static_cast<size_t>(D) * npad, 0.0);
-    std::vector<float> qtf(qt.size(), 0.0f);
-    for (int i = 0; i < n; ++i)
+    std::vector<float> qtf(static_cast<size_t>(D) * 1024, 0.0f);
+    for (int i = 0; i < n; ++i) {
+      const int G = i >> 4, lane = G & 31, sg = G >> 5, c = (i >> 2) & 3, e = i & 3;
+      const size_t pos = static_cast<size_t>(512 * sg + 128 * c + 4 * lane + e);
       for (int j = 0; j < D; ++j) {
         qt[static_cast<size_t>(j) * npad + i] = mh->Q[static_cast<size_t>(i) * D + j];
-        qtf[static_cast<size_t>(j) * npad + i] = static_cast<float>(mh->Q[static_cast<size_t>(i) * D + j]);
+        qtf[static_cast<size_t>(j) * 1024 + pos] = static_cast<float>(mh->Q[static_cast<size_t>(i) * D + j]);
       }
+    }
     std::vector<uint16_t> img;
     tc_bimage(mh->Q.data(), n, D, img);
     if ((rc = upload(reinterpret_cast<void**>(&mh->qt), qt.data(), qt.size() * sizeof(double))) ||

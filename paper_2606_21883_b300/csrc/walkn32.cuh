@@ -7,7 +7,9 @@
 // per-lane partial sums and one butterfly reduction.
 //
 // Draws of step k of walk (p, i): Philox4x32-10 at counter (k, j, i, p),
-//   Theta direction: j = b;  Z_l direction: j = 256 (1 + l) + b;
+//   Theta direction: j = b;  Z_l direction: j = 256 (1 + l) + b (the embedded
+//   sphere instead draws in 16-component groups, gen_groups, the layout of the
+//   tensor-core walk and of walkn32s.cuh);
 //   U_l = u23(word l mod 4) of block j = 256 (1 + N_V) + l / 4,
 // the per-walk and per-step parts of rounds 0..2 computed once (dev_common.cuh,
 // Philox32Step), each word pair giving two components sqrt(-log2 u)(cos, sin)
@@ -112,23 +114,53 @@ __device__ __forceinline__ void wsum(float (&v)[NV]) {
     for (int q = 0; q < NV; ++q) v[q] += __shfl_xor_sync(0xffffffffu, v[q], off);
 }
 
-// (Q^T g)_lane for D <= 31 rows of the transposed, zero-padded Q^T (row stride
-// npad floats): per-lane partial products, then one reduce-scatter.
+// The embedded sphere's draws in 16-component groups (the layout of the FP32
+// walk in R^n, gauss_group16): lane owns groups G = lane + 32 s, s < MB / 4,
+// components 16 G + q in g[16 s + q].  X = A0 ^ 256 v.  Returns the lane's part
+// of |g|^2.
+template <int MB>
+__device__ __forceinline__ float gen_groups(float (&g)[4 * MB], uint32_t X, const Philox32Step& st,
+                                            const PhiloxKeys& K, int lane, int n) {
+  static_assert(MB % 4 == 0, "groups of 16 components");
+  float sl = 0.0f;
+#pragma unroll
+  for (int s = 0; s < MB / 4; ++s) {
+    const int G = lane + 32 * s;
+    float gq[16];
+    if (16 * G < n) {
+      sl += gauss_group16(X, G, st, K, n, gq);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 16; ++q) gq[q] = 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 16; ++q) g[16 * s + q] = gq[q];
+  }
+  return sl;
+}
+
+// (Q^T g)_lane for the group layout.  The FP32 Q^T is stored in group order
+// (rows of 1024 floats, zero past n): the 16-byte slice c of group
+// G = lane + 32 s sits at 512 s + 128 c + 4 lane, so each load of a slice is
+// contiguous across the warp.
 template <int DQ, int MB>
-__device__ __forceinline__ float qt_times32(const float* QT, int npad, const float (&g)[4 * MB], int lane, int D,
-                                            int nb) {
+__device__ __forceinline__ float qt_groups(const float* QT, const float (&g)[4 * MB], int lane, int D, int n) {
   float acc[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
 #pragma unroll
-  for (int m = 0; m < MB; ++m) {
-    const int b = lane + 32 * m;
-    if (b < nb) {
+  for (int s = 0; s < MB / 4; ++s) {
+    if (16 * 32 * s < n) {   // warp-uniform: some lane holds a group of this slot
 #pragma unroll
-      for (int j = 0; j < DQ; ++j) {
-        if (j < D) {
-          const float4 q4 = *reinterpret_cast<const float4*>(QT + static_cast<size_t>(j) * npad + 4 * b);
-          acc[j] += q4.x * g[4 * m] + q4.y * g[4 * m + 1] + q4.z * g[4 * m + 2] + q4.w * g[4 * m + 3];
+      for (int c = 0; c < 4; ++c) {
+#pragma unroll
+        for (int j = 0; j < DQ; ++j) {
+          if (j < D) {
+            const float4 q4 =
+                *reinterpret_cast<const float4*>(QT + static_cast<size_t>(j) * 1024 + 512 * s + 128 * c + 4 * lane);
+            const float* gg = g + 16 * s + 4 * c;
+            acc[j] += q4.x * gg[0] + q4.y * gg[1] + q4.z * gg[2] + q4.w * gg[3];
+          }
         }
       }
     }
@@ -145,7 +177,7 @@ __device__ __forceinline__ void walk_body(const DevProblem& pb, WarpRow& row) {
   int64_t w = pb.wk_w0 + ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
   if (w >= total) return;
   const int n = pb.n;
-  const int nbf = n >> 2, rem = n & 3, nb = (n + 3) >> 2;
+  const int nbf = n >> 2, rem = n & 3;
   const PhiloxKeys& K = pb.keys;
   const int nv = pb.n_v;
   const float eps = pb.sf.eps, h = pb.sf.h, rgeo = pb.sf.rho_geo, theta = pb.sf.theta;
@@ -156,9 +188,8 @@ __device__ __forceinline__ void walk_body(const DevProblem& pb, WarpRow& row) {
   float e0[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) e0[q] = bnd ? pb.e_s0[4 * lane + q] : 0.0f;
-  // embedded sphere: Q^T (D x npad), the SPHERE_QUAD data
+  // embedded sphere: D = d + 1 intrinsic coordinates
   const int D = pb.d + 1;
-  const int npad = (n + 3) & ~3;
   // hypersurface of revolution: profile, c_kappa, f's scalars
   const float rv_al = pb.rv_alpha_f, rv_k = pb.rv_kappa_f, rv_mA = pb.rv_mA_f, ck = pb.rv_ck_f;
   const float c0f = pb.f.c0_f, c1f = pb.f.coef_f[0], c2f = pb.f.coef_f[1];
@@ -309,9 +340,13 @@ __device__ __forceinline__ void walk_body(const DevProblem& pb, WarpRow& row) {
       const int s4 = l & 3;
       const float U = u23(s4 == 0 ? bu.x : (s4 == 1 ? bu.y : (s4 == 2 ? bu.z : bu.w)));
       const float t = fminf(fmaxf(table_lookup32(pb, a, U), 0.0f), 1.0f);
-      float sl = gen_vec<MB>(g, xl ^ static_cast<uint32_t>(256 * (1 + l)), st, K, lane, nbf, rem);
+      float sl;
+      if constexpr (MK == kEmbeddedSphere)
+        sl = gen_groups<MB>(g, pw.A0 ^ static_cast<uint32_t>(256 * (1 + l)), st, K, lane, n);
+      else
+        sl = gen_vec<MB>(g, xl ^ static_cast<uint32_t>(256 * (1 + l)), st, K, lane, nbf, rem);
       if constexpr (MK == kEmbeddedSphere) {
-        const float qgj = qt_times32<DQ, MB>(pb.Qf, npad, g, lane, D, nb);
+        const float qgj = qt_groups<DQ, MB>(pb.Qf, g, lane, D, n);
         float acc[1] = {sl};
         wsum<1>(acc);
         const float zs = (r * t) * rsqrtf(fmaxf(acc[0], 1e-30f));
@@ -376,9 +411,13 @@ __device__ __forceinline__ void walk_body(const DevProblem& pb, WarpRow& row) {
     }
     if (nv > 1) F /= static_cast<float>(nv);
     // ---- Theta = Y + r g/|g|, Y = cp(Theta) --------------------------------------
-    const float sl = gen_vec<MB>(g, xl, st, K, lane, nbf, rem);
+    float sl;
+    if constexpr (MK == kEmbeddedSphere)
+      sl = gen_groups<MB>(g, pw.A0, st, K, lane, n);
+    else
+      sl = gen_vec<MB>(g, xl, st, K, lane, nbf, rem);
     if constexpr (MK == kEmbeddedSphere) {
-      const float qgj = qt_times32<DQ, MB>(pb.Qf, npad, g, lane, D, nb);
+      const float qgj = qt_groups<DQ, MB>(pb.Qf, g, lane, D, n);
       float acc[1] = {sl};
       wsum<1>(acc);
       const float sc = r * rsqrtf(fmaxf(acc[0], 1e-30f));

@@ -48,39 +48,6 @@ __device__ __forceinline__ int ypos(int c) {
   return (G / LPW) * (16 * LPW) + (q >> 2) * (4 * LPW) + (G % LPW) * 4 + (q & 3);
 }
 
-// Radial half of one block: R = sqrt(-log2 u) of four pairs; returns the sum
-// of -log2 u.
-__device__ __forceinline__ float radial4(const U4& r, float* R) {
-  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
-  float sl = 0.0f;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float u = 2.0f - __uint_as_float(0x3f800000u | (w[k] & 0x7FFFFFu));
-    const float l = __log2f(u);
-    R[k] = sqrtf(-l);
-    sl -= l;
-  }
-  return sl;
-}
-
-// Angle halves: the group's 16 components g[2q] = R_q cos, g[2q+1] = R_q sin,
-// angle of pair 2k from the low and of pair 2k + 1 from the high 16 bits of
-// word k (as the fraction bits of a float in [1, 2): sine and cosine have
-// period 1 there).
-__device__ __forceinline__ void angle8(const U4& a, const float (&R)[8], float (&g)[16]) {
-  const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    float s, c;
-    __sincosf(kTwoPiF * __uint_as_float(0x3f800000u | ((w[k] << 7) & 0x7FFF80u)), &s, &c);
-    g[4 * k] = R[2 * k] * c;
-    g[4 * k + 1] = R[2 * k] * s;
-    __sincosf(kTwoPiF * __uint_as_float(0x3f800000u | ((w[k] >> 9) & 0x7FFF80u)), &s, &c);
-    g[4 * k + 2] = R[2 * k + 1] * c;
-    g[4 * k + 3] = R[2 * k + 1] * s;
-  }
-}
-
 // Sum over the LPW lanes of a walker (a butterfly within the lane group).
 template <int LPW, int NV>
 __device__ __forceinline__ void wsum(float (&v)[NV], unsigned mask) {
