@@ -20,9 +20,11 @@
 //     component along Y's rest, then T's; chi^2 attempt a at blocks 64 v + 32 + 2a
 //     (normal) and 64 v + 33 + 2a (U = u53 of words 0, 1); U_l at block
 //     64 (1 + N_V) + l, u53 of words 0, 1.
-//   FP32: normals four per block (u23 words); chi^2 attempt a at block
-//     64 v + 32 + a (normal from words 0, 1, U from word 2); U_l = word 3 of
-//     block 64 (1 + l) + 32 (the first chi^2 block of Z_l, drawn anyway).
+//   FP32: Philox4x32-10 at counter (k, j, i, p) instead (the hoisted form of
+//     the other FP32 walks); normals four per block j = 64 v + b (u23 words);
+//     chi^2 attempt a at block 64 v + 32 + a (normal from words 0, 1, U from
+//     word 2); U_l = word 3 of block 64 (1 + l) + 32 (the first chi^2 block of
+//     Z_l, drawn anyway).
 // chi^2_m: 0 (m = 0), x^2 (m = 1), else 2 Gamma(m/2) by Marsaglia-Tsang
 // (ACM TOMS 26, 2000) with the exact log acceptance test, at most 16 attempts.
 #pragma once
@@ -53,13 +55,22 @@ __device__ __forceinline__ void red_normals(const PhiloxKeys& K, uint32_t j0, ui
     }
   }
 }
+// The FP32 walk's blocks: Philox4x32-10 at counter (k, j, i, p) with the
+// per-walk and per-step parts of its first rounds computed once (the form of
+// the other FP32 walks).
+struct RedStream32 {
+  uint32_t A0;
+  Philox32Step st;
+  const PhiloxKeys* K;
+  __device__ __forceinline__ U4 operator()(uint32_t j) const { return philox32_block(A0 ^ j, st, *K); }
+};
+
 template <int NG>
-__device__ __forceinline__ void red_normals(const PhiloxKeys& K, uint32_t j0, uint32_t kk, uint32_t i, uint32_t p,
-                                            int ng, float (&g)[NG]) {
+__device__ __forceinline__ void red_normals(const RedStream32& S, uint32_t j0, int ng, float (&g)[NG]) {
 #pragma unroll
   for (int b = 0; b < (NG + 3) / 4; ++b) {
     if (4 * b < ng) {
-      const U4 r = philox4x32_10(j0 + static_cast<uint32_t>(b), kk, i, p, K);
+      const U4 r = S(j0 + static_cast<uint32_t>(b));
       float v[4];
       box_muller32(u23(r.x), u23(r.y), v[0], v[1]);
       box_muller32(u23(r.z), u23(r.w), v[2], v[3]);
@@ -115,18 +126,18 @@ __device__ __forceinline__ float mt_log_term(float t) {
 // t = c x (identical to d - d v + d log v for v = (1 + t)^3), which avoids the
 // cancellation of d - d v in single precision.  `first` is attempt 0's block
 // (j0), which the caller also uses for the radius uniform.
-__device__ __forceinline__ float red_chi2(const PhiloxKeys& K, uint32_t j0, uint32_t kk, uint32_t i, uint32_t p,
-                                          int m, const U4& first) {
+// d = m / 2 - 1 / 3 and c = 1 / sqrt(9 d) are the launch's constants.
+__device__ __forceinline__ float red_chi2(const RedStream32& S, uint32_t j0, int m, float d, float c,
+                                          const U4& first) {
   if (m <= 0) return 0.0f;
   if (m == 1) {
     float x, y;
     box_muller32(u23(first.x), u23(first.y), x, y);
     return x * x;
   }
-  const float d = 0.5f * static_cast<float>(m) - 1.0f / 3.0f, c = rsqrtf(9.0f * d);
   float cand = d;
   for (uint32_t a = 0; a < kChi2Attempts; ++a) {
-    const U4 r = a == 0 ? first : philox4x32_10(j0 + a, kk, i, p, K);
+    const U4 r = a == 0 ? first : S(j0 + a);
     float x, y;
     box_muller32(u23(r.x), u23(r.y), x, y);
     const float t = c * x;
@@ -224,9 +235,14 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
   wa.set_tau(pb.tau_w);
   int64_t k = 0, o = 0;
   uint32_t p = 0, wi = 0;
+  Philox32Walk pw{0u, 0u};
+  // Marsaglia-Tsang constants of chi^2_rest (FP32; rest >= 2)
+  const float mt_d = 0.5f * static_cast<float>(rest) - 1.0f / 3.0f;
+  const float mt_c = rest >= 2 ? rsqrtf(9.0f * mt_d) : 0.0f;
   auto init = [&](int64_t ww) {
     const WalkId id = walk_id(pb, ww);
     p = id.p; wi = id.i; o = id.o;
+    if constexpr (!kF64) pw = philox32_walk(wi, K);
     wa.reset();
     k = 0;
     if constexpr (kEmb) {
@@ -305,6 +321,8 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
       r_prev = r;
     }
     const uint32_t kk = static_cast<uint32_t>(k);
+    RedStream32 S32{0u, Philox32Step{0u, 0u, 0u, 0u}, &K};
+    if constexpr (!kF64) S32 = RedStream32{pw.A0, philox32_step(pw, kk, p, K), &K};
     T g[NG];
     // ---- interior samples Z_l and F_k ----------------------------------------
     T F = T(0);
@@ -318,11 +336,12 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
         t = green_invert64(law, U, guess);
         X = red_chi2(K, jv + 32u, kk, wi, p, rest, 0.0);
       } else {
-        const U4 c0 = philox4x32_10(jv + 32u, kk, wi, p, K);
+        const U4 c0 = S32(jv + 32u);
         t = fminf(fmaxf(table_lookup32(pb, a, u23(c0.w)), 0.0f), 1.0f);
-        X = red_chi2(K, jv + 32u, kk, wi, p, rest, c0);
+        X = red_chi2(S32, jv + 32u, rest, mt_d, mt_c, c0);
       }
-      red_normals<NG>(K, jv, kk, wi, p, ng, g);
+      if constexpr (kF64) red_normals<NG>(K, jv, kk, wi, p, ng, g);
+      else red_normals<NG>(S32, jv, ng, g);
       T gg = X;
 #pragma unroll
       for (int q = 0; q < NG; ++q) gg += g[q] * g[q];
@@ -347,12 +366,13 @@ __device__ __forceinline__ void walkr_body(const DevProblem& pb, const T* As, co
     }
     if (nv > 1) F /= T(nv);
     // ---- Theta = Y + r g/|g|, Y = cp(Theta) ------------------------------------
-    red_normals<NG>(K, 0u, kk, wi, p, ng, g);
     T X;
     if constexpr (kF64) {
+      red_normals<NG>(K, 0u, kk, wi, p, ng, g);
       X = red_chi2(K, 32u, kk, wi, p, rest, 0.0);
     } else {
-      X = red_chi2(K, 32u, kk, wi, p, rest, philox4x32_10(32u, kk, wi, p, K));
+      red_normals<NG>(S32, 0u, ng, g);
+      X = red_chi2(S32, 32u, rest, mt_d, mt_c, S32(32u));
     }
     T gg = X;
 #pragma unroll
