@@ -628,8 +628,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "torus_closed R=1 a=0.4 sigma=2, 4096 pts x 1e4 walks (sampled)",
-                       "model": "MPWoS CPU oracle"},
+            "config": {"workload": "torus_closed R=1 a=0.4 sigma=2 u=sin(th)cos(2ph)", "points": 4096,
+                       "walks_per_point": 10000, "steps_per_walk": 525,
+                       "sampled": "each step is a bounded sample of the workload on the host cores "
+                                  "(cpu_baseline.sample), the oracle as it stands"},
             "cpu_baseline": base,
             "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
