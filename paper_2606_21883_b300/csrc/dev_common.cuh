@@ -166,6 +166,9 @@ struct DevProblem {
   float e_s0[128];
   // output slot of walk (p, i): p * out_stride + i - out_i0 (a walk range's own buffer)
   int64_t out_i0;
+  // the warp-cooperative point-cloud walk: one walker per cl_spread lanes (1 ..
+  // 32, a power of two), so that a launch of few walks spreads over more warps
+  int cl_spread;
 };
 
 __host__ __device__ __forceinline__ PhiloxKeys philox_keys(uint32_t k0, uint32_t k1) {

@@ -982,7 +982,16 @@ int launch_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   if (!pb.S_out || !pb.K_out || !pb.flag_out || !pb.pts || !pb.tab64 || !pb.tabc)
     return fail(ctx, MPWOS_EINVAL, "internal: walk launch without its buffers");
   if (pb.wk_next) CK(cudaMemsetAsync(pb.wk_next, 0, sizeof(unsigned long long), st));
-  const LaunchShape sh = launch_shape(ctx, pb, fp64, max_grid, block_req);
+  LaunchShape sh = launch_shape(ctx, pb, fp64, max_grid, block_req);
+  pb.cl_spread = 1;
+  if (!fp64 && pb.mkind == kPointCloud && pb.cl_k >= 12) {
+    // the warp-cooperative search runs the warp's walkers' queries one after
+    // another: a launch of fewer walks than the grid holds spreads them over
+    // more warps (up to one walker per warp), which shortens each step
+    const int64_t slots = sh.grid * sh.per_block, walks = pb.wk_w1 - pb.wk_w0;
+    while (pb.cl_spread < 32 && walks * 2 * pb.cl_spread <= slots) pb.cl_spread *= 2;
+    sh.per_block /= pb.cl_spread;
+  }
   const int64_t need = (pb.wk_w1 - pb.wk_w0 + sh.per_block - 1) / sh.per_block;
   const int grid = static_cast<int>(std::min(sh.grid, need));
   cudaError_t e;

@@ -474,10 +474,14 @@ __device__ __forceinline__ void walk3_f32_body(const DevProblem& pb) {
 // searches always have all 32 lanes.
 template <int KM>
 __device__ __forceinline__ void walk3_f32_cloud_body(const DevProblem& pb) {
+  // one walker per `spread` lanes (lanes l with l % spread == 0); every lane
+  // takes part in the warp's neighbour searches
+  const int spread = pb.cl_spread > 1 ? pb.cl_spread : 1;
+  const bool holder = (threadIdx.x & (spread - 1)) == 0;
   const int64_t total = pb.wk_w1;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  int64_t w = pb.wk_w0 + static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  bool active = w < total;
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x / spread;
+  int64_t w = pb.wk_w0 + (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) / spread;
+  bool active = holder && w < total;
   const PhiloxKeys& K = pb.keys;
   const int nv = pb.n_v;
   const int max_steps = static_cast<int>(pb.max_steps);

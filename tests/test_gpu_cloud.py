@@ -81,3 +81,25 @@ def test_e4_fp32_rmse_decays_with_walks(ctx):
     m64, s64, _, _ = ctx.solve(w.problem, w.params, w.points[:10], 1000, precision=M.FP64)
     m32, s32, _, _ = ctx.solve(w.problem, w.params, w.points[:10], 8000, precision=M.FP32)
     assert np.all(np.abs(m32 - m64) < 4 * np.sqrt(s32 ** 2 + s64 ** 2))
+
+
+def test_cloud_coop_walks_do_not_depend_on_the_launch(ctx):
+    """The FP32 200k-cloud walk (k_nn = 16: the warp-cooperative search) spreads a launch
+    of few walks over more warps; walk (p, i) must come out the same bit for bit as in a
+    launch that fills the GPU."""
+    import torch
+    w = W.point_cloud(P=4, walks=1)
+    w.params.tau_w = 1e-4
+    pts = torch.tensor(w.points, dtype=torch.float64, device="cuda")
+
+    def run(N):
+        S = torch.empty((4, N), dtype=torch.float64, device="cuda")
+        K = torch.empty((4, N), dtype=torch.int32, device="cuda")
+        F = torch.empty((4, N), dtype=torch.int32, device="cuda")
+        ctx.walk_scores_device(w.problem, w.params, pts, N, M.FP32, S, K, F)
+        return S.cpu().numpy(), K.cpu().numpy(), F.cpu().numpy()
+
+    small = run(32)           # 128 walks: one walker per warp
+    large = run(65536)        # 262,144 walks: one walker per lane
+    for a, b in zip(small, large):
+        assert np.array_equal(a, b[:, :32])
