@@ -317,7 +317,10 @@ int64_t mpwos_noalloc_max_walks(void);
  * HOST, copied at submit) with a walk budget per point and an optional target
  * standard error: walks per point start at min(256, budget) and double for the
  * points whose standard error is still above the target, up to the budget
- * (target 0: exactly `walk_budget` walks, as mpwos_solve).  Requests are
+ * (target 0: exactly `walk_budget` walks, as mpwos_solve).  A request (not on
+ * a point cloud) whose P x budget walks fill at most a quarter of one resident
+ * wave of its walk kernel runs the whole budget in its first round (its
+ * latency is its walks' length, which more rounds would only repeat).  Requests are
  * admitted while a stream slot and serving memory are free (16 slots and a
  * quarter of the free device memory by default), run concurrently on their
  * own streams, and are advanced by a scheduler thread of the context.  A

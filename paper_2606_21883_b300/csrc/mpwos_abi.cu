@@ -2164,7 +2164,15 @@ int req_start(mpwos_ctx* ctx, Request& r) {
   for (auto& pair : r.cev)
     for (auto& e : pair)
       if (!e) CK(cudaEventCreate(&e));
-  const int64_t n0 = r.target > 0.0 ? std::min(r.budget, kFirstRoundWalks) : r.budget;
+  int64_t n0 = r.target > 0.0 ? std::min(r.budget, kFirstRoundWalks) : r.budget;
+  if (r.target > 0.0 && r.pb.mkind != kPointCloud) {
+    // a request whose whole budget fills at most a quarter of one resident wave
+    // is bound by its walks' length, not by the GPU: one round of the full
+    // budget ends no later than the first of the doubling rounds (not so on a
+    // point cloud, whose cooperative search slows as a warp holds more walkers)
+    const LaunchShape sh = launch_shape(ctx, r.pb, r.prm.precision == MPWOS_FP64, 0, 0);
+    if (r.P * r.budget * 4 <= sh.grid * sh.per_block) n0 = r.budget;
+  }
   return req_round(ctx, r, n0);
 }
 
