@@ -212,7 +212,7 @@ def _fifo(arrivals, service):
     return out
 
 
-def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
+def serving_leg(M, ctx, n_req=48, seed=7, baseline=True):
     """p50/p99 latency of Poisson arrivals at ~70% of the measured capacity, and the
     same arrivals served one request at a time (the latency baselines)."""
     import time as _t
@@ -255,11 +255,12 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
             out.setdefault(kind, []).append(lt)
         return out
 
-    calib = _serving_mix(rng, n_calib, cloud_w)
-    _, _, T_c = run(ctx, calib, np.zeros(n_calib), M.FP32)     # all at once: capacity
-    cap_rate = n_calib / T_c
-    rate = 0.7 * cap_rate
+    # capacity of this very stream: its requests submitted at once (16 in flight),
+    # then the same requests again with Poisson arrivals at 0.7 x that rate
     reqs = _serving_mix(rng, n_req, cloud_w)
+    _, _, T_c = run(ctx, reqs, np.zeros(n_req), M.FP32)
+    cap_rate = n_req / T_c
+    rate = 0.7 * cap_rate
     arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
     log(f"capacity {cap_rate:.2f} requests/s")
     lat, steps, T = run(ctx, reqs, arrivals, M.FP32)
@@ -267,7 +268,7 @@ def serving_leg(M, ctx, n_calib=24, n_req=48, seed=7, baseline=True):
     kinds = {k: sum(1 for r in reqs if r[0] == k) for k in ["torus", "cap", "cloud", "s999", "s20"]}
     out = {**_lat_summary(lat, by_kind(reqs, lat)), "requests": int(len(lat)), "arrival_rate_hz": rate,
            "capacity_hz": cap_rate, "walk_steps_per_s": float(steps.sum()) / T, "mix": kinds,
-           "recipe": "Poisson arrivals at 0.7 x capacity (capacity from a burst of 24); points log-uniform "
+           "recipe": "Poisson arrivals at 0.7 x capacity (capacity: the same 48 requests submitted at once, served 16 at a time); points log-uniform "
                      "(torus <=4096, cap/cloud/S^999 <=64, S^20 <=4), budget log-uniform 256-65536 (S^999 <=4096, "
                      "S^20 <=1024), target stderr log-uniform 1e-3-1e-2, FP32 walks, reduced sampler on S^999/S^20; "
                      "chunks sized to ~10 ms of GPU time"}

@@ -105,6 +105,25 @@ cudaError_t launch_walkr_f32(const DevProblem& pb, int grid, int block, cudaStre
   return cudaLaunchKernel(walkr32_fn(pb), dim3(grid), dim3(block), args, 0, st);
 }
 
+bool walkr_lat_eligible(const DevProblem& pb) {
+  return pb.reduced && pb.mkind == kEmbeddedSphere && pb.n_v == 1 && pb.red_nT <= 32;
+}
+
+cudaError_t launch_walkr_lat_f32(const DevProblem& pb, int grid, cudaStream_t st) {
+  if (!walkr_lat_eligible(pb)) return cudaErrorInvalidValue;
+  const void* fn;
+  switch (walkr_nt(pb.red_nT)) {
+    case 4: fn = reinterpret_cast<const void*>(walkr_lat_kernel<4>); break;
+    case 8: fn = reinterpret_cast<const void*>(walkr_lat_kernel<8>); break;
+    case 16: fn = reinterpret_cast<const void*>(walkr_lat_kernel<16>); break;
+    case 24: fn = reinterpret_cast<const void*>(walkr_lat_kernel<24>); break;
+    default: fn = reinterpret_cast<const void*>(walkr_lat_kernel<32>); break;
+  }
+  DevProblem arg = pb;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(fn, dim3(grid), dim3(128), args, 0, st);
+}
+
 int occupancy_walkr_f64(const DevProblem& pb, int block);
 
 const void* walk_fn_f32(const DevProblem& pb) {

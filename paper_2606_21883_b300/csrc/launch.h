@@ -31,6 +31,11 @@ cudaError_t launch_tc_project(const uint4* bimg, const float* G, int64_t rows, i
 cudaError_t launch_walkr_f64(const DevProblem& pb, int grid, int block, cudaStream_t st);
 cudaError_t launch_walkr_f32(const DevProblem& pb, int grid, int block, cudaStream_t st);
 int occupancy_walkr(const DevProblem& pb, bool fp64, int block);
+// The reduced embedded-sphere walk with one warp per walker (FP32, N_V = 1): for
+// launches of few walks; bit-identical walks to launch_walkr_f32's.  128-thread
+// blocks, 4 walkers each.
+bool walkr_lat_eligible(const DevProblem& pb);
+cudaError_t launch_walkr_lat_f32(const DevProblem& pb, int grid, cudaStream_t st);
 // Reduced start states (y_T, |y_rest|) of the query points.
 cudaError_t launch_reduced_start(const double* pts, int n, const int* T, int nT, int64_t P, int sphere, double* out,
                                  cudaStream_t st);

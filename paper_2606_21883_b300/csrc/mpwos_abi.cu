@@ -995,7 +995,12 @@ int launch_walks(mpwos_ctx* ctx, DevProblem& pb, bool fp64, cudaStream_t st, int
   const int64_t need = (pb.wk_w1 - pb.wk_w0 + sh.per_block - 1) / sh.per_block;
   const int grid = static_cast<int>(std::min(sh.grid, need));
   cudaError_t e;
-  if (pb.reduced) {
+  const int64_t walks = pb.wk_w1 - pb.wk_w0;
+  if (pb.reduced && !fp64 && walkr_lat_eligible(pb) && walks <= 32 * static_cast<int64_t>(ctx->sm_count)) {
+    // few walks on an embedded sphere: one warp per walker shortens each step
+    // (the walks are the same bit for bit)
+    e = launch_walkr_lat_f32(pb, static_cast<int>((walks + 3) / 4), st);
+  } else if (pb.reduced) {
     e = fp64 ? launch_walkr_f64(pb, grid, sh.block, st) : launch_walkr_f32(pb, grid, sh.block, st);
   } else if (pb.tc_bimg && !fp64) {
     e = launch_embed_tc(pb, grid, st);

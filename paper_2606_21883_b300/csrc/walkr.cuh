@@ -65,6 +65,15 @@ struct RedStream32 {
   __device__ __forceinline__ U4 operator()(uint32_t j) const { return philox32_block(A0 ^ j, st, *K); }
 };
 
+// Block b of a direction's FP32 normals: v[q] = normal 4 b + q (zero past ng).
+__device__ __forceinline__ void red_normal_block(const RedStream32& S, uint32_t j0, int b, int ng, float (&v)[4]) {
+  const U4 r = S(j0 + static_cast<uint32_t>(b));
+  box_muller32(u23(r.x), u23(r.y), v[0], v[1]);
+  box_muller32(u23(r.z), u23(r.w), v[2], v[3]);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = (4 * b + q < ng) ? v[q] : 0.0f;
+}
+
 template <int NG>
 __device__ __forceinline__ void red_normals(const RedStream32& S, uint32_t j0, int ng, float (&g)[NG]) {
 #pragma unroll
@@ -173,6 +182,18 @@ __device__ __forceinline__ T red_poly(const DevFunc& fn, const T (&x)[NT]) {
   return total;
 }
 
+// SPHERE_QUAD from |z|^2, v.z and z^T A z.
+template <typename T>
+__device__ __forceinline__ T red_quad_finish(const DevProblem& pb, T trA, T zz, T lin, T quad, int D) {
+  const T iz = T(1) / dsqrt<T>(zz);
+  lin *= iz;
+  quad *= iz * iz;
+  const T c0 = pick<T>(pb.f.c0, pb.f.c0_f);
+  if (!pb.f.apply_op) return c0 + lin + quad;
+  const T dm = T(D - 1), sg = pick<T>(pb.sigma, pb.sf.sigma), mean = trA / T(D);
+  return sg * (c0 + mean) + (dm + sg) * lin + (T(2) * (dm + T(1)) + sg) * (quad - mean);
+}
+
 // SPHERE_QUAD at the direction of z (NT components, zero padded): A (NT x NT,
 // zero padded), v and tr(A) in shared memory; zrow is this thread's shared row
 // for the rolled loop over the D rows of A.
@@ -195,13 +216,7 @@ __device__ __forceinline__ T red_quad(const DevProblem& pb, const T* As, const T
     for (int b = 0; b < NT; ++b) Az += Ar[b] * z[b];
     quad += zrow[a] * Az;
   }
-  const T iz = T(1) / dsqrt<T>(zz);
-  lin *= iz;
-  quad *= iz * iz;
-  const T c0 = pick<T>(pb.f.c0, pb.f.c0_f);
-  if (!pb.f.apply_op) return c0 + lin + quad;
-  const T dm = T(D - 1), sg = pick<T>(pb.sigma, pb.sf.sigma), mean = trA / T(D);
-  return sg * (c0 + mean) + (dm + sg) * lin + (T(2) * (dm + T(1)) + sg) * (quad - mean);
+  return red_quad_finish<T>(pb, trA, zz, lin, quad, D);
 }
 
 template <typename T, int MK, int NT>
@@ -426,6 +441,167 @@ __global__ void __launch_bounds__(128) walkr_kernel(const DevProblem pb) {
     for (int a = 0; a < D; ++a) trA += As[a * NT + a];
   }
   walkr_body<T, MK, NT>(pb, As, vs, trA, zrows + (kEmb ? threadIdx.x * (NT + 1) : 0));
+}
+
+// The reduced walk on an embedded sphere (FP32, N_V = 1) with one warp per
+// walker, for launches of few walks, whose time is the walks' length: lanes
+// b < NB draw the normals' Philox blocks, lane NB the chi^2 (and Z's radius
+// uniform), lanes a < D the rows of A z, in parallel; every sum then runs on
+// every lane in walkr_body's order, so the walks are bit-identical to
+// walkr_kernel's.  gsh: NT floats, azsh: NT floats of the warp's shared memory.
+template <int NT>
+__device__ __forceinline__ void walkr_lat_body(const DevProblem& pb, const float* As, const float* vs, float trA,
+                                               float* gsh, float* azsh) {
+  constexpr int NB = (NT + 3) / 4;   // Philox blocks of a direction's normals
+  static_assert(NB < 32, "one lane per block and one for the chi^2");
+  const int lane = threadIdx.x & 31;
+  const int nT = pb.red_nT, ng = nT, rest = pb.red_rest, D = nT;
+  const PhiloxKeys& K = pb.keys;
+  const float theta_t = pb.sf.theta, rgeo_t = pb.sf.rho_geo, sqs_t = pb.sf.sqrt_sigma;
+  const float mt_d = 0.5f * static_cast<float>(rest) - 1.0f / 3.0f;
+  const float mt_c = rest >= 2 ? rsqrtf(9.0f * mt_d) : 0.0f;
+  const int64_t total = pb.wk_w1;
+  const int64_t stride = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
+  int64_t w = pb.wk_w0 + ((static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  if (w >= total) return;   // warp-uniform
+  float y[NT];
+  WalkAcc<float> wa;
+  wa.set_tau(pb.tau_w);
+  int64_t k = 0, o = 0;
+  uint32_t p = 0, wi = 0;
+  Philox32Walk pw{0u, 0u};
+  auto init = [&](int64_t ww) {
+    const WalkId id = walk_id(pb, ww);
+    p = id.p; wi = id.i; o = id.o;
+    pw = philox32_walk(wi, K);
+    wa.reset();
+    k = 0;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) y[q] = q < nT ? static_cast<float>(pb.s0[static_cast<size_t>(p) * nT + q]) : 0.0f;
+  };
+  // a direction's normals into g on every lane, its chi^2 into X (lane NB's
+  // draw, broadcast); c0: the first chi^2 block when the caller drew it
+  auto direction = [&](const RedStream32& S, uint32_t j0, float (&g)[NT], float& X, float& uz, bool z) {
+    float xl = 0.0f, ul = 0.0f;
+    if (lane < NB) {
+      float v[4];
+      red_normal_block(S, j0, lane, ng, v);
+      *reinterpret_cast<float4*>(gsh + 4 * lane) = make_float4(v[0], v[1], v[2], v[3]);
+    } else if (lane == NB) {
+      const U4 c0 = S(j0 + 32u);
+      ul = u23(c0.w);
+      xl = red_chi2(S, j0 + 32u, rest, mt_d, mt_c, c0);
+    }
+    X = __shfl_sync(0xffffffffu, xl, NB);
+    if (z) uz = __shfl_sync(0xffffffffu, ul, NB);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < NT; q += 4) {
+      const float4 t4 = *reinterpret_cast<const float4*>(gsh + q);
+      g[q] = t4.x; g[q + 1] = t4.y; g[q + 2] = t4.z; g[q + 3] = t4.w;
+    }
+    __syncwarp();
+  };
+  init(w);
+  float r_prev = -1.0f;
+  for (;;) {
+    bool done = wa.below();
+    int flag = 0;
+    if (!done && k >= pb.max_steps) { done = true; flag = 1; }
+    if (done) {
+      if (lane == 0) {
+        pb.S_out[o] = wa.score();
+        pb.K_out[o] = static_cast<int32_t>(k);
+        pb.flag_out[o] = flag;
+      }
+      int64_t nxt = 0;
+      if (lane == 0) nxt = next_walk(pb, w, stride);
+      w = __shfl_sync(0xffffffffu, nxt, 0);
+      if (w >= total) break;
+      init(w);
+      continue;
+    }
+    const float r = theta_t * rgeo_t;   // closed: delta_Gamma is infinite
+    const float a = sqs_t * r;
+    if (r != r_prev) {
+      if (!pb.em1_fp64) {
+        wa.set_from_em1(em1_poly32(pb, 0.25f * a * a), pb.sf.inv_sigma);
+      } else {
+        const double ad = static_cast<double>(a);
+        const double em1 = em1_series(0.5 * static_cast<double>(pb.n - 2), 0.25 * (ad * ad));
+        const double cc = 1.0 / (1.0 + em1);
+        wa.set(cc, one_minus_c(em1, cc) / pb.sigma);
+      }
+      r_prev = r;
+    }
+    const uint32_t kk = static_cast<uint32_t>(k);
+    const RedStream32 S32{pw.A0, philox32_step(pw, kk, p, K), &K};
+    float g[NT];
+    // ---- interior sample Z and F ---------------------------------------------
+    float X, U;
+    direction(S32, 64u, g, X, U, true);
+    const float t = fminf(fmaxf(table_lookup32(pb, a, U), 0.0f), 1.0f);
+    float gg = X;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) gg += g[q] * g[q];
+    const float zs = (r * t) / dsqrt<float>(gg);
+    float z[NT];
+#pragma unroll
+    for (int q = 0; q < NT; ++q) z[q] = y[q] + zs * g[q];
+    float zz = 0.0f, lin = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      zz += z[j] * z[j];
+      lin += vs[j] * z[j];
+    }
+    if (lane < D) {
+      const float* Ar = As + lane * NT;
+      float Az = 0.0f;
+#pragma unroll
+      for (int b = 0; b < NT; ++b) Az += Ar[b] * z[b];
+      azsh[lane] = Az;
+    }
+    __syncwarp();
+    float quad = 0.0f;
+#pragma unroll
+    for (int aa = 0; aa < NT; ++aa)
+      if (aa < D) quad += z[aa] * azsh[aa];
+    __syncwarp();
+    const float F = red_quad_finish<float>(pb, trA, zz, lin, quad, D);
+    // ---- Theta = Y + r g/|g|, Y = cp(Theta) ------------------------------------
+    direction(S32, 0u, g, X, U, false);
+    gg = X;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) gg += g[q] * g[q];
+    const float sc = r / dsqrt<float>(gg);
+    float tt = 0.0f;
+#pragma unroll
+    for (int q = 0; q < NT; ++q) { y[q] = y[q] + sc * g[q]; tt += y[q] * y[q]; }
+    const float it = 1.0f / dsqrt<float>(tt);
+#pragma unroll
+    for (int q = 0; q < NT; ++q) y[q] *= it;
+    wa.add_step(F);
+    ++k;
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128) walkr_lat_kernel(const DevProblem pb) {
+  __shared__ float As[NT * NT];
+  __shared__ float vs[NT];
+  __shared__ __align__(16) float gsh[4][NT];
+  __shared__ float azsh[4][NT];
+  const int D = pb.red_nT;
+  for (int q = threadIdx.x; q < NT * NT; q += blockDim.x) {
+    const int a = q / NT, b = q - a * NT;
+    As[q] = (a < D && b < D) ? pb.f.Af[a * D + b] : 0.0f;
+  }
+  for (int q = threadIdx.x; q < NT; q += blockDim.x) vs[q] = q < D ? pb.f.vf[q] : 0.0f;
+  __syncthreads();
+  float trA = 0.0f;
+  for (int a = 0; a < D; ++a) trA += As[a * NT + a];
+  const int wv = threadIdx.x >> 5;
+  walkr_lat_body<NT>(pb, As, vs, trA, gsh[wv], azsh[wv]);
 }
 
 inline int walkr_nt(int nT) { return nT <= 4 ? 4 : (nT <= 8 ? 8 : (nT <= 16 ? 16 : (nT <= 24 ? 24 : 32))); }

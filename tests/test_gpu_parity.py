@@ -182,8 +182,12 @@ def test_fp32_vs_oracle_torus(ctx):
     assert np.all(t32 == 525)
 
 
-def test_fp32_vs_fp64_gpu_hypersphere(ctx):
-    w = W.hypersphere_half(P=4, walks=1, seed=2)
+@pytest.mark.parametrize("n", [1000, 1024, 5, 17])
+def test_fp32_vs_fp64_gpu_hypersphere(ctx, n):
+    """The FP32 shared-memory walk against the FP64 walk on S^{n-1}: n = 1000 (an even
+    partial last group), 1024 (64 whole groups, the maximum), 5 and 17 (one lane's
+    partial group; a whole group plus one component)."""
+    w = W.hypersphere_half(P=4, walks=1, n=n, seed=2)
     pts = w.points.copy()
     pts[:, 0] = 0.01
     pts[:, 1:] *= np.sqrt(1 - 1e-4) / np.linalg.norm(pts[:, 1:], axis=1, keepdims=True)

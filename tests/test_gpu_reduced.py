@@ -118,3 +118,20 @@ def test_reduced_rejected_where_unsupported(ctx):
     with pytest.raises(M.MpwosError) as e:
         ctx.walk_scores(c.problem, c.params, c.points, 4, precision=M.FP32)
     assert e.value.code == M.MPWOS_EINVAL
+
+
+@pytest.mark.parametrize("case", ["s20_r1000", "s5_r64"])
+def test_embedded_reduced_walks_do_not_depend_on_the_launch(ctx, case):
+    """A launch of few walks on an embedded sphere runs one warp per walker (FP32);
+    walk (p, i) must come out the same bit for bit as in a launch of many walks
+    (one thread per walker)."""
+    if case == "s20_r1000":
+        w = W.embedded_s20(P=4, walks=1)
+        w.params.max_steps = 3000
+    else:
+        w = W.embedded_s20(P=4, walks=1, n=64, d=5, sigma=6.0)
+    w.params.sampler = W.SAMPLER_REDUCED
+    small = ctx.walk_scores(w.problem, w.params, w.points, 64, precision=M.FP32)      # 256 walks
+    large = ctx.walk_scores(w.problem, w.params, w.points, 4096, precision=M.FP32)    # 16,384 walks
+    for a, b in zip(small, large):
+        assert np.array_equal(np.asarray(a), np.asarray(b)[:, :64])
