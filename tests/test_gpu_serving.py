@@ -105,3 +105,15 @@ def test_submit_validation(ctx):
     with pytest.raises(M.MpwosError) as ei:
         ctx.fetch(987654321, 1)
     assert ei.value.code == M.MPWOS_ENOTFOUND
+
+
+def test_small_request_runs_its_budget_in_one_round(ctx):
+    """A request whose P x budget walks fill a small part of one resident wave (not on a
+    point cloud) runs the whole budget at once: walks == budget for every point, even where
+    the target was met earlier, and the results equal mpwos_solve's with that budget."""
+    w = W.embedded_s20(P=2, walks=1, n=64, d=5, sigma=6.0)
+    w.params.sampler = W.SAMPLER_REDUCED
+    mean, se, ms, walks, lat, rc = _serve(ctx, w, 1024, 0.5, M.FP32)
+    assert np.all(walks == 1024)
+    m2, s2, t2, rc2 = ctx.solve(w.problem, w.params, w.points, 1024, precision=M.FP32)
+    assert np.array_equal(mean, m2) and np.array_equal(se, s2)
