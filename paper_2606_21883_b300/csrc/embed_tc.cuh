@@ -7,9 +7,9 @@
 // lockstep: a closed embedded sphere has constant radius, so every walk of the
 // tile stops at the same index.  For each Gaussian vector of a step (the
 // interior samples Z_l, then the sphere sample Theta) the tile's components are
-// generated in K-chunks of 64 — four threads per walker, 16 components (4
-// Philox blocks) each, the same draws as the FP32 warp walk (walkn32.cuh) —
-// split into BF16
+// generated in K-chunks of 64 — four threads per walker, one 16-component
+// group (3 Philox blocks: two of radial words, one of 16-bit angles) each, the
+// same draws as the FP32 warp walk (walkn32.cuh) — split into BF16
 // hi + lo and stored into a 128-byte-swizzled K-major A tile (128 rows =
 // walkers; two stages).  One elected thread issues, per 16-wide K slice, three
 // tcgen05.mma kind::f16 products into one FP32 TMEM accumulator (128 x 32):
