@@ -404,7 +404,7 @@ def torus_generic(P, walks=1):
     return w
 
 
-def config3_leg(M, ctx, sm, mhz, src):
+def s999_half_reduced_leg(M, ctx, sm, mhz, src):
     """S^999 half at its stated size (16384 points x 4096 walks) with the
     dimension-reduced sampler in FP32: walk-steps/s, RMSE, FP32-vs-FP64 agreement
     on 8 sampled points, roofline of the reduced walk, and the oracle on a subset."""
@@ -423,7 +423,7 @@ def config3_leg(M, ctx, sm, mhz, src):
     mo, so, to, _ = O.solve(w.problem, w.params, w.points[:16], 64, n_threads=cores)
     t_orc = time.perf_counter() - t0
     return {"workload": "S^999 in R^1000, x_1 > 0, sigma = 1, eps = 1e-3, 16384 pts x 4096 walks to completion, "
-                        "dimension-reduced sampler, FP32 (BASELINE config 3 at full size)",
+                        "dimension-reduced sampler, FP32",
             "walk_steps_per_s": steps / dt, "query_pts_per_s": len(w.points) / dt, "seconds": dt,
             "walk_steps": steps, "mean_steps_per_walk": float(ms.mean()),
             "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))), "mean_stderr": float(se.mean()),
@@ -434,7 +434,7 @@ def config3_leg(M, ctx, sm, mhz, src):
                              "sample": f"16 points x 64 walks, reduced sampler, FP64, {t_orc:.1f} s"}}
 
 
-def config4_leg(M, ctx, sm, mhz, src):
+def s20_in_r1000_leg(M, ctx, sm, mhz, src):
     """S^20 in R^1000 (32768 points x 2048 walks of 226,786 steps): a fixed window
     of steps for every walk (the full sampler with Q^T g on the tensor cores, and
     the reduced sampler), and the RMSE of complete walks on a 256-point subset."""
@@ -442,7 +442,7 @@ def config4_leg(M, ctx, sm, mhz, src):
     N = 2048
     out = {"workload": "S^20 randomly embedded in R^1000 (seeded orthonormal Q, shift b), sigma = 0.5, "
                        "32768 pts x 2048 walks; every walk runs a fixed window of steps (flagged at the window; "
-                       "a complete walk is 226,786 steps), FP32 (BASELINE config 4)"}
+                       "a complete walk is 226,786 steps), FP32"}
     w.params.max_steps = 16
     dt, S, K = kernel_run(M, ctx, w, N, M.FP32, projection=M.PROJ_TENSOR)
     steps = float(K.sum(dtype=np.int64))
@@ -485,10 +485,10 @@ def secondary_leg(M, ctx, sm, mhz, src):
     walk-steps/s and RMSE; the n = 1000 walks and the tensor-core walk also with
     their roofline (kernel alone, CUDA events)."""
     out = {}
-    # S^2 cap (config 1) at its stated size, FP64 (the per-walk parity mode)
+    # S^2 cap, 64 points x 1000 walks, FP64 (the per-walk parity mode)
     w = W.sphere_cap(P=64, walks=1)
     dt, (mean, se, ms) = solve_run(M, ctx, w, 1000, M.FP64)
-    out["s2_cap_fp64"] = {"workload": "S^2 cap z > 0, 64 pts x 1000 walks, FP64 (BASELINE config 1)",
+    out["s2_cap_fp64"] = {"workload": "S^2 cap z > 0, 64 pts x 1000 walks, FP64",
                           "walk_steps_per_s": float(ms.sum() * 1000) / dt, "query_pts_per_s": 64 / dt,
                           "latency_ms": 1e3 * dt, "rmse": float(np.sqrt(np.mean((mean - w.exact) ** 2))),
                           "mean_steps_per_walk": float(ms.mean())}
@@ -501,7 +501,7 @@ def secondary_leg(M, ctx, sm, mhz, src):
         "walk_steps_per_s": steps / dt, "seconds": dt,
         "rmse": float(np.sqrt(np.mean((S.mean(axis=1) - w.exact) ** 2)))}
     del S, K
-    out["s999_half_reduced_config3"] = config3_leg(M, ctx, sm, mhz, src)
+    out["s999_half_reduced_16384x4096"] = s999_half_reduced_leg(M, ctx, sm, mhz, src)
     # S^999 with the full sampler (the paper's form of the step: n Gaussians per direction)
     w = W.hypersphere_half(P=4096, walks=1)
     dt, S, K = kernel_run(M, ctx, w, 16, M.FP32)
@@ -513,7 +513,7 @@ def secondary_leg(M, ctx, sm, mhz, src):
         "roofline": roofline_block("walkn32s_kernel<sphere, 16, 4>", ops_full_sampler(1000), steps, dt, sm, mhz, src,
                                    mufu_per_step=MUFU_PER_PAIR * 1000)}
     del S, K
-    out["s20_in_r1000_config4"] = config4_leg(M, ctx, sm, mhz, src)
+    out["s20_in_r1000_32768x2048"] = s20_in_r1000_leg(M, ctx, sm, mhz, src)
     # Example 2's dumbbell (full sampler, Newton closest point)
     w = W.dumbbell(P=2368, walks=1)
     dt, S, K = kernel_run(M, ctx, w, 64, M.FP32)
