@@ -52,7 +52,7 @@ OPS_PER_STEP = 148
 # DRAM bytes (read + write) of one bench launch of the walk kernel, measured
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum, one pass) on the
 # kernel as built now; the profile summary gives the command.
-TRAFFIC_BYTES = 14.96e6 + 600.09e6
+TRAFFIC_BYTES = 15.51e6 + 600.60e6
 
 
 # Algorithmic lane-operations per walk-step of the other walk kernels (N_V = 1),

@@ -369,9 +369,11 @@ __device__ __forceinline__ void box_muller64(double ua, double ub, double& g0, d
 
 // FP32 Box-Muller pair (hardware approximations: MUFU lg2 / sin / cos).
 // The fifth 23-bit uniform of a block whose four words' low 23 bits are already
-// used: the high 9 bits of x and y and bits 23..27 of z (disjoint from those).
+// used: bits 24..31 of x and y and bits 24..30 of z (disjoint from those), the
+// top bytes gathered by two byte permutes.
 __device__ __forceinline__ float u23_high(const U4& b) {
-  return u23((b.x >> 23) | ((b.y >> 23) << 9) | ((b.z >> 23) << 18));
+  const uint32_t xy = __byte_perm(b.x, b.y, 0x0073u);   // bytes: x.b3, y.b3, x.b0, x.b0
+  return u23(__byte_perm(xy, b.z, 0x0710u));            // bytes: x.b3, y.b3, z.b3, x.b3
 }
 
 // A uniform direction on S^2 from two uniforms in (0, 1] (Archimedes: the height
