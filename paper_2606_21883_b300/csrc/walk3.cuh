@@ -730,13 +730,16 @@ __device__ __forceinline__ void walk3_fixed_body(const DevProblem& pb) {
 
 // Entry points: the analytic manifolds run 256-thread blocks; the
 // fixed-radius loop fits 40 registers (6 blocks, 48 warps per SM: measured
-// fastest on B300; 7 blocks spill), the general loop 64 (4 blocks); the point-cloud walk uses
-// 128-thread blocks with a larger register budget.  MQ >= 0 (torus, one
-// Fourier term with modes m = (MQ / 4) % 4, q = MQ % 4 and its trig choices in
-// bits 4 and 5, N_V = 1): the host launches the instance with those built in.  COMP: with the compensation term
-// (general loop only).
+// fastest on B300; 7 blocks spill), the general loop 64 (4 blocks, with some
+// spills: measured faster than 3 blocks at 80 registers on the S^2 cap and the
+// uncompensated cut torus), the general loop with the compensation term 80
+// (3 blocks, spill-free: 4.5 % faster than 4 blocks on Example 1); the
+// point-cloud walk uses 128-thread blocks with a larger register budget.
+// MQ >= 0 (torus, one Fourier term with modes m = (MQ / 4) % 4, q = MQ % 4 and
+// its trig choices in bits 4 and 5, N_V = 1): the host launches the instance
+// with those built in.  COMP: with the compensation term (general loop only).
 template <int MK, int KM, bool FIXED, int MQ = -1, bool COMP = false>
-__global__ void __launch_bounds__(256, FIXED ? 6 : 4) walk3_f32_kernel(const DevProblem pb) {
+__global__ void __launch_bounds__(256, FIXED ? 6 : (COMP ? 3 : 4)) walk3_f32_kernel(const DevProblem pb) {
   if constexpr (FIXED) {
     if (pb.n_v == 1) {
       walk3_fixed_body<MK, 1, MQ>(pb);
